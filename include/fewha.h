@@ -1,0 +1,180 @@
+/*
+ * fewha.h -- C ABI of libfewha.so, the FEWHA hot path on one B300 (sm_103a).
+ *
+ * FEWHA (Finite Element Wavelet Hybrid Algorithm) solves the discretised MAP
+ * normal equations of atmospheric tomography (Sec. 2.2, Eq. (fewha)):
+ *
+ *     M c = b,  M = W P^T Gamma^T C^{-1} Gamma P W^T + alpha D,
+ *               b = W P^T Gamma^T C^{-1} s,
+ *
+ * by a few iterations of Jacobi-preconditioned CG (Alg. 2), warm-started from
+ * the previous frame (Alg. 1), followed by the mirror fit and gain (Alg. 1).
+ * W is the periodic orthonormal db3 wavelet transform of each layer, P the
+ * bilinear layer-to-sensor propagation (cone effect for laser guide stars,
+ * Sec. 2.1), Gamma the Shack-Hartmann operator on the bilinear grid (Sec. 2.1),
+ * C^{-1} the diagonal noise weight and D a diagonal wavelet-domain
+ * regulariser (Sec. 2.2).
+ *
+ * Conventions used by every entry point:
+ *   - Every function returns an int status: FEWHA_OK or one FEWHA_ERR_* code;
+ *     fewha_last_error() gives a message.  No C++ exception crosses the ABI.
+ *   - The handle owns all device state.  Input pointers are borrowed for the
+ *     duration of the call only (their contents are copied).
+ *   - Arrays are in the handle's precision (float for FEWHA_FP32, double for
+ *     FEWHA_FP64).  on_device = 1: a device pointer on this GPU, ordered on the
+ *     handle's stream; on_device = 0: a host pointer (the call then
+ *     synchronises the stream where it must read or write host memory).
+ *   - Work is enqueued on the stream given to fewha_create (0 = legacy
+ *     default stream); only calls that touch host memory, fewha_sync and
+ *     fewha_get_* with host pointers synchronise.
+ *   - Layouts (row-major, "y" = row index i, "x" = column index j):
+ *       layers / wavelet coefficients: [layer][y][x], layer-major, n_l x n_l
+ *         each, Mallat layout for coefficients (Sec. 2.2, Table 1);
+ *       slopes: [wfs][x-slopes | y-slopes][i][j], n_sub x n_sub each (Sec. 2.1);
+ *       mirror commands: [dm][y][x], n_act x n_act each.
+ */
+#ifndef FEWHA_H
+#define FEWHA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FEWHA_OK            0
+#define FEWHA_ERR_ARG       1   /* invalid argument (null, size, range)                 */
+#define FEWHA_ERR_INPUT     2   /* non-finite slopes detected on the device             */
+#define FEWHA_ERR_GEOMETRY  3   /* a sample point falls outside a layer or mirror grid  */
+#define FEWHA_ERR_BREAKDOWN 4   /* PCG step denominator <= 0 or non-finite (Alg. 2)     */
+#define FEWHA_ERR_TIMEOUT   5   /* a bounded grid barrier expired; state left unchanged */
+#define FEWHA_ERR_LAUNCH    6   /* the persistent kernel cannot be made co-resident     */
+#define FEWHA_ERR_CUDA      7   /* a CUDA runtime call failed                           */
+#define FEWHA_ERR_STATE     8   /* call out of order (e.g. solve before set_frame)      */
+
+#define FEWHA_FP32 0
+#define FEWHA_FP64 1
+
+#define FEWHA_PATH_PLAIN 0      /* one simple kernel per operator (FP32 or FP64)       */
+#define FEWHA_PATH_FUSED 1      /* persistent whole-frame kernel (FP32 only)           */
+
+#define FEWHA_MAX_WFS      16
+#define FEWHA_MAX_LAYERS   64
+#define FEWHA_MAX_DMS      8
+#define FEWHA_MAX_FIT_DIRS 64
+
+/* Telescope, guide stars / wavefront sensors, mirrors, fitting directions.
+ * Angles in radians, heights and lengths in metres (Sec. 2.1, Sec. 4.1). */
+typedef struct {
+    double D;                              /* telescope diameter                                */
+    double obstruction;                    /* central obstruction, diameter ratio [0, 1)        */
+    int    n_wfs;                          /* number of Shack-Hartmann sensors (1..MAX_WFS)     */
+    int    n_sub[FEWHA_MAX_WFS];           /* subapertures per side of each sensor (>= 1)       */
+    double theta_x[FEWHA_MAX_WFS];         /* guide-star direction                              */
+    double theta_y[FEWHA_MAX_WFS];
+    double gs_height[FEWHA_MAX_WFS];       /* LGS height H (cone factor 1 - h/H); 0 = NGS       */
+    double noise_sigma[FEWHA_MAX_WFS];     /* slope noise std (rad); C^{-1} = mask / sigma^2    */
+    int    n_dm;                           /* deformable mirrors for the fit (0 = no fit)       */
+    double dm_height[FEWHA_MAX_DMS];
+    double dm_pitch[FEWHA_MAX_DMS];        /* actuator pitch                                    */
+    int    n_fit_dir;                      /* fitting directions (NGS-type)                     */
+    double fit_theta_x[FEWHA_MAX_FIT_DIRS];
+    double fit_theta_y[FEWHA_MAX_FIT_DIRS];
+    int    fit_n_sub;                      /* pupil sample grid of the fit: fit_n_sub+1 nodes   */
+    int    precision;                      /* FEWHA_FP32 or FEWHA_FP64, fixed at create         */
+} fewha_geometry;
+
+/* Turbulence layers reconstructed (Sec. 2.1 layered model; Table 1 sizes). */
+typedef struct {
+    int    n_layers;                       /* 1..MAX_LAYERS                                     */
+    double height[FEWHA_MAX_LAYERS];       /* m                                                 */
+    double cn2[FEWHA_MAX_LAYERS];          /* Cn^2 fraction gamma_l (> 0), enters D as 1/gamma  */
+    int    n_side[FEWHA_MAX_LAYERS];       /* layer grid n_l: power of two, 8..1024             */
+    int    levels[FEWHA_MAX_LAYERS];       /* db3 levels J_l, 1 <= J_l, n_l >> J_l >= 2         */
+    double r0;                             /* Fried parameter at 500 nm (m)                     */
+    double alpha;                          /* regularisation weight alpha (> 0), Eq. (fewha)    */
+} fewha_profile;
+
+typedef struct fewha_handle fewha_handle;
+
+/* Build all geometry tables (layer grids, sample/gather tables, D, Jacobi
+ * J = diag(M)) on the host in FP64, allocate device state (cudaMalloc) on the
+ * current device and upload.  The state (c, b, r, mirror commands) starts at
+ * zero.  stream: a cudaStream_t (may be 0).  On failure *out is NULL and the
+ * message is available from fewha_last_error(NULL).  Errors: ARG, GEOMETRY
+ * (a sensor or fitting footprint leaves a layer grid), CUDA. */
+int fewha_create(const fewha_geometry* geom, const fewha_profile* prof, void* stream,
+                 fewha_handle** out);
+
+/* Free all device and host memory of the handle (synchronises its stream). */
+int fewha_destroy(fewha_handle* h);
+
+/* Message of the last error on this handle (h = NULL: of the last failed
+ * fewha_create in this thread).  The pointer stays valid until the next call. */
+const char* fewha_last_error(const fewha_handle* h);
+
+/* Sizes: N coefficients (sum n_l^2), S slopes (sum 2 n_sub^2), A actuators. */
+int fewha_sizes(const fewha_handle* h, long* n_coeff, long* n_slopes, long* n_act);
+
+/* Select the execution path for FP32 handles (FP64 handles always use the
+ * plain path).  Default: FEWHA_PATH_FUSED for FP32. */
+int fewha_set_path(fewha_handle* h, int path);
+
+/* Residual replacement period k_rr (Alg. 1 warm restart, reading: every
+ * k_rr-th frame r = b - M c instead of r = (b - b_prev) + r_prev); 0 = never.
+ * Default 10. */
+int fewha_set_residual_replacement(fewha_handle* h, int k_rr);
+
+/* Copy the measurement vector s (S values, slopes layout above) into the
+ * handle (Alg. 1 input s).  Masked subapertures are ignored by the solve. */
+int fewha_set_frame(fewha_handle* h, const void* slopes, int on_device);
+
+/* Alg. 1 up to the PCG: b1 = W P^T Gamma^T C^{-1} s; warm_start = 1:
+ * r = (b1 - b0) + r0 (or the replacement), c from the previous frame;
+ * warm_start = 0: c = 0, r = b1.  Then n_iter iterations of Alg. 2
+ * (n_iter >= 1).  Asynchronous; errors detected on the device (INPUT,
+ * BREAKDOWN, TIMEOUT) are reported by the next fewha_sync. */
+int fewha_solve(fewha_handle* h, int n_iter, int warm_start);
+
+/* Alg. 1 fitting and open-loop gain: a~ = F W^{-1} c (least squares over the
+ * fitting directions, n_fit CG iterations warm-started from the previous a~),
+ * a1 = (1 - gain) a0 + gain a~.  dm_out (A values, may be NULL) receives a1.
+ * Errors: STATE if the geometry has no mirrors. */
+int fewha_fit_dm(fewha_handle* h, double gain, int n_fit, void* dm_out, int on_device);
+
+/* phi = W^{-1} c (N values, layers layout). */
+int fewha_get_layers(fewha_handle* h, void* out, int on_device);
+
+/* Vectors of the solver state, N values each: which = 0 c, 1 r, 2 b,
+ * 3 Jacobi diagonal diag(M), 4 alpha*D.  Host copies synchronise. */
+int fewha_get_vector(fewha_handle* h, int which, void* out, int on_device);
+
+/* Checkpoint / resume of the Alg. 1 state (c0, b0, r0): N values each. */
+int fewha_get_state(fewha_handle* h, void* c, void* b, void* r, int on_device);
+int fewha_set_state(fewha_handle* h, const void* c, const void* b, const void* r, int on_device,
+                    long frame_count);
+
+/* y = M x (N values each), one operator application (Eq. (fewha) left side). */
+int fewha_apply_M(fewha_handle* h, const void* x, void* y, int on_device);
+
+/* One whole frame as one CUDA graph: set_frame (host slopes, pinned or not),
+ * solve(n_iter, warm), optional fit, optional layers, device->host results.
+ * The graph is captured on the first call and re-captured when n_iter, the
+ * flags or the output pointers change.  Synchronises (host outputs).
+ * layers_out / dm_out may be NULL. */
+int fewha_frame(fewha_handle* h, const void* slopes_host, int n_iter, int warm_start,
+                double gain, int n_fit, void* layers_out, void* dm_out);
+
+/* Wait for the handle's stream and return the device error word (OK, INPUT,
+ * BREAKDOWN, TIMEOUT).  The word is cleared after it has been read. */
+int fewha_sync(fewha_handle* h);
+
+/* Grid-barrier spin budget of the fused kernel in clock cycles (0 makes every
+ * barrier expire at once; used to exercise the TIMEOUT path).  Default 2^31. */
+int fewha_set_barrier_budget(fewha_handle* h, long long cycles);
+
+/* Kernel launches enqueued by this handle since creation (all paths). */
+long long fewha_launch_count(const fewha_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEWHA_H */

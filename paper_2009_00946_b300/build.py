@@ -1,0 +1,70 @@
+"""Build libfewha.so in-tree for sm_103a (B300) with nvcc / g++.
+
+    python -m paper_2009_00946_b300.build [--force]
+
+Host setup code is compiled by g++ with FP contraction off (the FP64 geometry
+tables are then evaluated exactly as written); CUDA sources by nvcc for
+compute_103a / sm_103a.  The library links the CUDA runtime dynamically.
+"""
+
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libfewha.so")
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+CU_SOURCES = ["solver.cu", "fused.cu"]
+CPP_SOURCES = ["setup.cpp", "api.cpp"]
+HEADERS = ["setup.h", "solver.h", "fused.h"]
+
+
+def _newer(target: str, deps: list[str]) -> bool:
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def _run(cmd: list[str]) -> None:
+    print(" ".join(cmd), flush=True)
+    subprocess.run(cmd, check=True)
+
+
+def build(force: bool = False, verbose_ptxas: bool = False) -> str:
+    os.makedirs(BUILD, exist_ok=True)
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "fewha.h")]
+    objs = []
+    for src in CPP_SOURCES:
+        s = os.path.join(CSRC, src)
+        o = os.path.join(BUILD, src + ".o")
+        objs.append(o)
+        if force or _newer(o, [s] + hdrs):
+            _run(["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", "-Wno-unused-variable",
+                  "-I", INCLUDE, "-I", CSRC, "-I", "/usr/local/cuda/include", "-c", s, "-o", o])
+    for src in CU_SOURCES:
+        s = os.path.join(CSRC, src)
+        o = os.path.join(BUILD, src + ".o")
+        objs.append(o)
+        if force or _newer(o, [s] + hdrs):
+            cmd = [NVCC] + ARCH + ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
+                                   "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-c", s, "-o", o]
+            if verbose_ptxas:
+                cmd.insert(1, "-Xptxas=-v")
+            _run(cmd)
+    if force or _newer(LIB, objs):
+        _run([NVCC] + ARCH + ["-shared", "-cudart", "shared", "-o", LIB] + objs +
+             ["-Xlinker", "-rpath,/usr/local/cuda/lib64"])
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, verbose_ptxas="--ptxas-v" in sys.argv)

@@ -1,0 +1,171 @@
+// C ABI of libfewha.so (declared in include/fewha.h).  Argument checking and
+// dispatch only; the work runs in the kernels of solver.cu / fused.cu.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fewha.h"
+#include "setup.h"
+#include "solver.h"
+
+struct fewha_handle {
+    fewha::SolverBase* s = nullptr;
+    std::string msg;
+};
+
+namespace {
+thread_local std::string g_create_error;
+
+int fail(fewha_handle* h, int code, const std::string& m) {
+    if (h) h->msg = m;
+    return code;
+}
+
+int done(fewha_handle* h, int st) {
+    if (st != FEWHA_OK && h && h->s) h->msg = h->s->err;
+    return st;
+}
+}  // namespace
+
+extern "C" {
+
+int fewha_create(const fewha_geometry* geom, const fewha_profile* prof, void* stream, fewha_handle** out) {
+    if (!out) return FEWHA_ERR_ARG;
+    *out = nullptr;
+    if (!geom || !prof) {
+        g_create_error = "null geometry or profile";
+        return FEWHA_ERR_ARG;
+    }
+    try {
+        fewha::HostSetup hs;
+        std::string err;
+        int st = fewha::build_setup(*geom, *prof, hs, err);
+        if (st) {
+            g_create_error = err;
+            return st;
+        }
+        fewha::SolverBase* s = fewha::make_solver(hs, (cudaStream_t)stream, err, st);
+        if (!s) {
+            g_create_error = err;
+            return st ? st : FEWHA_ERR_CUDA;
+        }
+        fewha_handle* h = new fewha_handle();
+        h->s = s;
+        *out = h;
+        return FEWHA_OK;
+    } catch (const std::bad_alloc&) {
+        g_create_error = "host out of memory";
+        return FEWHA_ERR_ARG;
+    } catch (...) {
+        g_create_error = "unexpected host exception";
+        return FEWHA_ERR_ARG;
+    }
+}
+
+int fewha_destroy(fewha_handle* h) {
+    if (!h) return FEWHA_ERR_ARG;
+    delete h->s;
+    delete h;
+    return FEWHA_OK;
+}
+
+const char* fewha_last_error(const fewha_handle* h) {
+    if (!h) return g_create_error.c_str();
+    return h->msg.c_str();
+}
+
+int fewha_sizes(const fewha_handle* h, long* n_coeff, long* n_slopes, long* n_act) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (n_coeff) *n_coeff = h->s->hs.N;
+    if (n_slopes) *n_slopes = h->s->hs.S;
+    if (n_act) *n_act = h->s->hs.NA;
+    return FEWHA_OK;
+}
+
+int fewha_set_path(fewha_handle* h, int path) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (path != FEWHA_PATH_PLAIN && path != FEWHA_PATH_FUSED) return fail(h, FEWHA_ERR_ARG, "unknown path");
+    if (path == FEWHA_PATH_FUSED && h->s->hs.prec != FEWHA_FP32)
+        return fail(h, FEWHA_ERR_ARG, "the fused path is FP32 only");
+    h->s->path = path;
+    return FEWHA_OK;
+}
+
+int fewha_set_residual_replacement(fewha_handle* h, int k_rr) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (k_rr < 0) return fail(h, FEWHA_ERR_ARG, "k_rr must be >= 0");
+    h->s->k_rr = k_rr;
+    return FEWHA_OK;
+}
+
+int fewha_set_frame(fewha_handle* h, const void* slopes, int on_device) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->set_frame(slopes, on_device));
+}
+
+int fewha_solve(fewha_handle* h, int n_iter, int warm_start) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->solve(n_iter, warm_start));
+}
+
+int fewha_fit_dm(fewha_handle* h, double gain, int n_fit, void* dm_out, int on_device) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->fit(gain, n_fit, dm_out, on_device));
+}
+
+int fewha_get_layers(fewha_handle* h, void* out, int on_device) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->get_layers(out, on_device));
+}
+
+int fewha_get_vector(fewha_handle* h, int which, void* out, int on_device) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->get_vector(which, out, on_device));
+}
+
+int fewha_get_state(fewha_handle* h, void* c, void* b, void* r, int on_device) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->get_state(c, b, r, on_device));
+}
+
+int fewha_set_state(fewha_handle* h, const void* c, const void* b, const void* r, int on_device, long frame_count) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (frame_count < 0) return fail(h, FEWHA_ERR_ARG, "frame_count must be >= 0");
+    int st = h->s->set_state(c, b, r, on_device, frame_count);
+    if (!st) h->s->have_frame = h->s->have_frame;
+    return done(h, st);
+}
+
+int fewha_apply_M(fewha_handle* h, const void* x, void* y, int on_device) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->apply_M(x, y, on_device));
+}
+
+int fewha_frame(fewha_handle* h, const void* slopes_host, int n_iter, int warm_start, double gain, int n_fit,
+                void* layers_out, void* dm_out) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (dm_out && (n_fit < 0 || !(gain >= 0.0 && gain <= 1.0)))
+        return fail(h, FEWHA_ERR_ARG, "gain must be in [0, 1] and n_fit >= 0");
+    return done(h, h->s->frame(slopes_host, n_iter, warm_start, gain, n_fit, layers_out, dm_out));
+}
+
+int fewha_sync(fewha_handle* h) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->sync());
+}
+
+int fewha_set_barrier_budget(fewha_handle* h, long long cycles) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (cycles < 0) return fail(h, FEWHA_ERR_ARG, "budget must be >= 0");
+    h->s->barrier_budget = cycles;
+    return FEWHA_OK;
+}
+
+long long fewha_launch_count(const fewha_handle* h) {
+    if (!h) return -1;
+    return h->s->launches;
+}
+
+}  // extern "C"

@@ -1,0 +1,35 @@
+// Fused FP32 path: one persistent kernel runs a whole frame (RHS, warm
+// restart, n_iter iterations of Alg. 2) with bounded grid barriers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "setup.h"
+
+namespace fewha {
+
+template <typename T>
+struct DevGeo;
+
+// State vectors shared with the plain path (device pointers, FP32).
+struct FusedBuffers {
+    float *c, *r, *p, *q, *b, *bprev, *phi;
+    const float *Jinv, *aD;
+    double* sc;
+    int* errw;
+};
+
+struct FusedPlan;
+
+// Build the fused plan (tiles, work lists, cluster shape); nullptr if the
+// device cannot run it (err says why), in which case the plain path is used.
+FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const FusedBuffers& fb, std::string& err);
+void fused_destroy(FusedPlan* plan);
+
+// Enqueue one frame on `stream`: b = W P^T Gamma^T C^{-1} s; warm restart
+// (or replacement r = b - M c, or cold start); n_iter iterations of Alg. 2.
+int fused_solve(FusedPlan* plan, const float* slopes, int n_iter, int warm, int replace, long long budget,
+                cudaStream_t stream, std::string& err, long long& launches);
+
+}  // namespace fewha

@@ -1,0 +1,1173 @@
+// Plain FEWHA path: one simple kernel per operator (Sec. 3.2 matrix-free
+// operators), templated on float / double, with FP64 reductions; plus the
+// solver object that owns the device state of one instance.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+
+#include "fused.h"
+#include "solver.h"
+
+namespace fewha {
+
+#define FEWHA_CUDA(call)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                      \
+            return FEWHA_ERR_CUDA;                                                         \
+        }                                                                                  \
+    } while (0)
+
+#define FEWHA_LAUNCHED()                                                                   \
+    do {                                                                                   \
+        ++launches;                                                                        \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess) {                                                           \
+            err = std::string("kernel launch: ") + cudaGetErrorString(e_);                 \
+            return FEWHA_ERR_CUDA;                                                         \
+        }                                                                                  \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;   // valid in thread 0
+}
+
+// z = Jinv * r ; partial (r, z)
+template <typename T>
+__global__ void k_precond_dot(int N, const T* __restrict__ Jinv, const T* __restrict__ r, T* __restrict__ z,
+                              double* __restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        T zi = Jinv[i] * r[i];
+        z[i] = zi;
+        acc += (double)r[i] * (double)zi;
+    }
+    double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// s += aD * z ; partial (s, z)
+template <typename T>
+__global__ void k_reg_dot(int N, const T* __restrict__ aD, const T* __restrict__ z, T* __restrict__ s,
+                          double* __restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        T si = s[i] + aD[i] * z[i];
+        s[i] = si;
+        acc += (double)si * (double)z[i];
+    }
+    double v = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// generic partial dot (a, b)
+template <typename T>
+__global__ void k_dot(int N, const T* __restrict__ a, const T* __restrict__ b, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    double v = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+__device__ double sum_partials(const double* part, int n, double* sh) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+    return block_sum(acc, sh);
+}
+
+// Alg. 2 scalar recurrence: beta = rho/rho_old, alpha = rho/(mu - rho beta/alpha_old).
+__global__ void k_alg2_scalars(const double* part_rho, const double* part_mu, double* sc, int k, int* errw) {
+    __shared__ double sh[32];
+    double rho = sum_partials(part_rho, kRedBlocks, sh);
+    __syncthreads();
+    double mu = sum_partials(part_mu, kRedBlocks, sh);
+    if (threadIdx.x == 0) {
+        double beta = 0.0, denom = mu;
+        if (k > 0) {
+            beta = rho / sc[kRhoOld];
+            denom = mu - rho * beta / sc[kAlphaOld];
+        }
+        double a = rho / denom;
+        if (!(denom > 0.0) || !isfinite(a) || !isfinite(beta)) {
+            atomicOr(errw, kErrBreakdown);
+            a = 0.0;
+            beta = 0.0;
+        }
+        sc[kRho] = rho;
+        sc[kMu] = mu;
+        sc[kBeta] = beta;
+        sc[kAlphaK] = a;
+        sc[kRhoOld] = rho;
+        sc[kAlphaOld] = (a != 0.0) ? a : sc[kAlphaOld];
+    }
+}
+
+// p = z + beta p ; q = s + beta q ; c += alpha p ; r -= alpha q
+template <typename T>
+__global__ void k_alg2_update(int N, const double* __restrict__ sc, int first, const T* __restrict__ z,
+                              const T* __restrict__ s, T* __restrict__ p, T* __restrict__ q, T* __restrict__ c,
+                              T* __restrict__ r) {
+    const T beta = (T)sc[kBeta], a = (T)sc[kAlphaK];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        T pi = first ? z[i] : z[i] + beta * p[i];
+        T qi = first ? s[i] : s[i] + beta * q[i];
+        p[i] = pi;
+        q[i] = qi;
+        c[i] += a * pi;
+        r[i] -= a * qi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// periodic db3 DWT, one pass over the active LL block of every layer
+// ---------------------------------------------------------------------------
+
+// forward, rows: row y, output col c: a_c / d_{c-m/2} of x[y][(2k+t) mod m]
+template <typename T>
+__global__ void k_fwd_rows(DevGeo<T> G, int j, const T* __restrict__ src, T* __restrict__ dst) {
+    int l = blockIdx.y;
+    if (j > G.lay_J[l]) return;
+    int n = G.lay_n[l], m = n >> (j - 1), half = m >> 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    int y = idx / m, c = idx - y * m;
+    const T* s = src + G.lay_off[l] + (long)y * n;
+    int k = c < half ? c : c - half;
+    const T* f = c < half ? G.h : G.g;
+    T acc = 0;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) acc += f[t] * s[(2 * k + t) % m];
+    dst[G.lay_off[l] + (long)y * n + c] = acc;
+}
+
+template <typename T>
+__global__ void k_fwd_cols(DevGeo<T> G, int j, const T* __restrict__ src, T* __restrict__ dst) {
+    int l = blockIdx.y;
+    if (j > G.lay_J[l]) return;
+    int n = G.lay_n[l], m = n >> (j - 1), half = m >> 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    int rr = idx / m, x = idx - rr * m;
+    const T* s = src + G.lay_off[l] + x;
+    int k = rr < half ? rr : rr - half;
+    const T* f = rr < half ? G.h : G.g;
+    T acc = 0;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) acc += f[t] * s[(long)((2 * k + t) % m) * n];
+    dst[G.lay_off[l] + (long)rr * n + x] = acc;
+}
+
+// inverse, columns: x[i] = sum over taps t with (i - t) mod m even of
+// h_t a_k + g_t d_k, k = ((i - t) mod m) / 2
+template <typename T>
+__global__ void k_inv_cols(DevGeo<T> G, int j, const T* __restrict__ src, T* __restrict__ dst) {
+    int l = blockIdx.y;
+    if (j > G.lay_J[l]) return;
+    int n = G.lay_n[l], m = n >> (j - 1), half = m >> 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    int i = idx / m, x = idx - i * m;
+    const T* s = src + G.lay_off[l] + x;
+    T acc = 0;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        int r = ((i - t) % m + m) % m;
+        if (r & 1) continue;
+        int k = r >> 1;
+        acc += G.h[t] * s[(long)k * n] + G.g[t] * s[(long)(half + k) * n];
+    }
+    dst[G.lay_off[l] + (long)i * n + x] = acc;
+}
+
+template <typename T>
+__global__ void k_inv_rows(DevGeo<T> G, int j, const T* __restrict__ src, T* __restrict__ dst) {
+    int l = blockIdx.y;
+    if (j > G.lay_J[l]) return;
+    int n = G.lay_n[l], m = n >> (j - 1), half = m >> 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * m) return;
+    int y = idx / m, i = idx - y * m;
+    const T* s = src + G.lay_off[l] + (long)y * n;
+    T acc = 0;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        int r = ((i - t) % m + m) % m;
+        if (r & 1) continue;
+        int k = r >> 1;
+        acc += G.h[t] * s[k] + G.g[t] * s[half + k];
+    }
+    dst[G.lay_off[l] + (long)y * n + i] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// P, Gamma, C^{-1}, Gamma^T, P^T
+// ---------------------------------------------------------------------------
+
+// psi_g(i, j) = sum_l bilinear(phi_l) at the node's sample point (Sec. 2.1)
+template <typename T>
+__global__ void k_P(DevGeo<T> G, const T* __restrict__ phi, T* __restrict__ psi) {
+    int g = blockIdx.y, ns = G.wfs_n[g], np1 = ns + 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= np1 * np1) return;
+    int i = idx / np1, jx = idx - i * np1;
+    T acc = 0;
+    for (int l = 0; l < G.L; ++l) {
+        int base = G.tab_off[g * G.L + l], n = G.lay_n[l];
+        int cy = G.cy[base + i], cx = G.cx[base + jx];
+        T ty = G.ty[base + i], tx = G.tx[base + jx];
+        const T* f = phi + G.lay_off[l] + (long)cy * n + cx;
+        acc += (1 - ty) * ((1 - tx) * f[0] + tx * f[1]) + ty * ((1 - tx) * f[n] + tx * f[n + 1]);
+    }
+    psi[G.wfs_noff[g] + idx] = acc;
+}
+
+// weighted slopes w_g mask (Gamma psi)  (C^{-1} Gamma, Sec. 2.1 / Sec. 2.2)
+template <typename T>
+__global__ void k_gamma_w(DevGeo<T> G, const T* __restrict__ psi, T* __restrict__ sl) {
+    int g = blockIdx.y, ns = G.wfs_n[g], np1 = ns + 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ns * ns) return;
+    int a = idx / ns, b = idx - a * ns;
+    const T* p = psi + G.wfs_noff[g] + (long)a * np1 + b;
+    T sx = ((p[1] - p[0]) + (p[np1 + 1] - p[np1])) / 2;
+    T sy = ((p[np1] - p[0]) + (p[np1 + 1] - p[1])) / 2;
+    T wm = G.mask[G.wfs_moff[g] + idx] ? G.wfs_w[g] : (T)0;
+    sl[G.wfs_soff[g] + idx] = wm * sx;
+    sl[G.wfs_soff[g] + ns * ns + idx] = wm * sy;
+}
+
+// weighted measurement slopes for the right-hand side; non-finite active
+// slopes raise the INPUT error bit, inactive ones are ignored
+template <typename T>
+__global__ void k_weight_meas(DevGeo<T> G, const T* __restrict__ s, T* __restrict__ sl, int* errw) {
+    int g = blockIdx.y, ns = G.wfs_n[g];
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ns * ns) return;
+    bool on = G.mask[G.wfs_moff[g] + idx] != 0;
+    T vx = s[G.wfs_soff[g] + idx], vy = s[G.wfs_soff[g] + ns * ns + idx];
+    if (on && (!isfinite((double)vx) || !isfinite((double)vy))) atomicOr(errw, kErrInput);
+    T w = G.wfs_w[g];
+    sl[G.wfs_soff[g] + idx] = on && isfinite((double)vx) ? w * vx : (T)0;
+    sl[G.wfs_soff[g] + ns * ns + idx] = on && isfinite((double)vy) ? w * vy : (T)0;
+}
+
+// psi'(i, j) = (Gamma^T sl)(i, j): gather of the <= 4 adjacent subapertures
+template <typename T>
+__global__ void k_gammaT(DevGeo<T> G, const T* __restrict__ sl, T* __restrict__ psi) {
+    int g = blockIdx.y, ns = G.wfs_n[g], np1 = ns + 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= np1 * np1) return;
+    int i = idx / np1, jx = idx - i * np1;
+    const T* SX = sl + G.wfs_soff[g];
+    const T* SY = SX + ns * ns;
+    T acc = 0;
+    for (int a = i - 1; a <= i; ++a) {
+        if (a < 0 || a >= ns) continue;
+        for (int b = jx - 1; b <= jx; ++b) {
+            if (b < 0 || b >= ns) continue;
+            T sx = SX[a * ns + b], sy = SY[a * ns + b];
+            acc += (b == jx - 1 ? sx : -sx) + (a == i - 1 ? sy : -sy);
+        }
+    }
+    psi[G.wfs_noff[g] + idx] = acc / 2;
+}
+
+// y_l(p, q) = sum_g (P_gl^T psi'_g)(p, q): deterministic gather over the
+// sensor nodes whose sample point lies in one of the 4 cells around (p, q)
+template <typename T>
+__global__ void k_PT(DevGeo<T> G, const T* __restrict__ psi, T* __restrict__ y) {
+    int l = blockIdx.y, n = G.lay_n[l];
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int p = idx / n, q = idx - p * n;
+    T acc = 0;
+    for (int g = 0; g < G.G; ++g) {
+        int base = G.tab_off[g * G.L + l], gb = G.gat_off[g * G.L + l];
+        int i0 = G.ilo[gb + p], i1 = G.ihi[gb + p], j0 = G.jlo[gb + q], j1 = G.jhi[gb + q];
+        int np1 = G.wfs_n[g] + 1;
+        const T* P = psi + G.wfs_noff[g];
+        for (int i = i0; i < i1; ++i) {
+            T wy = (G.cy[base + i] == p) ? 1 - G.ty[base + i] : G.ty[base + i];
+            T row = 0;
+            for (int jx = j0; jx < j1; ++jx) {
+                T wx = (G.cx[base + jx] == q) ? 1 - G.tx[base + jx] : G.tx[base + jx];
+                row += wx * P[(long)i * np1 + jx];
+            }
+            acc += wy * row;
+        }
+    }
+    y[G.lay_off[l] + idx] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// frame bookkeeping (Alg. 1)
+// ---------------------------------------------------------------------------
+
+// warm restart r = (b1 - b0) + r0 ; b0 = b1
+template <typename T>
+__global__ void k_warm(int N, const T* __restrict__ b, T* __restrict__ bprev, T* __restrict__ r) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        T bi = b[i];
+        r[i] = (bi - bprev[i]) + r[i];
+        bprev[i] = bi;
+    }
+}
+
+// residual replacement r = b1 - M c0 (accumulated in FP64) ; b0 = b1
+template <typename T>
+__global__ void k_replace(int N, const T* __restrict__ b, const T* __restrict__ Mc, T* __restrict__ bprev,
+                          T* __restrict__ r) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        T bi = b[i];
+        r[i] = (T)((double)bi - (double)Mc[i]);
+        bprev[i] = bi;
+    }
+}
+
+// cold start c = 0, r = b1 ; b0 = b1
+template <typename T>
+__global__ void k_cold(int N, const T* __restrict__ b, T* __restrict__ bprev, T* __restrict__ r, T* __restrict__ c) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        T bi = b[i];
+        r[i] = bi;
+        bprev[i] = bi;
+        c[i] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fitting: least squares over the fitting directions (NGS-type)
+// ---------------------------------------------------------------------------
+
+// v_t(node) = sum_l bilinear(phi_l) along direction t on the pupil grid
+template <typename T>
+__global__ void k_fit_lay(DevFit<T> F, const T* __restrict__ phi, T* __restrict__ v) {
+    int t = blockIdx.y, np1 = F.np1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= np1 * np1) return;
+    int i = idx / np1, jx = idx - i * np1;
+    T acc = 0;
+    for (int l = 0; l < F.L; ++l) {
+        int base = F.ftab_off[t * F.L + l], n = F.lay_n[l];
+        int cy = F.fcy[base + i], cx = F.fcx[base + jx];
+        T ty = F.fty[base + i], tx = F.ftx[base + jx];
+        const T* f = phi + F.lay_off[l] + (long)cy * n + cx;
+        acc += (1 - ty) * ((1 - tx) * f[0] + tx * f[1]) + ty * ((1 - tx) * f[n] + tx * f[n + 1]);
+    }
+    v[(long)t * np1 * np1 + idx] = acc;
+}
+
+// v_t(node) = sum_m bilinear(a_m) along direction t
+template <typename T>
+__global__ void k_fit_dm(DevFit<T> F, const T* __restrict__ a, T* __restrict__ v) {
+    int t = blockIdx.y, np1 = F.np1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= np1 * np1) return;
+    int i = idx / np1, jx = idx - i * np1;
+    T acc = 0;
+    for (int m = 0; m < F.M; ++m) {
+        int base = F.dtab_off[t * F.M + m], n = F.dm_n[m];
+        int cy = F.dcy[base + i], cx = F.dcx[base + jx];
+        T ty = F.dty[base + i], tx = F.dtx[base + jx];
+        const T* f = a + F.dm_off[m] + (long)cy * n + cx;
+        acc += (1 - ty) * ((1 - tx) * f[0] + tx * f[1]) + ty * ((1 - tx) * f[n] + tx * f[n + 1]);
+    }
+    v[(long)t * np1 * np1 + idx] = acc;
+}
+
+// out(actuator) = sum_t (P_DM_t^T v_t)(actuator) [+ eps * x(actuator)] ;
+// optional partial dot (x, out)
+template <typename T>
+__global__ void k_fit_dmT(DevFit<T> F, const T* __restrict__ v, const T* __restrict__ x, T eps, T* __restrict__ out) {
+    int m = blockIdx.y, n = F.dm_n[m];
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int p = idx / n, q = idx - p * n, np1 = F.np1;
+    T acc = 0;
+    for (int t = 0; t < F.T_; ++t) {
+        int base = F.dtab_off[t * F.M + m], gb = F.dgat_off[t * F.M + m];
+        int i0 = F.dilo[gb + p], i1 = F.dihi[gb + p], j0 = F.djlo[gb + q], j1 = F.djhi[gb + q];
+        const T* V = v + (long)t * np1 * np1;
+        for (int i = i0; i < i1; ++i) {
+            T wy = (F.dcy[base + i] == p) ? 1 - F.dty[base + i] : F.dty[base + i];
+            T row = 0;
+            for (int jx = j0; jx < j1; ++jx) {
+                T wx = (F.dcx[base + jx] == q) ? 1 - F.dtx[base + jx] : F.dtx[base + jx];
+                row += wx * V[(long)i * np1 + jx];
+            }
+            acc += wy * row;
+        }
+    }
+    long o = F.dm_off[m] + idx;
+    if (x) acc += eps * x[o];
+    out[o] = acc;
+}
+
+// r = rhs - A x ; p = r
+template <typename T>
+__global__ void k_fit_init(int NA, const T* __restrict__ rhs, const T* __restrict__ Ax, T* __restrict__ r,
+                           T* __restrict__ p) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NA; i += gridDim.x * blockDim.x) {
+        T v = rhs[i] - Ax[i];
+        r[i] = v;
+        p[i] = v;
+    }
+}
+
+// CG step: a = rr / pq (0 if pq <= 0 or rr == 0); x += a p ; r -= a q ; partial (r, r)
+template <typename T>
+__global__ void k_fit_step(int NA, const double* __restrict__ sc, T* __restrict__ x, T* __restrict__ r,
+                           const T* __restrict__ p, const T* __restrict__ q, double* __restrict__ part) {
+    __shared__ double sh[32];
+    double rr = sc[kRR], pq = sc[kMu];
+    T a = (pq > 0.0 && rr > 0.0) ? (T)(rr / pq) : (T)0;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NA; i += gridDim.x * blockDim.x) {
+        x[i] += a * p[i];
+        T ri = r[i] - a * q[i];
+        r[i] = ri;
+        acc += (double)ri * (double)ri;
+    }
+    double v = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// scalar helpers for the fit CG: which = 0 -> sc[kRR] = sum ; 1 -> sc[kMu] = sum ;
+// 2 -> beta: sc[kBeta] = sum / sc[kRR], sc[kRR] = sum
+__global__ void k_fit_scalar(const double* part, double* sc, int which) {
+    __shared__ double sh[32];
+    double s = sum_partials(part, kRedBlocks, sh);
+    if (threadIdx.x == 0) {
+        if (which == 0) sc[kRR] = s;
+        else if (which == 1) sc[kMu] = s;
+        else {
+            double old = sc[kRR];
+            sc[kBeta] = old > 0.0 ? s / old : 0.0;
+            sc[kRR] = s;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_fit_dir(int NA, const double* __restrict__ sc, const T* __restrict__ r, T* __restrict__ p) {
+    T b = (T)sc[kBeta];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NA; i += gridDim.x * blockDim.x) p[i] = r[i] + b * p[i];
+}
+
+// a1 = (1 - g) a0 + g a~ ; a(-1) = a0 ; a0 = a1
+template <typename T>
+__global__ void k_gain(int NA, T gain, const T* __restrict__ afit, T* __restrict__ acur, T* __restrict__ aprev) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NA; i += gridDim.x * blockDim.x) {
+        T a0 = acur[i];
+        aprev[i] = a0;
+        acur[i] = (1 - gain) * a0 + gain * afit[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// solver object
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static void to_T(const std::vector<double>& v, std::vector<T>& o) {
+    o.resize(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+}
+
+template <typename T>
+class Solver : public SolverBase {
+  public:
+    DevGeo<T> G{};
+    DevFit<T> F{};
+    std::vector<void*> allocs;
+    void* pinned_in = nullptr;    // staging for fewha_frame
+    void* pinned_out = nullptr;
+    void* pinned_dm = nullptr;
+    T *slopes = nullptr, *c = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *s = nullptr;
+    T *b = nullptr, *bprev = nullptr, *phi = nullptr, *tmp = nullptr, *y = nullptr, *wpsi = nullptr, *wpsi2 = nullptr,
+      *wsl = nullptr, *Jinv = nullptr, *aD = nullptr, *Jd = nullptr, *ext = nullptr;
+    T *afit = nullptr, *acur = nullptr, *aprev = nullptr, *fr = nullptr, *fp = nullptr, *fq = nullptr, *frhs = nullptr,
+      *fv = nullptr;
+    double *part = nullptr, *part2 = nullptr, *sc = nullptr;
+    int* errw = nullptr;
+    int* errw_host = nullptr;
+    FusedPlan* fused = nullptr;
+    // graph cache
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    struct Key {
+        int n_iter = -1, warm = -1, n_fit = -1, path = -1, k_rr = -1;
+        double gain = -1;
+        const void* sin = nullptr;
+        void* lout = nullptr;
+        void* dout = nullptr;
+        bool operator==(const Key& o) const {
+            return n_iter == o.n_iter && warm == o.warm && n_fit == o.n_fit && gain == o.gain && sin == o.sin &&
+                   lout == o.lout && dout == o.dout && path == o.path && k_rr == o.k_rr;
+        }
+    } gkey[2];
+
+    ~Solver() override {
+        if (stream) cudaStreamSynchronize(stream);
+        else cudaDeviceSynchronize();
+        for (int i = 0; i < 2; ++i)
+            if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+        if (fused) fused_destroy(fused);
+        for (void* a : allocs) cudaFree(a);
+        if (pinned_in) cudaFreeHost(pinned_in);
+        if (pinned_out) cudaFreeHost(pinned_out);
+        if (pinned_dm) cudaFreeHost(pinned_dm);
+        if (errw_host) cudaFreeHost(errw_host);
+    }
+
+    template <typename U>
+    int alloc(U*& ptr, size_t count) {
+        void* v = nullptr;
+        FEWHA_CUDA(cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(U)));
+        allocs.push_back(v);
+        ptr = (U*)v;
+        return FEWHA_OK;
+    }
+    template <typename U>
+    int upload(U*& ptr, const std::vector<U>& v) {
+        int st = alloc(ptr, v.size());
+        if (st) return st;
+        if (!v.empty()) FEWHA_CUDA(cudaMemcpy(ptr, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice));
+        return FEWHA_OK;
+    }
+    template <typename U>
+    int uploadT(U*& ptr, const std::vector<double>& v) {
+        std::vector<U> t;
+        to_T(v, t);
+        return upload(ptr, t);
+    }
+
+#define TRY(x)                   \
+    do {                         \
+        int st_ = (x);           \
+        if (st_) return st_;     \
+    } while (0)
+
+    int init() {
+        const HostSetup& H = hs;
+        std::vector<int> lay_n, lay_J, lay_off, wfs_n, wfs_soff, wfs_noff, wfs_moff;
+        std::vector<double> wfs_w;
+        int Jmax = 0, nmax = 0, nsmax = 0;
+        for (auto& L : H.lay) {
+            lay_n.push_back(L.n);
+            lay_J.push_back(L.J);
+            lay_off.push_back((int)L.off);
+            Jmax = std::max(Jmax, L.J);
+            nmax = std::max(nmax, L.n);
+        }
+        for (auto& w : H.wfs) {
+            wfs_n.push_back(w.n);
+            wfs_soff.push_back((int)w.soff);
+            wfs_noff.push_back((int)w.noff);
+            wfs_moff.push_back((int)w.moff);
+            wfs_w.push_back(w.w);
+            nsmax = std::max(nsmax, w.n);
+        }
+        G.L = H.L;
+        G.G = H.G;
+        G.N = (int)H.N;
+        G.S = (int)H.S;
+        G.NW = (int)H.NW;
+        G.NS = (int)H.NS;
+        G.Jmax = Jmax;
+        G.nmax = nmax;
+        G.nsmax = nsmax;
+        for (int i = 0; i < 6; ++i) {
+            G.h[i] = (T)H.h[i];
+            G.g[i] = (T)H.g[i];
+        }
+        int *d_lay_n, *d_lay_J, *d_lay_off, *d_wfs_n, *d_wfs_soff, *d_wfs_noff, *d_wfs_moff;
+        TRY(upload(d_lay_n, lay_n));
+        TRY(upload(d_lay_J, lay_J));
+        TRY(upload(d_lay_off, lay_off));
+        TRY(upload(d_wfs_n, wfs_n));
+        TRY(upload(d_wfs_soff, wfs_soff));
+        TRY(upload(d_wfs_noff, wfs_noff));
+        TRY(upload(d_wfs_moff, wfs_moff));
+        G.lay_n = d_lay_n;
+        G.lay_J = d_lay_J;
+        G.lay_off = d_lay_off;
+        G.wfs_n = d_wfs_n;
+        G.wfs_soff = d_wfs_soff;
+        G.wfs_noff = d_wfs_noff;
+        G.wfs_moff = d_wfs_moff;
+        T* d_w;
+        TRY(uploadT(d_w, wfs_w));
+        G.wfs_w = d_w;
+        unsigned char* d_mask;
+        TRY(upload(d_mask, H.mask));
+        G.mask = d_mask;
+        int *d_tab_off, *d_cx, *d_cy, *d_gat_off, *d_jlo, *d_jhi, *d_ilo, *d_ihi;
+        T *d_tx, *d_ty;
+        TRY(upload(d_tab_off, H.tab_off));
+        TRY(upload(d_cx, H.cx));
+        TRY(upload(d_cy, H.cy));
+        TRY(uploadT(d_tx, H.tx));
+        TRY(uploadT(d_ty, H.ty));
+        TRY(upload(d_gat_off, H.gat_off));
+        TRY(upload(d_jlo, H.jlo));
+        TRY(upload(d_jhi, H.jhi));
+        TRY(upload(d_ilo, H.ilo));
+        TRY(upload(d_ihi, H.ihi));
+        G.tab_off = d_tab_off;
+        G.cx = d_cx;
+        G.cy = d_cy;
+        G.tx = d_tx;
+        G.ty = d_ty;
+        G.gat_off = d_gat_off;
+        G.jlo = d_jlo;
+        G.jhi = d_jhi;
+        G.ilo = d_ilo;
+        G.ihi = d_ihi;
+        std::vector<double> jinv(H.N);
+        for (long i = 0; i < H.N; ++i) jinv[i] = 1.0 / H.Jdiag[i];
+        TRY(uploadT(Jinv, jinv));
+        TRY(uploadT(aD, H.aD));
+        TRY(uploadT(Jd, H.Jdiag));
+        G.Jinv = Jinv;
+        G.aD = aD;
+        const size_t N = H.N;
+        for (T** v : {&c, &r, &p, &q, &z, &s, &b, &bprev, &phi, &tmp, &y, &ext}) TRY(alloc(*v, N));
+        TRY(alloc(slopes, H.S));
+        TRY(alloc(wsl, H.S));
+        TRY(alloc(wpsi, H.NW));
+        TRY(alloc(wpsi2, H.NW));
+        TRY(alloc(part, kRedBlocks));
+        TRY(alloc(part2, kRedBlocks));
+        TRY(alloc(sc, kNumScalars));
+        TRY(alloc(errw, 1));
+        FEWHA_CUDA(cudaMallocHost((void**)&errw_host, sizeof(int)));
+        for (T* v : {c, r, p, q, z, s, b, bprev, phi, tmp, y, ext}) FEWHA_CUDA(cudaMemset(v, 0, N * sizeof(T)));
+        FEWHA_CUDA(cudaMemset(slopes, 0, H.S * sizeof(T)));
+        FEWHA_CUDA(cudaMemset(sc, 0, kNumScalars * sizeof(double)));
+        FEWHA_CUDA(cudaMemset(errw, 0, sizeof(int)));
+        if (H.M > 0) TRY(init_fit());
+        FEWHA_CUDA(cudaDeviceSynchronize());
+        return FEWHA_OK;
+    }
+
+    int init_fit() {
+        const HostSetup& H = hs;
+        F.L = H.L;
+        F.M = H.M;
+        F.T_ = H.T;
+        F.NA = (int)H.NA;
+        F.np1 = H.fit_n + 1;
+        F.eps = (T)H.fit_eps;
+        F.lay_n = G.lay_n;
+        F.lay_off = G.lay_off;
+        std::vector<int> dm_n, dm_off;
+        for (auto& d : H.dm) {
+            dm_n.push_back(d.na);
+            dm_off.push_back((int)d.off);
+        }
+        int *d_dm_n, *d_dm_off, *a, *bb, *cc, *dd, *e, *f, *g1, *h1, *i1, *j1;
+        T *tx1, *ty1, *tx2, *ty2;
+        TRY(upload(d_dm_n, dm_n));
+        TRY(upload(d_dm_off, dm_off));
+        TRY(upload(a, H.ftab_off));
+        TRY(upload(bb, H.fcx));
+        TRY(upload(cc, H.fcy));
+        TRY(uploadT(tx1, H.ftx));
+        TRY(uploadT(ty1, H.fty));
+        TRY(upload(dd, H.dtab_off));
+        TRY(upload(e, H.dcx));
+        TRY(upload(f, H.dcy));
+        TRY(uploadT(tx2, H.dtx));
+        TRY(uploadT(ty2, H.dty));
+        TRY(upload(g1, H.dgat_off));
+        TRY(upload(h1, H.djlo));
+        TRY(upload(i1, H.djhi));
+        TRY(upload(j1, H.dilo));
+        int* k1;
+        TRY(upload(k1, H.dihi));
+        F.dm_n = d_dm_n;
+        F.dm_off = d_dm_off;
+        F.ftab_off = a;
+        F.fcx = bb;
+        F.fcy = cc;
+        F.ftx = tx1;
+        F.fty = ty1;
+        F.dtab_off = dd;
+        F.dcx = e;
+        F.dcy = f;
+        F.dtx = tx2;
+        F.dty = ty2;
+        F.dgat_off = g1;
+        F.djlo = h1;
+        F.djhi = i1;
+        F.dilo = j1;
+        F.dihi = k1;
+        for (T** v : {&afit, &acur, &aprev, &fr, &fp, &fq, &frhs}) {
+            TRY(alloc(*v, H.NA));
+            FEWHA_CUDA(cudaMemset(*v, 0, H.NA * sizeof(T)));
+        }
+        TRY(alloc(fv, (size_t)H.T * F.np1 * F.np1));
+        return FEWHA_OK;
+    }
+
+    // ---- building blocks (all enqueued on `stream`) ----
+    dim3 grid_layers(int count) const { return dim3((count + 255) / 256, G.L); }
+
+    int inv_dwt(const T* src, T* dst) {   // dst = W^T src (dst != src)
+        FEWHA_CUDA(cudaMemcpyAsync(dst, src, (size_t)G.N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+        for (int j = G.Jmax; j >= 1; --j) {
+            int m = G.nmax >> (j - 1);
+            k_inv_cols<T><<<grid_layers(m * m), 256, 0, stream>>>(G, j, dst, tmp);
+            FEWHA_LAUNCHED();
+            k_inv_rows<T><<<grid_layers(m * m), 256, 0, stream>>>(G, j, tmp, dst);
+            FEWHA_LAUNCHED();
+        }
+        return FEWHA_OK;
+    }
+
+    int fwd_dwt(const T* src, T* dst) {   // dst = W src (dst != src)
+        FEWHA_CUDA(cudaMemcpyAsync(dst, src, (size_t)G.N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+        for (int j = 1; j <= G.Jmax; ++j) {
+            int m = G.nmax >> (j - 1);
+            k_fwd_rows<T><<<grid_layers(m * m), 256, 0, stream>>>(G, j, dst, tmp);
+            FEWHA_LAUNCHED();
+            k_fwd_cols<T><<<grid_layers(m * m), 256, 0, stream>>>(G, j, tmp, dst);
+            FEWHA_LAUNCHED();
+        }
+        return FEWHA_OK;
+    }
+
+    int backproject(const T* weighted_slopes, T* out) {   // out = W P^T Gamma^T sl
+        int np1 = G.nsmax + 1;
+        k_gammaT<T><<<dim3((np1 * np1 + 255) / 256, G.G), 256, 0, stream>>>(G, weighted_slopes, wpsi2);
+        FEWHA_LAUNCHED();
+        k_PT<T><<<grid_layers(G.nmax * G.nmax), 256, 0, stream>>>(G, wpsi2, y);
+        FEWHA_LAUNCHED();
+        return fwd_dwt(y, out);
+    }
+
+    int data_term(const T* x, T* out) {   // out = W P^T Gamma^T C^{-1} Gamma P W^T x
+        TRY(inv_dwt(x, phi));
+        int np1 = G.nsmax + 1;
+        k_P<T><<<dim3((np1 * np1 + 255) / 256, G.G), 256, 0, stream>>>(G, phi, wpsi);
+        FEWHA_LAUNCHED();
+        k_gamma_w<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, wpsi, wsl);
+        FEWHA_LAUNCHED();
+        return backproject(wsl, out);
+    }
+
+    int rhs_and_restart(int warm) {
+        k_weight_meas<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, slopes, wsl, errw);
+        FEWHA_LAUNCHED();
+        TRY(backproject(wsl, b));
+        if (!warm) {
+            k_cold<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, b, bprev, r, c);
+            FEWHA_LAUNCHED();
+        } else if (k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0) {
+            TRY(apply_M_dev(c, ext));
+            k_replace<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, b, ext, bprev, r);
+            FEWHA_LAUNCHED();
+        } else {
+            k_warm<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, b, bprev, r);
+            FEWHA_LAUNCHED();
+        }
+        return FEWHA_OK;
+    }
+
+    int apply_M_dev(const T* x, T* out) {
+        TRY(data_term(x, out));
+        k_reg_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, aD, x, out, part2);
+        FEWHA_LAUNCHED();
+        return FEWHA_OK;
+    }
+
+    int pcg_plain(int n_iter) {
+        for (int k = 0; k < n_iter; ++k) {
+            k_precond_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, Jinv, r, z, part);
+            FEWHA_LAUNCHED();
+            TRY(data_term(z, s));
+            k_reg_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, aD, z, s, part2);
+            FEWHA_LAUNCHED();
+            k_alg2_scalars<<<1, 256, 0, stream>>>(part, part2, sc, k, errw);
+            FEWHA_LAUNCHED();
+            k_alg2_update<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, sc, k == 0, z, s, p, q, c, r);
+            FEWHA_LAUNCHED();
+        }
+        return FEWHA_OK;
+    }
+
+    int fit_dev(double gain, int n_fit) {
+        if (hs.M == 0) {
+            err = "the geometry has no deformable mirrors";
+            return FEWHA_ERR_STATE;
+        }
+        TRY(inv_dwt(c, phi));
+        int np1 = F.np1;
+        dim3 gdir((np1 * np1 + 255) / 256, F.T_);
+        int amax = 0;
+        for (auto& d : hs.dm) amax = std::max(amax, d.na);
+        dim3 gact((amax * amax + 255) / 256, F.M);
+        k_fit_lay<T><<<gdir, 256, 0, stream>>>(F, phi, fv);
+        FEWHA_LAUNCHED();
+        k_fit_dmT<T><<<gact, 256, 0, stream>>>(F, fv, nullptr, (T)0, frhs);
+        FEWHA_LAUNCHED();
+        // r = rhs - A x ; p = r ; rr = (r, r)
+        k_fit_dm<T><<<gdir, 256, 0, stream>>>(F, afit, fv);
+        FEWHA_LAUNCHED();
+        k_fit_dmT<T><<<gact, 256, 0, stream>>>(F, fv, afit, F.eps, fq);
+        FEWHA_LAUNCHED();
+        k_fit_init<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, frhs, fq, fr, fp);
+        FEWHA_LAUNCHED();
+        k_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, fr, fr, part);
+        FEWHA_LAUNCHED();
+        k_fit_scalar<<<1, 256, 0, stream>>>(part, sc, 0);
+        FEWHA_LAUNCHED();
+        for (int it = 0; it < n_fit; ++it) {
+            k_fit_dm<T><<<gdir, 256, 0, stream>>>(F, fp, fv);
+            FEWHA_LAUNCHED();
+            k_fit_dmT<T><<<gact, 256, 0, stream>>>(F, fv, fp, F.eps, fq);
+            FEWHA_LAUNCHED();
+            k_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, fp, fq, part);
+            FEWHA_LAUNCHED();
+            k_fit_scalar<<<1, 256, 0, stream>>>(part, sc, 1);
+            FEWHA_LAUNCHED();
+            k_fit_step<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, sc, afit, fr, fp, fq, part);
+            FEWHA_LAUNCHED();
+            k_fit_scalar<<<1, 256, 0, stream>>>(part, sc, 2);
+            FEWHA_LAUNCHED();
+            k_fit_dir<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, sc, fr, fp);
+            FEWHA_LAUNCHED();
+        }
+        k_gain<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, (T)gain, afit, acur, aprev);
+        FEWHA_LAUNCHED();
+        return FEWHA_OK;
+    }
+
+    // ---- copies ----
+    int copy_in(T* dst, const void* src, size_t count, int on_device) {
+        if (!src) {
+            err = "null input pointer";
+            return FEWHA_ERR_ARG;
+        }
+        FEWHA_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T),
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
+        if (!on_device) FEWHA_CUDA(cudaStreamSynchronize(stream));
+        return FEWHA_OK;
+    }
+    int copy_out(void* dst, const T* src, size_t count, int on_device) {
+        if (!dst) {
+            err = "null output pointer";
+            return FEWHA_ERR_ARG;
+        }
+        FEWHA_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T),
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+        if (!on_device) FEWHA_CUDA(cudaStreamSynchronize(stream));
+        return FEWHA_OK;
+    }
+
+    // ---- SolverBase ----
+    int set_frame(const void* sl, int on_device) override {
+        TRY(copy_in(slopes, sl, hs.S, on_device));
+        have_frame = true;
+        return FEWHA_OK;
+    }
+
+    bool use_fused() const { return path == FEWHA_PATH_FUSED && fused != nullptr; }
+
+    int solve_enqueue(int n_iter, int warm) {
+        if (use_fused()) {
+            bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
+            int st = fused_solve(fused, (const float*)slopes, n_iter, warm, replace ? 1 : 0, barrier_budget,
+                                 stream, err, launches);
+            if (st) return st;
+        } else {
+            TRY(rhs_and_restart(warm));
+            TRY(pcg_plain(n_iter));
+        }
+        frame_count += 1;
+        return FEWHA_OK;
+    }
+
+    int solve(int n_iter, int warm) override {
+        if (n_iter < 1 || n_iter > 100000) {
+            err = "n_iter must be >= 1";
+            return FEWHA_ERR_ARG;
+        }
+        if (!have_frame) {
+            err = "fewha_solve before fewha_set_frame";
+            return FEWHA_ERR_STATE;
+        }
+        return solve_enqueue(n_iter, warm);
+    }
+
+    int fit(double gain, int n_fit, void* out, int on_device) override {
+        if (n_fit < 0 || !(gain >= 0.0 && gain <= 1.0)) {
+            err = "gain must be in [0, 1] and n_fit >= 0";
+            return FEWHA_ERR_ARG;
+        }
+        TRY(fit_dev(gain, n_fit));
+        if (out) TRY(copy_out(out, acur, hs.NA, on_device));
+        return FEWHA_OK;
+    }
+
+    int get_layers(void* out, int on_device) override {
+        TRY(inv_dwt(c, phi));
+        return copy_out(out, phi, hs.N, on_device);
+    }
+
+    int get_vector(int which, void* out, int on_device) override {
+        const T* src = nullptr;
+        switch (which) {
+            case 0: src = c; break;
+            case 1: src = r; break;
+            case 2: src = b; break;
+            case 3: src = Jd; break;
+            case 4: src = aD; break;
+            default: err = "unknown vector"; return FEWHA_ERR_ARG;
+        }
+        return copy_out(out, src, hs.N, on_device);
+    }
+
+    int get_state(void* oc, void* ob, void* orr, int on_device) override {
+        if (oc) TRY(copy_out(oc, c, hs.N, on_device));
+        if (ob) TRY(copy_out(ob, bprev, hs.N, on_device));
+        if (orr) TRY(copy_out(orr, r, hs.N, on_device));
+        return FEWHA_OK;
+    }
+
+    int set_state(const void* ic, const void* ib, const void* ir, int on_device, long count) override {
+        if (!ic || !ib || !ir) {
+            err = "set_state needs c, b and r";
+            return FEWHA_ERR_ARG;
+        }
+        TRY(copy_in(c, ic, hs.N, on_device));
+        TRY(copy_in(bprev, ib, hs.N, on_device));
+        TRY(copy_in(r, ir, hs.N, on_device));
+        frame_count = count;
+        return FEWHA_OK;
+    }
+
+    int apply_M(const void* x, void* yout, int on_device) override {
+        TRY(copy_in(z, x, hs.N, on_device));
+        TRY(apply_M_dev(z, s));
+        return copy_out(yout, s, hs.N, on_device);
+    }
+
+    int check_err() {
+        FEWHA_CUDA(cudaMemcpyAsync(errw_host, errw, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        int e = *errw_host;
+        if (e) {
+            FEWHA_CUDA(cudaMemsetAsync(errw, 0, sizeof(int), stream));
+            FEWHA_CUDA(cudaStreamSynchronize(stream));
+            if (e & kErrTimeout) {
+                err = "a grid barrier of the fused kernel expired";
+                return FEWHA_ERR_TIMEOUT;
+            }
+            if (e & kErrInput) {
+                err = "non-finite slopes in active subapertures";
+                return FEWHA_ERR_INPUT;
+            }
+            if (e & kErrBreakdown) {
+                err = "PCG breakdown (step denominator <= 0 or non-finite)";
+                return FEWHA_ERR_BREAKDOWN;
+            }
+        }
+        return FEWHA_OK;
+    }
+
+    int sync() override {
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        return check_err();
+    }
+
+    int frame(const void* s_host, int n_iter, int warm, double gain, int n_fit, void* lout, void* dout) override {
+        if (!s_host) {
+            err = "null slopes";
+            return FEWHA_ERR_ARG;
+        }
+        if (n_iter < 1) {
+            err = "n_iter must be >= 1";
+            return FEWHA_ERR_ARG;
+        }
+        if (dout && hs.M == 0) {
+            err = "the geometry has no deformable mirrors";
+            return FEWHA_ERR_STATE;
+        }
+        // pinned host pointers are captured directly, pageable ones are staged
+        auto pinned = [](const void* ptr) {
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            return at.type == cudaMemoryTypeHost;
+        };
+        const void* sin = s_host;
+        void* lo = lout;
+        void* dm = dout;
+        bool stage_in = !pinned(s_host), stage_l = lout && !pinned(lout), stage_d = dout && !pinned(dout);
+        if (stage_in) {
+            if (!pinned_in) FEWHA_CUDA(cudaMallocHost(&pinned_in, hs.S * sizeof(T)));
+            std::memcpy(pinned_in, s_host, hs.S * sizeof(T));
+            sin = pinned_in;
+        }
+        if (stage_l) {
+            if (!pinned_out) FEWHA_CUDA(cudaMallocHost(&pinned_out, hs.N * sizeof(T)));
+            lo = pinned_out;
+        }
+        if (stage_d) {
+            if (!pinned_dm) FEWHA_CUDA(cudaMallocHost(&pinned_dm, std::max<long>(hs.NA, 1) * sizeof(T)));
+            dm = pinned_dm;
+        }
+        bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
+        int slot = replace ? 1 : 0;
+        Key key;
+        key.n_iter = n_iter;
+        key.warm = warm;
+        key.n_fit = dout ? n_fit : -1;
+        key.gain = dout ? gain : -1;
+        key.sin = sin;
+        key.lout = lo;
+        key.dout = dm;
+        key.path = path;
+        key.k_rr = k_rr;
+        if (!gexec[slot] || !(gkey[slot] == key)) {
+            if (gexec[slot]) {
+                cudaGraphExecDestroy(gexec[slot]);
+                gexec[slot] = nullptr;
+            }
+            if (stream == 0) {
+                err = "fewha_frame needs a non-default stream (graph capture)";
+                return FEWHA_ERR_STATE;
+            }
+            cudaGraph_t graph;
+            long long fc = frame_count;
+            FEWHA_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+            int st = FEWHA_OK;
+            long long l0 = launches;
+            do {
+                cudaError_t e = cudaMemcpyAsync(slopes, sin, hs.S * sizeof(T), cudaMemcpyHostToDevice, stream);
+                if (e != cudaSuccess) {
+                    err = cudaGetErrorString(e);
+                    st = FEWHA_ERR_CUDA;
+                    break;
+                }
+                if ((st = solve_enqueue(n_iter, warm))) break;
+                if (dm && (st = fit_dev(gain, n_fit))) break;
+                if (lo && (st = inv_dwt(c, phi))) break;
+                if (lo && cudaMemcpyAsync(lo, phi, hs.N * sizeof(T), cudaMemcpyDeviceToHost, stream) != cudaSuccess) {
+                    st = FEWHA_ERR_CUDA;
+                    err = "copy of layers";
+                    break;
+                }
+                if (dm && cudaMemcpyAsync(dm, acur, hs.NA * sizeof(T), cudaMemcpyDeviceToHost, stream) != cudaSuccess) {
+                    st = FEWHA_ERR_CUDA;
+                    err = "copy of mirror commands";
+                    break;
+                }
+            } while (0);
+            cudaError_t ec = cudaStreamEndCapture(stream, &graph);
+            frame_count = fc;              // capture only recorded the work
+            graph_launches = launches - l0;
+            launches = l0;
+            if (st) return st;
+            if (ec != cudaSuccess) {
+                err = std::string("graph capture: ") + cudaGetErrorString(ec);
+                return FEWHA_ERR_CUDA;
+            }
+            cudaError_t ei = cudaGraphInstantiate(&gexec[slot], graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) {
+                err = std::string("graph instantiate: ") + cudaGetErrorString(ei);
+                gexec[slot] = nullptr;
+                return FEWHA_ERR_CUDA;
+            }
+            gkey[slot] = key;
+            graph_launch_count[slot] = graph_launches;
+        } else if (stage_in) {
+            // staging buffer already holds this frame (copied above)
+        }
+        FEWHA_CUDA(cudaGraphLaunch(gexec[slot], stream));
+        launches += graph_launch_count[slot];
+        frame_count += 1;
+        have_frame = true;
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        if (stage_l) std::memcpy(lout, pinned_out, hs.N * sizeof(T));
+        if (stage_d) std::memcpy(dout, pinned_dm, hs.NA * sizeof(T));
+        return check_err();
+    }
+
+    long long graph_launches = 0;
+    long long graph_launch_count[2] = {0, 0};
+};
+
+SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& err, int& status) {
+    SolverBase* out = nullptr;
+    if (hs.prec == FEWHA_FP64) {
+        auto* s = new Solver<double>();
+        s->hs = hs;
+        s->stream = stream;
+        s->path = FEWHA_PATH_PLAIN;
+        status = s->init();
+        if (status) {
+            err = s->err;
+            delete s;
+            return nullptr;
+        }
+        out = s;
+    } else {
+        auto* s = new Solver<float>();
+        s->hs = hs;
+        s->stream = stream;
+        status = s->init();
+        if (status) {
+            err = s->err;
+            delete s;
+            return nullptr;
+        }
+        FusedBuffers fb;
+        fb.c = s->c;
+        fb.r = s->r;
+        fb.p = s->p;
+        fb.q = s->q;
+        fb.b = s->b;
+        fb.bprev = s->bprev;
+        fb.phi = s->phi;
+        fb.Jinv = s->Jinv;
+        fb.aD = s->aD;
+        fb.sc = s->sc;
+        fb.errw = s->errw;
+        std::string ferr;
+        s->fused = fused_create(hs, s->G, fb, ferr);
+        s->path = s->fused ? FEWHA_PATH_FUSED : FEWHA_PATH_PLAIN;
+        out = s;
+    }
+    status = FEWHA_OK;
+    return out;
+}
+
+}  // namespace fewha

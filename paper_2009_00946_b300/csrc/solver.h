@@ -1,0 +1,108 @@
+// Device-side solver of one FEWHA instance: buffers, tables and the plain
+// (one kernel per operator) path; the fused persistent path lives in fused.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "setup.h"
+
+namespace fewha {
+
+constexpr int kRedBlocks = 296;    // fixed reduction grid (2 x 148 SMs): deterministic sums
+constexpr int kRedThreads = 256;
+
+// Error bits of the device error word.
+constexpr int kErrInput = 1;
+constexpr int kErrBreakdown = 2;
+constexpr int kErrTimeout = 4;
+
+// Device geometry tables (pointers into one allocation), passed by value.
+template <typename T>
+struct DevGeo {
+    int L, G, N, S, NW, NS, Jmax, nmax, nsmax;
+    const int* lay_n;
+    const int* lay_J;
+    const int* lay_off;
+    const int* wfs_n;
+    const int* wfs_soff;
+    const int* wfs_noff;
+    const int* wfs_moff;
+    const T* wfs_w;
+    const unsigned char* mask;
+    const int* tab_off;
+    const int* cx;
+    const int* cy;
+    const T* tx;
+    const T* ty;
+    const int* gat_off;
+    const int* jlo;
+    const int* jhi;
+    const int* ilo;
+    const int* ihi;
+    const T* Jinv;
+    const T* aD;
+    T h[6], g[6];
+};
+
+// Device fitting tables.
+template <typename T>
+struct DevFit {
+    int L, M, T_, NA, np1;   // np1 = pupil nodes per side
+    T eps;
+    const int* lay_n;
+    const int* lay_off;
+    const int* dm_n;
+    const int* dm_off;
+    const int* ftab_off;
+    const int* fcx;
+    const int* fcy;
+    const T* ftx;
+    const T* fty;
+    const int* dtab_off;
+    const int* dcx;
+    const int* dcy;
+    const T* dtx;
+    const T* dty;
+    const int* dgat_off;
+    const int* djlo;
+    const int* djhi;
+    const int* dilo;
+    const int* dihi;
+};
+
+struct FusedPlan;   // fused.cu
+
+// Alg. 2 scalars kept on the device (FP64).
+enum Scalar { kRho = 0, kMu, kRhoOld, kAlphaOld, kBeta, kAlphaK, kRR, kRRold, kNumScalars = 16 };
+
+class SolverBase {
+  public:
+    virtual ~SolverBase() {}
+    virtual int set_frame(const void* s, int on_device) = 0;
+    virtual int solve(int n_iter, int warm) = 0;
+    virtual int fit(double gain, int n_fit, void* out, int on_device) = 0;
+    virtual int get_layers(void* out, int on_device) = 0;
+    virtual int get_vector(int which, void* out, int on_device) = 0;
+    virtual int get_state(void* c, void* b, void* r, int on_device) = 0;
+    virtual int set_state(const void* c, const void* b, const void* r, int on_device, long count) = 0;
+    virtual int apply_M(const void* x, void* y, int on_device) = 0;
+    virtual int frame(const void* s_host, int n_iter, int warm, double gain, int n_fit, void* layers_out,
+                      void* dm_out) = 0;
+    virtual int sync() = 0;
+
+    HostSetup hs;
+    cudaStream_t stream = 0;
+    int path = FEWHA_PATH_PLAIN;
+    int k_rr = 10;
+    long long barrier_budget = (1LL << 31);
+    long long frame_count = 0;
+    long long launches = 0;
+    bool have_frame = false;
+    std::string err;
+};
+
+SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& err, int& status);
+
+}  // namespace fewha

@@ -1,0 +1,286 @@
+"""Python binding of libfewha.so (ctypes): argument marshalling only.
+
+Every step of the reconstruction runs in the library's CUDA kernels.  The
+binding loads the in-tree ``libfewha.so`` and raises if it is missing: there is
+no CPU fallback.  Arrays may be numpy arrays (host) or torch CUDA tensors
+(device, ordered on the solver's stream).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfewha.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "fewha.h")
+
+MAX_WFS, MAX_LAYERS, MAX_DMS, MAX_FIT_DIRS = 16, 64, 8, 64
+FP32, FP64 = 0, 1
+PATH_PLAIN, PATH_FUSED = 0, 1
+ERRORS = {0: "OK", 1: "ARG", 2: "INPUT", 3: "GEOMETRY", 4: "BREAKDOWN", 5: "TIMEOUT", 6: "LAUNCH", 7: "CUDA",
+          8: "STATE"}
+VEC_C, VEC_R, VEC_B, VEC_JACOBI, VEC_ALPHA_D = 0, 1, 2, 3, 4
+
+
+class FewhaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("FEWHA_ERR_%s: %s" % (ERRORS.get(code, code), msg))
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_double), ("obstruction", ctypes.c_double), ("n_wfs", ctypes.c_int),
+                ("n_sub", ctypes.c_int * MAX_WFS), ("theta_x", ctypes.c_double * MAX_WFS),
+                ("theta_y", ctypes.c_double * MAX_WFS), ("gs_height", ctypes.c_double * MAX_WFS),
+                ("noise_sigma", ctypes.c_double * MAX_WFS), ("n_dm", ctypes.c_int),
+                ("dm_height", ctypes.c_double * MAX_DMS), ("dm_pitch", ctypes.c_double * MAX_DMS),
+                ("n_fit_dir", ctypes.c_int), ("fit_theta_x", ctypes.c_double * MAX_FIT_DIRS),
+                ("fit_theta_y", ctypes.c_double * MAX_FIT_DIRS), ("fit_n_sub", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int), ("height", ctypes.c_double * MAX_LAYERS),
+                ("cn2", ctypes.c_double * MAX_LAYERS), ("n_side", ctypes.c_int * MAX_LAYERS),
+                ("levels", ctypes.c_int * MAX_LAYERS), ("r0", ctypes.c_double), ("alpha", ctypes.c_double)]
+
+
+_lib = None
+
+
+def declared_symbols() -> list[str]:
+    """Entry points declared in include/fewha.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fewha_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load libfewha.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError("libfewha.so not built: run python -m paper_2009_00946_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ci, cd, cl, cll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_longlong
+    sig = {
+        "fewha_create": (ci, [ctypes.POINTER(Geometry), ctypes.POINTER(Profile), vp, ctypes.POINTER(vp)]),
+        "fewha_destroy": (ci, [vp]),
+        "fewha_last_error": (ctypes.c_char_p, [vp]),
+        "fewha_sizes": (ci, [vp, ctypes.POINTER(cl), ctypes.POINTER(cl), ctypes.POINTER(cl)]),
+        "fewha_set_path": (ci, [vp, ci]),
+        "fewha_set_residual_replacement": (ci, [vp, ci]),
+        "fewha_set_frame": (ci, [vp, vp, ci]),
+        "fewha_solve": (ci, [vp, ci, ci]),
+        "fewha_fit_dm": (ci, [vp, cd, ci, vp, ci]),
+        "fewha_get_layers": (ci, [vp, vp, ci]),
+        "fewha_get_vector": (ci, [vp, ci, vp, ci]),
+        "fewha_get_state": (ci, [vp, vp, vp, vp, ci]),
+        "fewha_set_state": (ci, [vp, vp, vp, vp, ci, cl]),
+        "fewha_apply_M": (ci, [vp, vp, vp, ci]),
+        "fewha_frame": (ci, [vp, vp, ci, ci, cd, ci, vp, vp]),
+        "fewha_sync": (ci, [vp]),
+        "fewha_set_barrier_budget": (ci, [vp, cll]),
+        "fewha_launch_count": (cll, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def structs_from_config(cfg: dict, precision: int | None = None):
+    """fewha_geometry / fewha_profile from a configuration dict."""
+    g = Geometry()
+    g.D = cfg["D"]
+    g.obstruction = cfg.get("obstruction", 0.0)
+    wfs = cfg["wfs"]
+    if len(wfs) > MAX_WFS:
+        raise ValueError("too many sensors")
+    g.n_wfs = len(wfs)
+    for i, w in enumerate(wfs):
+        g.n_sub[i] = int(w["n_sub"])
+        g.theta_x[i] = w["theta_x"]
+        g.theta_y[i] = w["theta_y"]
+        g.gs_height[i] = w["gs_height"]
+        g.noise_sigma[i] = w["sigma"]
+    dms = cfg.get("dms", [])
+    g.n_dm = len(dms)
+    for i, d in enumerate(dms):
+        g.dm_height[i] = d["height"]
+        g.dm_pitch[i] = d["pitch"]
+    fd = cfg.get("fit_dirs", [])
+    g.n_fit_dir = len(fd)
+    for i, (tx, ty) in enumerate(fd):
+        g.fit_theta_x[i] = tx
+        g.fit_theta_y[i] = ty
+    g.fit_n_sub = int(cfg.get("fit_n_sub", 0))
+    if precision is None:
+        precision = FP64 if cfg.get("precision", "fp32") == "fp64" else FP32
+    g.precision = precision
+    p = Profile()
+    lay = cfg["layers"]
+    if len(lay) > MAX_LAYERS:
+        raise ValueError("too many layers")
+    p.n_layers = len(lay)
+    for i, l in enumerate(lay):
+        p.height[i] = l["height"]
+        p.cn2[i] = l["cn2"]
+        p.n_side[i] = int(l["n"])
+        p.levels[i] = int(l["levels"])
+    p.r0 = cfg["r0"]
+    p.alpha = cfg["alpha"]
+    return g, p
+
+
+def _ptr(a, dtype, count, on_device):
+    """Pointer of a numpy array (host) or torch CUDA tensor (device)."""
+    if hasattr(a, "data_ptr"):
+        if a.dtype != dtype[1] or a.numel() != count or not a.is_contiguous():
+            raise ValueError("tensor must be contiguous %s with %d elements" % (dtype[1], count))
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    arr = a
+    if arr.dtype != dtype[0] or arr.size != count or not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous %s with %d elements" % (dtype[0], count))
+    return ctypes.c_void_p(arr.ctypes.data), 0
+
+
+class Solver:
+    """One FEWHA instance on the current CUDA device (a fewha_handle)."""
+
+    def __init__(self, cfg: dict, precision: int | None = None, stream=None, path: int | None = None,
+                 k_rr: int | None = None):
+        import torch
+        L = lib()
+        g, p = structs_from_config(cfg, precision)
+        self.precision = g.precision
+        self.np_dtype = np.float64 if self.precision == FP64 else np.float32
+        self.torch_dtype = torch.float64 if self.precision == FP64 else torch.float32
+        if stream is None:
+            self._stream_obj = torch.cuda.Stream()
+        else:
+            self._stream_obj = stream
+        self.stream = self._stream_obj
+        h = ctypes.c_void_p()
+        st = L.fewha_create(ctypes.byref(g), ctypes.byref(p), ctypes.c_void_p(self._stream_obj.cuda_stream),
+                            ctypes.byref(h))
+        if st != 0:
+            raise FewhaError(st, L.fewha_last_error(None).decode())
+        self.h = h
+        n, s, a = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+        L.fewha_sizes(h, ctypes.byref(n), ctypes.byref(s), ctypes.byref(a))
+        self.N, self.S, self.NA = n.value, s.value, a.value
+        self.cfg = cfg
+        if path is not None:
+            self.set_path(path)
+        if k_rr is not None:
+            self._check(L.fewha_set_residual_replacement(self.h, int(k_rr)))
+
+    # -- plumbing --
+    def _check(self, st):
+        if st != 0:
+            raise FewhaError(st, lib().fewha_last_error(self.h).decode())
+
+    def _dt(self):
+        return (self.np_dtype, self.torch_dtype)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fewha_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- API --
+    def set_path(self, path: int):
+        self._check(lib().fewha_set_path(self.h, int(path)))
+
+    def set_residual_replacement(self, k_rr: int):
+        self._check(lib().fewha_set_residual_replacement(self.h, int(k_rr)))
+
+    def set_barrier_budget(self, cycles: int):
+        self._check(lib().fewha_set_barrier_budget(self.h, int(cycles)))
+
+    def set_frame(self, slopes):
+        ptr, dev = _ptr(slopes, self._dt(), self.S, None)
+        self._check(lib().fewha_set_frame(self.h, ptr, dev))
+
+    def solve(self, n_iter: int, warm: bool = True):
+        self._check(lib().fewha_solve(self.h, int(n_iter), 1 if warm else 0))
+
+    def sync(self):
+        self._check(lib().fewha_sync(self.h))
+
+    def fit_dm(self, gain: float = 1.0, n_fit: int = 8, out=None):
+        if out is None:
+            out = np.empty(self.NA, self.np_dtype)
+        ptr, dev = _ptr(out, self._dt(), self.NA, None)
+        self._check(lib().fewha_fit_dm(self.h, float(gain), int(n_fit), ptr, dev))
+        return out
+
+    def layers(self, out=None):
+        if out is None:
+            out = np.empty(self.N, self.np_dtype)
+        ptr, dev = _ptr(out, self._dt(), self.N, None)
+        self._check(lib().fewha_get_layers(self.h, ptr, dev))
+        return out
+
+    def vector(self, which: int, out=None):
+        if out is None:
+            out = np.empty(self.N, self.np_dtype)
+        ptr, dev = _ptr(out, self._dt(), self.N, None)
+        self._check(lib().fewha_get_vector(self.h, int(which), ptr, dev))
+        return out
+
+    def get_state(self):
+        c, b, r = (np.empty(self.N, self.np_dtype) for _ in range(3))
+        self._check(lib().fewha_get_state(self.h, ctypes.c_void_p(c.ctypes.data), ctypes.c_void_p(b.ctypes.data),
+                                          ctypes.c_void_p(r.ctypes.data), 0))
+        return c, b, r
+
+    def set_state(self, c, b, r, frame_count: int):
+        c, b, r = (np.ascontiguousarray(v, dtype=self.np_dtype) for v in (c, b, r))
+        self._check(lib().fewha_set_state(self.h, ctypes.c_void_p(c.ctypes.data), ctypes.c_void_p(b.ctypes.data),
+                                          ctypes.c_void_p(r.ctypes.data), 0, int(frame_count)))
+
+    def apply_M(self, x, out=None):
+        if out is None:
+            out = np.empty(self.N, self.np_dtype) if not hasattr(x, "data_ptr") else x.new_empty(self.N)
+        px, dx = _ptr(x, self._dt(), self.N, None)
+        py, dy = _ptr(out, self._dt(), self.N, None)
+        if dx != dy:
+            raise ValueError("x and out must both be host or both be device")
+        self._check(lib().fewha_apply_M(self.h, px, py, dx))
+        return out
+
+    def frame(self, slopes_host, n_iter: int, warm: bool = True, gain: float = 1.0, n_fit: int = 8,
+              layers_out=None, dm_out=None):
+        """One whole frame through the captured CUDA graph (host in, host out)."""
+        ps, ds = _ptr(slopes_host, self._dt(), self.S, None)
+        if ds:
+            raise ValueError("fewha_frame takes host slopes")
+        pl = _ptr(layers_out, self._dt(), self.N, None)[0] if layers_out is not None else None
+        pd = _ptr(dm_out, self._dt(), self.NA, None)[0] if dm_out is not None else None
+        self._check(lib().fewha_frame(self.h, ps, int(n_iter), 1 if warm else 0, float(gain), int(n_fit), pl, pd))
+
+    def launch_count(self) -> int:
+        return int(lib().fewha_launch_count(self.h))

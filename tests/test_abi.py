@@ -1,0 +1,76 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry point
+declared in include/fewha.h, and rejects invalid arguments before touching a
+GPU (no compute call is made here)."""
+
+import ctypes
+
+import pytest
+
+from paper_2009_00946_b300 import configs, fewha
+
+
+def test_library_exports_every_declared_symbol():
+    L = fewha.lib()
+    names = fewha.declared_symbols()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_symbol():
+    L = fewha.lib()
+    for n in fewha.declared_symbols():
+        assert getattr(L, n).restype is not None or n in ("fewha_destroy",), n
+
+
+def _create(g, p):
+    L = fewha.lib()
+    h = ctypes.c_void_p()
+    st = L.fewha_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(h))
+    return st, h, L.fewha_last_error(None).decode()
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda g, p: setattr(g, "D", -1.0), 1),
+    (lambda g, p: setattr(g, "n_wfs", 0), 1),
+    (lambda g, p: setattr(g, "n_wfs", 17), 1),
+    (lambda g, p: setattr(g, "precision", 5), 1),
+    (lambda g, p: setattr(p, "alpha", 0.0), 1),
+    (lambda g, p: p.n_side.__setitem__(0, 48), 1),          # not a power of two
+    (lambda g, p: p.levels.__setitem__(0, 5), 1),            # 32 >> 5 < 2
+    (lambda g, p: p.cn2.__setitem__(1, 0.0), 1),
+    (lambda g, p: g.noise_sigma.__setitem__(0, 0.0), 1),
+    (lambda g, p: setattr(g, "obstruction", 1.0), 1),
+])
+def test_create_rejects_invalid_arguments_on_host(mutate, code):
+    g, p = fewha.structs_from_config(configs.c1_plain())
+    mutate(g, p)
+    st, h, msg = _create(g, p)
+    assert st == code and not h.value and msg
+
+
+def test_create_rejects_layer_above_lgs():
+    cfg = configs.c5_autograd()
+    cfg["layers"][-1]["height"] = 95000.0
+    g, p = fewha.structs_from_config(cfg)
+    st, h, msg = _create(g, p)
+    assert st == 3 and "guide star" in msg
+
+
+def test_null_pointers_rejected():
+    L = fewha.lib()
+    assert L.fewha_create(None, None, None, None) == 1
+    assert L.fewha_destroy(None) == 1
+    assert L.fewha_solve(None, 4, 1) == 1
+    assert L.fewha_sync(None) == 1
+    assert L.fewha_launch_count(None) == -1
+
+
+def test_header_documents_every_entry_point():
+    import os
+    import re
+    hdr = open(fewha.HEADER).read()
+    for n in fewha.declared_symbols():
+        # every declaration is preceded by a comment block
+        m = re.search(r"\*/\s*\n(?:[^\n]*\n){0,4}[^\n;]*\b" + n + r"\s*\(", hdr)
+        assert m, n
