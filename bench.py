@@ -1,0 +1,346 @@
+"""FEWHA benchmark: ELT frame latency p50/p99 (us) and PCG iterations/s on one
+B300, FP32 fused-graph path beside the plain FP64 path, on synthetic
+von Karman frames of the ELT bulk configuration (D = 39 m, 6 LGS, 84x84
+subapertures, 9 layers on 128^2 grids, db3 with 4 levels, 4 warm-started PCG
+iterations per frame).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fewha|reference]
+
+A step is one frame of Alg. 1 up to the layers: slopes in -> RHS -> warm
+restart (residual replacement every 10 frames) -> 4 iterations of Alg. 2 ->
+layers phi = W^T c out.  Prints one JSON line (rank 0).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2009_00946_b300 import configs, synth  # noqa: E402
+
+METRIC = "ELT frame latency p50/p99 µs & PCG iter/s, FP32-graph vs plain FP64 on B300"
+UNIT = "us"
+N_ITER = 4
+K_RR = 10
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_config():
+    return configs.c2_elt()
+
+
+def config_block(cfg, extra=None):
+    d = {"workload": "ELT MCAO bulk: D=39 m, 6 LGS (90 km) on a 1-arcmin-radius hexagon, 84x84 subapertures, "
+                     "9 layers 0-16 km on 128^2 grids, db3 J=4, 4 warm-started PCG iterations per frame, "
+                     "residual replacement every 10 frames",
+         "frames": "synthetic von Karman frozen flow (r0=0.157 m, L0=25 m), 500 Hz, sigma=0.1 rad",
+         "n_coeff": sum(l["n"] ** 2 for l in cfg["layers"]),
+         "n_slopes": sum(2 * w["n_sub"] ** 2 for w in cfg["wfs"]),
+         "l2": "flushed between timed frames (512 MiB write, untimed)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def algorithmic_bytes_per_frame(cfg, n_iter, elem=4):
+    """Per PCG iteration 16N + 4 NW elements (each operator reads its input and
+    writes its output once: inverse DWT 2N, P N+NW, Gamma/C/Gamma^T 2NW,
+    P^T NW+N, forward DWT + alpha D z 3N, update 9N); per frame add the RHS
+    and restart S + 2NW + 8N and the layers output 2N."""
+    N = sum(l["n"] ** 2 for l in cfg["layers"])
+    NW = sum((w["n_sub"] + 1) ** 2 for w in cfg["wfs"])
+    S = sum(2 * w["n_sub"] ** 2 for w in cfg["wfs"])
+    return elem * (n_iter * (16 * N + 4 * NW) + S + 2 * NW + 10 * N)
+
+
+def slope_pool(cfg, count, seed=None):
+    atm = synth.Atmosphere(cfg, seed)
+    return np.stack([atm.slopes(k) for k in range(count)]).astype(np.float32)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 20):
+        self.cmd = ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                    "--format=csv,noheader,nounits", "-lms", str(period_ms)]
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_latency(cfg, n_frames, pool_np):
+    """The FP64 CPU oracle as it stands, one host core: per-frame latency (us)."""
+    from oracle import fewha_oracle as fo
+    R = fo.Reconstructor(cfg)
+    times = []
+    for k in range(n_frames):
+        s = pool_np[k % len(pool_np)].astype(np.float64)
+        t0 = time.perf_counter()
+        R.frame(s, N_ITER, warm=True, k_rr=K_RR)
+        R.layers()
+        times.append((time.perf_counter() - t0) * 1e6)
+    return times
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle (there is no runnable reference code)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = workload_config()
+    n_time = min(args.steps, 40)
+    n_warm = min(args.warmup, 3)
+    pool = slope_pool(cfg, n_time + n_warm)
+    t = cpu_oracle_latency(cfg, n_time + n_warm, pool)[n_warm:]
+    p50 = float(np.percentile(t, 50))
+    line = {"impl": "reference", "metric": METRIC, "value": p50, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(t)) / 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(cfg),
+            "p99_us": float(np.percentile(t, 99)),
+            "cpu_baseline": {"value": p50, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d frames of the workload after %d warm-up frames (of the %d requested)"
+                                       % (n_time, n_warm, args.steps)},
+            "e2e": {"value": p50, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_frames(S, torch, pool_dev, start, K, layers_dev, flush, events=True):
+    """K frames through the device-pointer graph, L2 flushed before each."""
+    st = S.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        with torch.cuda.stream(st):
+            flush.fill_(float(k & 7))
+        ev[k][0].record(st)
+        S.frame(pool_dev[(start + k) % pool_dev.shape[0]], N_ITER, warm=True, layers_out=layers_dev)
+        ev[k][1].record(st)
+    st.synchronize()
+    return [a.elapsed_time(b) * 1e3 for a, b in ev]
+
+
+def time_solve(S, torch, n_iter, K, flush):
+    """Average duration (us) of one solve launch (RHS + restart + n_iter iterations)."""
+    st = S.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        with torch.cuda.stream(st):
+            flush.fill_(1.0)
+        ev[k][0].record(st)
+        S.solve(n_iter, warm=True)
+        ev[k][1].record(st)
+    st.synchronize()
+    S.sync()
+    return float(np.mean([a.elapsed_time(b) * 1e3 for a, b in ev]))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="fewha", choices=["fewha", "reference"])
+    ap.add_argument("--pool", type=int, default=64, help="distinct synthetic frames, cycled")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg = workload_config()
+    pool = slope_pool(cfg, args.pool, seed=cfg["seed"] + 100 * rank)
+
+    # CPU oracle baseline first (rank 0, N = 1), before any CUDA call
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = cpu_oracle_latency(cfg, 30, pool)[2:]
+        cpu = {"value": float(np.percentile(t, 50)), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "28 ELT frames (after 2 warm-up frames), FP64 numpy oracle, one host thread (%d cores "
+                         "on the host)" % os.cpu_count()}
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2009_00946_b300 import fewha
+
+    dev = torch.device("cuda", local_rank)
+    pool_dev = torch.from_numpy(pool).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    S = fewha.Solver(cfg, precision=fewha.FP32, path=fewha.PATH_FUSED, k_rr=K_RR)
+    layers_dev = torch.empty(S.N, dtype=torch.float32, device=dev)
+    W, K = args.warmup, args.steps
+    time_frames(S, torch, pool_dev, 0, W, layers_dev, flush)
+    S.sync()
+
+    # ---- timed region: K frames, device-resident inputs ----
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = S.launch_count()
+    with ClockSampler(local_rank) as clk:
+        lat = time_frames(S, torch, pool_dev, W, K, layers_dev, flush)
+        S.sync()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = S.launch_count() - l0
+    p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+    mean = float(np.mean(lat))
+
+    # ---- kernel-level: solve duration (roofline) and per-iteration cost ----
+    t4 = time_solve(S, torch, N_ITER, 100, flush)
+    t100 = time_solve(S, torch, 100, 20, flush)
+    per_iter = (t100 - t4) / 96.0
+    hbm, peak_kind = measured_peaks()
+    alg = algorithmic_bytes_per_frame(cfg, N_ITER)
+    achieved = alg / (t4 * 1e-6) / 1e9
+
+    # ---- end to end: pinned host slopes in, layers out, through fewha_frame ----
+    pin_s = torch.empty(S.S, dtype=torch.float32).pin_memory()
+    pin_l = torch.empty(S.N, dtype=torch.float32).pin_memory()
+    e2e = []
+    n_e2e = min(K, 300)
+    for k in range(n_e2e + 5):
+        pin_s.numpy()[:] = pool[(W + K + k) % len(pool)]
+        with torch.cuda.stream(S.stream):
+            flush.fill_(2.0)
+        S.stream.synchronize()
+        t0 = time.perf_counter()
+        S.frame(pin_s.numpy(), N_ITER, warm=True, layers_out=pin_l.numpy())
+        e2e.append((time.perf_counter() - t0) * 1e6)
+    e2e = e2e[5:]
+
+    # ---- the plain FP64 path (one kernel per operator) on the same frames ----
+    P64 = fewha.Solver(cfg, precision=fewha.FP64, k_rr=K_RR)
+    pool64 = pool_dev.double()
+    lay64 = torch.empty(P64.N, dtype=torch.float64, device=dev)
+    n64 = min(K, 200)
+    time_frames(P64, torch, pool64, 0, 5, lay64, flush)
+    lat64 = time_frames(P64, torch, pool64, 5, n64, lay64, flush)
+    p64_t4 = time_solve(P64, torch, N_ITER, 10, flush)
+    p64_t20 = time_solve(P64, torch, 20, 5, flush)
+    p64_iter = (p64_t20 - p64_t4) / 16.0
+    P64.close()
+
+    # max over ranks
+    vals = np.array([p50, p99, mean, per_iter], dtype=np.float64)
+    if dist:
+        tv = torch.tensor(vals, device=dev)
+        dist.all_reduce(tv, op=dist.ReduceOp.MAX)
+        vals = tv.cpu().numpy()
+    p50, p99, mean, per_iter = [float(v) for v in vals]
+    if rank != 0:
+        S.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": p50, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": mean / 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64 dots/scalars)", "data": "synthetic",
+        "config": config_block(cfg, {"path": "fused persistent kernel, CUDA graph per frame",
+                                     "parallelism": "replicas" if world > 1 else "1 GPU"}),
+        "p50_us": p50, "p99_us": p99,
+        "pcg_iter_per_s": 1e6 / per_iter if per_iter > 0 else None,
+        "us_per_pcg_iter": per_iter,
+        "frames_per_s_total": world * 1e6 / mean,
+        "plain_fp64": {"p50_us": float(np.percentile(lat64, 50)), "p99_us": float(np.percentile(lat64, 99)),
+                       "us_per_pcg_iter": p64_iter, "pcg_iter_per_s": 1e6 / p64_iter if p64_iter > 0 else None,
+                       "frames": n64},
+        "e2e": {"value": float(np.percentile(e2e, 50)), "unit": UNIT, "p99": float(np.percentile(e2e, 99)),
+                "h2d_bytes_per_step": S.S * 4, "d2h_bytes_per_step": S.N * 4, "frames": n_e2e,
+                "how": "fewha_frame with pinned host slopes and layers, host wall clock per frame"},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "k_fused_frame", "duration_us": t4, "algorithmic_bytes": alg,
+                     "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+        "clocks": clocks,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    S.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

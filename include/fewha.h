@@ -155,13 +155,17 @@ int fewha_set_state(fewha_handle* h, const void* c, const void* b, const void* r
 /* y = M x (N values each), one operator application (Eq. (fewha) left side). */
 int fewha_apply_M(fewha_handle* h, const void* x, void* y, int on_device);
 
-/* One whole frame as one CUDA graph: set_frame (host slopes, pinned or not),
- * solve(n_iter, warm), optional fit, optional layers, device->host results.
- * The graph is captured on the first call and re-captured when n_iter, the
- * flags or the output pointers change.  Synchronises (host outputs).
+/* One whole frame of Alg. 1 as one CUDA graph: copy in the slopes s, RHS,
+ * warm restart, n_iter iterations of Alg. 2, optional fit + gain (dm_out),
+ * optional layers phi = W^{-1} c (layers_out), copy out.  on_device = 0: the
+ * three pointers are host memory (pinned memory is used in place, pageable
+ * memory is staged) and the call synchronises; on_device = 1: device
+ * pointers, the call only enqueues.  The graph is captured on the first call
+ * and re-captured when n_iter, the flags or the pointers change; frames that
+ * fall on the residual-replacement period use a second graph.
  * layers_out / dm_out may be NULL. */
-int fewha_frame(fewha_handle* h, const void* slopes_host, int n_iter, int warm_start,
-                double gain, int n_fit, void* layers_out, void* dm_out);
+int fewha_frame(fewha_handle* h, const void* slopes, int n_iter, int warm_start,
+                double gain, int n_fit, void* layers_out, void* dm_out, int on_device);
 
 /* Wait for the handle's stream and return the device error word (OK, INPUT,
  * BREAKDOWN, TIMEOUT).  The word is cleared after it has been read. */

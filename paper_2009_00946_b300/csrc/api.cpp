@@ -143,12 +143,12 @@ int fewha_apply_M(fewha_handle* h, const void* x, void* y, int on_device) {
     return done(h, h->s->apply_M(x, y, on_device));
 }
 
-int fewha_frame(fewha_handle* h, const void* slopes_host, int n_iter, int warm_start, double gain, int n_fit,
-                void* layers_out, void* dm_out) {
+int fewha_frame(fewha_handle* h, const void* slopes, int n_iter, int warm_start, double gain, int n_fit,
+                void* layers_out, void* dm_out, int on_device) {
     if (!h) return FEWHA_ERR_ARG;
     if (dm_out && (n_fit < 0 || !(gain >= 0.0 && gain <= 1.0)))
         return fail(h, FEWHA_ERR_ARG, "gain must be in [0, 1] and n_fit >= 0");
-    return done(h, h->s->frame(slopes_host, n_iter, warm_start, gain, n_fit, layers_out, dm_out));
+    return done(h, h->s->frame(slopes, n_iter, warm_start, gain, n_fit, layers_out, dm_out, on_device));
 }
 
 int fewha_sync(fewha_handle* h) {

@@ -1,19 +1,918 @@
-// Fused FP32 path (placeholder until the persistent kernel is written).
+// Fused FP32 FEWHA frame: one persistent cooperative kernel runs Alg. 1 up to
+// the PCG and n_iter iterations of Alg. 2 (operator M of Eq. (fewha) applied
+// matrix-free once per iteration), with FP64 reductions and scalars.
+//
+// Work decomposition (two kinds of phases, separated by grid barriers):
+//   * layer phase: one thread-block cluster per layer; the layer's n x n array
+//     is split into row stripes of R = n / C rows, one per CTA of the cluster,
+//     kept in shared memory.  P^T (deterministic gather from the sensor
+//     fields), the forward db3 DWT W, the Alg. 2 update, z = J^{-1} r and the
+//     inverse DWT W^T run there; the column passes of the DWT read the other
+//     stripes through distributed shared memory, one cluster barrier per level.
+//   * sensor phase: one CTA per sensor tile: bilinear P of every layer (the
+//     layer windows are staged in shared memory), Gamma, C^{-1}, Gamma^T; the
+//     data part of mu = (M z, z) = sum_g w_g |mask Gamma P W^T z|^2 is reduced
+//     here, the regulariser part alpha (D z, z) in the layer phase.
+// Per iteration: layer phase -> barrier -> sensor phase -> barrier.  Every sum
+// is taken in a fixed order (per-item partials), so results are bit-identical
+// from run to run.  The control flow never depends on data, so cluster
+// barriers are always reached by every CTA; grid barriers spin with a clock
+// budget and set the TIMEOUT bit when it runs out.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
 #include "fused.h"
 #include "solver.h"
 
+namespace cg = cooperative_groups;
+
 namespace fewha {
 
-struct FusedPlan {};
+constexpr int kFThreads = 512;
+constexpr int kMaxC = 16;
+constexpr int kMaxLayersFused = 64;
+constexpr int kMaxWfsFused = 16;
 
-FusedPlan* fused_create(const HostSetup&, const DevGeo<float>&, const FusedBuffers&, std::string& err) {
-    err = "fused path not available";
-    return nullptr;
+enum { kModeRhs = 0, kModeData = 1 };
+enum { kLpRhsStart = 0, kLpRhsRepl = 1, kLpReplStart = 2, kLpIter = 3 };
+
+// One instance's device tables and state.
+struct FInst {
+    int L, G, N, NW;
+    const int *lay_n, *lay_J, *lay_off;
+    const int *wfs_n, *wfs_soff, *wfs_noff, *wfs_moff;
+    const float* wfs_w;
+    const unsigned char* mask;
+    const int *tab_off, *cx, *cy;
+    const float *tx, *ty;
+    const int *gat_off, *jlo, *jhi, *ilo, *ihi;
+    const float *Jinv, *aD;
+    float *c, *r, *p, *q, *b, *bprev, *phi, *psi;
+    const float* slopes;
+    double* scal;          // [2 parities][2] = rho_old, alpha_old
+    double* sc_out;        // final scalars for the host (kRho...)
+    int w0, nw, l0, nl;    // ranges in the item lists
+};
+
+struct WItem { int inst, g, i0, i1, j0, j1; };
+struct LItem { int inst, l, stg; };
+
+struct FParams {
+    const FInst* inst;
+    const WItem* witems;
+    const LItem* litems;
+    const int2* stg;       // Pt staging row ranges per (layer item, rank, sensor)
+    double* wpart;         // [n_witems]
+    double* lpart;         // [2][n_litems * C][2]
+    unsigned* bar;
+    int* errw;
+    long long budget;
+    int n_inst, n_witems, n_litems;
+    int n_iter, warm, replace, out_layers;
+    int C;
+    int stripe_floats, stage_floats, win_floats, tile_nodes, tile_subaps;
+    float h[6], g[6];
+};
+
+// ---------------------------------------------------------------------------
+// grid barrier with a clock budget
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
-void fused_destroy(FusedPlan* plan) { delete plan; }
-int fused_solve(FusedPlan*, const float*, int, int, int, long long, cudaStream_t, std::string& err, long long&) {
-    err = "fused path not available";
-    return FEWHA_ERR_STATE;
+
+__device__ void grid_barrier(const FParams& P, unsigned& target, int* s_abort) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += gridDim.x;
+        __threadfence();
+        atomicAdd(P.bar, 1u);
+        if (!*s_abort) {
+            long long t0 = clock64();
+            while ((int)(ld_acquire_gpu(P.bar) - target) < 0) {
+                if (clock64() - t0 > P.budget) {
+                    atomicOr(P.errw, kErrTimeout);
+                    *s_abort = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_reduce(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;   // thread 0
+}
+
+// ---------------------------------------------------------------------------
+// sensor phase: P, Gamma, C^{-1}, Gamma^T on one tile of nodes
+// ---------------------------------------------------------------------------
+__device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, bool want_mu, int* wdesc, double* red) {
+    const WItem W = P.witems[item];
+    const FInst& I = P.inst[W.inst];
+    const int g = W.g, ns = I.wfs_n[g], np1 = ns + 1, L = I.L;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    // psi nodes [a_lo, a_hi] x [b_lo, b_hi]; subapertures [a_lo, sa_hi) x [b_lo, sb_hi)
+    const int a_lo = max(W.i0 - 1, 0), a_hi = min(W.i1, ns);
+    const int b_lo = max(W.j0 - 1, 0), b_hi = min(W.j1, ns);
+    const int sa_hi = min(W.i1, ns), sb_hi = min(W.j1, ns);
+    const int nsr = max(sa_hi - a_lo, 0), nsc = max(sb_hi - b_lo, 0);
+    const int pr = a_hi - a_lo + 1, pc = b_hi - b_lo + 1;
+    float* win = sm;
+    float* psi = sm + P.win_floats;
+    float* slx = psi + P.tile_nodes;
+    float* sly = slx + P.tile_subaps;
+    double mu = 0.0;
+    const int ns2 = ns * ns;
+    if (mode == kModeData) {
+        if (tid < L) {
+            const int base = I.tab_off[g * L + tid];
+            const int r0 = I.cy[base + a_lo], r1 = I.cy[base + a_hi] + 1;
+            const int c0 = I.cx[base + b_lo], c1 = I.cx[base + b_hi] + 1;
+            wdesc[tid * 5 + 0] = r0;
+            wdesc[tid * 5 + 1] = c0;
+            wdesc[tid * 5 + 2] = r1 - r0 + 1;
+            wdesc[tid * 5 + 3] = c1 - c0 + 1;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int o = 0;
+            for (int l = 0; l < L; ++l) {
+                wdesc[l * 5 + 4] = o;
+                o += wdesc[l * 5 + 2] * wdesc[l * 5 + 3];
+            }
+        }
+        __syncthreads();
+        for (int l = 0; l < L; ++l) {
+            const int r0 = wdesc[l * 5], c0 = wdesc[l * 5 + 1], nc = wdesc[l * 5 + 3];
+            const int cnt = wdesc[l * 5 + 2] * nc, so = wdesc[l * 5 + 4], n = I.lay_n[l];
+            const float* src = I.phi + I.lay_off[l] + (long)r0 * n + c0;
+            for (int e = tid; e < cnt; e += NT) {
+                const int rr = e / nc, cc = e - rr * nc;
+                win[so + e] = __ldcg(src + (long)rr * n + cc);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < pr * pc; e += NT) {
+            const int ii = e / pc, jj = e - ii * pc;
+            const int i = a_lo + ii, j = b_lo + jj;
+            float acc = 0.f;
+            for (int l = 0; l < L; ++l) {
+                const int base = I.tab_off[g * L + l];
+                const int nc = wdesc[l * 5 + 3];
+                const int cyv = __ldg(I.cy + base + i) - wdesc[l * 5];
+                const int cxv = __ldg(I.cx + base + j) - wdesc[l * 5 + 1];
+                const float ty = __ldg(I.ty + base + i), tx = __ldg(I.tx + base + j);
+                const float* f = win + wdesc[l * 5 + 4] + cyv * nc + cxv;
+                acc += (1.f - ty) * ((1.f - tx) * f[0] + tx * f[1]) + ty * ((1.f - tx) * f[nc] + tx * f[nc + 1]);
+            }
+            psi[e] = acc;
+        }
+        __syncthreads();
+        const float w = I.wfs_w[g];
+        for (int e = tid; e < nsr * nsc; e += NT) {
+            const int aa = e / nsc, bb = e - aa * nsc;
+            const int a = a_lo + aa, b = b_lo + bb;
+            const float* pp = psi + aa * pc + bb;
+            const float sx = ((pp[1] - pp[0]) + (pp[pc + 1] - pp[pc])) / 2;
+            const float sy = ((pp[pc] - pp[0]) + (pp[pc + 1] - pp[1])) / 2;
+            const float wm = I.mask[I.wfs_moff[g] + a * ns + b] ? w : 0.f;
+            slx[e] = wm * sx;
+            sly[e] = wm * sy;
+            if (want_mu && a >= W.i0 && b >= W.j0) mu += (double)wm * ((double)sx * sx + (double)sy * sy);
+        }
+    } else {
+        const float w = I.wfs_w[g];
+        const float* S = I.slopes + I.wfs_soff[g];
+        for (int e = tid; e < nsr * nsc; e += NT) {
+            const int aa = e / nsc, bb = e - aa * nsc;
+            const int a = a_lo + aa, b = b_lo + bb;
+            const bool on = I.mask[I.wfs_moff[g] + a * ns + b] != 0;
+            const float vx = __ldcg(S + a * ns + b), vy = __ldcg(S + ns2 + a * ns + b);
+            const bool fx = isfinite(vx), fy = isfinite(vy);
+            if (on && (!fx || !fy) && a >= W.i0 && b >= W.j0) atomicOr(P.errw, kErrInput);
+            slx[e] = (on && fx) ? w * vx : 0.f;
+            sly[e] = (on && fy) ? w * vy : 0.f;
+        }
+    }
+    __syncthreads();
+    const int ti = W.i1 - W.i0, tj = W.j1 - W.j0;
+    float* out = I.psi + I.wfs_noff[g];
+    for (int e = tid; e < ti * tj; e += NT) {
+        const int ii = e / tj, jj = e - ii * tj;
+        const int i = W.i0 + ii, j = W.j0 + jj;
+        float acc = 0.f;
+        for (int a = i - 1; a <= i; ++a) {
+            if (a < 0 || a >= ns) continue;
+            for (int b = j - 1; b <= j; ++b) {
+                if (b < 0 || b >= ns) continue;
+                const int idx = (a - a_lo) * nsc + (b - b_lo);
+                const float sx = slx[idx], sy = sly[idx];
+                acc += (b == j - 1 ? sx : -sx) + (a == i - 1 ? sy : -sy);
+            }
+        }
+        out[i * np1 + j] = acc / 2;
+    }
+    if (want_mu) {
+        const double s = block_reduce(mu, red);
+        if (tid == 0) P.wpart[item] = s;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// distributed DWT on the cluster's row stripes
+// ---------------------------------------------------------------------------
+struct Stripe {
+    int n, J, R, row0;
+};
+
+__device__ __forceinline__ void csync(cg::cluster_group& cl, bool multi) {
+    if (multi) cl.sync();
+    else __syncthreads();
+}
+
+// Z (own rows) <- W Z; P buffers alternate by level (remote reads in the
+// column passes); one cluster barrier per level whose block spans CTAs.
+__device__ void fwd_dwt(const FParams& P, const Stripe& s, float* Z, float* P0, float* P1, float* const* rem0,
+                        float* const* rem1, cg::cluster_group& cl) {
+    const int tid = threadIdx.x, NT = blockDim.x, n = s.n, R = s.R;
+    __syncthreads();
+    for (int j = 1; j <= s.J; ++j) {
+        const int m = n >> (j - 1), half = m >> 1, mask = m - 1;
+        const bool multi = m > R;
+        float* Pj = (j & 1) ? P0 : P1;
+        float* const* rem = (j & 1) ? rem0 : rem1;
+        const int nrows = max(0, min(m - s.row0, R));
+        for (int e = tid; e < nrows * half; e += NT) {
+            const int rr = e / half, k = e - rr * half;
+            const float* x = Z + rr * n;
+            float a = 0.f, d = 0.f;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                const float v = x[(2 * k + t) & mask];
+                a += P.h[t] * v;
+                d += P.g[t] * v;
+            }
+            Pj[rr * n + k] = a;
+            Pj[rr * n + half + k] = d;
+        }
+        csync(cl, multi);
+        for (int e = tid; e < nrows * m; e += NT) {
+            const int rr = e / m, x = e - rr * m;
+            const int row = s.row0 + rr;
+            const int k = row < half ? row : row - half;
+            const float* f = row < half ? P.h : P.g;
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                const int src = (2 * k + t) & mask;
+                acc += f[t] * rem[src / R][(src % R) * n + x];
+            }
+            Z[rr * n + x] = acc;
+        }
+        const bool next_multi = (j < s.J) && (half > R);
+        csync(cl, multi && !next_multi);
+    }
+}
+
+// returns the buffer holding W^T Z (own rows); Z, Q0, Q1 read remotely.
+__device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb, float* Q0, float* Q1,
+                          float* const* remZ, float* const* remQ0, float* const* remQ1, cg::cluster_group& cl) {
+    const int tid = threadIdx.x, NT = blockDim.x, n = s.n, R = s.R;
+    csync(cl, (n >> (s.J - 1)) > R);
+    float* out = Q1;
+    for (int j = s.J; j >= 1; --j) {
+        const int m = n >> (j - 1), half = m >> 1, mask = m - 1;
+        float* const* remLL = (j == s.J) ? remZ : (((j + 1) & 1) ? remQ1 : remQ0);
+        float* Qj = (j & 1) ? Q1 : Q0;
+        const int nrows = max(0, min(m - s.row0, R));
+        for (int e = tid; e < nrows * m; e += NT) {
+            const int rr = e / m, x = e - rr * m;
+            const int i = s.row0 + rr;
+            float* const* ra = (x < half) ? remLL : remZ;
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                const int r = (i - t) & mask;
+                if (r & 1) continue;
+                const int k = r >> 1, kd = half + k;
+                acc += P.h[t] * ra[k / R][(k % R) * n + x] + P.g[t] * remZ[kd / R][(kd % R) * n + x];
+            }
+            Pb[rr * n + x] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < nrows * m; e += NT) {
+            const int rr = e / m, x = e - rr * m;
+            const float* pr = Pb + rr * n;
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                const int r = (x - t) & mask;
+                if (r & 1) continue;
+                const int k = r >> 1;
+                acc += P.h[t] * pr[k] + P.g[t] * pr[half + k];
+            }
+            Qj[rr * n + x] = acc;
+        }
+        out = Qj;
+        if (j > 1) csync(cl, (m << 1) > R);
+        else __syncthreads();
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// layer phase
+// ---------------------------------------------------------------------------
+__device__ void alg2_scalars(const FParams& P, const FInst& I, int k, double* sh) {
+    // rho_k and mu_k of the instance, summed in a fixed order; alpha_k, beta_k
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, C = P.C, par = k & 1;
+        const double* lp = P.lpart + (size_t)par * P.n_litems * C * 2;
+        double rho = 0.0, mu = 0.0;
+        // written by other CTAs in this launch: read through L2, never L1
+        for (int e = lane; e < I.nl * C; e += 32) {
+            rho += __ldcg(lp + ((size_t)I.l0 * C + e) * 2 + 0);
+            mu += __ldcg(lp + ((size_t)I.l0 * C + e) * 2 + 1);
+        }
+        for (int e = lane; e < I.nw; e += 32) mu += __ldcg(P.wpart + I.w0 + e);
+        for (int o = 16; o > 0; o >>= 1) {
+            rho += __shfl_down_sync(0xffffffffu, rho, o);
+            mu += __shfl_down_sync(0xffffffffu, mu, o);
+        }
+        if (lane == 0) {
+            double beta = 0.0, denom = mu, aold = 0.0;
+            if (k > 0) {
+                const double* so = I.scal + ((k - 1) & 1) * 2;
+                beta = rho / __ldcg(so);
+                aold = __ldcg(so + 1);
+                denom = mu - rho * beta / aold;
+            }
+            double a = rho / denom;
+            bool bad = !(denom > 0.0) || !isfinite(a) || !isfinite(beta);
+            if (bad) {
+                a = 0.0;
+                beta = 0.0;
+            }
+            sh[0] = a;
+            sh[1] = beta;
+            sh[2] = rho;
+            sh[3] = mu;
+            sh[4] = bad ? 1.0 : 0.0;
+            sh[5] = (a != 0.0) ? a : aold;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm, float* const (*rem)[kMaxC],
+                            cg::cluster_group& cl, double* red, double* sh) {
+    const LItem LI = P.litems[li];
+    const FInst& I = P.inst[LI.inst];
+    const int l = LI.l, C = P.C, rank = (int)cl.block_rank();
+    const int n = I.lay_n[l], J = I.lay_J[l], off = I.lay_off[l];
+    const int R = n / C, row0 = rank * R;
+    const int tid = threadIdx.x, NT = blockDim.x, G = I.G, L = I.L;
+    const int SF = P.stripe_floats;
+    float* Z = sm;
+    float* B1 = sm + SF;
+    float* B2 = sm + 2 * SF;
+    float* B3 = sm + 3 * SF;
+    float* stg = sm + 4 * SF;
+    Stripe s{n, J, R, row0};
+
+    // ---- P^T: gather of the sensor fields into the own rows ----
+    {
+        int so = 0;
+        for (int g = 0; g < G; ++g) {
+            const int2 rg = P.stg[LI.stg + rank * G + g];
+            const int np1 = I.wfs_n[g] + 1;
+            const int cnt = (rg.y - rg.x) * np1;
+            const float* src = I.psi + I.wfs_noff[g] + rg.x * np1;
+            for (int e = tid; e < cnt; e += NT) stg[so + e] = __ldcg(src + e);
+            so += cnt;
+        }
+        __syncthreads();
+        for (int e = tid; e < R * n; e += NT) {
+            const int p = row0 + e / n, q = e % n;
+            float acc = 0.f;
+            int so2 = 0;
+            for (int g = 0; g < G; ++g) {
+                const int2 rg = P.stg[LI.stg + rank * G + g];
+                const int np1 = I.wfs_n[g] + 1;
+                const int base = I.tab_off[g * L + l], gb = I.gat_off[g * L + l];
+                const int i0 = __ldg(I.ilo + gb + p), i1 = __ldg(I.ihi + gb + p);
+                const int j0 = __ldg(I.jlo + gb + q), j1 = __ldg(I.jhi + gb + q);
+                for (int i = i0; i < i1; ++i) {
+                    const float ty = __ldg(I.ty + base + i);
+                    const float wy = (__ldg(I.cy + base + i) == p) ? 1.f - ty : ty;
+                    const float* row = stg + so2 + (i - rg.x) * np1;
+                    float racc = 0.f;
+                    for (int j = j0; j < j1; ++j) {
+                        const float tx = __ldg(I.tx + base + j);
+                        const float wx = (__ldg(I.cx + base + j) == q) ? 1.f - tx : tx;
+                        racc += wx * row[j];
+                    }
+                    acc += wy * racc;
+                }
+                so2 += (rg.y - rg.x) * np1;
+            }
+            Z[e] = acc;
+        }
+    }
+
+    // ---- forward DWT ----
+    fwd_dwt(P, s, Z, B1, B2, rem[1], rem[2], cl);
+
+    // ---- elementwise (Alg. 1 restart / Alg. 2 update) ----
+    double alpha = 0.0, beta = 0.0;
+    if (mode == kLpIter) {
+        alg2_scalars(P, I, k, sh);
+        alpha = sh[0];
+        beta = sh[1];
+        if (tid == 0 && li == I.l0 && rank == 0) {
+            double* sw = I.scal + (k & 1) * 2;
+            sw[0] = sh[2];
+            sw[1] = sh[5];
+            if (sh[4] != 0.0) atomicOr(P.errw, kErrBreakdown);
+            if (I.sc_out) {
+                I.sc_out[kRho] = sh[2];
+                I.sc_out[kMu] = sh[3];
+                I.sc_out[kBeta] = beta;
+                I.sc_out[kAlphaK] = alpha;
+            }
+        }
+    }
+    const bool last = (mode == kLpIter) && (k + 1 >= P.n_iter);
+    const bool make_z = (mode == kLpRhsStart) || (mode == kLpReplStart) || (mode == kLpIter && !last);
+    double rho_p = 0.0, dz_p = 0.0;
+    const long gbase = (long)off + (long)row0 * n;
+    const float fa = (float)alpha, fb = (float)beta;
+    for (int e = tid; e < R * n; e += NT) {
+        const long i = gbase + e;
+        const float jinv = __ldg(I.Jinv + i), ad = __ldg(I.aD + i);
+        float zout = 0.f;
+        if (mode == kLpRhsStart) {
+            const float bv = Z[e];
+            float rv;
+            if (!P.warm) {
+                rv = bv;
+                I.c[i] = 0.f;
+            } else {
+                rv = (bv - I.bprev[i]) + I.r[i];
+            }
+            I.b[i] = bv;
+            I.bprev[i] = bv;
+            I.r[i] = rv;
+            zout = jinv * rv;
+            rho_p += (double)rv * zout;
+            dz_p += (double)ad * zout * zout;
+        } else if (mode == kLpRhsRepl) {
+            I.b[i] = Z[e];
+            zout = I.c[i];
+        } else if (mode == kLpReplStart) {
+            const float cv = I.c[i];
+            const float Mc = Z[e] + ad * cv;
+            const float bv = I.b[i];
+            const float rv = (float)((double)bv - (double)Mc);
+            I.bprev[i] = bv;
+            I.r[i] = rv;
+            zout = jinv * rv;
+            rho_p += (double)rv * zout;
+            dz_p += (double)ad * zout * zout;
+        } else {
+            const float rold = I.r[i];
+            const float z = jinv * rold;
+            const float sv = Z[e] + ad * z;
+            const float pv = (k == 0) ? z : z + fb * I.p[i];
+            const float qv = (k == 0) ? sv : sv + fb * I.q[i];
+            const float cv = I.c[i] + fa * pv;
+            const float rv = rold - fa * qv;
+            I.p[i] = pv;
+            I.q[i] = qv;
+            I.c[i] = cv;
+            I.r[i] = rv;
+            if (!last) {
+                zout = jinv * rv;
+                rho_p += (double)rv * zout;
+                dz_p += (double)ad * zout * zout;
+            } else {
+                zout = cv;
+            }
+        }
+        Z[e] = zout;
+    }
+    if (make_z) {
+        const int par = (mode == kLpIter) ? ((k + 1) & 1) : 0;
+        const double rs = block_reduce(rho_p, red);
+        const double ds = block_reduce(dz_p, red);
+        if (tid == 0) {
+            double* lp = P.lpart + ((size_t)par * P.n_litems * C + (size_t)li * C + rank) * 2;
+            lp[0] = rs;
+            lp[1] = ds;
+        }
+    }
+
+    // ---- inverse DWT -> phi ----
+    const bool need_phi = make_z || mode == kLpRhsRepl || (last && P.out_layers);
+    if (need_phi) {
+        float* res = inv_dwt(P, s, Z, B3, B1, B2, rem[0], rem[1], rem[2], cl);
+        for (int e = tid; e < R * n; e += NT) I.phi[gbase + e] = res[e];
+    }
+    // the stripes may still be read by the other CTAs of the cluster
+    cl.sync();
+}
+
+// ---------------------------------------------------------------------------
+// the frame kernel
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFThreads, 1) k_fused_frame(const __grid_constant__ FParams P) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ float* rem[4][kMaxC];
+    __shared__ double red[32];
+    __shared__ double sh[8];
+    __shared__ int wdesc[kMaxLayersFused * 5];
+    __shared__ int s_abort;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = P.C;
+    const int cid = blockIdx.x / C, ncl = gridDim.x / C;
+    if (threadIdx.x < 4 * C) {
+        const int b = threadIdx.x / C, r = threadIdx.x % C;
+        rem[b][r] = cl.map_shared_rank(sm + b * P.stripe_floats, r);
+    }
+    if (threadIdx.x == 0) s_abort = 0;
+    unsigned target = 0;
+    __syncthreads();
+
+    // Alg. 1 RHS: Gamma^T C^{-1} s per sensor tile
+    for (int it = blockIdx.x; it < P.n_witems; it += gridDim.x) sensor_tile(P, it, sm, kModeRhs, false, wdesc, red);
+    grid_barrier(P, target, &s_abort);
+    // P^T, W -> b; warm restart (or c -> phi for the replacement); z_0 -> phi
+    const int m1 = P.replace ? kLpRhsRepl : kLpRhsStart;
+    for (int li = cid; li < P.n_litems; li += ncl) layer_phase(P, li, m1, 0, sm, rem, cl, red, sh);
+    grid_barrier(P, target, &s_abort);
+    if (P.replace) {
+        // r = b - M c: data term of M on phi_c, then the layer phase
+        for (int it = blockIdx.x; it < P.n_witems; it += gridDim.x)
+            sensor_tile(P, it, sm, kModeData, false, wdesc, red);
+        grid_barrier(P, target, &s_abort);
+        for (int li = cid; li < P.n_litems; li += ncl) layer_phase(P, li, kLpReplStart, 0, sm, rem, cl, red, sh);
+        grid_barrier(P, target, &s_abort);
+    }
+    for (int k = 0; k < P.n_iter; ++k) {
+        for (int it = blockIdx.x; it < P.n_witems; it += gridDim.x)
+            sensor_tile(P, it, sm, kModeData, true, wdesc, red);
+        grid_barrier(P, target, &s_abort);
+        for (int li = cid; li < P.n_litems; li += ncl) layer_phase(P, li, kLpIter, k, sm, rem, cl, red, sh);
+        if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host plan
+// ---------------------------------------------------------------------------
+struct FusedPlan {
+    int C = 1, nclusters = 0, grid = 0, smem = 0;
+    bool cooperative = true;
+    FParams P{};
+    std::vector<void*> allocs;
+    FInst* d_inst = nullptr;
+    std::vector<FInst> inst;
+    float* psi = nullptr;
+};
+
+namespace {
+
+template <typename U>
+bool dalloc(FusedPlan* pl, U*& p, size_t n, std::string& err) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(n, 1) * sizeof(U));
+    if (e != cudaSuccess) {
+        err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return false;
+    }
+    pl->allocs.push_back(v);
+    p = (U*)v;
+    return true;
+}
+
+template <typename U>
+bool dupload(FusedPlan* pl, U*& p, const std::vector<U>& v, std::string& err) {
+    if (!dalloc(pl, p, v.size(), err)) return false;
+    if (v.empty()) return true;
+    cudaError_t e = cudaMemcpy(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMemcpy: ") + cudaGetErrorString(e);
+        return false;
+    }
+    return true;
+}
+
+// tiles of the (ns+1)^2 node grid: ty x tx tiles of near-equal size
+void make_tiles(int inst, int g, int np1, int nty, int ntx, std::vector<WItem>& out) {
+    for (int a = 0; a < nty; ++a)
+        for (int b = 0; b < ntx; ++b) {
+            WItem w;
+            w.inst = inst;
+            w.g = g;
+            w.i0 = (int)((long)np1 * a / nty);
+            w.i1 = (int)((long)np1 * (a + 1) / nty);
+            w.j0 = (int)((long)np1 * b / ntx);
+            w.j1 = (int)((long)np1 * (b + 1) / ntx);
+            if (w.i1 > w.i0 && w.j1 > w.j0) out.push_back(w);
+        }
+}
+
+}  // namespace
+
+FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const FusedBuffers& fb, std::string& err) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        err = "no device";
+        return nullptr;
+    }
+    if (prop.major < 9) {
+        err = "the fused path needs thread-block clusters (sm_90 or newer)";
+        return nullptr;
+    }
+    if (hs.L > kMaxLayersFused || hs.G > kMaxWfsFused) {
+        err = "too many layers or sensors for the fused path";
+        return nullptr;
+    }
+    int nmin = 1 << 30, nmax = 0;
+    for (auto& L : hs.lay) {
+        nmin = std::min(nmin, L.n);
+        nmax = std::max(nmax, L.n);
+    }
+    const int sms = prop.multiProcessorCount;
+    const size_t smem_cap = (size_t)prop.sharedMemPerBlockOptin - 4096;
+
+    FusedPlan* best = nullptr;
+    for (int C : {8, 4, 16, 2, 1}) {
+        if (C > nmin) continue;
+        if ((size_t)nmax * nmax / C * 4 * sizeof(float) > smem_cap) continue;
+        auto* pl = new FusedPlan();
+        pl->C = C;
+        // items
+        std::vector<LItem> litems;
+        std::vector<int2> stg;
+        int stage_max = 0;
+        for (int l = 0; l < hs.L; ++l) {
+            LItem li{0, l, (int)stg.size()};
+            const int n = hs.lay[l].n, R = n / C;
+            for (int rank = 0; rank < C; ++rank) {
+                int tot = 0;
+                for (int g = 0; g < hs.G; ++g) {
+                    const int gb = hs.gat_off[g * hs.L + l];
+                    int lo = 1 << 30, hi = 0;
+                    for (int p = rank * R; p < (rank + 1) * R; ++p) {
+                        if (hs.ihi[gb + p] > hs.ilo[gb + p]) {
+                            lo = std::min(lo, hs.ilo[gb + p]);
+                            hi = std::max(hi, hs.ihi[gb + p]);
+                        }
+                    }
+                    if (lo >= hi) lo = hi = 0;
+                    stg.push_back(make_int2(lo, hi));
+                    tot += (hi - lo) * (hs.wfs[g].n + 1);
+                }
+                stage_max = std::max(stage_max, tot);
+            }
+            litems.push_back(li);
+        }
+        // occupancy first (grid size decides the tiling)
+        const int stripe = nmax * nmax / C;
+        // sensor tiles: aim at about one tile per CTA
+        int grid_guess = (sms / C) * C;
+        std::vector<WItem> witems;
+        int per = std::max(1, grid_guess / std::max(1, hs.G));
+        for (int g = 0; g < hs.G; ++g) {
+            const int np1 = hs.wfs[g].n + 1;
+            int nty = std::max(1, (int)std::floor(std::sqrt((double)per)));
+            while (nty > 1 && per / nty < 1) --nty;
+            int ntx = std::max(1, per / nty);
+            nty = std::min(nty, np1);
+            ntx = std::min(ntx, np1);
+            make_tiles(0, g, np1, nty, ntx, witems);
+        }
+        int tile_nodes = 0, tile_sub = 0, win_max = 0;
+        for (auto& w : witems) {
+            const int ns = hs.wfs[w.g].n;
+            const int a_lo = std::max(w.i0 - 1, 0), a_hi = std::min(w.i1, ns);
+            const int b_lo = std::max(w.j0 - 1, 0), b_hi = std::min(w.j1, ns);
+            tile_nodes = std::max(tile_nodes, (a_hi - a_lo + 1) * (b_hi - b_lo + 1));
+            tile_sub = std::max(tile_sub, (std::min(w.i1, ns) - a_lo) * (std::min(w.j1, ns) - b_lo));
+            int win = 0;
+            for (int l = 0; l < hs.L; ++l) {
+                const int base = hs.tab_off[w.g * hs.L + l];
+                const int nr = hs.cy[base + a_hi] + 1 - hs.cy[base + a_lo] + 1;
+                const int nc = hs.cx[base + b_hi] + 1 - hs.cx[base + b_lo] + 1;
+                win += nr * nc;
+            }
+            win_max = std::max(win_max, win);
+        }
+        tile_nodes = (tile_nodes + 3) & ~3;
+        tile_sub = (tile_sub + 3) & ~3;
+        win_max = (win_max + 3) & ~3;
+        stage_max = (stage_max + 3) & ~3;
+        const size_t layer_floats = 4 * (size_t)stripe + stage_max;
+        const size_t sensor_floats = (size_t)win_max + tile_nodes + 2 * (size_t)tile_sub;
+        const size_t smem = std::max(layer_floats, sensor_floats) * sizeof(float);
+        if (smem > smem_cap) {
+            delete pl;
+            continue;
+        }
+        pl->smem = (int)smem;
+        // the attribute is per function: allow the device maximum once for all plans
+        cudaFuncSetAttribute(k_fused_frame, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+        if (C > 8) cudaFuncSetAttribute(k_fused_frame, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3(C * 1024);
+        cfg.blockDim = dim3(kFThreads);
+        cfg.dynamicSmemBytes = smem;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        cudaError_t oe = cudaOccupancyMaxActiveClusters(&ncl, k_fused_frame, &cfg);
+        if (oe != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            delete pl;
+            continue;
+        }
+        pl->nclusters = std::min(ncl, sms / C > 0 ? sms / C : 1);
+        pl->nclusters = std::max(1, std::min(pl->nclusters, ncl));
+        pl->grid = pl->nclusters * C;
+
+        // device data
+        FInst I{};
+        I.L = hs.L;
+        I.G = hs.G;
+        I.N = (int)hs.N;
+        I.NW = (int)hs.NW;
+        I.lay_n = G.lay_n;
+        I.lay_J = G.lay_J;
+        I.lay_off = G.lay_off;
+        I.wfs_n = G.wfs_n;
+        I.wfs_soff = G.wfs_soff;
+        I.wfs_noff = G.wfs_noff;
+        I.wfs_moff = G.wfs_moff;
+        I.wfs_w = G.wfs_w;
+        I.mask = G.mask;
+        I.tab_off = G.tab_off;
+        I.cx = G.cx;
+        I.cy = G.cy;
+        I.tx = G.tx;
+        I.ty = G.ty;
+        I.gat_off = G.gat_off;
+        I.jlo = G.jlo;
+        I.jhi = G.jhi;
+        I.ilo = G.ilo;
+        I.ihi = G.ihi;
+        I.Jinv = fb.Jinv;
+        I.aD = fb.aD;
+        I.c = fb.c;
+        I.r = fb.r;
+        I.p = fb.p;
+        I.q = fb.q;
+        I.b = fb.b;
+        I.bprev = fb.bprev;
+        I.phi = fb.phi;
+        I.sc_out = fb.sc;
+        I.w0 = 0;
+        I.nw = (int)witems.size();
+        I.l0 = 0;
+        I.nl = (int)litems.size();
+        bool ok = dalloc(pl, I.psi, hs.NW, err) && dalloc(pl, I.scal, 4, err);
+        if (ok) cudaMemset(I.scal, 0, 4 * sizeof(double));
+        I.slopes = fb.slopes;
+        pl->psi = I.psi;
+        pl->inst.push_back(I);
+        WItem* dw = nullptr;
+        LItem* dl = nullptr;
+        int2* ds = nullptr;
+        double *wp = nullptr, *lp = nullptr;
+        unsigned* bar = nullptr;
+        ok = ok && dupload(pl, dw, witems, err) && dupload(pl, dl, litems, err) && dupload(pl, ds, stg, err) &&
+             dalloc(pl, wp, witems.size(), err) && dalloc(pl, lp, 2 * litems.size() * C * 2, err) &&
+             dalloc(pl, bar, 1, err) && dalloc(pl, pl->d_inst, 1, err);
+        if (ok) {
+            cudaError_t ce = cudaMemcpy(pl->d_inst, &I, sizeof(FInst), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) {
+                err = std::string("cudaMemcpy: ") + cudaGetErrorString(ce);
+                ok = false;
+            }
+        }
+        if (!ok) {
+            fused_destroy(pl);
+            return nullptr;
+        }
+        FParams& P = pl->P;
+        P.witems = dw;
+        P.litems = dl;
+        P.stg = ds;
+        P.wpart = wp;
+        P.lpart = lp;
+        P.bar = bar;
+        P.errw = fb.errw;
+        P.n_inst = 1;
+        P.n_witems = (int)witems.size();
+        P.n_litems = (int)litems.size();
+        P.C = C;
+        P.stripe_floats = stripe;
+        P.stage_floats = stage_max;
+        P.win_floats = win_max;
+        P.tile_nodes = tile_nodes;
+        P.tile_subaps = tile_sub;
+        for (int i = 0; i < 6; ++i) {
+            P.h[i] = (float)hs.h[i];
+            P.g[i] = (float)hs.g[i];
+        }
+        P.inst = pl->d_inst;
+        best = pl;
+        break;
+    }
+    if (!best) {
+        if (err.empty()) err = "no cluster shape fits this geometry";
+        return nullptr;
+    }
+    return best;
+}
+
+void fused_destroy(FusedPlan* plan) {
+    if (!plan) return;
+    for (void* a : plan->allocs) cudaFree(a);
+    delete plan;
+}
+
+int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int replace, long long budget,
+                cudaStream_t stream, std::string& err, long long& launches) {
+    (void)slopes;   // the instance reads the solver's slope buffer (fixed at create)
+    cudaError_t e = cudaMemsetAsync(pl->P.bar, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) {
+        err = std::string("fused setup copy: ") + cudaGetErrorString(e);
+        return FEWHA_ERR_CUDA;
+    }
+    FParams P = pl->P;
+    P.n_iter = n_iter;
+    P.warm = warm;
+    P.replace = replace;
+    P.out_layers = 1;
+    P.budget = budget;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[2];
+    cfg.gridDim = dim3(pl->grid);
+    cfg.blockDim = dim3(kFThreads);
+    cfg.dynamicSmemBytes = pl->smem;
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pl->C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pl->cooperative ? 2 : 1;
+    e = cudaLaunchKernelEx(&cfg, k_fused_frame, P);
+    if (e != cudaSuccess && pl->cooperative) {
+        // cooperative + cluster not accepted: the grid is sized from the
+        // occupancy query, so every cluster is resident; barriers stay bounded
+        cudaGetLastError();
+        pl->cooperative = false;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_fused_frame, P);
+    }
+    if (e != cudaSuccess) {
+        err = std::string("fused launch: ") + cudaGetErrorString(e);
+        return FEWHA_ERR_LAUNCH;
+    }
+    launches += 1;
+    return FEWHA_OK;
 }
 
 }  // namespace fewha

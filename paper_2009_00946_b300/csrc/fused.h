@@ -15,7 +15,7 @@ struct DevGeo;
 // State vectors shared with the plain path (device pointers, FP32).
 struct FusedBuffers {
     float *c, *r, *p, *q, *b, *bprev, *phi;
-    const float *Jinv, *aD;
+    const float *Jinv, *aD, *slopes;
     double* sc;
     int* errw;
 };

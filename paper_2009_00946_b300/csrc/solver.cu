@@ -903,9 +903,11 @@ class Solver : public SolverBase {
             int st = fused_solve(fused, (const float*)slopes, n_iter, warm, replace ? 1 : 0, barrier_budget,
                                  stream, err, launches);
             if (st) return st;
+            fused_layers_ready = true;
         } else {
             TRY(rhs_and_restart(warm));
             TRY(pcg_plain(n_iter));
+            fused_layers_ready = false;
         }
         frame_count += 1;
         return FEWHA_OK;
@@ -934,7 +936,7 @@ class Solver : public SolverBase {
     }
 
     int get_layers(void* out, int on_device) override {
-        TRY(inv_dwt(c, phi));
+        TRY(layers_enqueue());
         return copy_out(out, phi, hs.N, on_device);
     }
 
@@ -967,10 +969,12 @@ class Solver : public SolverBase {
         TRY(copy_in(bprev, ib, hs.N, on_device));
         TRY(copy_in(r, ir, hs.N, on_device));
         frame_count = count;
+        fused_layers_ready = false;
         return FEWHA_OK;
     }
 
     int apply_M(const void* x, void* yout, int on_device) override {
+        fused_layers_ready = false;   // phi is scratch of the operator
         TRY(copy_in(z, x, hs.N, on_device));
         TRY(apply_M_dev(z, s));
         return copy_out(yout, s, hs.N, on_device);
@@ -1004,8 +1008,9 @@ class Solver : public SolverBase {
         return check_err();
     }
 
-    int frame(const void* s_host, int n_iter, int warm, double gain, int n_fit, void* lout, void* dout) override {
-        if (!s_host) {
+    int frame(const void* s_in, int n_iter, int warm, double gain, int n_fit, void* lout, void* dout,
+              int on_device) override {
+        if (!s_in) {
             err = "null slopes";
             return FEWHA_ERR_ARG;
         }
@@ -1026,23 +1031,30 @@ class Solver : public SolverBase {
             }
             return at.type == cudaMemoryTypeHost;
         };
-        const void* sin = s_host;
+        const void* sin = s_in;
         void* lo = lout;
         void* dm = dout;
-        bool stage_in = !pinned(s_host), stage_l = lout && !pinned(lout), stage_d = dout && !pinned(dout);
-        if (stage_in) {
-            if (!pinned_in) FEWHA_CUDA(cudaMallocHost(&pinned_in, hs.S * sizeof(T)));
-            std::memcpy(pinned_in, s_host, hs.S * sizeof(T));
-            sin = pinned_in;
+        bool stage_in = false, stage_l = false, stage_d = false;
+        if (!on_device) {
+            stage_in = !pinned(s_in);
+            stage_l = lout && !pinned(lout);
+            stage_d = dout && !pinned(dout);
+            if (stage_in) {
+                if (!pinned_in) FEWHA_CUDA(cudaMallocHost(&pinned_in, hs.S * sizeof(T)));
+                std::memcpy(pinned_in, s_in, hs.S * sizeof(T));
+                sin = pinned_in;
+            }
+            if (stage_l) {
+                if (!pinned_out) FEWHA_CUDA(cudaMallocHost(&pinned_out, hs.N * sizeof(T)));
+                lo = pinned_out;
+            }
+            if (stage_d) {
+                if (!pinned_dm) FEWHA_CUDA(cudaMallocHost(&pinned_dm, std::max<long>(hs.NA, 1) * sizeof(T)));
+                dm = pinned_dm;
+            }
         }
-        if (stage_l) {
-            if (!pinned_out) FEWHA_CUDA(cudaMallocHost(&pinned_out, hs.N * sizeof(T)));
-            lo = pinned_out;
-        }
-        if (stage_d) {
-            if (!pinned_dm) FEWHA_CUDA(cudaMallocHost(&pinned_dm, std::max<long>(hs.NA, 1) * sizeof(T)));
-            dm = pinned_dm;
-        }
+        const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
         int slot = replace ? 1 : 0;
         Key key;
@@ -1053,7 +1065,7 @@ class Solver : public SolverBase {
         key.sin = sin;
         key.lout = lo;
         key.dout = dm;
-        key.path = path;
+        key.path = path * 2 + (on_device ? 1 : 0);
         key.k_rr = k_rr;
         if (!gexec[slot] || !(gkey[slot] == key)) {
             if (gexec[slot]) {
@@ -1070,7 +1082,7 @@ class Solver : public SolverBase {
             int st = FEWHA_OK;
             long long l0 = launches;
             do {
-                cudaError_t e = cudaMemcpyAsync(slopes, sin, hs.S * sizeof(T), cudaMemcpyHostToDevice, stream);
+                cudaError_t e = cudaMemcpyAsync(slopes, sin, hs.S * sizeof(T), kin, stream);
                 if (e != cudaSuccess) {
                     err = cudaGetErrorString(e);
                     st = FEWHA_ERR_CUDA;
@@ -1078,21 +1090,21 @@ class Solver : public SolverBase {
                 }
                 if ((st = solve_enqueue(n_iter, warm))) break;
                 if (dm && (st = fit_dev(gain, n_fit))) break;
-                if (lo && (st = inv_dwt(c, phi))) break;
-                if (lo && cudaMemcpyAsync(lo, phi, hs.N * sizeof(T), cudaMemcpyDeviceToHost, stream) != cudaSuccess) {
+                if (lo && (st = layers_enqueue())) break;
+                if (lo && cudaMemcpyAsync(lo, phi, hs.N * sizeof(T), kout, stream) != cudaSuccess) {
                     st = FEWHA_ERR_CUDA;
                     err = "copy of layers";
                     break;
                 }
-                if (dm && cudaMemcpyAsync(dm, acur, hs.NA * sizeof(T), cudaMemcpyDeviceToHost, stream) != cudaSuccess) {
+                if (dm && cudaMemcpyAsync(dm, acur, hs.NA * sizeof(T), kout, stream) != cudaSuccess) {
                     st = FEWHA_ERR_CUDA;
                     err = "copy of mirror commands";
                     break;
                 }
             } while (0);
             cudaError_t ec = cudaStreamEndCapture(stream, &graph);
-            frame_count = fc;              // capture only recorded the work
-            graph_launches = launches - l0;
+            frame_count = fc;              // the capture only recorded the work
+            long long gl = launches - l0;
             launches = l0;
             if (st) return st;
             if (ec != cudaSuccess) {
@@ -1107,21 +1119,26 @@ class Solver : public SolverBase {
                 return FEWHA_ERR_CUDA;
             }
             gkey[slot] = key;
-            graph_launch_count[slot] = graph_launches;
-        } else if (stage_in) {
-            // staging buffer already holds this frame (copied above)
+            graph_launch_count[slot] = gl;
         }
         FEWHA_CUDA(cudaGraphLaunch(gexec[slot], stream));
         launches += graph_launch_count[slot];
         frame_count += 1;
         have_frame = true;
+        if (on_device) return FEWHA_OK;
         FEWHA_CUDA(cudaStreamSynchronize(stream));
         if (stage_l) std::memcpy(lout, pinned_out, hs.N * sizeof(T));
         if (stage_d) std::memcpy(dout, pinned_dm, hs.NA * sizeof(T));
         return check_err();
     }
 
-    long long graph_launches = 0;
+    // phi = W^T c for output (fused path: already produced by the frame kernel)
+    int layers_enqueue() {
+        if (use_fused() && fused_layers_ready) return FEWHA_OK;
+        return inv_dwt(c, phi);
+    }
+    bool fused_layers_ready = false;
+
     long long graph_launch_count[2] = {0, 0};
 };
 
@@ -1159,6 +1176,7 @@ SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& e
         fb.phi = s->phi;
         fb.Jinv = s->Jinv;
         fb.aD = s->aD;
+        fb.slopes = s->slopes;
         fb.sc = s->sc;
         fb.errw = s->errw;
         std::string ferr;

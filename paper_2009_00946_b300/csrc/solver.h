@@ -88,8 +88,8 @@ class SolverBase {
     virtual int get_state(void* c, void* b, void* r, int on_device) = 0;
     virtual int set_state(const void* c, const void* b, const void* r, int on_device, long count) = 0;
     virtual int apply_M(const void* x, void* y, int on_device) = 0;
-    virtual int frame(const void* s_host, int n_iter, int warm, double gain, int n_fit, void* layers_out,
-                      void* dm_out) = 0;
+    virtual int frame(const void* s, int n_iter, int warm, double gain, int n_fit, void* layers_out,
+                      void* dm_out, int on_device) = 0;
     virtual int sync() = 0;
 
     HostSetup hs;

@@ -85,7 +85,7 @@ def lib():
         "fewha_get_state": (ci, [vp, vp, vp, vp, ci]),
         "fewha_set_state": (ci, [vp, vp, vp, vp, ci, cl]),
         "fewha_apply_M": (ci, [vp, vp, vp, ci]),
-        "fewha_frame": (ci, [vp, vp, ci, ci, cd, ci, vp, vp]),
+        "fewha_frame": (ci, [vp, vp, ci, ci, cd, ci, vp, vp, ci]),
         "fewha_sync": (ci, [vp]),
         "fewha_set_barrier_budget": (ci, [vp, cll]),
         "fewha_launch_count": (cll, [vp]),
@@ -272,15 +272,23 @@ class Solver:
         self._check(lib().fewha_apply_M(self.h, px, py, dx))
         return out
 
-    def frame(self, slopes_host, n_iter: int, warm: bool = True, gain: float = 1.0, n_fit: int = 8,
+    def frame(self, slopes, n_iter: int, warm: bool = True, gain: float = 1.0, n_fit: int = 8,
               layers_out=None, dm_out=None):
-        """One whole frame through the captured CUDA graph (host in, host out)."""
-        ps, ds = _ptr(slopes_host, self._dt(), self.S, None)
-        if ds:
-            raise ValueError("fewha_frame takes host slopes")
-        pl = _ptr(layers_out, self._dt(), self.N, None)[0] if layers_out is not None else None
-        pd = _ptr(dm_out, self._dt(), self.NA, None)[0] if dm_out is not None else None
-        self._check(lib().fewha_frame(self.h, ps, int(n_iter), 1 if warm else 0, float(gain), int(n_fit), pl, pd))
+        """One whole frame through the captured CUDA graph.  All arrays host
+        (numpy; the call synchronises) or all device (torch CUDA tensors; the
+        call only enqueues on the solver's stream)."""
+        ps, ds = _ptr(slopes, self._dt(), self.S, None)
+        pl = pd = None
+        if layers_out is not None:
+            pl, dl = _ptr(layers_out, self._dt(), self.N, None)
+            if dl != ds:
+                raise ValueError("slopes and layers_out must both be host or both be device")
+        if dm_out is not None:
+            pd, dd = _ptr(dm_out, self._dt(), self.NA, None)
+            if dd != ds:
+                raise ValueError("slopes and dm_out must both be host or both be device")
+        self._check(lib().fewha_frame(self.h, ps, int(n_iter), 1 if warm else 0, float(gain), int(n_fit), pl, pd,
+                                      ds))
 
     def launch_count(self) -> int:
         return int(lib().fewha_launch_count(self.h))

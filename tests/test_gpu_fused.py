@@ -1,0 +1,152 @@
+"""Parity of the fused persistent FP32 frame kernel with the FP64 oracle (<= 1e-4
+relative L2 on layers), through the C ABI, plus determinism, ragged sizes, the
+bounded-barrier timeout status and the graph-captured frame."""
+
+import numpy as np
+import pytest
+
+from oracle import fewha_oracle as fo
+from paper_2009_00946_b300 import configs, synth
+
+from _cases import ragged_cfg
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def fw():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2009_00946_b300 import fewha
+    return fewha
+
+
+def _fused(fw, cfg, **kw):
+    S = fw.Solver(cfg, precision=fw.FP32, **kw)
+    S.set_path(fw.PATH_FUSED)        # raises if the fused path is unavailable
+    return S
+
+
+@pytest.fixture(scope="module")
+def elt_frames():
+    cfg = configs.c2_elt()
+    S_in, _ = synth.frames(cfg, 13)
+    R = fo.Reconstructor(cfg)
+    ref = []
+    for k in range(13):
+        R.frame(S_in[k], 4, warm=True, k_rr=10)
+        ref.append((R.layers(), R.state.c.copy()))
+    return cfg, S_in.astype(np.float32), ref
+
+
+def test_fused_elt_frames_match_oracle(fw, elt_frames):
+    """ELT bulk, 4 warm iterations per frame, 13 frames across the residual
+    replacement of frame 10: layers and coefficients <= 1e-4."""
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as S:
+        for k in range(13):
+            S.set_frame(S_in[k])
+            S.solve(4, warm=True)
+            S.sync()
+            assert rel(S.layers(), ref[k][0]) < 1e-4, k
+            assert rel(S.vector(fw.VEC_C), ref[k][1]) < 1e-4, k
+
+
+def test_fused_matches_plain_fp32(fw, elt_frames):
+    cfg, S_in, _ = elt_frames
+    with _fused(fw, cfg, k_rr=10) as A, fw.Solver(cfg, precision=fw.FP32, path=fw.PATH_PLAIN, k_rr=10) as B:
+        for k in range(12):
+            for S in (A, B):
+                S.set_frame(S_in[k])
+                S.solve(4, warm=True)
+                S.sync()
+            assert rel(A.vector(fw.VEC_C), B.vector(fw.VEC_C).astype(np.float64)) < 2e-5, k
+            assert rel(A.vector(fw.VEC_R), B.vector(fw.VEC_R).astype(np.float64)) < 1e-3, k
+
+
+def test_fused_bit_deterministic(fw, elt_frames):
+    cfg, S_in, _ = elt_frames
+    outs = []
+    for _ in range(2):
+        with _fused(fw, cfg) as S:
+            for k in range(3):
+                S.set_frame(S_in[k])
+                S.solve(4, warm=True)
+            S.sync()
+            outs.append((S.vector(fw.VEC_C), S.layers()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("name", ["c1_plain", "c5_autograd", "ragged"])
+def test_fused_small_and_ragged_geometries(fw, name):
+    cfg = ragged_cfg() if name == "ragged" else configs.ALL[name]()
+    S_in, _ = synth.frames(cfg, 3)
+    R = fo.Reconstructor(cfg)
+    with _fused(fw, cfg, k_rr=2) as S:
+        for k in range(3):
+            R.frame(S_in[k], 6, warm=(k > 0), k_rr=2)
+            S.set_frame(S_in[k].astype(np.float32))
+            S.solve(6, warm=(k > 0))
+            S.sync()
+            assert rel(S.layers(), R.layers()) < 1e-4, (name, k)
+
+
+def test_fused_timeout_reported_and_recoverable(fw, elt_frames):
+    """Barrier budget 0: every grid barrier expires at once; the kernel runs to
+    its end without waiting and the TIMEOUT status is returned.  The context
+    stays usable: after restoring the state the next frame is correct."""
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg) as S:
+        S.set_frame(S_in[0])
+        S.solve(4, warm=True)
+        S.sync()
+        state = S.get_state()
+        S.set_barrier_budget(0)
+        S.set_frame(S_in[1])
+        S.solve(4, warm=True)
+        with pytest.raises(fw.FewhaError) as ei:
+            S.sync()
+        assert ei.value.name == "TIMEOUT"
+        S.set_barrier_budget(1 << 31)
+        S.set_state(*state, frame_count=1)
+        S.set_frame(S_in[1])
+        S.solve(4, warm=True)
+        S.sync()
+        assert rel(S.layers(), ref[1][0]) < 1e-4
+
+
+def test_fused_nan_slopes_reported(fw):
+    cfg = configs.c2_elt()
+    g = fo.Geometry(cfg)
+    s = synth.random_slopes(cfg, 4).astype(np.float32)
+    active = int(np.flatnonzero(g.mask[2].ravel() == 1)[5])
+    s[g.soff[2] + active] = np.inf
+    with _fused(fw, cfg) as S:
+        S.set_frame(s)
+        S.solve(2, warm=False)
+        with pytest.raises(fw.FewhaError) as ei:
+            S.sync()
+        assert ei.value.name == "INPUT"
+
+
+def test_fused_graph_frame_host_and_device(fw, elt_frames):
+    import torch
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as A, _fused(fw, cfg, k_rr=10) as B:
+        lb = np.empty(A.N, np.float32)
+        dev_s = torch.empty(A.S, dtype=torch.float32, device="cuda")
+        dev_l = torch.empty(A.N, dtype=torch.float32, device="cuda")
+        for k in range(12):
+            pin = torch.from_numpy(S_in[k]).pin_memory()
+            A.frame(pin.numpy(), 4, warm=True, layers_out=lb)
+            with torch.cuda.stream(B.stream):
+                dev_s.copy_(torch.from_numpy(S_in[k]).to("cuda", non_blocking=False))
+            B.stream.synchronize()
+            B.frame(dev_s, 4, warm=True, layers_out=dev_l)
+            B.sync()
+            assert rel(lb, ref[k][0]) < 1e-4, k
+            assert np.array_equal(lb, dev_l.cpu().numpy()), k

@@ -8,6 +8,8 @@ import pytest
 from oracle import fewha_oracle as fo
 from paper_2009_00946_b300 import configs, synth
 
+from _cases import ragged_cfg
+
 pytestmark = pytest.mark.gpu
 
 
@@ -21,18 +23,6 @@ def fw():
     assert torch.cuda.is_available(), "GPU tests need CUDA"
     from paper_2009_00946_b300 import fewha
     return fewha
-
-
-def ragged_cfg():
-    """Uneven instance: odd subaperture counts, NGS + LGS, obstruction, layers
-    of different sizes and level counts (several tiles and ragged edges)."""
-    cfg = configs.tiny(n_sub=7, n=16, levels=(3, 1), G=3, lgs=True, obstruction=0.25, D=6.0)
-    cfg["wfs"][1]["n_sub"] = 9
-    cfg["wfs"][2]["gs_height"] = 0.0
-    cfg["layers"][1]["n"] = 64
-    cfg["layers"][1]["levels"] = 4
-    cfg["layers"].append({"height": 9000.0, "cn2": 0.2, "n": 32, "levels": 2})
-    return cfg
 
 
 FP64_CFGS = {"c1": configs.c1_plain, "ragged": ragged_cfg,
