@@ -202,6 +202,51 @@ def time_solve(S, torch, n_iter, K, flush):
     return float(np.mean([a.elapsed_time(b) * 1e3 for a, b in ev]))
 
 
+def phase_breakdown(S, pool_dev, n_iter=N_ITER):
+    """One traced non-replacement frame: critical-path time of each phase (the
+    latest CTA's work between two barriers) and the barrier latencies (us)."""
+    S.set_trace(True)
+    S.set_residual_replacement(0)
+    S.set_frame(pool_dev[0])
+    S.solve(n_iter, warm=True)
+    tr = S.trace().astype(np.int64)
+    S.set_trace(False)
+    S.set_residual_replacement(K_RR)
+    work, bars = [], []
+    for b in range(1, tr.shape[0]):
+        work.append(float((tr[b, :, 0] - tr[b - 1, :, 1]).max()) / 1e3)
+        if b < tr.shape[0] - 1:
+            bars.append(float(tr[b, :, 1].max() - tr[b, :, 0].max()) / 1e3)
+    sensor, layer = work[2::2], work[3::2]
+    return {"rhs_sensor_us": work[0], "rhs_layer_us": work[1],
+            "sensor_phase_us": float(np.mean(sensor)) if sensor else None,
+            "layer_phase_us": float(np.mean(layer)) if layer else None,
+            "grid_barrier_us": float(np.mean(bars)) if bars else None,
+            "kernel_us": float(tr[-1, :, 0].max() - tr[0, :, 1].min()) / 1e3,
+            "n_barriers": len(bars)}
+
+
+def profile_mode(args):
+    """Stream launches only (no CUDA graph), for ncu: W + K frames of
+    set_frame (device) + solve + layers on the fused path."""
+    import torch
+    from paper_2009_00946_b300 import fewha
+    cfg = workload_config()
+    pool = slope_pool(cfg, args.pool)
+    dev = torch.device("cuda", 0)
+    pool_dev = torch.from_numpy(pool).to(dev)
+    S = fewha.Solver(cfg, precision=fewha.FP32, path=fewha.PATH_FUSED, k_rr=K_RR)
+    out = torch.empty(S.N, dtype=torch.float32, device=dev)
+    for k in range(args.warmup + args.steps):
+        S.set_frame(pool_dev[k % len(pool)])
+        S.solve(N_ITER, warm=True)
+        S.layers(out)
+    S.sync()
+    print(json.dumps({"profile_mode": True, "frames": args.warmup + args.steps, "plan": S.describe(),
+                      "phases": phase_breakdown(S, pool_dev)}), flush=True)
+    S.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -210,11 +255,15 @@ def main():
     ap.add_argument("--impl", default="fewha", choices=["fewha", "reference"])
     ap.add_argument("--pool", type=int, default=64, help="distinct synthetic frames, cycled")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="stream launches only (for ncu), no timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile:
+        profile_mode(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -267,6 +316,8 @@ def main():
     t4 = time_solve(S, torch, N_ITER, 100, flush)
     t100 = time_solve(S, torch, 100, 20, flush)
     per_iter = (t100 - t4) / 96.0
+    phases = phase_breakdown(S, pool_dev)
+    plan = S.describe()
     hbm, peak_kind = measured_peaks()
     alg = algorithmic_bytes_per_frame(cfg, N_ITER)
     achieved = alg / (t4 * 1e-6) / 1e9
@@ -333,6 +384,8 @@ def main():
                      "kernel": "k_fused_frame", "duration_us": t4, "algorithmic_bytes": alg,
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
         "clocks": clocks,
+        "phases": phases,
+        "plan": plan,
     }
     if cpu:
         line["cpu_baseline"] = cpu

@@ -178,6 +178,21 @@ int fewha_set_barrier_budget(fewha_handle* h, long long cycles);
 /* Kernel launches enqueued by this handle since creation (all paths). */
 long long fewha_launch_count(const fewha_handle* h);
 
+/* One-line summary of the execution plan (precision, path, sizes; for the
+ * fused path the cluster shape, grid, shared memory and work items), written
+ * into buf (len bytes, NUL-terminated, truncated if short). */
+int fewha_describe(fewha_handle* h, char* buf, int len);
+
+/* Phase trace of the fused kernel (a profiling aid, off by default).  on = 1:
+ * every following fused launch records, per CTA, the globaltimer (ns) when it
+ * arrives at and leaves each grid barrier (slot 0 = kernel start, the last
+ * slot = kernel end).  fewha_get_trace synchronises and copies the last
+ * launch's record, laid out [slot][cta][arrive, depart] (at most max_entries
+ * values; out may be NULL to query the sizes), and returns the slot and CTA
+ * counts.  Errors: STATE on the plain path. */
+int fewha_set_trace(fewha_handle* h, int on);
+int fewha_get_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* slots, int* grid);
+
 #ifdef __cplusplus
 }
 #endif

@@ -163,6 +163,22 @@ int fewha_set_barrier_budget(fewha_handle* h, long long cycles) {
     return FEWHA_OK;
 }
 
+int fewha_describe(fewha_handle* h, char* buf, int len) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->describe(buf, len));
+}
+
+int fewha_set_trace(fewha_handle* h, int on) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->set_trace(on));
+}
+
+int fewha_get_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* slots, int* grid) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (!slots || !grid || max_entries < 0) return fail(h, FEWHA_ERR_ARG, "bad trace arguments");
+    return done(h, h->s->get_trace(out, max_entries, slots, grid));
+}
+
 long long fewha_launch_count(const fewha_handle* h) {
     if (!h) return -1;
     return h->s->launches;

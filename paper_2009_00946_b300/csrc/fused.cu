@@ -71,6 +71,8 @@ struct FParams {
     double* lpart;         // [2][n_litems * C][2]
     unsigned* bar;
     int* errw;
+    unsigned long long* trace;   // optional: [slot][cta][arrive, depart] globaltimer (ns)
+    int trace_slots;
     long long budget;
     int n_inst, n_witems, n_litems;
     int n_iter, warm, replace, out_layers;
@@ -88,9 +90,24 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     return v;
 }
 
-__device__ void grid_barrier(const FParams& P, unsigned& target, int* s_abort) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void trace_mark(const FParams& P, int slot, int which) {
+    if (P.trace && slot < P.trace_slots)
+        P.trace[((size_t)slot * gridDim.x + blockIdx.x) * 2 + which] = global_ns();
+}
+
+// Arrive: one fenced atomic per CTA; wait: thread 0 polls with acquire loads
+// and a short back-off (fewer polls on the counter's line leave the L2 slice
+// free for the arrivals), bounded by the clock budget.
+__device__ void grid_barrier(const FParams& P, unsigned& target, int* s_abort, int& slot) {
     __syncthreads();
     if (threadIdx.x == 0) {
+        trace_mark(P, slot, 0);
         target += gridDim.x;
         __threadfence();
         atomicAdd(P.bar, 1u);
@@ -102,10 +119,13 @@ __device__ void grid_barrier(const FParams& P, unsigned& target, int* s_abort) {
                     *s_abort = 1;
                     break;
                 }
+                __nanosleep(32);
             }
         }
         __threadfence();
+        trace_mark(P, slot, 1);
     }
+    ++slot;
     __syncthreads();
 }
 
@@ -555,7 +575,18 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_frame(const __grid_const
     __shared__ int s_abort;
     cg::cluster_group cl = cg::this_cluster();
     const int C = P.C;
+    // every shared-memory address below assumes the planned cluster shape
+    if ((int)cl.num_blocks() != C || (gridDim.x % C) != 0) {
+        if (threadIdx.x == 0) atomicOr(P.errw, kErrLaunch);
+        return;
+    }
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
+    int slot = 0;
+    if (threadIdx.x == 0) {
+        trace_mark(P, 0, 0);
+        trace_mark(P, 0, 1);
+    }
+    ++slot;
     if (threadIdx.x < 4 * C) {
         const int b = threadIdx.x / C, r = threadIdx.x % C;
         rem[b][r] = cl.map_shared_rank(sm + b * P.stripe_floats, r);
@@ -566,25 +597,30 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_frame(const __grid_const
 
     // Alg. 1 RHS: Gamma^T C^{-1} s per sensor tile
     for (int it = blockIdx.x; it < P.n_witems; it += gridDim.x) sensor_tile(P, it, sm, kModeRhs, false, wdesc, red);
-    grid_barrier(P, target, &s_abort);
+    grid_barrier(P, target, &s_abort, slot);
     // P^T, W -> b; warm restart (or c -> phi for the replacement); z_0 -> phi
     const int m1 = P.replace ? kLpRhsRepl : kLpRhsStart;
     for (int li = cid; li < P.n_litems; li += ncl) layer_phase(P, li, m1, 0, sm, rem, cl, red, sh);
-    grid_barrier(P, target, &s_abort);
+    grid_barrier(P, target, &s_abort, slot);
     if (P.replace) {
         // r = b - M c: data term of M on phi_c, then the layer phase
         for (int it = blockIdx.x; it < P.n_witems; it += gridDim.x)
             sensor_tile(P, it, sm, kModeData, false, wdesc, red);
-        grid_barrier(P, target, &s_abort);
+        grid_barrier(P, target, &s_abort, slot);
         for (int li = cid; li < P.n_litems; li += ncl) layer_phase(P, li, kLpReplStart, 0, sm, rem, cl, red, sh);
-        grid_barrier(P, target, &s_abort);
+        grid_barrier(P, target, &s_abort, slot);
     }
     for (int k = 0; k < P.n_iter; ++k) {
         for (int it = blockIdx.x; it < P.n_witems; it += gridDim.x)
             sensor_tile(P, it, sm, kModeData, true, wdesc, red);
-        grid_barrier(P, target, &s_abort);
+        grid_barrier(P, target, &s_abort, slot);
         for (int li = cid; li < P.n_litems; li += ncl) layer_phase(P, li, kLpIter, k, sm, rem, cl, red, sh);
-        if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort);
+        if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort, slot);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        trace_mark(P, slot, 0);
+        trace_mark(P, slot, 1);
     }
 }
 
@@ -594,6 +630,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_frame(const __grid_const
 struct FusedPlan {
     int C = 1, nclusters = 0, grid = 0, smem = 0;
     bool cooperative = true;
+    bool trace_on = false;
+    unsigned long long* trace = nullptr;
+    int trace_slots = 0;
+    int last_slots = 0;
     FParams P{};
     std::vector<void*> allocs;
     FInst* d_inst = nullptr;
@@ -864,8 +904,27 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
     return best;
 }
 
+int fused_describe(const FusedPlan* pl, char* buf, int len) {
+    return snprintf(buf, len,
+                    "fused: %d clusters x %d CTAs (grid %d, %d threads), smem %d B, %d sensor tiles, %d layer items, "
+                    "cooperative %d",
+                    pl->nclusters, pl->C, pl->grid, kFThreads, pl->smem, pl->P.n_witems, pl->P.n_litems,
+                    pl->cooperative ? 1 : 0);
+}
+
+void fused_set_trace(FusedPlan* pl, bool on) { pl->trace_on = on; }
+
+int fused_get_trace(FusedPlan* pl, unsigned long long* out, int max_entries, int* slots, int* grid) {
+    *slots = pl->trace ? pl->last_slots : 0;
+    *grid = pl->grid;
+    if (!pl->trace || !out) return 0;
+    size_t n = std::min((size_t)max_entries, (size_t)pl->last_slots * pl->grid * 2);
+    return cudaMemcpy(out, pl->trace, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : 1;
+}
+
 void fused_destroy(FusedPlan* plan) {
     if (!plan) return;
+    if (plan->trace) cudaFree(plan->trace);
     for (void* a : plan->allocs) cudaFree(a);
     delete plan;
 }
@@ -879,6 +938,23 @@ int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int re
         return FEWHA_ERR_CUDA;
     }
     FParams P = pl->P;
+    P.trace = nullptr;
+    P.trace_slots = 0;
+    if (pl->trace_on) {
+        // start, RHS barrier, first layer-phase barrier, 2 n_iter - 1 iteration
+        // barriers (+2 for the replacement), end
+        const int need = 3 + 2 * n_iter + (replace ? 2 : 0);
+        if (need > pl->trace_slots) {
+            if (pl->trace) cudaFree(pl->trace);
+            pl->trace = nullptr;
+            pl->trace_slots = 0;
+            if (cudaMalloc(&pl->trace, (size_t)need * pl->grid * 2 * sizeof(unsigned long long)) == cudaSuccess)
+                pl->trace_slots = need;
+        }
+        P.trace = pl->trace;
+        P.trace_slots = pl->trace_slots;
+        pl->last_slots = need;
+    }
     P.n_iter = n_iter;
     P.warm = warm;
     P.replace = replace;

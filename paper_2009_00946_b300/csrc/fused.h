@@ -32,4 +32,11 @@ void fused_destroy(FusedPlan* plan);
 int fused_solve(FusedPlan* plan, const float* slopes, int n_iter, int warm, int replace, long long budget,
                 cudaStream_t stream, std::string& err, long long& launches);
 
+// Plan summary (cluster shape, grid, shared memory, work items).
+int fused_describe(const FusedPlan* plan, char* buf, int len);
+// Per-phase globaltimer trace of the following launches (arrival / departure
+// of every CTA at every grid barrier).
+void fused_set_trace(FusedPlan* plan, bool on);
+int fused_get_trace(FusedPlan* plan, unsigned long long* out, int max_entries, int* slots, int* grid);
+
 }  // namespace fewha

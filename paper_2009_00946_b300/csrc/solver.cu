@@ -987,6 +987,10 @@ class Solver : public SolverBase {
         if (e) {
             FEWHA_CUDA(cudaMemsetAsync(errw, 0, sizeof(int), stream));
             FEWHA_CUDA(cudaStreamSynchronize(stream));
+            if (e & kErrLaunch) {
+                err = "the fused kernel was launched with a grid or cluster shape it was not planned for";
+                return FEWHA_ERR_LAUNCH;
+            }
             if (e & kErrTimeout) {
                 err = "a grid barrier of the fused kernel expired";
                 return FEWHA_ERR_TIMEOUT;
@@ -1006,6 +1010,39 @@ class Solver : public SolverBase {
     int sync() override {
         FEWHA_CUDA(cudaStreamSynchronize(stream));
         return check_err();
+    }
+
+    int describe(char* buf, int len) override {
+        if (!buf || len <= 0) {
+            err = "null buffer";
+            return FEWHA_ERR_ARG;
+        }
+        int k = snprintf(buf, len, "precision %s, path %s, N %ld, S %ld, A %ld; ", sizeof(T) == 8 ? "fp64" : "fp32",
+                         use_fused() ? "fused" : "plain", hs.N, hs.S, hs.NA);
+        if (fused && k >= 0 && k < len) fused_describe(fused, buf + k, len - k);
+        return FEWHA_OK;
+    }
+
+    int set_trace(int on) override {
+        if (!fused) {
+            err = "tracing is available on the fused path only";
+            return FEWHA_ERR_STATE;
+        }
+        fused_set_trace(fused, on != 0);
+        return FEWHA_OK;
+    }
+
+    int get_trace(unsigned long long* out, int max_entries, int* slots, int* grid) override {
+        if (!fused) {
+            err = "tracing is available on the fused path only";
+            return FEWHA_ERR_STATE;
+        }
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        if (fused_get_trace(fused, out, max_entries, slots, grid)) {
+            err = "trace copy failed";
+            return FEWHA_ERR_CUDA;
+        }
+        return FEWHA_OK;
     }
 
     int frame(const void* s_in, int n_iter, int warm, double gain, int n_fit, void* lout, void* dout,

@@ -17,6 +17,7 @@ constexpr int kRedThreads = 256;
 constexpr int kErrInput = 1;
 constexpr int kErrBreakdown = 2;
 constexpr int kErrTimeout = 4;
+constexpr int kErrLaunch = 8;      // the fused kernel found a launch shape it was not planned for
 
 // Device geometry tables (pointers into one allocation), passed by value.
 template <typename T>
@@ -91,6 +92,9 @@ class SolverBase {
     virtual int frame(const void* s, int n_iter, int warm, double gain, int n_fit, void* layers_out,
                       void* dm_out, int on_device) = 0;
     virtual int sync() = 0;
+    virtual int describe(char* buf, int len) = 0;
+    virtual int set_trace(int on) = 0;
+    virtual int get_trace(unsigned long long* out, int max_entries, int* slots, int* grid) = 0;
 
     HostSetup hs;
     cudaStream_t stream = 0;

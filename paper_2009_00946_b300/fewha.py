@@ -89,6 +89,10 @@ def lib():
         "fewha_sync": (ci, [vp]),
         "fewha_set_barrier_budget": (ci, [vp, cll]),
         "fewha_launch_count": (cll, [vp]),
+        "fewha_describe": (ci, [vp, ctypes.c_char_p, ci]),
+        "fewha_set_trace": (ci, [vp, ci]),
+        "fewha_get_trace": (ci, [vp, ctypes.POINTER(ctypes.c_ulonglong), ci, ctypes.POINTER(ci),
+                                 ctypes.POINTER(ci)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -292,3 +296,21 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(lib().fewha_launch_count(self.h))
+
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        self._check(lib().fewha_describe(self.h, buf, 512))
+        return buf.value.decode()
+
+    def set_trace(self, on: bool = True):
+        self._check(lib().fewha_set_trace(self.h, 1 if on else 0))
+
+    def trace(self):
+        """Last fused launch: array [slot, cta, (arrive, depart)] of globaltimer ns."""
+        slots, grid = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().fewha_get_trace(self.h, None, 0, ctypes.byref(slots), ctypes.byref(grid)))
+        n = slots.value * grid.value * 2
+        out = np.zeros(max(n, 1), np.uint64)
+        self._check(lib().fewha_get_trace(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), n,
+                                          ctypes.byref(slots), ctypes.byref(grid)))
+        return out[:n].reshape(slots.value, grid.value, 2)
