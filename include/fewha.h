@@ -193,6 +193,26 @@ int fewha_describe(fewha_handle* h, char* buf, int len);
 int fewha_set_trace(fewha_handle* h, int on);
 int fewha_get_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* slots, int* grid);
 
+/* The paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory (a control loop that reserves all memory at start-up
+ * and allows no allocation while it runs, code inside a framework that owns
+ * the device memory).  It computes layers = W^{-1} coeffs, the same layer
+ * reconstruction as fewha_get_layers, for a stack of n_layers FP32 layers
+ * without a handle and without allocating anything.  coeffs / layers: device
+ * pointers, sum n_side[l]^2 floats each, layer-major, Mallat layout in, nodal
+ * values out; they must not overlap.  n_side[l]: power of two in 8..1024;
+ * levels[l]: 1 <= J, n_side >> J >= 2.  Work is enqueued on `stream`
+ * (0 = legacy default stream); the call does not wait for it.
+ * The intermediate of each level lives in one fixed 4 MiB array that every
+ * GPU loading the library reserves until exit, so the total coefficient count
+ * may not exceed 2^20 (ARG error with a message otherwise).  The first call on
+ * a device looks up that array's address; make it before any stream capture.
+ * Every call reuses the same array: calls that overlap on the GPU race.
+ * errbuf (errlen bytes, may be NULL) receives a message on failure.
+ * Errors: ARG (null, aliasing or out-of-range sizes), CUDA. */
+int fewha_layers_noalloc(const float* coeffs, float* layers, int n_layers, const int* n_side,
+                         const int* levels, void* stream, char* errbuf, int errlen);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,8 @@ def lib():
         "fewha_set_trace": (ci, [vp, ci]),
         "fewha_get_trace": (ci, [vp, ctypes.POINTER(ctypes.c_ulonglong), ci, ctypes.POINTER(ci),
                                  ctypes.POINTER(ci)]),
+        "fewha_layers_noalloc": (ci, [vp, vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), vp, ctypes.c_char_p,
+                                      ci]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
