@@ -202,6 +202,17 @@ def time_solve(S, torch, n_iter, K, flush):
     return float(np.mean([a.elapsed_time(b) * 1e3 for a, b in ev]))
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (replicas: the slowest rank
+    sets the job's latency); identity without a process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu().tolist()]
+
+
 def phase_breakdown(S, pool_dev, n_iter=N_ITER):
     """One traced non-replacement frame: critical-path time of each phase (the
     latest CTA's work between two barriers) and the barrier latencies (us)."""
@@ -350,12 +361,7 @@ def main():
     P64.close()
 
     # max over ranks
-    vals = np.array([p50, p99, mean, per_iter], dtype=np.float64)
-    if dist:
-        tv = torch.tensor(vals, device=dev)
-        dist.all_reduce(tv, op=dist.ReduceOp.MAX)
-        vals = tv.cpu().numpy()
-    p50, p99, mean, per_iter = [float(v) for v in vals]
+    p50, p99, mean, per_iter = max_over_ranks([p50, p99, mean, per_iter], dist, dev)
     if rank != 0:
         S.close()
         if dist:

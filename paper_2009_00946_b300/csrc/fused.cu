@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "fused.h"
@@ -57,6 +58,11 @@ struct FInst {
     double* scal;          // [2 parities][2] = rho_old, alpha_old
     double* sc_out;        // final scalars for the host (kRho...)
     int w0, nw, l0, nl;    // ranges in the item lists
+    // compact gather tables of P^T per (g, l): n x KG column entries (j, w)
+    // then n x KG row entries (i, w); w as float bits, padding has w = 0
+    const int2* gtab;
+    const int* gtab_off;
+    int KG;
 };
 
 struct WItem { int inst, g, i0, i1, j0, j1; };
@@ -77,7 +83,8 @@ struct FParams {
     int n_inst, n_witems, n_litems;
     int n_iter, warm, replace, out_layers;
     int C;
-    int stripe_floats, stage_floats, win_floats, tile_nodes, tile_subaps;
+    int stripe_floats, stage_floats, win_floats, tile_nodes, tile_subaps, tile_rows, tile_cols;
+    int G_max, n_max;
     float h[6], g[6];
 };
 
@@ -161,6 +168,11 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     float* psi = sm + P.win_floats;
     float* slx = psi + P.tile_nodes;
     float* sly = slx + P.tile_subaps;
+    // per-tile interpolation tables: [l][row] window offset / weight, [l][col]
+    int* roff = (int*)(sly + P.tile_subaps);
+    float* rw = (float*)(roff + L * P.tile_rows);
+    int* coff = (int*)(rw + L * P.tile_rows);
+    float* cw = (float*)(coff + L * P.tile_cols);
     double mu = 0.0;
     const int ns2 = ns * ns;
     if (mode == kModeData) {
@@ -180,29 +192,52 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 wdesc[l * 5 + 4] = o;
                 o += wdesc[l * 5 + 2] * wdesc[l * 5 + 3];
             }
+            wdesc[L * 5 + 4] = o;
         }
         __syncthreads();
-        for (int l = 0; l < L; ++l) {
-            const int r0 = wdesc[l * 5], c0 = wdesc[l * 5 + 1], nc = wdesc[l * 5 + 3];
-            const int cnt = wdesc[l * 5 + 2] * nc, so = wdesc[l * 5 + 4], n = I.lay_n[l];
-            const float* src = I.phi + I.lay_off[l] + (long)r0 * n + c0;
-            for (int e = tid; e < cnt; e += NT) {
-                const int rr = e / nc, cc = e - rr * nc;
-                win[so + e] = __ldcg(src + (long)rr * n + cc);
+        // windows of every layer, flattened, 8 loads in flight per thread
+        const int total = wdesc[L * 5 + 4];
+        for (int e0 = tid; e0 < total; e0 += 8 * NT) {
+            float v[8];
+            int d[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * NT;
+                d[u] = -1;
+                if (e < total) {
+                    int l = 0;
+                    while (l + 1 < L && wdesc[(l + 1) * 5 + 4] <= e) ++l;
+                    const int nc = wdesc[l * 5 + 3], r = e - wdesc[l * 5 + 4];
+                    const int rr = r / nc, cc = r - rr * nc, n = I.lay_n[l];
+                    v[u] = __ldcg(I.phi + I.lay_off[l] + (long)(wdesc[l * 5] + rr) * n + wdesc[l * 5 + 1] + cc);
+                    d[u] = e;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (d[u] >= 0) win[d[u]] = v[u];
+        }
+        for (int e = tid; e < L * (pr + pc); e += NT) {
+            const int l = e / (pr + pc), k = e - l * (pr + pc);
+            const int base = I.tab_off[g * L + l];
+            if (k < pr) {
+                roff[l * P.tile_rows + k] = (__ldg(I.cy + base + a_lo + k) - wdesc[l * 5]) * wdesc[l * 5 + 3] +
+                                            wdesc[l * 5 + 4];
+                rw[l * P.tile_rows + k] = __ldg(I.ty + base + a_lo + k);
+            } else {
+                const int kk = k - pr;
+                coff[l * P.tile_cols + kk] = __ldg(I.cx + base + b_lo + kk) - wdesc[l * 5 + 1];
+                cw[l * P.tile_cols + kk] = __ldg(I.tx + base + b_lo + kk);
             }
         }
         __syncthreads();
         for (int e = tid; e < pr * pc; e += NT) {
             const int ii = e / pc, jj = e - ii * pc;
-            const int i = a_lo + ii, j = b_lo + jj;
             float acc = 0.f;
             for (int l = 0; l < L; ++l) {
-                const int base = I.tab_off[g * L + l];
                 const int nc = wdesc[l * 5 + 3];
-                const int cyv = __ldg(I.cy + base + i) - wdesc[l * 5];
-                const int cxv = __ldg(I.cx + base + j) - wdesc[l * 5 + 1];
-                const float ty = __ldg(I.ty + base + i), tx = __ldg(I.tx + base + j);
-                const float* f = win + wdesc[l * 5 + 4] + cyv * nc + cxv;
+                const float ty = rw[l * P.tile_rows + ii], tx = cw[l * P.tile_cols + jj];
+                const float* f = win + roff[l * P.tile_rows + ii] + coff[l * P.tile_cols + jj];
                 acc += (1.f - ty) * ((1.f - tx) * f[0] + tx * f[1]) + ty * ((1.f - tx) * f[nc] + tx * f[nc + 1]);
             }
             psi[e] = acc;
@@ -263,7 +298,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
 // distributed DWT on the cluster's row stripes
 // ---------------------------------------------------------------------------
 struct Stripe {
-    int n, J, R, row0;
+    int n, J, R, row0, ln, lR;
 };
 
 __device__ __forceinline__ void csync(cg::cluster_group& cl, bool multi) {
@@ -273,42 +308,74 @@ __device__ __forceinline__ void csync(cg::cluster_group& cl, bool multi) {
 
 // Z (own rows) <- W Z; P buffers alternate by level (remote reads in the
 // column passes); one cluster barrier per level whose block spans CTAs.
+// Sizes are powers of two: n = 2^ln, R = 2^lR, a level block m = 2^lm.
+// Every pass handles up to kB outputs per thread per round and issues all of
+// their loads (shared or distributed shared) before any store.
+constexpr int kB = 4;
+
 __device__ void fwd_dwt(const FParams& P, const Stripe& s, float* Z, float* P0, float* P1, float* const* rem0,
                         float* const* rem1, cg::cluster_group& cl) {
-    const int tid = threadIdx.x, NT = blockDim.x, n = s.n, R = s.R;
+    const int tid = threadIdx.x, NT = blockDim.x, n = s.n, R = s.R, ln = s.ln, lR = s.lR;
     __syncthreads();
     for (int j = 1; j <= s.J; ++j) {
-        const int m = n >> (j - 1), half = m >> 1, mask = m - 1;
+        const int lm = ln - (j - 1), m = 1 << lm, half = m >> 1, mask = m - 1;
         const bool multi = m > R;
         float* Pj = (j & 1) ? P0 : P1;
         float* const* rem = (j & 1) ? rem0 : rem1;
         const int nrows = max(0, min(m - s.row0, R));
-        for (int e = tid; e < nrows * half; e += NT) {
-            const int rr = e / half, k = e - rr * half;
-            const float* x = Z + rr * n;
-            float a = 0.f, d = 0.f;
+        const int cnt_r = nrows << (lm - 1);
+        for (int e0 = tid; e0 < cnt_r; e0 += kB * NT) {
+            float a[kB], d[kB];
 #pragma unroll
-            for (int t = 0; t < 6; ++t) {
-                const float v = x[(2 * k + t) & mask];
-                a += P.h[t] * v;
-                d += P.g[t] * v;
+            for (int u = 0; u < kB; ++u) {
+                const int e = e0 + u * NT;
+                a[u] = d[u] = 0.f;
+                if (e < cnt_r) {
+                    const int rr = e >> (lm - 1), k = e & (half - 1);
+                    const float* x = Z + (rr << ln);
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) {
+                        const float v = x[(2 * k + t) & mask];
+                        a[u] += P.h[t] * v;
+                        d[u] += P.g[t] * v;
+                    }
+                }
             }
-            Pj[rr * n + k] = a;
-            Pj[rr * n + half + k] = d;
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int e = e0 + u * NT;
+                if (e < cnt_r) {
+                    const int rr = e >> (lm - 1), k = e & (half - 1);
+                    Pj[(rr << ln) + k] = a[u];
+                    Pj[(rr << ln) + half + k] = d[u];
+                }
+            }
         }
         csync(cl, multi);
-        for (int e = tid; e < nrows * m; e += NT) {
-            const int rr = e / m, x = e - rr * m;
-            const int row = s.row0 + rr;
-            const int k = row < half ? row : row - half;
-            const float* f = row < half ? P.h : P.g;
-            float acc = 0.f;
+        const int cnt_c = nrows << lm;
+        for (int e0 = tid; e0 < cnt_c; e0 += kB * NT) {
+            float acc[kB];
 #pragma unroll
-            for (int t = 0; t < 6; ++t) {
-                const int src = (2 * k + t) & mask;
-                acc += f[t] * rem[src / R][(src % R) * n + x];
+            for (int u = 0; u < kB; ++u) {
+                const int e = e0 + u * NT;
+                acc[u] = 0.f;
+                if (e < cnt_c) {
+                    const int rr = e >> lm, x = e & mask;
+                    const int row = s.row0 + rr;
+                    const int k = row < half ? row : row - half;
+                    const float* f = row < half ? P.h : P.g;
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) {
+                        const int src = (2 * k + t) & mask;
+                        acc[u] += f[t] * rem[src >> lR][((src & (R - 1)) << ln) + x];
+                    }
+                }
             }
-            Z[rr * n + x] = acc;
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int e = e0 + u * NT;
+                if (e < cnt_c) Z[((e >> lm) << ln) + (e & mask)] = acc[u];
+            }
         }
         const bool next_multi = (j < s.J) && (half > R);
         csync(cl, multi && !next_multi);
@@ -318,41 +385,64 @@ __device__ void fwd_dwt(const FParams& P, const Stripe& s, float* Z, float* P0, 
 // returns the buffer holding W^T Z (own rows); Z, Q0, Q1 read remotely.
 __device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb, float* Q0, float* Q1,
                           float* const* remZ, float* const* remQ0, float* const* remQ1, cg::cluster_group& cl) {
-    const int tid = threadIdx.x, NT = blockDim.x, n = s.n, R = s.R;
+    const int tid = threadIdx.x, NT = blockDim.x, n = s.n, R = s.R, ln = s.ln, lR = s.lR;
     csync(cl, (n >> (s.J - 1)) > R);
     float* out = Q1;
     for (int j = s.J; j >= 1; --j) {
-        const int m = n >> (j - 1), half = m >> 1, mask = m - 1;
+        const int lm = ln - (j - 1), m = 1 << lm, half = m >> 1, mask = m - 1;
         float* const* remLL = (j == s.J) ? remZ : (((j + 1) & 1) ? remQ1 : remQ0);
         float* Qj = (j & 1) ? Q1 : Q0;
         const int nrows = max(0, min(m - s.row0, R));
-        for (int e = tid; e < nrows * m; e += NT) {
-            const int rr = e / m, x = e - rr * m;
-            const int i = s.row0 + rr;
-            float* const* ra = (x < half) ? remLL : remZ;
-            float acc = 0.f;
+        const int cnt = nrows << lm;
+        for (int e0 = tid; e0 < cnt; e0 += kB * NT) {
+            float acc[kB];
 #pragma unroll
-            for (int t = 0; t < 6; ++t) {
-                const int r = (i - t) & mask;
-                if (r & 1) continue;
-                const int k = r >> 1, kd = half + k;
-                acc += P.h[t] * ra[k / R][(k % R) * n + x] + P.g[t] * remZ[kd / R][(kd % R) * n + x];
+            for (int u = 0; u < kB; ++u) {
+                const int e = e0 + u * NT;
+                acc[u] = 0.f;
+                if (e < cnt) {
+                    const int i = s.row0 + (e >> lm), x = e & mask;
+                    float* const* ra = (x < half) ? remLL : remZ;
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) {
+                        const int r = (i - t) & mask;
+                        if (r & 1) continue;
+                        const int k = r >> 1, kd = half + k;
+                        acc[u] += P.h[t] * ra[k >> lR][((k & (R - 1)) << ln) + x] +
+                                  P.g[t] * remZ[kd >> lR][((kd & (R - 1)) << ln) + x];
+                    }
+                }
             }
-            Pb[rr * n + x] = acc;
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int e = e0 + u * NT;
+                if (e < cnt) Pb[((e >> lm) << ln) + (e & mask)] = acc[u];
+            }
         }
         __syncthreads();
-        for (int e = tid; e < nrows * m; e += NT) {
-            const int rr = e / m, x = e - rr * m;
-            const float* pr = Pb + rr * n;
-            float acc = 0.f;
+        for (int e0 = tid; e0 < cnt; e0 += kB * NT) {
+            float acc[kB];
 #pragma unroll
-            for (int t = 0; t < 6; ++t) {
-                const int r = (x - t) & mask;
-                if (r & 1) continue;
-                const int k = r >> 1;
-                acc += P.h[t] * pr[k] + P.g[t] * pr[half + k];
+            for (int u = 0; u < kB; ++u) {
+                const int e = e0 + u * NT;
+                acc[u] = 0.f;
+                if (e < cnt) {
+                    const int x = e & mask;
+                    const float* pr = Pb + ((e >> lm) << ln);
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) {
+                        const int r = (x - t) & mask;
+                        if (r & 1) continue;
+                        const int k = r >> 1;
+                        acc[u] += P.h[t] * pr[k] + P.g[t] * pr[half + k];
+                    }
+                }
             }
-            Qj[rr * n + x] = acc;
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int e = e0 + u * NT;
+                if (e < cnt) Qj[((e >> lm) << ln) + (e & mask)] = acc[u];
+            }
         }
         out = Qj;
         if (j > 1) csync(cl, (m << 1) > R);
@@ -414,50 +504,87 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     const int R = n / C, row0 = rank * R;
     const int tid = threadIdx.x, NT = blockDim.x, G = I.G, L = I.L;
     const int SF = P.stripe_floats;
+    __shared__ int sgi[4 * kMaxWfsFused];
     float* Z = sm;
     float* B1 = sm + SF;
     float* B2 = sm + 2 * SF;
     float* B3 = sm + 3 * SF;
     float* stg = sm + 4 * SF;
-    Stripe s{n, J, R, row0};
+    int2* xt = (int2*)(stg + P.stage_floats);          // [g][q][KG]  (j, w)
+    int2* yt = xt + P.G_max * P.n_max * I.KG;           // [g][row][KG] (i, w)
+    const int ln = 31 - __clz(n), lR = 31 - __clz(R), KG = I.KG;
+    Stripe s{n, J, R, row0, ln, lR};
 
     // ---- P^T: gather of the sensor fields into the own rows ----
     {
-        int so = 0;
-        for (int g = 0; g < G; ++g) {
-            const int2 rg = P.stg[LI.stg + rank * G + g];
-            const int np1 = I.wfs_n[g] + 1;
-            const int cnt = (rg.y - rg.x) * np1;
-            const float* src = I.psi + I.wfs_noff[g] + rg.x * np1;
-            for (int e = tid; e < cnt; e += NT) stg[so + e] = __ldcg(src + e);
-            so += cnt;
+        if (tid < G) {
+            // staged row range, staging offset and row length of sensor tid
+            const int2 rg = P.stg[LI.stg + rank * G + tid];
+            int so = 0;
+            for (int g = 0; g < tid; ++g) {
+                const int2 r2 = P.stg[LI.stg + rank * G + g];
+                so += (r2.y - r2.x) * (I.wfs_n[g] + 1);
+            }
+            sgi[tid * 4 + 0] = rg.x;
+            sgi[tid * 4 + 1] = rg.y;
+            sgi[tid * 4 + 2] = so;
+            sgi[tid * 4 + 3] = I.wfs_n[tid] + 1;
         }
         __syncthreads();
-        for (int e = tid; e < R * n; e += NT) {
-            const int p = row0 + e / n, q = e % n;
-            float acc = 0.f;
-            int so2 = 0;
-            for (int g = 0; g < G; ++g) {
-                const int2 rg = P.stg[LI.stg + rank * G + g];
-                const int np1 = I.wfs_n[g] + 1;
-                const int base = I.tab_off[g * L + l], gb = I.gat_off[g * L + l];
-                const int i0 = __ldg(I.ilo + gb + p), i1 = __ldg(I.ihi + gb + p);
-                const int j0 = __ldg(I.jlo + gb + q), j1 = __ldg(I.jhi + gb + q);
-                for (int i = i0; i < i1; ++i) {
-                    const float ty = __ldg(I.ty + base + i);
-                    const float wy = (__ldg(I.cy + base + i) == p) ? 1.f - ty : ty;
-                    const float* row = stg + so2 + (i - rg.x) * np1;
-                    float racc = 0.f;
-                    for (int j = j0; j < j1; ++j) {
-                        const float tx = __ldg(I.tx + base + j);
-                        const float wx = (__ldg(I.cx + base + j) == q) ? 1.f - tx : tx;
-                        racc += wx * row[j];
-                    }
-                    acc += wy * racc;
-                }
-                so2 += (rg.y - rg.x) * np1;
+        // rows of the sensor fields (8 loads in flight per thread)
+        for (int g = 0; g < G; ++g) {
+            const int cnt = (sgi[g * 4 + 1] - sgi[g * 4]) * sgi[g * 4 + 3];
+            const float* src = I.psi + I.wfs_noff[g] + sgi[g * 4] * sgi[g * 4 + 3];
+            float* dst = stg + sgi[g * 4 + 2];
+            for (int e0 = tid; e0 < cnt; e0 += 8 * NT) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (e0 + u * NT < cnt) v[u] = __ldcg(src + e0 + u * NT);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (e0 + u * NT < cnt) dst[e0 + u * NT] = v[u];
             }
-            Z[e] = acc;
+        }
+        // compact gather tables: columns for every sensor, rows of this stripe
+        for (int e = tid; e < G * n * KG; e += NT) {
+            const int g = e / (n * KG), r = e - g * n * KG;
+            xt[e] = __ldg(I.gtab + I.gtab_off[g * L + l] + r);
+        }
+        for (int e = tid; e < G * R * KG; e += NT) {
+            const int g = e / (R * KG), r = e - g * R * KG;
+            yt[e] = __ldg(I.gtab + I.gtab_off[g * L + l] + n * KG + row0 * KG + r);
+        }
+        __syncthreads();
+        for (int e0 = tid; e0 < (R << ln); e0 += 2 * NT) {
+            float acc[2] = {0.f, 0.f};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e = e0 + u * NT;
+                if (e >= (R << ln)) break;
+                const int rr = e >> ln, q = e & (n - 1);
+                for (int g = 0; g < G; ++g) {
+                    const int imin = sgi[g * 4], imax = sgi[g * 4 + 1];
+                    if (imax <= imin) continue;
+                    const int np1 = sgi[g * 4 + 3];
+                    const float* base = stg + sgi[g * 4 + 2];
+                    const int2* xq = xt + ((g * n + q) * KG);
+                    const int2* yr = yt + ((g * R + rr) * KG);
+                    for (int a = 0; a < KG; ++a) {
+                        const int2 ye = yr[a];
+                        const float* row = base + max(ye.x - imin, 0) * np1;
+                        float racc = 0.f;
+                        for (int b = 0; b < KG; ++b) {
+                            const int2 xe = xq[b];
+                            racc += __int_as_float(xe.y) * row[xe.x];
+                        }
+                        acc[u] += __int_as_float(ye.y) * racc;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (e0 + u * NT < (R << ln)) Z[e0 + u * NT] = acc[u];
         }
     }
 
@@ -488,6 +615,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     double rho_p = 0.0, dz_p = 0.0;
     const long gbase = (long)off + (long)row0 * n;
     const float fa = (float)alpha, fb = (float)beta;
+#pragma unroll 4
     for (int e = tid; e < R * n; e += NT) {
         const long i = gbase + e;
         const float jinv = __ldg(I.Jinv + i), ad = __ldg(I.aD + i);
@@ -571,7 +699,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_frame(const __grid_const
     __shared__ float* rem[4][kMaxC];
     __shared__ double red[32];
     __shared__ double sh[8];
-    __shared__ int wdesc[kMaxLayersFused * 5];
+    __shared__ int wdesc[(kMaxLayersFused + 1) * 5];
     __shared__ int s_abort;
     cg::cluster_group cl = cg::this_cluster();
     const int C = P.C;
@@ -709,6 +837,46 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
     const int sms = prop.multiProcessorCount;
     const size_t smem_cap = (size_t)prop.sharedMemPerBlockOptin - 4096;
 
+    // compact P^T gather tables: for layer column q the sensor columns j with
+    // cell_j in {q-1, q} and their bilinear weights (1 - t if cell_j == q,
+    // t if cell_j == q-1), padded to KG entries (weight 0, index 0 / -1);
+    // the same for rows
+    int KG = 1;
+    for (int g = 0; g < hs.G; ++g)
+        for (int l = 0; l < hs.L; ++l) {
+            const int gb = hs.gat_off[g * hs.L + l];
+            for (int q = 0; q < hs.lay[l].n; ++q) {
+                KG = std::max(KG, hs.jhi[gb + q] - hs.jlo[gb + q]);
+                KG = std::max(KG, hs.ihi[gb + q] - hs.ilo[gb + q]);
+            }
+        }
+    std::vector<int2> gtab;
+    std::vector<int> gtab_off((size_t)hs.G * hs.L);
+    auto fbits = [](float f) {
+        int i;
+        std::memcpy(&i, &f, sizeof i);
+        return i;
+    };
+    for (int g = 0; g < hs.G; ++g)
+        for (int l = 0; l < hs.L; ++l) {
+            const int n = hs.lay[l].n, base = hs.tab_off[g * hs.L + l], gb = hs.gat_off[g * hs.L + l];
+            gtab_off[g * hs.L + l] = (int)gtab.size();
+            for (int axis = 0; axis < 2; ++axis) {
+                const int* lo = axis ? hs.ilo.data() : hs.jlo.data();
+                const int* hi = axis ? hs.ihi.data() : hs.jhi.data();
+                const int* cell = axis ? hs.cy.data() : hs.cx.data();
+                const double* t = axis ? hs.ty.data() : hs.tx.data();
+                for (int q = 0; q < n; ++q) {
+                    int cnt = 0;
+                    for (int k = lo[gb + q]; k < hi[gb + q]; ++k, ++cnt) {
+                        const float w = cell[base + k] == q ? (float)(1.0 - t[base + k]) : (float)t[base + k];
+                        gtab.push_back(make_int2(k, fbits(w)));
+                    }
+                    for (; cnt < KG; ++cnt) gtab.push_back(make_int2(axis ? -1 : 0, fbits(0.f)));
+                }
+            }
+        }
+
     FusedPlan* best = nullptr;
     for (int C : {8, 4, 16, 2, 1}) {
         if (C > nmin) continue;
@@ -741,26 +909,65 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
             }
             litems.push_back(li);
         }
-        // occupancy first (grid size decides the tiling)
         const int stripe = nmax * nmax / C;
-        // sensor tiles: aim at about one tile per CTA
-        int grid_guess = (sms / C) * C;
+        const int Rmax = nmax / C;
+        stage_max = (stage_max + 3) & ~3;
+        const size_t gtab_floats = 2 * (size_t)hs.G * nmax * KG + 2 * (size_t)hs.G * Rmax * KG;
+        const size_t layer_floats = 4 * (size_t)stripe + stage_max + gtab_floats;
+
+        // co-resident clusters: one 512-thread CTA per SM (register-limited),
+        // so the answer does not depend on the shared memory below the cap
+        // the attribute is per function: allow the device maximum once for all plans
+        cudaFuncSetAttribute(k_fused_frame, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+        if (C > 8) cudaFuncSetAttribute(k_fused_frame, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3(C * 1024);
+        cfg.blockDim = dim3(kFThreads);
+        cfg.dynamicSmemBytes = std::min(smem_cap, layer_floats * sizeof(float));
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        cudaError_t oe = cudaOccupancyMaxActiveClusters(&ncl, k_fused_frame, &cfg);
+        if (oe != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            delete pl;
+            continue;
+        }
+        pl->nclusters = std::max(1, std::min(ncl, std::max(1, sms / C)));
+        pl->grid = pl->nclusters * C;
+
+        // sensor tiles: at most one round over the grid, near-square tiles
         std::vector<WItem> witems;
-        int per = std::max(1, grid_guess / std::max(1, hs.G));
+        const int per = std::max(1, pl->grid / std::max(1, hs.G));
         for (int g = 0; g < hs.G; ++g) {
             const int np1 = hs.wfs[g].n + 1;
-            int nty = std::max(1, (int)std::floor(std::sqrt((double)per)));
-            while (nty > 1 && per / nty < 1) --nty;
-            int ntx = std::max(1, per / nty);
-            nty = std::min(nty, np1);
-            ntx = std::min(ntx, np1);
-            make_tiles(0, g, np1, nty, ntx, witems);
+            int best_ty = 1, best_tx = 1;
+            double best_cost = 1e30;
+            for (int ty = 1; ty <= std::min(per, np1); ++ty)
+                for (int tx = 1; tx <= std::min(per / ty, np1); ++tx) {
+                    // cost: the largest tile with its halo (rounds are 1 by construction)
+                    const double h = std::ceil((double)np1 / ty) + 2, w = std::ceil((double)np1 / tx) + 2;
+                    const double cost = h * w + 0.5 * (h + w);
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        best_ty = ty;
+                        best_tx = tx;
+                    }
+                }
+            make_tiles(0, g, np1, best_ty, best_tx, witems);
         }
-        int tile_nodes = 0, tile_sub = 0, win_max = 0;
+        int tile_nodes = 0, tile_sub = 0, win_max = 0, tile_rows = 0, tile_cols = 0;
         for (auto& w : witems) {
             const int ns = hs.wfs[w.g].n;
             const int a_lo = std::max(w.i0 - 1, 0), a_hi = std::min(w.i1, ns);
             const int b_lo = std::max(w.j0 - 1, 0), b_hi = std::min(w.j1, ns);
+            tile_rows = std::max(tile_rows, a_hi - a_lo + 1);
+            tile_cols = std::max(tile_cols, b_hi - b_lo + 1);
             tile_nodes = std::max(tile_nodes, (a_hi - a_lo + 1) * (b_hi - b_lo + 1));
             tile_sub = std::max(tile_sub, (std::min(w.i1, ns) - a_lo) * (std::min(w.j1, ns) - b_lo));
             int win = 0;
@@ -775,39 +982,14 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         tile_nodes = (tile_nodes + 3) & ~3;
         tile_sub = (tile_sub + 3) & ~3;
         win_max = (win_max + 3) & ~3;
-        stage_max = (stage_max + 3) & ~3;
-        const size_t layer_floats = 4 * (size_t)stripe + stage_max;
-        const size_t sensor_floats = (size_t)win_max + tile_nodes + 2 * (size_t)tile_sub;
+        const size_t sensor_floats = (size_t)win_max + tile_nodes + 2 * (size_t)tile_sub +
+                                     2 * (size_t)hs.L * (tile_rows + tile_cols);
         const size_t smem = std::max(layer_floats, sensor_floats) * sizeof(float);
         if (smem > smem_cap) {
             delete pl;
             continue;
         }
         pl->smem = (int)smem;
-        // the attribute is per function: allow the device maximum once for all plans
-        cudaFuncSetAttribute(k_fused_frame, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
-        if (C > 8) cudaFuncSetAttribute(k_fused_frame, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        cfg.gridDim = dim3(C * 1024);
-        cfg.blockDim = dim3(kFThreads);
-        cfg.dynamicSmemBytes = smem;
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int ncl = 0;
-        cudaError_t oe = cudaOccupancyMaxActiveClusters(&ncl, k_fused_frame, &cfg);
-        if (oe != cudaSuccess || ncl < 1) {
-            cudaGetLastError();
-            delete pl;
-            continue;
-        }
-        pl->nclusters = std::min(ncl, sms / C > 0 ? sms / C : 1);
-        pl->nclusters = std::max(1, std::min(pl->nclusters, ncl));
-        pl->grid = pl->nclusters * C;
 
         // device data
         FInst I{};
@@ -848,7 +1030,13 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         I.nw = (int)witems.size();
         I.l0 = 0;
         I.nl = (int)litems.size();
-        bool ok = dalloc(pl, I.psi, hs.NW, err) && dalloc(pl, I.scal, 4, err);
+        I.KG = KG;
+        int2* d_gtab = nullptr;
+        int* d_gtab_off = nullptr;
+        bool ok = dalloc(pl, I.psi, hs.NW, err) && dalloc(pl, I.scal, 4, err) && dupload(pl, d_gtab, gtab, err) &&
+                  dupload(pl, d_gtab_off, gtab_off, err);
+        I.gtab = d_gtab;
+        I.gtab_off = d_gtab_off;
         if (ok) cudaMemset(I.scal, 0, 4 * sizeof(double));
         I.slopes = fb.slopes;
         pl->psi = I.psi;
@@ -889,6 +1077,10 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         P.win_floats = win_max;
         P.tile_nodes = tile_nodes;
         P.tile_subaps = tile_sub;
+        P.tile_rows = tile_rows;
+        P.tile_cols = tile_cols;
+        P.G_max = hs.G;
+        P.n_max = nmax;
         for (int i = 0; i < 6; ++i) {
             P.h[i] = (float)hs.h[i];
             P.g[i] = (float)hs.g[i];
