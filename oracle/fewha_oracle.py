@@ -745,3 +745,160 @@ class Reconstructor:
     def layers(self, c: np.ndarray | None = None) -> np.ndarray:
         c = self.state.c if c is None else c
         return np.concatenate([p.ravel() for p in layers_from_coeffs(self.geom, c)])
+
+
+# ---------------------------------------------------------------------------
+# reverse mode through the unrolled Alg. 2 (differentiation of the solve)
+# ---------------------------------------------------------------------------
+# Reading R12: the derivative is taken of the fixed-iteration solve exactly as
+# computed (K iterations of Alg. 2 from c = 0, r = b), with the preconditioner
+# J held fixed; theta = (Cn^2 fractions gamma_l, alpha, sensor weights w_g).
+# M depends on theta through alpha D (D ~ 1/gamma_l) and w_g; b through w_g.
+
+def pcg_alg2_tape(Mop, Jinv: np.ndarray, b: np.ndarray, n_iter: int):
+    """Alg. 2 from c = 0, r = b, keeping every intermediate for the adjoint."""
+    N = b.size
+    c = np.zeros(N)
+    r = b.copy()
+    p = q = np.zeros(N)
+    tape = []
+    rho_old = alpha_old = None
+    for k in range(n_iter):
+        z = Jinv * r
+        s = Mop(z)
+        rho = float(r @ z)
+        mu = float(s @ z)
+        if k == 0:
+            beta, d = 0.0, mu
+        else:
+            beta = rho / rho_old
+            d = mu - rho * beta / alpha_old
+        if not d > 0.0:
+            raise BreakdownError("PCG denominator %r at iteration %d" % (d, k))
+        alpha = rho / d
+        tape.append(dict(r=r, z=z, s=s, p_old=p, q_old=q, rho=rho, mu=mu, beta=beta, d=d, alpha=alpha,
+                         rho_old=rho_old, alpha_old=alpha_old))
+        p = z + beta * p
+        q = s + beta * q
+        c = c + alpha * p
+        r = r - alpha * q
+        tape[-1]["p"] = p
+        tape[-1]["q"] = q
+        rho_old, alpha_old = rho, alpha
+    return c, r, tape
+
+
+def pcg_alg2_adjoint(Mop, Jinv: np.ndarray, tape: list, cbar: np.ndarray):
+    """Adjoint of :func:`pcg_alg2_tape` for a cotangent cbar of the final c.
+    Returns (bbar, [(z_k, sbar_k)]): the cotangent of b and, per iteration,
+    the pair that contracts with dM/dtheta (s_k = M z_k)."""
+    N = cbar.size
+    cb = cbar.copy()          # cotangent of c_{k+1}
+    rb = np.zeros(N)          # cotangent of r_{k+1}
+    pb = np.zeros(N)          # cotangent of p_k (from later iterations)
+    qb = np.zeros(N)
+    rhob_next = 0.0           # contribution to rho_k from iteration k+1
+    alphab_next = 0.0         # contribution to alpha_k from iteration k+1
+    pairs = []
+    for k in range(len(tape) - 1, -1, -1):
+        t = tape[k]
+        # c_{k+1} = c_k + alpha_k p_k ; r_{k+1} = r_k - alpha_k q_k
+        alphab = alphab_next + float(cb @ t["p"]) - float(rb @ t["q"])
+        pb = pb + t["alpha"] * cb
+        qb = qb - t["alpha"] * rb
+        # p_k = z_k + beta_k p_{k-1} ; q_k = s_k + beta_k q_{k-1}
+        zb = pb.copy()
+        sb = qb.copy()
+        betab = float(pb @ t["p_old"]) + float(qb @ t["q_old"]) if k > 0 else 0.0
+        pb_prev = t["beta"] * pb
+        qb_prev = t["beta"] * qb
+        # alpha_k = rho_k / d_k
+        rhob = rhob_next + alphab / t["d"]
+        db = -alphab * t["rho"] / t["d"] ** 2
+        mub = db
+        alphab_prev = 0.0
+        rhob_prev = 0.0
+        if k > 0:
+            # d_k = mu_k - rho_k beta_k / alpha_{k-1}
+            rhob -= db * t["beta"] / t["alpha_old"]
+            betab -= db * t["rho"] / t["alpha_old"]
+            alphab_prev = db * t["rho"] * t["beta"] / t["alpha_old"] ** 2
+            # beta_k = rho_k / rho_{k-1}
+            rhob += betab / t["rho_old"]
+            rhob_prev = -betab * t["rho"] / t["rho_old"] ** 2
+        # mu_k = (s_k, z_k) ; rho_k = (r_k, z_k)
+        sb = sb + mub * t["z"]
+        zb = zb + mub * t["s"] + rhob * t["r"]
+        rb_k = rb + rhob * t["z"]
+        # s_k = M z_k (M symmetric)
+        zb = zb + Mop(sb)
+        pairs.append((t["z"], sb))
+        # z_k = J^{-1} r_k
+        rb = rb_k + Jinv * zb
+        pb, qb = pb_prev, qb_prev
+        rhob_next, alphab_next = rhob_prev, alphab_prev
+        # c_k receives cb unchanged (c_{k+1} = c_k + ...)
+    return rb, pairs[::-1]
+
+
+def _sensor_slopes_of(geom: Geometry, c: np.ndarray):
+    """Gamma P_g W^T c for every sensor g: list of (sx, sy)."""
+    phi = layers_from_coeffs(geom, c)
+    return [Gamma(P_apply(geom, phi, g)) for g in range(geom.G)]
+
+
+def dM_contract(geom: Geometry, params: Params, z: np.ndarray, sbar: np.ndarray):
+    """sbar^T (dM/dtheta) z for theta = (gamma_l..., alpha, w_g...)."""
+    D = geom.D_diag(params) / 1.0               # D without alpha
+    t = sbar * D * z
+    galpha = float(t.sum())
+    ggam = np.array([-params.alpha * float(t[geom.off[l]:geom.off[l + 1]].sum()) / params.cn2[l]
+                     for l in range(geom.L)])
+    A = _sensor_slopes_of(geom, z)
+    B = _sensor_slopes_of(geom, sbar)
+    gw = np.array([float(np.sum(geom.mask[g] * (A[g][0] * B[g][0] + A[g][1] * B[g][1]))) for g in range(geom.G)])
+    return ggam, galpha, gw
+
+
+def db_contract(geom: Geometry, s: np.ndarray, bbar: np.ndarray):
+    """bbar^T (db/dw_g) = (Gamma P_g W^T bbar) . (mask_g s_g)."""
+    B = _sensor_slopes_of(geom, bbar)
+    out = []
+    for g in range(geom.G):
+        sx, sy = geom.split_slopes(s, g)
+        out.append(float(np.sum(geom.mask[g] * (B[g][0] * sx + B[g][1] * sy))))
+    return np.array(out)
+
+
+def solve_loss(geom: Geometry, params: Params, Jinv: np.ndarray, s: np.ndarray, phi_true: np.ndarray,
+               n_iter: int):
+    """Loss |W^T c_K - phi_true|^2 of one frame solved from a cold start."""
+    b = rhs(geom, s, params)
+    c, _, _ = pcg_alg2_tape(lambda v: apply_M(geom, v, params), Jinv, b, n_iter)
+    phi = np.concatenate([p.ravel() for p in layers_from_coeffs(geom, c)])
+    return float(np.sum((phi - phi_true) ** 2))
+
+
+def solve_loss_grad(geom: Geometry, params: Params, Jinv: np.ndarray, s: np.ndarray, phi_true: np.ndarray,
+                    n_iter: int):
+    """(loss, d loss / d gamma, d loss / d alpha, d loss / d w) by reverse mode."""
+    Mop = lambda v: apply_M(geom, v, params)
+    b = rhs(geom, s, params)
+    c, _, tape = pcg_alg2_tape(Mop, Jinv, b, n_iter)
+    phi_l = layers_from_coeffs(geom, c)
+    phi = np.concatenate([p.ravel() for p in phi_l])
+    res = phi - phi_true
+    loss = float(np.sum(res ** 2))
+    # phi = W^T c  ->  cbar = W (2 res)
+    cbar = coeffs_from_layers(geom, [2.0 * geom.layer(res, l) for l in range(geom.L)])
+    bbar, pairs = pcg_alg2_adjoint(Mop, Jinv, tape, cbar)
+    ggam = np.zeros(geom.L)
+    galpha = 0.0
+    gw = np.zeros(geom.G)
+    for z, sb in pairs:
+        a, b2, c2 = dM_contract(geom, params, z, sb)
+        ggam += a
+        galpha += b2
+        gw += c2
+    gw += db_contract(geom, s, bbar)
+    return loss, ggam, galpha, gw
