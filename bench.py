@@ -221,7 +221,18 @@ def phase_breakdown(S, pool_dev, n_iter=N_ITER):
     S.set_frame(pool_dev[0])
     S.solve(n_iter, warm=True)
     tr = S.trace().astype(np.int64)
+    fine = S.fine_trace()
     S.set_trace(False)
+    # sub-phase steps: mean over CTAs and phases of the time between marks
+    names = {(10, 11): "layer_stage_rows_us", (11, 12): "layer_PT_us", (12, 13): "layer_fwd_dwt_us",
+             (13, 14): "layer_update_us", (14, 15): "layer_inv_dwt_us", (15, 16): "layer_store_sync_us",
+             (14, 16): "layer_no_inverse_us", (20, 21): "sensor_stage_windows_us", (21, 22): "sensor_P_us",
+             (22, 23): "sensor_slopes_us", (23, 24): "sensor_gammaT_store_us"}
+    steps = {}
+    for row in fine:
+        for (ta, a), (tb, b) in zip(row[:-1], row[1:]):
+            if (ta, tb) in names:
+                steps.setdefault(names[(ta, tb)], []).append((b - a) / 1e3)
     S.set_residual_replacement(K_RR)
     work, bars = [], []
     for b in range(1, tr.shape[0]):
@@ -234,7 +245,9 @@ def phase_breakdown(S, pool_dev, n_iter=N_ITER):
             "layer_phase_us": float(np.mean(layer)) if layer else None,
             "grid_barrier_us": float(np.mean(bars)) if bars else None,
             "kernel_us": float(tr[-1, :, 0].max() - tr[0, :, 1].min()) / 1e3,
-            "n_barriers": len(bars)}
+            "n_barriers": len(bars),
+            "steps_mean_us": {k: float(np.mean(v)) for k, v in sorted(steps.items())},
+            "steps_max_us": {k: float(np.max(v)) for k, v in sorted(steps.items())}}
 
 
 def profile_mode(args):

@@ -193,6 +193,14 @@ int fewha_describe(fewha_handle* h, char* buf, int len);
 int fewha_set_trace(fewha_handle* h, int on);
 int fewha_get_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* slots, int* grid);
 
+/* Marks inside the phases of the last traced fused launch (profiling aid):
+ * per CTA a row of per_cta values (tag << 56 | globaltimer ns), 0 = unused.
+ * Tags: 10..16 layer phase (start, sensor rows staged, P^T done, forward DWT
+ * done, update done, inverse DWT done, end); 20..24 sensor tile (start,
+ * windows staged, P done, slopes done, end); 30 RHS sensor tile start.
+ * Synchronises.  Errors: STATE on the plain path. */
+int fewha_get_fine_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* per_cta, int* grid);
+
 /* The paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory (a control loop that reserves all memory at start-up
  * and allows no allocation while it runs, code inside a framework that owns

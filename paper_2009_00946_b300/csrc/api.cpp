@@ -179,6 +179,12 @@ int fewha_get_trace(fewha_handle* h, unsigned long long* out, int max_entries, i
     return done(h, h->s->get_trace(out, max_entries, slots, grid));
 }
 
+int fewha_get_fine_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* per_cta, int* grid) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (!per_cta || !grid || max_entries < 0) return fail(h, FEWHA_ERR_ARG, "bad trace arguments");
+    return done(h, h->s->get_fine_trace(out, max_entries, per_cta, grid));
+}
+
 long long fewha_launch_count(const fewha_handle* h) {
     if (!h) return -1;
     return h->s->launches;

@@ -38,6 +38,7 @@ constexpr int kFThreads = 512;
 constexpr int kMaxC = 16;
 constexpr int kMaxLayersFused = 64;
 constexpr int kMaxWfsFused = 16;
+constexpr int kFineCap = 1024;   // sub-phase marks per CTA per traced launch
 
 enum { kModeRhs = 0, kModeData = 1 };
 enum { kLpRhsStart = 0, kLpRhsRepl = 1, kLpReplStart = 2, kLpIter = 3 };
@@ -79,6 +80,8 @@ struct FParams {
     int* errw;
     unsigned long long* trace;   // optional: [slot][cta][arrive, depart] globaltimer (ns)
     int trace_slots;
+    unsigned long long* ftrace;  // optional: [cta][fcap] (tag << 56 | ns) marks inside the phases
+    int fcap;
     long long budget;
     int n_inst, n_witems, n_litems;
     int n_iter, warm, replace, out_layers;
@@ -106,6 +109,24 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ void trace_mark(const FParams& P, int slot, int which) {
     if (P.trace && slot < P.trace_slots)
         P.trace[((size_t)slot * gridDim.x + blockIdx.x) * 2 + which] = global_ns();
+}
+
+// Sub-phase mark: thread 0 records (tag, time) in this CTA's row.  Callers
+// synchronise the CTA first (only when tracing), so the mark closes the step.
+__device__ int* fmark_counter() {
+    __shared__ int cnt;
+    return &cnt;
+}
+
+__device__ __forceinline__ void fmark(const FParams& P, int tag) {
+    if (!P.ftrace) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int* c = fmark_counter();
+        if (*c < P.fcap)
+            P.ftrace[(size_t)blockIdx.x * P.fcap + (*c)++] = ((unsigned long long)tag << 56) |
+                                                             (global_ns() & 0x00FFFFFFFFFFFFFFull);
+    }
 }
 
 // Arrive: one fenced atomic per CTA; wait: thread 0 polls with acquire loads
@@ -158,6 +179,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     const FInst& I = P.inst[W.inst];
     const int g = W.g, ns = I.wfs_n[g], np1 = ns + 1, L = I.L;
     const int tid = threadIdx.x, NT = blockDim.x;
+    fmark(P, mode == kModeData ? 20 : 30);
     // psi nodes [a_lo, a_hi] x [b_lo, b_hi]; subapertures [a_lo, sa_hi) x [b_lo, sb_hi)
     const int a_lo = max(W.i0 - 1, 0), a_hi = min(W.i1, ns);
     const int b_lo = max(W.j0 - 1, 0), b_hi = min(W.j1, ns);
@@ -231,6 +253,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             }
         }
         __syncthreads();
+        fmark(P, 21);
         for (int e = tid; e < pr * pc; e += NT) {
             const int ii = e / pc, jj = e - ii * pc;
             float acc = 0.f;
@@ -243,6 +266,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             psi[e] = acc;
         }
         __syncthreads();
+        fmark(P, 22);
         const float w = I.wfs_w[g];
         for (int e = tid; e < nsr * nsc; e += NT) {
             const int aa = e / nsc, bb = e - aa * nsc;
@@ -270,6 +294,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         }
     }
     __syncthreads();
+    fmark(P, 23);
     const int ti = W.i1 - W.i0, tj = W.j1 - W.j0;
     float* out = I.psi + I.wfs_noff[g];
     for (int e = tid; e < ti * tj; e += NT) {
@@ -292,6 +317,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         if (tid == 0) P.wpart[item] = s;
     }
     __syncthreads();
+    fmark(P, 24);
 }
 
 // ---------------------------------------------------------------------------
@@ -505,6 +531,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     const int tid = threadIdx.x, NT = blockDim.x, G = I.G, L = I.L;
     const int SF = P.stripe_floats;
     __shared__ int sgi[4 * kMaxWfsFused];
+    fmark(P, 10);
     float* Z = sm;
     float* B1 = sm + SF;
     float* B2 = sm + 2 * SF;
@@ -556,6 +583,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             yt[e] = __ldg(I.gtab + I.gtab_off[g * L + l] + n * KG + row0 * KG + r);
         }
         __syncthreads();
+        fmark(P, 11);
         for (int e0 = tid; e0 < (R << ln); e0 += 2 * NT) {
             float acc[2] = {0.f, 0.f};
 #pragma unroll
@@ -589,7 +617,9 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     }
 
     // ---- forward DWT ----
+    fmark(P, 12);
     fwd_dwt(P, s, Z, B1, B2, rem[1], rem[2], cl);
+    fmark(P, 13);
 
     // ---- elementwise (Alg. 1 restart / Alg. 2 update) ----
     double alpha = 0.0, beta = 0.0;
@@ -682,19 +712,26 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     }
 
     // ---- inverse DWT -> phi ----
+    fmark(P, 14);
     const bool need_phi = make_z || mode == kLpRhsRepl || (last && P.out_layers);
     if (need_phi) {
         float* res = inv_dwt(P, s, Z, B3, B1, B2, rem[0], rem[1], rem[2], cl);
+        fmark(P, 15);
         for (int e = tid; e < R * n; e += NT) I.phi[gbase + e] = res[e];
     }
     // the stripes may still be read by the other CTAs of the cluster
     cl.sync();
+    fmark(P, 16);
 }
 
 // ---------------------------------------------------------------------------
 // the frame kernel
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kFThreads, 1) k_fused_frame(const __grid_constant__ FParams P) {
+// The cluster shape is compiled into each instance (one per cluster size), so
+// it belongs to the kernel and not to the launch configuration.
+template <int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
+    k_fused_frame(const __grid_constant__ FParams P) {
     extern __shared__ __align__(16) float sm[];
     __shared__ float* rem[4][kMaxC];
     __shared__ double red[32];
@@ -719,7 +756,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_frame(const __grid_const
         const int b = threadIdx.x / C, r = threadIdx.x % C;
         rem[b][r] = cl.map_shared_rank(sm + b * P.stripe_floats, r);
     }
-    if (threadIdx.x == 0) s_abort = 0;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        *fmark_counter() = 0;
+    }
     unsigned target = 0;
     __syncthreads();
 
@@ -752,6 +792,19 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused_frame(const __grid_const
     }
 }
 
+using FusedKernel = void (*)(FParams);
+
+FusedKernel fused_kernel_for(int C) {
+    switch (C) {
+        case 1: return k_fused_frame<1>;
+        case 2: return k_fused_frame<2>;
+        case 4: return k_fused_frame<4>;
+        case 8: return k_fused_frame<8>;
+        case 16: return k_fused_frame<16>;
+        default: return nullptr;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host plan
 // ---------------------------------------------------------------------------
@@ -759,6 +812,7 @@ struct FusedPlan {
     int C = 1, nclusters = 0, grid = 0, smem = 0;
     bool cooperative = true;
     bool trace_on = false;
+    unsigned long long* ftrace = nullptr;
     unsigned long long* trace = nullptr;
     int trace_slots = 0;
     int last_slots = 0;
@@ -918,21 +972,16 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         // co-resident clusters: one 512-thread CTA per SM (register-limited),
         // so the answer does not depend on the shared memory below the cap
         // the attribute is per function: allow the device maximum once for all plans
-        cudaFuncSetAttribute(k_fused_frame, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
-        if (C > 8) cudaFuncSetAttribute(k_fused_frame, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        const FusedKernel kern = fused_kernel_for(C);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+        if (C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
         cfg.gridDim = dim3(C * 1024);
         cfg.blockDim = dim3(kFThreads);
         cfg.dynamicSmemBytes = std::min(smem_cap, layer_floats * sizeof(float));
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = 0;   // the cluster shape is compiled into the instance
         int ncl = 0;
-        cudaError_t oe = cudaOccupancyMaxActiveClusters(&ncl, k_fused_frame, &cfg);
+        cudaError_t oe = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
         if (oe != cudaSuccess || ncl < 1) {
             cudaGetLastError();
             delete pl;
@@ -1114,9 +1163,19 @@ int fused_get_trace(FusedPlan* pl, unsigned long long* out, int max_entries, int
     return cudaMemcpy(out, pl->trace, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : 1;
 }
 
+int fused_get_fine_trace(FusedPlan* pl, unsigned long long* out, int max_entries, int* per_cta, int* grid) {
+    *per_cta = pl->ftrace ? kFineCap : 0;
+    *grid = pl->grid;
+    if (!pl->ftrace || !out) return 0;
+    size_t n = std::min((size_t)max_entries, (size_t)kFineCap * pl->grid);
+    return cudaMemcpy(out, pl->ftrace, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost) == cudaSuccess ? 0
+                                                                                                            : 1;
+}
+
 void fused_destroy(FusedPlan* plan) {
     if (!plan) return;
     if (plan->trace) cudaFree(plan->trace);
+    if (plan->ftrace) cudaFree(plan->ftrace);
     for (void* a : plan->allocs) cudaFree(a);
     delete plan;
 }
@@ -1132,6 +1191,8 @@ int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int re
     FParams P = pl->P;
     P.trace = nullptr;
     P.trace_slots = 0;
+    P.ftrace = nullptr;
+    P.fcap = 0;
     if (pl->trace_on) {
         // start, RHS barrier, first layer-phase barrier, 2 n_iter - 1 iteration
         // barriers (+2 for the replacement), end
@@ -1146,34 +1207,39 @@ int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int re
         P.trace = pl->trace;
         P.trace_slots = pl->trace_slots;
         pl->last_slots = need;
+        if (!pl->ftrace && cudaMalloc(&pl->ftrace, (size_t)kFineCap * pl->grid * sizeof(unsigned long long)) !=
+                               cudaSuccess)
+            pl->ftrace = nullptr;
+        if (pl->ftrace) {
+            cudaMemsetAsync(pl->ftrace, 0, (size_t)kFineCap * pl->grid * sizeof(unsigned long long), stream);
+            P.ftrace = pl->ftrace;
+            P.fcap = kFineCap;
+        }
     }
     P.n_iter = n_iter;
     P.warm = warm;
     P.replace = replace;
     P.out_layers = 1;
     P.budget = budget;
+    const FusedKernel kern = fused_kernel_for(pl->C);
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3(pl->grid);
     cfg.blockDim = dim3(kFThreads);
     cfg.dynamicSmemBytes = pl->smem;
     cfg.stream = stream;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = pl->C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeCooperative;
-    attr[1].val.cooperative = 1;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = pl->cooperative ? 2 : 1;
-    e = cudaLaunchKernelEx(&cfg, k_fused_frame, P);
+    cfg.numAttrs = pl->cooperative ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, kern, P);
     if (e != cudaSuccess && pl->cooperative) {
         // cooperative + cluster not accepted: the grid is sized from the
         // occupancy query, so every cluster is resident; barriers stay bounded
         cudaGetLastError();
         pl->cooperative = false;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_fused_frame, P);
+        cfg.numAttrs = 0;
+        e = cudaLaunchKernelEx(&cfg, kern, P);
     }
     if (e != cudaSuccess) {
         err = std::string("fused launch: ") + cudaGetErrorString(e);

@@ -38,5 +38,7 @@ int fused_describe(const FusedPlan* plan, char* buf, int len);
 // of every CTA at every grid barrier).
 void fused_set_trace(FusedPlan* plan, bool on);
 int fused_get_trace(FusedPlan* plan, unsigned long long* out, int max_entries, int* slots, int* grid);
+// Sub-phase marks of the last traced launch: [cta][per_cta] of (tag << 56 | ns).
+int fused_get_fine_trace(FusedPlan* plan, unsigned long long* out, int max_entries, int* per_cta, int* grid);
 
 }  // namespace fewha

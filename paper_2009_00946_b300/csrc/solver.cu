@@ -1045,6 +1045,19 @@ class Solver : public SolverBase {
         return FEWHA_OK;
     }
 
+    int get_fine_trace(unsigned long long* out, int max_entries, int* per_cta, int* grid) override {
+        if (!fused) {
+            err = "tracing is available on the fused path only";
+            return FEWHA_ERR_STATE;
+        }
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        if (fused_get_fine_trace(fused, out, max_entries, per_cta, grid)) {
+            err = "trace copy failed";
+            return FEWHA_ERR_CUDA;
+        }
+        return FEWHA_OK;
+    }
+
     int frame(const void* s_in, int n_iter, int warm, double gain, int n_fit, void* lout, void* dout,
               int on_device) override {
         if (!s_in) {

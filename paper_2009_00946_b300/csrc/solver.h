@@ -95,6 +95,7 @@ class SolverBase {
     virtual int describe(char* buf, int len) = 0;
     virtual int set_trace(int on) = 0;
     virtual int get_trace(unsigned long long* out, int max_entries, int* slots, int* grid) = 0;
+    virtual int get_fine_trace(unsigned long long* out, int max_entries, int* per_cta, int* grid) = 0;
 
     HostSetup hs;
     cudaStream_t stream = 0;

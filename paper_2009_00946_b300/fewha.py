@@ -95,6 +95,8 @@ def lib():
                                  ctypes.POINTER(ci)]),
         "fewha_layers_noalloc": (ci, [vp, vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), vp, ctypes.c_char_p,
                                       ci]),
+        "fewha_get_fine_trace": (ci, [vp, ctypes.POINTER(ctypes.c_ulonglong), ci, ctypes.POINTER(ci),
+                                      ctypes.POINTER(ci)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -316,3 +318,18 @@ class Solver:
         self._check(lib().fewha_get_trace(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), n,
                                           ctypes.byref(slots), ctypes.byref(grid)))
         return out[:n].reshape(slots.value, grid.value, 2)
+
+    def fine_trace(self):
+        """Last fused launch: per CTA a list of (tag, ns) marks inside the phases."""
+        per, grid = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().fewha_get_fine_trace(self.h, None, 0, ctypes.byref(per), ctypes.byref(grid)))
+        n = per.value * grid.value
+        out = np.zeros(max(n, 1), np.uint64)
+        self._check(lib().fewha_get_fine_trace(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), n,
+                                               ctypes.byref(per), ctypes.byref(grid)))
+        rows = out[:n].reshape(grid.value, per.value)
+        marks = []
+        for r in rows:
+            r = r[r != 0]
+            marks.append([(int(v >> np.uint64(56)), int(v & np.uint64(0x00FFFFFFFFFFFFFF))) for v in r])
+        return marks
