@@ -39,6 +39,7 @@ constexpr int kMaxC = 16;
 constexpr int kMaxLayersFused = 64;
 constexpr int kMaxWfsFused = 16;
 constexpr int kFineCap = 1024;   // sub-phase marks per CTA per traced launch
+constexpr int kMaxKG = 4;        // P^T gather entries per layer row / column
 
 enum { kModeRhs = 0, kModeData = 1 };
 enum { kLpRhsStart = 0, kLpRhsRepl = 1, kLpReplStart = 2, kLpIter = 3 };
@@ -157,6 +158,44 @@ __device__ void grid_barrier(const FParams& P, unsigned& target, int* s_abort, i
     __syncthreads();
 }
 
+// 16-byte global -> shared copy that bypasses L1 (the source was written by
+// other SMs in this launch); both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Dot-product partials without per-element FP64 work (FP64 runs at a small
+// fraction of the FP32 rate on this part): a*b = p + e exactly (p = fl(a*b),
+// e = fma(a, b, -p)), and the running sum is kept as an unevaluated pair
+// hi + lo updated by TwoSum, so a thread's partial carries about 48 bits; the
+// partials are combined in FP64.
+// The _rn intrinsics keep the compiler from contracting these steps into FMAs,
+// which would break the error-free transforms.
+struct Acc2 {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = __fadd_rn(hi, x), bb = __fsub_rn(s, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb)));
+        hi = s;
+    }
+    // += a * b
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        add(p);
+        lo = __fadd_rn(lo, fmaf(a, b, -p));
+    }
+    // += a * b * c  (a*b split exactly first)
+    __device__ __forceinline__ void add_prod3(float a, float b, float c) {
+        const float p = __fmul_rn(a, b), e = fmaf(a, b, -p);
+        add_prod(p, c);
+        lo = __fadd_rn(lo, __fmul_rn(e, c));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 __device__ __forceinline__ double block_reduce(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -195,17 +234,20 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     float* rw = (float*)(roff + L * P.tile_rows);
     int* coff = (int*)(rw + L * P.tile_rows);
     float* cw = (float*)(coff + L * P.tile_cols);
-    double mu = 0.0;
+    Acc2 mu;
     const int ns2 = ns * ns;
     if (mode == kModeData) {
         if (tid < L) {
+            // window of layer tid: rows r0..r1, columns widened to 16-byte
+            // boundaries (c0 down, width up to a multiple of 4 floats; layer
+            // rows are multiples of 4 floats, so the widened window stays inside)
             const int base = I.tab_off[g * L + tid];
             const int r0 = I.cy[base + a_lo], r1 = I.cy[base + a_hi] + 1;
-            const int c0 = I.cx[base + b_lo], c1 = I.cx[base + b_hi] + 1;
+            const int c0 = I.cx[base + b_lo] & ~3, c1 = I.cx[base + b_hi] + 1;
             wdesc[tid * 5 + 0] = r0;
             wdesc[tid * 5 + 1] = c0;
             wdesc[tid * 5 + 2] = r1 - r0 + 1;
-            wdesc[tid * 5 + 3] = c1 - c0 + 1;
+            wdesc[tid * 5 + 3] = (c1 - c0 + 1 + 3) & ~3;
         }
         __syncthreads();
         if (tid == 0) {
@@ -217,27 +259,19 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             wdesc[L * 5 + 4] = o;
         }
         __syncthreads();
-        // windows of every layer, flattened, 8 loads in flight per thread
-        const int total = wdesc[L * 5 + 4];
-        for (int e0 = tid; e0 < total; e0 += 8 * NT) {
-            float v[8];
-            int d[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = e0 + u * NT;
-                d[u] = -1;
-                if (e < total) {
-                    int l = 0;
-                    while (l + 1 < L && wdesc[(l + 1) * 5 + 4] <= e) ++l;
-                    const int nc = wdesc[l * 5 + 3], r = e - wdesc[l * 5 + 4];
-                    const int rr = r / nc, cc = r - rr * nc, n = I.lay_n[l];
-                    v[u] = __ldcg(I.phi + I.lay_off[l] + (long)(wdesc[l * 5] + rr) * n + wdesc[l * 5 + 1] + cc);
-                    d[u] = e;
-                }
+        // 16-byte asynchronous copies (through L2, not L1): warps over rows,
+        // lanes over the float4 columns of a row
+        {
+            const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
+            for (int l = 0; l < L; ++l) {
+                const int nr = wdesc[l * 5 + 2], nc4 = wdesc[l * 5 + 3] >> 2, n = I.lay_n[l];
+                const float* src = I.phi + I.lay_off[l] + (long)wdesc[l * 5] * n + wdesc[l * 5 + 1];
+                float* dst = win + wdesc[l * 5 + 4];
+                for (int rr = warp; rr < nr; rr += nwarps)
+                    for (int c4 = lane; c4 < nc4; c4 += 32)
+                        cp_async16(dst + rr * (nc4 << 2) + (c4 << 2), src + (long)rr * n + (c4 << 2));
             }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (d[u] >= 0) win[d[u]] = v[u];
+            cp_async_wait_all();
         }
         for (int e = tid; e < L * (pr + pc); e += NT) {
             const int l = e / (pr + pc), k = e - l * (pr + pc);
@@ -277,7 +311,10 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             const float wm = I.mask[I.wfs_moff[g] + a * ns + b] ? w : 0.f;
             slx[e] = wm * sx;
             sly[e] = wm * sy;
-            if (want_mu && a >= W.i0 && b >= W.j0) mu += (double)wm * ((double)sx * sx + (double)sy * sy);
+            if (want_mu && a >= W.i0 && b >= W.j0) {
+                mu.add_prod3(wm, sx, sx);
+                mu.add_prod3(wm, sy, sy);
+            }
         }
     } else {
         const float w = I.wfs_w[g];
@@ -313,7 +350,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         out[i * np1 + j] = acc / 2;
     }
     if (want_mu) {
-        const double s = block_reduce(mu, red);
+        const double s = block_reduce(mu.value(), red);
         if (tid == 0) P.wpart[item] = s;
     }
     __syncthreads();
@@ -378,29 +415,34 @@ __device__ void fwd_dwt(const FParams& P, const Stripe& s, float* Z, float* P0, 
             }
         }
         csync(cl, multi);
-        const int cnt_c = nrows << lm;
-        for (int e0 = tid; e0 < cnt_c; e0 += kB * NT) {
-            float acc[kB];
+        // column pass: a thread produces kR consecutive output rows of one
+        // column from the 2 kR + 4 input rows they share (groups never
+        // straddle the a/d boundary: half and row0 are multiples of kR)
+        {
+            const int kR = min(4, min(R, half)), lkR = 31 - __clz(kR);
+            const int groups = nrows >> lkR, items = groups << lm;
+            for (int e = tid; e < items; e += NT) {
+                const int x = e & mask, grp = e >> lm;
+                const int row = s.row0 + (grp << lkR);
+                const int k0 = row < half ? row : row - half;
+                const float* f = row < half ? P.h : P.g;
+                float v[12];
 #pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int e = e0 + u * NT;
-                acc[u] = 0.f;
-                if (e < cnt_c) {
-                    const int rr = e >> lm, x = e & mask;
-                    const int row = s.row0 + rr;
-                    const int k = row < half ? row : row - half;
-                    const float* f = row < half ? P.h : P.g;
-#pragma unroll
-                    for (int t = 0; t < 6; ++t) {
-                        const int src = (2 * k + t) & mask;
-                        acc[u] += f[t] * rem[src >> lR][((src & (R - 1)) << ln) + x];
+                for (int i = 0; i < 12; ++i) {
+                    if (i < 2 * kR + 4) {
+                        const int src = (2 * k0 + i) & mask;
+                        v[i] = rem[src >> lR][((src & (R - 1)) << ln) + x];
                     }
                 }
-            }
 #pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int e = e0 + u * NT;
-                if (e < cnt_c) Z[((e >> lm) << ln) + (e & mask)] = acc[u];
+                for (int u = 0; u < 4; ++u) {
+                    if (u < kR) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int t = 0; t < 6; ++t) acc += f[t] * v[2 * u + t];
+                        Z[((row - s.row0 + u) << ln) + x] = acc;
+                    }
+                }
             }
         }
         const bool next_multi = (j < s.J) && (half > R);
@@ -420,29 +462,37 @@ __device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb
         float* Qj = (j & 1) ? Q1 : Q0;
         const int nrows = max(0, min(m - s.row0, R));
         const int cnt = nrows << lm;
-        for (int e0 = tid; e0 < cnt; e0 += kB * NT) {
-            float acc[kB];
+        // column pass: output rows i0 .. i0 + kR - 1 (i0 even) of one column
+        // need the a and d rows k0 - 2 .. k0 + kR/2 - 1 (k0 = i0 / 2); output
+        // i0 + u takes taps t = e + 2 s (e = u & 1) from rows k0 + u/2 - s
+        {
+            const int kR = min(4, R), lkR = 31 - __clz(kR), hmask = half - 1;
+            const int items = (nrows >> lkR) << lm;
+            for (int e = tid; e < items; e += NT) {
+                const int x = e & mask, i0 = s.row0 + ((e >> lm) << lkR), k0 = i0 >> 1;
+                float* const* ra = (x < half) ? remLL : remZ;
+                float va[4], vd[4];
 #pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int e = e0 + u * NT;
-                acc[u] = 0.f;
-                if (e < cnt) {
-                    const int i = s.row0 + (e >> lm), x = e & mask;
-                    float* const* ra = (x < half) ? remLL : remZ;
-#pragma unroll
-                    for (int t = 0; t < 6; ++t) {
-                        const int r = (i - t) & mask;
-                        if (r & 1) continue;
-                        const int k = r >> 1, kd = half + k;
-                        acc[u] += P.h[t] * ra[k >> lR][((k & (R - 1)) << ln) + x] +
-                                  P.g[t] * remZ[kd >> lR][((kd & (R - 1)) << ln) + x];
+                for (int mm = 0; mm < 4; ++mm) {
+                    if (mm < (kR >> 1) + 2) {
+                        const int k = (k0 - 2 + mm) & hmask, kd = half + k;
+                        va[mm] = ra[k >> lR][((k & (R - 1)) << ln) + x];
+                        vd[mm] = remZ[kd >> lR][((kd & (R - 1)) << ln) + x];
                     }
                 }
-            }
 #pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int e = e0 + u * NT;
-                if (e < cnt) Pb[((e >> lm) << ln) + (e & mask)] = acc[u];
+                for (int u = 0; u < 4; ++u) {
+                    if (u < kR) {
+                        const int ee = u & 1;
+                        float acc = 0.f;
+#pragma unroll
+                        for (int sgrp = 0; sgrp < 3; ++sgrp) {
+                            const int idx = (u >> 1) - sgrp + 2;
+                            acc += P.h[ee + 2 * sgrp] * va[idx] + P.g[ee + 2 * sgrp] * vd[idx];
+                        }
+                        Pb[((i0 - s.row0 + u) << ln) + x] = acc;
+                    }
+                }
             }
         }
         __syncthreads();
@@ -486,12 +536,28 @@ __device__ void alg2_scalars(const FParams& P, const FInst& I, int k, double* sh
         const int lane = threadIdx.x, C = P.C, par = k & 1;
         const double* lp = P.lpart + (size_t)par * P.n_litems * C * 2;
         double rho = 0.0, mu = 0.0;
-        // written by other CTAs in this launch: read through L2, never L1
-        for (int e = lane; e < I.nl * C; e += 32) {
-            rho += __ldcg(lp + ((size_t)I.l0 * C + e) * 2 + 0);
-            mu += __ldcg(lp + ((size_t)I.l0 * C + e) * 2 + 1);
+        // written by other CTAs in this launch: read through L2, never L1;
+        // up to 8 entries per lane per round, all loads issued before the adds
+        const int nlc = I.nl * C;
+        for (int e0 = lane; e0 < nlc; e0 += 8 * 32) {
+            double2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = (e0 + 32 * u < nlc) ? __ldcg((const double2*)(lp + ((size_t)I.l0 * C + e0 + 32 * u) * 2))
+                                           : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                rho += v[u].x;
+                mu += v[u].y;
+            }
         }
-        for (int e = lane; e < I.nw; e += 32) mu += __ldcg(P.wpart + I.w0 + e);
+        for (int e0 = lane; e0 < I.nw; e0 += 8 * 32) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (e0 + 32 * u < I.nw) ? __ldcg(P.wpart + I.w0 + e0 + 32 * u) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mu += v[u];
+        }
         for (int o = 16; o > 0; o >>= 1) {
             rho += __shfl_down_sync(0xffffffffu, rho, o);
             mu += __shfl_down_sync(0xffffffffu, mu, o);
@@ -530,7 +596,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     const int R = n / C, row0 = rank * R;
     const int tid = threadIdx.x, NT = blockDim.x, G = I.G, L = I.L;
     const int SF = P.stripe_floats;
-    __shared__ int sgi[4 * kMaxWfsFused];
+    __shared__ int sgi[8 * kMaxWfsFused];
     fmark(P, 10);
     float* Z = sm;
     float* B1 = sm + SF;
@@ -545,34 +611,40 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     // ---- P^T: gather of the sensor fields into the own rows ----
     {
         if (tid < G) {
-            // staged row range, staging offset and row length of sensor tid
-            const int2 rg = P.stg[LI.stg + rank * G + tid];
-            int so = 0;
-            for (int g = 0; g < tid; ++g) {
+            // staged rows imin..imax-1 of sensor tid are one contiguous range of
+            // the field array; it is copied from the 16-byte boundary below its
+            // start, so its data begin (start & 3) floats into its staging slot
+            auto range = [&](int g, int& a0, int& c4, int& s0) {
                 const int2 r2 = P.stg[LI.stg + rank * G + g];
-                so += (r2.y - r2.x) * (I.wfs_n[g] + 1);
+                const int np1 = I.wfs_n[g] + 1;
+                s0 = I.wfs_noff[g] + r2.x * np1;
+                const int e0 = I.wfs_noff[g] + r2.y * np1;
+                a0 = s0 & ~3;
+                c4 = (r2.y > r2.x) ? (e0 - a0 + 3) >> 2 : 0;
+            };
+            int so = 0, a0, c4, s0;
+            for (int g = 0; g < tid; ++g) {
+                range(g, a0, c4, s0);
+                so += c4 << 2;
             }
-            sgi[tid * 4 + 0] = rg.x;
-            sgi[tid * 4 + 1] = rg.y;
-            sgi[tid * 4 + 2] = so;
-            sgi[tid * 4 + 3] = I.wfs_n[tid] + 1;
+            range(tid, a0, c4, s0);
+            const int2 rg = P.stg[LI.stg + rank * G + tid];
+            sgi[tid * 8 + 0] = rg.x;
+            sgi[tid * 8 + 1] = rg.y;
+            sgi[tid * 8 + 2] = so + (s0 - a0);
+            sgi[tid * 8 + 3] = I.wfs_n[tid] + 1;
+            sgi[tid * 8 + 4] = a0;
+            sgi[tid * 8 + 5] = c4;
+            sgi[tid * 8 + 6] = so;
         }
         __syncthreads();
-        // rows of the sensor fields (8 loads in flight per thread)
         for (int g = 0; g < G; ++g) {
-            const int cnt = (sgi[g * 4 + 1] - sgi[g * 4]) * sgi[g * 4 + 3];
-            const float* src = I.psi + I.wfs_noff[g] + sgi[g * 4] * sgi[g * 4 + 3];
-            float* dst = stg + sgi[g * 4 + 2];
-            for (int e0 = tid; e0 < cnt; e0 += 8 * NT) {
-                float v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (e0 + u * NT < cnt) v[u] = __ldcg(src + e0 + u * NT);
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (e0 + u * NT < cnt) dst[e0 + u * NT] = v[u];
-            }
+            const int c4 = sgi[g * 8 + 5];
+            const float* src = I.psi + sgi[g * 8 + 4];
+            float* dst = stg + sgi[g * 8 + 6];
+            for (int e = tid; e < c4; e += NT) cp_async16(dst + (e << 2), src + (e << 2));
         }
+        cp_async_wait_all();
         // compact gather tables: columns for every sensor, rows of this stripe
         for (int e = tid; e < G * n * KG; e += NT) {
             const int g = e / (n * KG), r = e - g * n * KG;
@@ -584,35 +656,51 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
         }
         __syncthreads();
         fmark(P, 11);
-        for (int e0 = tid; e0 < (R << ln); e0 += 2 * NT) {
-            float acc[2] = {0.f, 0.f};
+        // each thread keeps one layer column q and walks rows rr0, rr0 + rstep,
+        // ...; per sensor the column weights are read once for all its rows
+        constexpr int kRows = 8;
+        const int qpt = min(n, NT), rstep = NT / qpt;
+        for (int qb = 0; qb < n; qb += qpt) {
+            const int q = qb + tid % qpt, rr0 = tid / qpt;
+            if (rr0 >= rstep) continue;
+            for (int rb = rr0; rb < R; rb += rstep * kRows) {
+                float acc[kRows];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int e = e0 + u * NT;
-                if (e >= (R << ln)) break;
-                const int rr = e >> ln, q = e & (n - 1);
+                for (int u = 0; u < kRows; ++u) acc[u] = 0.f;
                 for (int g = 0; g < G; ++g) {
-                    const int imin = sgi[g * 4], imax = sgi[g * 4 + 1];
+                    const int imin = sgi[g * 8], imax = sgi[g * 8 + 1];
                     if (imax <= imin) continue;
-                    const int np1 = sgi[g * 4 + 3];
-                    const float* base = stg + sgi[g * 4 + 2];
-                    const int2* xq = xt + ((g * n + q) * KG);
-                    const int2* yr = yt + ((g * R + rr) * KG);
-                    for (int a = 0; a < KG; ++a) {
-                        const int2 ye = yr[a];
-                        const float* row = base + max(ye.x - imin, 0) * np1;
-                        float racc = 0.f;
-                        for (int b = 0; b < KG; ++b) {
-                            const int2 xe = xq[b];
-                            racc += __int_as_float(xe.y) * row[xe.x];
+                    const int np1 = sgi[g * 8 + 3];
+                    const float* base = stg + sgi[g * 8 + 2] - imin * np1;
+                    int xj[kMaxKG];
+                    float xw[kMaxKG];
+#pragma unroll
+                    for (int b = 0; b < kMaxKG; ++b) {
+                        const int2 xe = b < KG ? xt[(g * n + q) * KG + b] : make_int2(0, 0);
+                        xj[b] = xe.x;
+                        xw[b] = __int_as_float(xe.y);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRows; ++u) {
+                        const int rr = rb + u * rstep;
+                        if (rr >= R) break;
+                        const int2* yr = yt + (g * R + rr) * KG;
+                        for (int a = 0; a < KG; ++a) {
+                            const int2 ye = yr[a];
+                            const float* row = base + max(ye.x, imin) * np1;
+                            float racc = 0.f;
+#pragma unroll
+                            for (int b = 0; b < kMaxKG; ++b) racc += xw[b] * row[xj[b]];
+                            acc[u] += __int_as_float(ye.y) * racc;
                         }
-                        acc[u] += __int_as_float(ye.y) * racc;
                     }
                 }
-            }
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-                if (e0 + u * NT < (R << ln)) Z[e0 + u * NT] = acc[u];
+                for (int u = 0; u < kRows; ++u) {
+                    const int rr = rb + u * rstep;
+                    if (rr < R) Z[(rr << ln) + q] = acc[u];
+                }
+            }
         }
     }
 
@@ -622,11 +710,34 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     fmark(P, 13);
 
     // ---- elementwise (Alg. 1 restart / Alg. 2 update) ----
-    double alpha = 0.0, beta = 0.0;
+    const bool last = (mode == kLpIter) && (k + 1 >= P.n_iter);
+    const bool make_z = (mode == kLpRhsStart) || (mode == kLpReplStart) || (mode == kLpIter && !last);
+    Acc2 rho_p, dz_p;
+    const long gbase = (long)off + (long)row0 * n;
     if (mode == kLpIter) {
+        // the state does not depend on the scalars: its first batch is loaded
+        // before the scalar reduction so the two latencies overlap
+        constexpr int kE = 4;
+        const int total = R * n;
+        float vr[kE], vp[kE], vq[kE], vc[kE], vj[kE], va[kE];
+        auto load = [&](int e0) {
+#pragma unroll
+            for (int u = 0; u < kE; ++u) {
+                const int e = e0 + u * NT;
+                if (e < total) {
+                    const long i = gbase + e;
+                    vr[u] = I.r[i];
+                    vp[u] = I.p[i];
+                    vq[u] = I.q[i];
+                    vc[u] = I.c[i];
+                    vj[u] = __ldg(I.Jinv + i);
+                    va[u] = __ldg(I.aD + i);
+                }
+            }
+        };
+        load(tid);
         alg2_scalars(P, I, k, sh);
-        alpha = sh[0];
-        beta = sh[1];
+        const double alpha = sh[0], beta = sh[1];
         if (tid == 0 && li == I.l0 && rank == 0) {
             double* sw = I.scal + (k & 1) * 2;
             sw[0] = sh[2];
@@ -639,14 +750,37 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
                 I.sc_out[kAlphaK] = alpha;
             }
         }
+        const float fa = (float)alpha, fb = (float)beta;
+        for (int e0 = tid; e0 < total; e0 += kE * NT) {
+            if (e0 != tid) load(e0);
+#pragma unroll
+            for (int u = 0; u < kE; ++u) {
+                const int e = e0 + u * NT;
+                if (e >= total) break;
+                const long i = gbase + e;
+                const float z = vj[u] * vr[u];
+                const float sv = Z[e] + va[u] * z;
+                const float pv = (k == 0) ? z : z + fb * vp[u];
+                const float qv = (k == 0) ? sv : sv + fb * vq[u];
+                const float cv = vc[u] + fa * pv;
+                const float rv = vr[u] - fa * qv;
+                I.p[i] = pv;
+                I.q[i] = qv;
+                I.c[i] = cv;
+                I.r[i] = rv;
+                float zout;
+                if (!last) {
+                    zout = vj[u] * rv;
+                    rho_p.add_prod(rv, zout);
+                    dz_p.add_prod3(va[u], zout, zout);
+                } else {
+                    zout = cv;
+                }
+                Z[e] = zout;
+            }
+        }
     }
-    const bool last = (mode == kLpIter) && (k + 1 >= P.n_iter);
-    const bool make_z = (mode == kLpRhsStart) || (mode == kLpReplStart) || (mode == kLpIter && !last);
-    double rho_p = 0.0, dz_p = 0.0;
-    const long gbase = (long)off + (long)row0 * n;
-    const float fa = (float)alpha, fb = (float)beta;
-#pragma unroll 4
-    for (int e = tid; e < R * n; e += NT) {
+    for (int e = tid; mode != kLpIter && e < R * n; e += NT) {
         const long i = gbase + e;
         const float jinv = __ldg(I.Jinv + i), ad = __ldg(I.aD + i);
         float zout = 0.f;
@@ -663,8 +797,8 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             I.bprev[i] = bv;
             I.r[i] = rv;
             zout = jinv * rv;
-            rho_p += (double)rv * zout;
-            dz_p += (double)ad * zout * zout;
+            rho_p.add_prod(rv, zout);
+            dz_p.add_prod3(ad, zout, zout);
         } else if (mode == kLpRhsRepl) {
             I.b[i] = Z[e];
             zout = I.c[i];
@@ -676,34 +810,15 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             I.bprev[i] = bv;
             I.r[i] = rv;
             zout = jinv * rv;
-            rho_p += (double)rv * zout;
-            dz_p += (double)ad * zout * zout;
-        } else {
-            const float rold = I.r[i];
-            const float z = jinv * rold;
-            const float sv = Z[e] + ad * z;
-            const float pv = (k == 0) ? z : z + fb * I.p[i];
-            const float qv = (k == 0) ? sv : sv + fb * I.q[i];
-            const float cv = I.c[i] + fa * pv;
-            const float rv = rold - fa * qv;
-            I.p[i] = pv;
-            I.q[i] = qv;
-            I.c[i] = cv;
-            I.r[i] = rv;
-            if (!last) {
-                zout = jinv * rv;
-                rho_p += (double)rv * zout;
-                dz_p += (double)ad * zout * zout;
-            } else {
-                zout = cv;
-            }
+            rho_p.add_prod(rv, zout);
+            dz_p.add_prod3(ad, zout, zout);
         }
         Z[e] = zout;
     }
     if (make_z) {
         const int par = (mode == kLpIter) ? ((k + 1) & 1) : 0;
-        const double rs = block_reduce(rho_p, red);
-        const double ds = block_reduce(dz_p, red);
+        const double rs = block_reduce(rho_p.value(), red);
+        const double ds = block_reduce(dz_p.value(), red);
         if (tid == 0) {
             double* lp = P.lpart + ((size_t)par * P.n_litems * C + (size_t)li * C + rank) * 2;
             lp[0] = rs;
@@ -904,6 +1019,10 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
                 KG = std::max(KG, hs.ihi[gb + q] - hs.ilo[gb + q]);
             }
         }
+    if (KG > kMaxKG) {
+        err = "layer grid much finer than the sensor grid (more than 4 samples per layer cell pair)";
+        return nullptr;
+    }
     std::vector<int2> gtab;
     std::vector<int> gtab_off((size_t)hs.G * hs.L);
     auto fbits = [](float f) {
@@ -933,7 +1052,7 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
 
     FusedPlan* best = nullptr;
     for (int C : {8, 4, 16, 2, 1}) {
-        if (C > nmin) continue;
+        if (2 * C > nmin) continue;   // stripes of at least 2 rows
         if ((size_t)nmax * nmax / C * 4 * sizeof(float) > smem_cap) continue;
         auto* pl = new FusedPlan();
         pl->C = C;
@@ -957,7 +1076,7 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
                     }
                     if (lo >= hi) lo = hi = 0;
                     stg.push_back(make_int2(lo, hi));
-                    tot += (hi - lo) * (hs.wfs[g].n + 1);
+                    tot += (hi - lo) * (hs.wfs[g].n + 1) + 8;   // + 16-byte alignment slack
                 }
                 stage_max = std::max(stage_max, tot);
             }
@@ -1023,7 +1142,8 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
             for (int l = 0; l < hs.L; ++l) {
                 const int base = hs.tab_off[w.g * hs.L + l];
                 const int nr = hs.cy[base + a_hi] + 1 - hs.cy[base + a_lo] + 1;
-                const int nc = hs.cx[base + b_hi] + 1 - hs.cx[base + b_lo] + 1;
+                const int c0 = hs.cx[base + b_lo] & ~3;   // as in the kernel: 16-byte aligned
+                const int nc = (hs.cx[base + b_hi] + 1 - c0 + 1 + 3) & ~3;
                 win += nr * nc;
             }
             win_max = std::max(win_max, win);
@@ -1082,7 +1202,8 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         I.KG = KG;
         int2* d_gtab = nullptr;
         int* d_gtab_off = nullptr;
-        bool ok = dalloc(pl, I.psi, hs.NW, err) && dalloc(pl, I.scal, 4, err) && dupload(pl, d_gtab, gtab, err) &&
+        // sensor fields (+8 floats: aligned copies may read up to 3 past the end)
+        bool ok = dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) && dupload(pl, d_gtab, gtab, err) &&
                   dupload(pl, d_gtab_off, gtab_off, err);
         I.gtab = d_gtab;
         I.gtab_off = d_gtab_off;
