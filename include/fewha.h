@@ -175,6 +175,19 @@ int fewha_sync(fewha_handle* h);
  * barrier expire at once; used to exercise the TIMEOUT path).  Default 2^31. */
 int fewha_set_barrier_budget(fewha_handle* h, long long cycles);
 
+/* Fused-path shape (FP32 handles): rebuild the plan with thread-block
+ * clusters of cluster_size CTAs per layer (1, 2, 4, 8 or 16).  Errors: ARG
+ * if no plan of that size fits the geometry or the device. */
+int fewha_set_cluster_size(fewha_handle* h, int cluster_size);
+
+/* Autotuner of the fused path: times every feasible cluster shape on the
+ * current frame (set_frame first) for n_iter warm-started iterations, reps
+ * timed launches each (CUDA events, median), keeps the fastest and restores
+ * the solver state (c, r, b) it found.  report (len bytes, may be NULL)
+ * receives the timings.  Synchronises.  Errors: STATE (FP64 handle or no
+ * frame), ARG. */
+int fewha_autotune(fewha_handle* h, int n_iter, int reps, char* report, int len);
+
 /* Kernel launches enqueued by this handle since creation (all paths). */
 long long fewha_launch_count(const fewha_handle* h);
 

@@ -185,6 +185,18 @@ int fewha_get_fine_trace(fewha_handle* h, unsigned long long* out, int max_entri
     return done(h, h->s->get_fine_trace(out, max_entries, per_cta, grid));
 }
 
+int fewha_set_cluster_size(fewha_handle* h, int cluster_size) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 && cluster_size != 16)
+        return fail(h, FEWHA_ERR_ARG, "cluster size must be 1, 2, 4, 8 or 16");
+    return done(h, h->s->set_cluster_size(cluster_size));
+}
+
+int fewha_autotune(fewha_handle* h, int n_iter, int reps, char* report, int len) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->autotune(n_iter, reps, report, len));
+}
+
 long long fewha_launch_count(const fewha_handle* h) {
     if (!h) return -1;
     return h->s->launches;

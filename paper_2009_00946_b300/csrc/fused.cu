@@ -982,7 +982,72 @@ void make_tiles(int inst, int g, int np1, int nty, int ntx, std::vector<WItem>& 
 
 }  // namespace
 
-FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const FusedBuffers& fb, std::string& err) {
+namespace {
+
+// Per-instance host tables of the fused path: compact P^T gather tables.
+struct InstPrep {
+    int KG = 1, nmin = 1 << 30, nmax = 0;
+    std::vector<int2> gtab;
+    std::vector<int> gtab_off;
+};
+
+// For layer column q the sensor columns j with cell_j in {q-1, q} and their
+// bilinear weights (1 - t if cell_j == q, t if cell_j == q-1), padded to KG
+// entries (weight 0, index 0 for columns / -1 for rows); the same for rows.
+bool prep_instance(const HostSetup& hs, InstPrep& ip, std::string& err) {
+    if (hs.L > kMaxLayersFused || hs.G > kMaxWfsFused) {
+        err = "too many layers or sensors for the fused path";
+        return false;
+    }
+    for (auto& L : hs.lay) {
+        ip.nmin = std::min(ip.nmin, L.n);
+        ip.nmax = std::max(ip.nmax, L.n);
+    }
+    for (int g = 0; g < hs.G; ++g)
+        for (int l = 0; l < hs.L; ++l) {
+            const int gb = hs.gat_off[g * hs.L + l];
+            for (int q = 0; q < hs.lay[l].n; ++q) {
+                ip.KG = std::max(ip.KG, hs.jhi[gb + q] - hs.jlo[gb + q]);
+                ip.KG = std::max(ip.KG, hs.ihi[gb + q] - hs.ilo[gb + q]);
+            }
+        }
+    if (ip.KG > kMaxKG) {
+        err = "layer grid much finer than the sensor grid (more than 4 samples per layer cell pair)";
+        return false;
+    }
+    auto fbits = [](float f) {
+        int i;
+        std::memcpy(&i, &f, sizeof i);
+        return i;
+    };
+    ip.gtab_off.assign((size_t)hs.G * hs.L, 0);
+    for (int g = 0; g < hs.G; ++g)
+        for (int l = 0; l < hs.L; ++l) {
+            const int n = hs.lay[l].n, base = hs.tab_off[g * hs.L + l], gb = hs.gat_off[g * hs.L + l];
+            ip.gtab_off[g * hs.L + l] = (int)ip.gtab.size();
+            for (int axis = 0; axis < 2; ++axis) {
+                const int* lo = axis ? hs.ilo.data() : hs.jlo.data();
+                const int* hi = axis ? hs.ihi.data() : hs.jhi.data();
+                const int* cell = axis ? hs.cy.data() : hs.cx.data();
+                const double* t = axis ? hs.ty.data() : hs.tx.data();
+                for (int q = 0; q < n; ++q) {
+                    int cnt = 0;
+                    for (int k = lo[gb + q]; k < hi[gb + q]; ++k, ++cnt) {
+                        const float w = cell[base + k] == q ? (float)(1.0 - t[base + k]) : (float)t[base + k];
+                        ip.gtab.push_back(make_int2(k, fbits(w)));
+                    }
+                    for (; cnt < ip.KG; ++cnt) ip.gtab.push_back(make_int2(axis ? -1 : 0, fbits(0.f)));
+                }
+            }
+        }
+    return true;
+}
+
+}  // namespace
+
+FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const std::vector<DevGeo<float>>& Gs,
+                              const std::vector<FusedBuffers>& fbs, int max_tile_side, std::string& err,
+                              int forced_C) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceProp prop;
@@ -994,103 +1059,73 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         err = "the fused path needs thread-block clusters (sm_90 or newer)";
         return nullptr;
     }
-    if (hs.L > kMaxLayersFused || hs.G > kMaxWfsFused) {
-        err = "too many layers or sensors for the fused path";
+    const int ninst = (int)hss.size();
+    if (ninst < 1 || (int)Gs.size() != ninst || (int)fbs.size() != ninst) {
+        err = "no instances";
         return nullptr;
     }
-    int nmin = 1 << 30, nmax = 0;
-    for (auto& L : hs.lay) {
-        nmin = std::min(nmin, L.n);
-        nmax = std::max(nmax, L.n);
+    std::vector<InstPrep> preps(ninst);
+    int nmin = 1 << 30, nmax = 0, KGmax = 1, Gmax = 0, Lmax = 0, Gtot = 0;
+    for (int i = 0; i < ninst; ++i) {
+        if (!prep_instance(*hss[i], preps[i], err)) return nullptr;
+        nmin = std::min(nmin, preps[i].nmin);
+        nmax = std::max(nmax, preps[i].nmax);
+        KGmax = std::max(KGmax, preps[i].KG);
+        Gmax = std::max(Gmax, hss[i]->G);
+        Lmax = std::max(Lmax, hss[i]->L);
+        Gtot += hss[i]->G;
     }
     const int sms = prop.multiProcessorCount;
     const size_t smem_cap = (size_t)prop.sharedMemPerBlockOptin - 4096;
 
-    // compact P^T gather tables: for layer column q the sensor columns j with
-    // cell_j in {q-1, q} and their bilinear weights (1 - t if cell_j == q,
-    // t if cell_j == q-1), padded to KG entries (weight 0, index 0 / -1);
-    // the same for rows
-    int KG = 1;
-    for (int g = 0; g < hs.G; ++g)
-        for (int l = 0; l < hs.L; ++l) {
-            const int gb = hs.gat_off[g * hs.L + l];
-            for (int q = 0; q < hs.lay[l].n; ++q) {
-                KG = std::max(KG, hs.jhi[gb + q] - hs.jlo[gb + q]);
-                KG = std::max(KG, hs.ihi[gb + q] - hs.ilo[gb + q]);
-            }
-        }
-    if (KG > kMaxKG) {
-        err = "layer grid much finer than the sensor grid (more than 4 samples per layer cell pair)";
-        return nullptr;
-    }
-    std::vector<int2> gtab;
-    std::vector<int> gtab_off((size_t)hs.G * hs.L);
-    auto fbits = [](float f) {
-        int i;
-        std::memcpy(&i, &f, sizeof i);
-        return i;
-    };
-    for (int g = 0; g < hs.G; ++g)
-        for (int l = 0; l < hs.L; ++l) {
-            const int n = hs.lay[l].n, base = hs.tab_off[g * hs.L + l], gb = hs.gat_off[g * hs.L + l];
-            gtab_off[g * hs.L + l] = (int)gtab.size();
-            for (int axis = 0; axis < 2; ++axis) {
-                const int* lo = axis ? hs.ilo.data() : hs.jlo.data();
-                const int* hi = axis ? hs.ihi.data() : hs.jhi.data();
-                const int* cell = axis ? hs.cy.data() : hs.cx.data();
-                const double* t = axis ? hs.ty.data() : hs.tx.data();
-                for (int q = 0; q < n; ++q) {
-                    int cnt = 0;
-                    for (int k = lo[gb + q]; k < hi[gb + q]; ++k, ++cnt) {
-                        const float w = cell[base + k] == q ? (float)(1.0 - t[base + k]) : (float)t[base + k];
-                        gtab.push_back(make_int2(k, fbits(w)));
-                    }
-                    for (; cnt < KG; ++cnt) gtab.push_back(make_int2(axis ? -1 : 0, fbits(0.f)));
-                }
-            }
-        }
-
     FusedPlan* best = nullptr;
     for (int C : {8, 4, 16, 2, 1}) {
+        if (forced_C > 0 && C != forced_C) continue;
         if (2 * C > nmin) continue;   // stripes of at least 2 rows
         if ((size_t)nmax * nmax / C * 4 * sizeof(float) > smem_cap) continue;
         auto* pl = new FusedPlan();
         pl->C = C;
-        // items
+        // layer items (instance, layer) with the staged sensor rows per rank
         std::vector<LItem> litems;
         std::vector<int2> stg;
+        std::vector<int> l0(ninst), nl(ninst);
         int stage_max = 0;
-        for (int l = 0; l < hs.L; ++l) {
-            LItem li{0, l, (int)stg.size()};
-            const int n = hs.lay[l].n, R = n / C;
-            for (int rank = 0; rank < C; ++rank) {
-                int tot = 0;
-                for (int g = 0; g < hs.G; ++g) {
-                    const int gb = hs.gat_off[g * hs.L + l];
-                    int lo = 1 << 30, hi = 0;
-                    for (int p = rank * R; p < (rank + 1) * R; ++p) {
-                        if (hs.ihi[gb + p] > hs.ilo[gb + p]) {
-                            lo = std::min(lo, hs.ilo[gb + p]);
-                            hi = std::max(hi, hs.ihi[gb + p]);
+        for (int i = 0; i < ninst; ++i) {
+            const HostSetup& hs = *hss[i];
+            l0[i] = (int)litems.size();
+            for (int l = 0; l < hs.L; ++l) {
+                LItem li{i, l, (int)stg.size()};
+                const int n = hs.lay[l].n, R = n / C;
+                for (int rank = 0; rank < C; ++rank) {
+                    int tot = 0;
+                    for (int g = 0; g < hs.G; ++g) {
+                        const int gb = hs.gat_off[g * hs.L + l];
+                        int lo = 1 << 30, hi = 0;
+                        for (int p = rank * R; p < (rank + 1) * R; ++p) {
+                            if (hs.ihi[gb + p] > hs.ilo[gb + p]) {
+                                lo = std::min(lo, hs.ilo[gb + p]);
+                                hi = std::max(hi, hs.ihi[gb + p]);
+                            }
                         }
+                        if (lo >= hi) lo = hi = 0;
+                        stg.push_back(make_int2(lo, hi));
+                        tot += (hi - lo) * (hs.wfs[g].n + 1) + 8;   // + 16-byte alignment slack
                     }
-                    if (lo >= hi) lo = hi = 0;
-                    stg.push_back(make_int2(lo, hi));
-                    tot += (hi - lo) * (hs.wfs[g].n + 1) + 8;   // + 16-byte alignment slack
+                    stage_max = std::max(stage_max, tot);
                 }
-                stage_max = std::max(stage_max, tot);
+                litems.push_back(li);
             }
-            litems.push_back(li);
+            nl[i] = (int)litems.size() - l0[i];
         }
         const int stripe = nmax * nmax / C;
         const int Rmax = nmax / C;
         stage_max = (stage_max + 3) & ~3;
-        const size_t gtab_floats = 2 * (size_t)hs.G * nmax * KG + 2 * (size_t)hs.G * Rmax * KG;
+        const size_t gtab_floats = 2 * (size_t)Gmax * nmax * KGmax + 2 * (size_t)Gmax * Rmax * KGmax;
         const size_t layer_floats = 4 * (size_t)stripe + stage_max + gtab_floats;
 
         // co-resident clusters: one 512-thread CTA per SM (register-limited),
-        // so the answer does not depend on the shared memory below the cap
-        // the attribute is per function: allow the device maximum once for all plans
+        // so the answer does not depend on the shared memory below the cap;
+        // the attribute is per function: allow the device maximum once
         const FusedKernel kern = fused_kernel_for(C);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
         if (C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1109,28 +1144,37 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         pl->nclusters = std::max(1, std::min(ncl, std::max(1, sms / C)));
         pl->grid = pl->nclusters * C;
 
-        // sensor tiles: at most one round over the grid, near-square tiles
+        // sensor tiles: near-square, about one round over the grid, and with
+        // max_tile_side > 0 no side longer than that (bounded windows)
         std::vector<WItem> witems;
-        const int per = std::max(1, pl->grid / std::max(1, hs.G));
-        for (int g = 0; g < hs.G; ++g) {
-            const int np1 = hs.wfs[g].n + 1;
-            int best_ty = 1, best_tx = 1;
-            double best_cost = 1e30;
-            for (int ty = 1; ty <= std::min(per, np1); ++ty)
-                for (int tx = 1; tx <= std::min(per / ty, np1); ++tx) {
-                    // cost: the largest tile with its halo (rounds are 1 by construction)
-                    const double h = std::ceil((double)np1 / ty) + 2, w = std::ceil((double)np1 / tx) + 2;
-                    const double cost = h * w + 0.5 * (h + w);
-                    if (cost < best_cost) {
-                        best_cost = cost;
-                        best_ty = ty;
-                        best_tx = tx;
+        std::vector<int> w0(ninst), nw(ninst);
+        const int per = std::max(1, pl->grid / std::max(1, Gtot));
+        for (int i = 0; i < ninst; ++i) {
+            const HostSetup& hs = *hss[i];
+            w0[i] = (int)witems.size();
+            for (int g = 0; g < hs.G; ++g) {
+                const int np1 = hs.wfs[g].n + 1;
+                const int tmin = max_tile_side > 0 ? (np1 + max_tile_side - 1) / max_tile_side : 1;
+                const int budget = std::max(per, tmin * tmin);
+                int best_ty = tmin, best_tx = tmin;
+                double best_cost = 1e30;
+                for (int ty = tmin; ty <= std::min(budget, np1); ++ty)
+                    for (int tx = tmin; tx <= std::min(budget / ty, np1); ++tx) {
+                        const double h = std::ceil((double)np1 / ty) + 2, w = std::ceil((double)np1 / tx) + 2;
+                        const double cost = h * w + 0.5 * (h + w);
+                        if (cost < best_cost) {
+                            best_cost = cost;
+                            best_ty = ty;
+                            best_tx = tx;
+                        }
                     }
-                }
-            make_tiles(0, g, np1, best_ty, best_tx, witems);
+                make_tiles(i, g, np1, best_ty, best_tx, witems);
+            }
+            nw[i] = (int)witems.size() - w0[i];
         }
         int tile_nodes = 0, tile_sub = 0, win_max = 0, tile_rows = 0, tile_cols = 0;
         for (auto& w : witems) {
+            const HostSetup& hs = *hss[w.inst];
             const int ns = hs.wfs[w.g].n;
             const int a_lo = std::max(w.i0 - 1, 0), a_hi = std::min(w.i1, ns);
             const int b_lo = std::max(w.j0 - 1, 0), b_hi = std::min(w.j1, ns);
@@ -1152,65 +1196,72 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         tile_sub = (tile_sub + 3) & ~3;
         win_max = (win_max + 3) & ~3;
         const size_t sensor_floats = (size_t)win_max + tile_nodes + 2 * (size_t)tile_sub +
-                                     2 * (size_t)hs.L * (tile_rows + tile_cols);
+                                     2 * (size_t)Lmax * (tile_rows + tile_cols);
         const size_t smem = std::max(layer_floats, sensor_floats) * sizeof(float);
         if (smem > smem_cap) {
+            if (err.empty()) err = "the staged windows do not fit in shared memory";
             delete pl;
             continue;
         }
         pl->smem = (int)smem;
 
         // device data
-        FInst I{};
-        I.L = hs.L;
-        I.G = hs.G;
-        I.N = (int)hs.N;
-        I.NW = (int)hs.NW;
-        I.lay_n = G.lay_n;
-        I.lay_J = G.lay_J;
-        I.lay_off = G.lay_off;
-        I.wfs_n = G.wfs_n;
-        I.wfs_soff = G.wfs_soff;
-        I.wfs_noff = G.wfs_noff;
-        I.wfs_moff = G.wfs_moff;
-        I.wfs_w = G.wfs_w;
-        I.mask = G.mask;
-        I.tab_off = G.tab_off;
-        I.cx = G.cx;
-        I.cy = G.cy;
-        I.tx = G.tx;
-        I.ty = G.ty;
-        I.gat_off = G.gat_off;
-        I.jlo = G.jlo;
-        I.jhi = G.jhi;
-        I.ilo = G.ilo;
-        I.ihi = G.ihi;
-        I.Jinv = fb.Jinv;
-        I.aD = fb.aD;
-        I.c = fb.c;
-        I.r = fb.r;
-        I.p = fb.p;
-        I.q = fb.q;
-        I.b = fb.b;
-        I.bprev = fb.bprev;
-        I.phi = fb.phi;
-        I.sc_out = fb.sc;
-        I.w0 = 0;
-        I.nw = (int)witems.size();
-        I.l0 = 0;
-        I.nl = (int)litems.size();
-        I.KG = KG;
-        int2* d_gtab = nullptr;
-        int* d_gtab_off = nullptr;
-        // sensor fields (+8 floats: aligned copies may read up to 3 past the end)
-        bool ok = dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) && dupload(pl, d_gtab, gtab, err) &&
-                  dupload(pl, d_gtab_off, gtab_off, err);
-        I.gtab = d_gtab;
-        I.gtab_off = d_gtab_off;
-        if (ok) cudaMemset(I.scal, 0, 4 * sizeof(double));
-        I.slopes = fb.slopes;
-        pl->psi = I.psi;
-        pl->inst.push_back(I);
+        bool ok = true;
+        for (int i = 0; i < ninst && ok; ++i) {
+            const HostSetup& hs = *hss[i];
+            const DevGeo<float>& G = Gs[i];
+            const FusedBuffers& fb = fbs[i];
+            FInst I{};
+            I.L = hs.L;
+            I.G = hs.G;
+            I.N = (int)hs.N;
+            I.NW = (int)hs.NW;
+            I.lay_n = G.lay_n;
+            I.lay_J = G.lay_J;
+            I.lay_off = G.lay_off;
+            I.wfs_n = G.wfs_n;
+            I.wfs_soff = G.wfs_soff;
+            I.wfs_noff = G.wfs_noff;
+            I.wfs_moff = G.wfs_moff;
+            I.wfs_w = G.wfs_w;
+            I.mask = G.mask;
+            I.tab_off = G.tab_off;
+            I.cx = G.cx;
+            I.cy = G.cy;
+            I.tx = G.tx;
+            I.ty = G.ty;
+            I.gat_off = G.gat_off;
+            I.jlo = G.jlo;
+            I.jhi = G.jhi;
+            I.ilo = G.ilo;
+            I.ihi = G.ihi;
+            I.Jinv = fb.Jinv;
+            I.aD = fb.aD;
+            I.c = fb.c;
+            I.r = fb.r;
+            I.p = fb.p;
+            I.q = fb.q;
+            I.b = fb.b;
+            I.bprev = fb.bprev;
+            I.phi = fb.phi;
+            I.sc_out = fb.sc;
+            I.slopes = fb.slopes;
+            I.w0 = w0[i];
+            I.nw = nw[i];
+            I.l0 = l0[i];
+            I.nl = nl[i];
+            I.KG = preps[i].KG;
+            int2* d_gtab = nullptr;
+            int* d_gtab_off = nullptr;
+            // sensor fields (+8 floats: aligned copies may read up to 3 past the end)
+            ok = dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) &&
+                 dupload(pl, d_gtab, preps[i].gtab, err) && dupload(pl, d_gtab_off, preps[i].gtab_off, err);
+            I.gtab = d_gtab;
+            I.gtab_off = d_gtab_off;
+            if (ok) cudaMemset(I.scal, 0, 4 * sizeof(double));
+            if (i == 0) pl->psi = I.psi;
+            pl->inst.push_back(I);
+        }
         WItem* dw = nullptr;
         LItem* dl = nullptr;
         int2* ds = nullptr;
@@ -1218,14 +1269,7 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         unsigned* bar = nullptr;
         ok = ok && dupload(pl, dw, witems, err) && dupload(pl, dl, litems, err) && dupload(pl, ds, stg, err) &&
              dalloc(pl, wp, witems.size(), err) && dalloc(pl, lp, 2 * litems.size() * C * 2, err) &&
-             dalloc(pl, bar, 1, err) && dalloc(pl, pl->d_inst, 1, err);
-        if (ok) {
-            cudaError_t ce = cudaMemcpy(pl->d_inst, &I, sizeof(FInst), cudaMemcpyHostToDevice);
-            if (ce != cudaSuccess) {
-                err = std::string("cudaMemcpy: ") + cudaGetErrorString(ce);
-                ok = false;
-            }
-        }
+             dalloc(pl, bar, 1, err) && dupload(pl, pl->d_inst, pl->inst, err);
         if (!ok) {
             fused_destroy(pl);
             return nullptr;
@@ -1237,8 +1281,8 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         P.wpart = wp;
         P.lpart = lp;
         P.bar = bar;
-        P.errw = fb.errw;
-        P.n_inst = 1;
+        P.errw = fbs[0].errw;
+        P.n_inst = ninst;
         P.n_witems = (int)witems.size();
         P.n_litems = (int)litems.size();
         P.C = C;
@@ -1249,11 +1293,11 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
         P.tile_subaps = tile_sub;
         P.tile_rows = tile_rows;
         P.tile_cols = tile_cols;
-        P.G_max = hs.G;
+        P.G_max = Gmax;
         P.n_max = nmax;
         for (int i = 0; i < 6; ++i) {
-            P.h[i] = (float)hs.h[i];
-            P.g[i] = (float)hs.g[i];
+            P.h[i] = (float)hss[0]->h[i];
+            P.g[i] = (float)hss[0]->g[i];
         }
         P.inst = pl->d_inst;
         best = pl;
@@ -1266,6 +1310,10 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
     return best;
 }
 
+FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const FusedBuffers& fb, std::string& err) {
+    return fused_create_multi({&hs}, {G}, {fb}, 0, err, 0);
+}
+
 int fused_describe(const FusedPlan* pl, char* buf, int len) {
     return snprintf(buf, len,
                     "fused: %d clusters x %d CTAs (grid %d, %d threads), smem %d B, %d sensor tiles, %d layer items, "
@@ -1275,6 +1323,8 @@ int fused_describe(const FusedPlan* pl, char* buf, int len) {
 }
 
 void fused_set_trace(FusedPlan* pl, bool on) { pl->trace_on = on; }
+
+int fused_cluster_size(const FusedPlan* pl) { return pl->C; }
 
 int fused_get_trace(FusedPlan* pl, unsigned long long* out, int max_entries, int* slots, int* grid) {
     *slots = pl->trace ? pl->last_slots : 0;

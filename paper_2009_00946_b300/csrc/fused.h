@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "setup.h"
 
@@ -25,6 +26,16 @@ struct FusedPlan;
 // Build the fused plan (tiles, work lists, cluster shape); nullptr if the
 // device cannot run it (err says why), in which case the plain path is used.
 FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const FusedBuffers& fb, std::string& err);
+
+// One plan over several independent instances (solved together in one
+// launch; every instance has its own tables, state and scalars).
+// max_tile_side > 0 bounds the sensor tiles (and so the staged windows).
+// forced_C > 0 builds only that cluster size (the autotuner's candidates).
+FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hs, const std::vector<DevGeo<float>>& G,
+                              const std::vector<FusedBuffers>& fb, int max_tile_side, std::string& err,
+                              int forced_C);
+// Cluster size of a plan.
+int fused_cluster_size(const FusedPlan* plan);
 void fused_destroy(FusedPlan* plan);
 
 // Enqueue one frame on `stream`: b = W P^T Gamma^T C^{-1} s; warm restart

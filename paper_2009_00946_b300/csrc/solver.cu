@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 
 #include "fused.h"
 #include "solver.h"
@@ -515,6 +516,7 @@ class Solver : public SolverBase {
     int* errw = nullptr;
     int* errw_host = nullptr;
     FusedPlan* fused = nullptr;
+    FusedBuffers fbuf{};     // state the fused plans point to (FP32 only)
     // graph cache
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     struct Key {
@@ -1058,6 +1060,128 @@ class Solver : public SolverBase {
         return FEWHA_OK;
     }
 
+    // a fused plan with cluster size C (FP32 instances only)
+    FusedPlan* make_plan(int C, std::string& e) {
+        if constexpr (std::is_same<T, float>::value) {
+            return fused_create_multi({&hs}, {G}, {fbuf}, 0, e, C);
+        } else {
+            e = "the fused path is FP32 only";
+            return nullptr;
+        }
+    }
+
+    // captured frame graphs hold the old plan's launch: drop them
+    void drop_graphs() {
+        for (int i = 0; i < 2; ++i)
+            if (gexec[i]) {
+                cudaGraphExecDestroy(gexec[i]);
+                gexec[i] = nullptr;
+            }
+    }
+
+    int set_cluster_size(int C) override {
+        if (sizeof(T) != 4) {
+            err = "the fused path is FP32 only";
+            return FEWHA_ERR_STATE;
+        }
+        std::string e;
+        FusedPlan* pl = make_plan(C, e);
+        if (!pl) {
+            err = "no fused plan with this cluster size: " + e;
+            return FEWHA_ERR_ARG;
+        }
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        if (fused) fused_destroy(fused);
+        fused = pl;
+        drop_graphs();
+        return FEWHA_OK;
+    }
+
+    // Time every feasible cluster shape on the current frame (warm start from
+    // the current state, restored before each trial and at the end) and keep
+    // the fastest plan.
+    int autotune(int n_iter, int reps, char* report, int len) override {
+        if (sizeof(T) != 4 || !fused) {
+            err = "the autotuner needs the fused FP32 path";
+            return FEWHA_ERR_STATE;
+        }
+        if (!have_frame) {
+            err = "autotune needs a frame (fewha_set_frame) to time";
+            return FEWHA_ERR_STATE;
+        }
+        if (n_iter < 1 || reps < 1) {
+            err = "n_iter and reps must be >= 1";
+            return FEWHA_ERR_ARG;
+        }
+        const size_t nb = (size_t)hs.N * sizeof(T);
+        T* saved = nullptr;
+        FEWHA_CUDA(cudaMalloc(&saved, 4 * nb));
+        T* vec[4] = {c, r, b, bprev};
+        for (int i = 0; i < 4; ++i)
+            FEWHA_CUDA(cudaMemcpyAsync((char*)saved + i * nb, vec[i], nb, cudaMemcpyDeviceToDevice, stream));
+        auto restore = [&]() {
+            for (int i = 0; i < 4; ++i)
+                cudaMemcpyAsync(vec[i], (char*)saved + i * nb, nb, cudaMemcpyDeviceToDevice, stream);
+        };
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        auto time_plan = [&](FusedPlan* pl) -> float {
+            std::vector<float> t;
+            for (int rep = 0; rep < reps + 1; ++rep) {
+                restore();
+                cudaEventRecord(e0, stream);
+                std::string e;
+                long long dummy = 0;
+                if (fused_solve(pl, (const float*)slopes, n_iter, 1, 0, barrier_budget, stream, e, dummy)) return -1.f;
+                cudaEventRecord(e1, stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) t.push_back(ms);
+            }
+            if (check_err() != FEWHA_OK) return -1.f;
+            std::sort(t.begin(), t.end());
+            return t[t.size() / 2];
+        };
+        std::string rep_s;
+        char buf[96];
+        FusedPlan* best = fused;
+        float best_t = time_plan(fused);
+        snprintf(buf, sizeof buf, "C=%d: %.1f us (current)", fused_cluster_size(fused), best_t * 1e3f);
+        rep_s += buf;
+        for (int C : {16, 8, 4, 2}) {
+            if (C == fused_cluster_size(best)) continue;
+            std::string e;
+            FusedPlan* pl = make_plan(C, e);
+            if (!pl) continue;
+            const float t = time_plan(pl);
+            snprintf(buf, sizeof buf, "; C=%d: %.1f us", C, t * 1e3f);
+            rep_s += buf;
+            if (t > 0.f && (best_t <= 0.f || t < best_t)) {
+                if (best != fused) fused_destroy(best);
+                best = pl;
+                best_t = t;
+            } else {
+                fused_destroy(pl);
+            }
+        }
+        restore();
+        cudaStreamSynchronize(stream);
+        cudaFree(saved);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (best != fused) {
+            fused_destroy(fused);
+            fused = best;
+            drop_graphs();
+        }
+        snprintf(buf, sizeof buf, "; chosen C=%d", fused_cluster_size(fused));
+        rep_s += buf;
+        if (report && len > 0) snprintf(report, len, "%s", rep_s.c_str());
+        return FEWHA_OK;
+    }
+
     int frame(const void* s_in, int n_iter, int warm, double gain, int n_fit, void* lout, void* dout,
               int on_device) override {
         if (!s_in) {
@@ -1230,6 +1354,7 @@ SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& e
         fb.sc = s->sc;
         fb.errw = s->errw;
         std::string ferr;
+        s->fbuf = fb;
         s->fused = fused_create(hs, s->G, fb, ferr);
         s->path = s->fused ? FEWHA_PATH_FUSED : FEWHA_PATH_PLAIN;
         out = s;

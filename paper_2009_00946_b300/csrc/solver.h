@@ -96,6 +96,8 @@ class SolverBase {
     virtual int set_trace(int on) = 0;
     virtual int get_trace(unsigned long long* out, int max_entries, int* slots, int* grid) = 0;
     virtual int get_fine_trace(unsigned long long* out, int max_entries, int* per_cta, int* grid) = 0;
+    virtual int set_cluster_size(int C) = 0;
+    virtual int autotune(int n_iter, int reps, char* report, int len) = 0;
 
     HostSetup hs;
     cudaStream_t stream = 0;

@@ -97,6 +97,8 @@ def lib():
                                       ci]),
         "fewha_get_fine_trace": (ci, [vp, ctypes.POINTER(ctypes.c_ulonglong), ci, ctypes.POINTER(ci),
                                       ctypes.POINTER(ci)]),
+        "fewha_set_cluster_size": (ci, [vp, ci]),
+        "fewha_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -300,6 +302,15 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(lib().fewha_launch_count(self.h))
+
+    def set_cluster_size(self, cluster_size: int):
+        self._check(lib().fewha_set_cluster_size(self.h, int(cluster_size)))
+
+    def autotune(self, n_iter: int = 4, reps: int = 5) -> str:
+        """Time the feasible fused-kernel shapes on the current frame, keep the fastest."""
+        buf = ctypes.create_string_buffer(512)
+        self._check(lib().fewha_autotune(self.h, int(n_iter), int(reps), buf, 512))
+        return buf.value.decode()
 
     def describe(self) -> str:
         buf = ctypes.create_string_buffer(512)

@@ -150,3 +150,40 @@ def test_fused_graph_frame_host_and_device(fw, elt_frames):
             B.sync()
             assert rel(lb, ref[k][0]) < 1e-4, k
             assert np.array_equal(lb, dev_l.cpu().numpy()), k
+
+
+@pytest.mark.parametrize("C", [1, 2, 4, 8, 16])
+def test_fused_every_cluster_shape_matches_oracle(fw, elt_frames, C):
+    """Each thread-block-cluster shape of the fused plan (row stripes of n/C
+    rows per CTA) gives the same frames as the oracle; shapes that do not fit
+    the device are refused with FEWHA_ERR_ARG, never launched."""
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as S:
+        try:
+            S.set_cluster_size(C)
+        except fw.FewhaError as e:
+            assert e.code == 1   # FEWHA_ERR_ARG
+            pytest.skip("cluster size %d has no plan on this device" % C)
+        assert (" x %d CTAs" % C) in S.describe()
+        for k in range(11):
+            S.set_frame(S_in[k])
+            S.solve(4, warm=True)
+            S.sync()
+            assert rel(S.layers(), ref[k][0]) < 1e-4, k
+
+
+def test_fused_autotune_keeps_state_and_parity(fw, elt_frames):
+    """The autotuner times candidate plans on the current frame but restores
+    the solver state: the frames that follow still match the oracle."""
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as S:
+        for k in range(3):
+            S.set_frame(S_in[k])
+            S.solve(4, warm=True)
+        rep = S.autotune(n_iter=4, reps=3)
+        assert "chosen C=" in rep
+        for k in range(3, 12):
+            S.set_frame(S_in[k])
+            S.solve(4, warm=True)
+            S.sync()
+            assert rel(S.layers(), ref[k][0]) < 1e-4, (k, rep)
