@@ -214,6 +214,57 @@ int fewha_get_trace(fewha_handle* h, unsigned long long* out, int max_entries, i
  * Synchronises.  Errors: STATE on the plain path. */
 int fewha_get_fine_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* per_cta, int* grid);
 
+/* ------------------------------------------------------------------------
+ * Batch of independent instances.  Sec. 4 finds the global parallelism of a
+ * single reconstruction (a handful of layers and sensors) far too small to
+ * fill a GPU; a batch advances many unrelated FP32 instances (different
+ * telescopes, sensors, layer grids) together, each by the frame of Alg. 1
+ * (RHS, warm restart with residual replacement every k_rr frames, n_iter
+ * steps of Alg. 2) exactly as fewha_solve does for one handle, in ONE launch
+ * of the persistent fused kernel per frame.  Instances share nothing but the
+ * launch: every one keeps its own tables, state and CG scalars.
+ *   slopes: the instances' slope vectors concatenated in instance order
+ *           (slope_off[i] .. slope_off[i+1]), each laid out as for a handle;
+ *   layers: the instances' layer stacks concatenated (coeff_off[i] ..).
+ * ------------------------------------------------------------------------ */
+typedef struct fewha_batch fewha_batch;
+
+/* Create a batch of count instances; geoms[i] / profs[i] as for fewha_create
+ * (precision must be FEWHA_FP32).  max_tile_side > 0 bounds the sensor tiles
+ * (nodes per side) so that large and small sensors give work items of
+ * similar size; 0 = one tile per CTA share.  cluster_size 0 = automatic, else
+ * 1, 2, 4, 8 or 16 CTAs per layer item.  On failure *out = NULL and
+ * fewha_batch_last_error(NULL) gives the reason.  Errors: ARG, GEOMETRY (an
+ * instance's geometry, or no fused plan fits the batch), CUDA. */
+int fewha_batch_create(int count, const fewha_geometry* geoms, const fewha_profile* profs, void* stream,
+                       int max_tile_side, int cluster_size, fewha_batch** out);
+int fewha_batch_destroy(fewha_batch* b);
+const char* fewha_batch_last_error(const fewha_batch* b);
+
+/* Instance count and total sizes; coeff_off / slope_off (count + 1 entries
+ * each, may be NULL) receive the offsets of every instance. */
+int fewha_batch_sizes(const fewha_batch* b, int* count, long* coeff_off, long* slope_off);
+
+/* Residual replacement period of the batch (as fewha_set_residual_replacement). */
+int fewha_batch_set_residual_replacement(fewha_batch* b, int k_rr);
+
+/* One frame for every instance: copy the slopes in, one fused launch, copy the
+ * layers phi = W^T c out (layers_out may be NULL).  on_device = 0: host
+ * buffers, the call synchronises and returns the device error word (INPUT if
+ * any instance's slopes are non-finite, BREAKDOWN if any instance's CG step
+ * broke down -- that instance keeps its state -- or TIMEOUT). */
+int fewha_batch_frame(fewha_batch* b, const void* slopes, int n_iter, int warm_start, void* layers_out,
+                      int on_device);
+
+/* State (c, the previous right-hand side b, r) of instance inst, as
+ * fewha_get_state.  Synchronises for host pointers. */
+int fewha_batch_get_state(fewha_batch* b, int inst, void* c, void* bprev, void* r, int on_device);
+
+/* Wait for the batch's stream and return its device error word (cleared). */
+int fewha_batch_sync(fewha_batch* b);
+int fewha_batch_describe(fewha_batch* b, char* buf, int len);
+long long fewha_batch_launch_count(const fewha_batch* b);
+
 /* The paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory (a control loop that reserves all memory at start-up
  * and allows no allocation while it runs, code inside a framework that owns

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "fewha.h"
 #include "setup.h"
@@ -15,8 +16,24 @@ struct fewha_handle {
     std::string msg;
 };
 
+struct fewha_batch {
+    fewha::BatchBase* b = nullptr;
+    std::string msg;
+};
+
 namespace {
 thread_local std::string g_create_error;
+thread_local std::string g_batch_error;
+
+int bfail(fewha_batch* b, int code, const std::string& m) {
+    b->msg = m;
+    return code;
+}
+
+int bdone(fewha_batch* b, int st) {
+    if (st != FEWHA_OK) b->msg = b->b->err;
+    return st;
+}
 
 int fail(fewha_handle* h, int code, const std::string& m) {
     if (h) h->msg = m;
@@ -200,6 +217,112 @@ int fewha_autotune(fewha_handle* h, int n_iter, int reps, char* report, int len)
 long long fewha_launch_count(const fewha_handle* h) {
     if (!h) return -1;
     return h->s->launches;
+}
+
+// ---- batch ----
+
+int fewha_batch_create(int count, const fewha_geometry* geoms, const fewha_profile* profs, void* stream,
+                       int max_tile_side, int cluster_size, fewha_batch** out) {
+    if (!out) return FEWHA_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || !geoms || !profs) {
+        g_batch_error = "count must be >= 1 with geometries and profiles";
+        return FEWHA_ERR_ARG;
+    }
+    if (max_tile_side < 0 || (cluster_size != 0 && cluster_size != 1 && cluster_size != 2 && cluster_size != 4 &&
+                              cluster_size != 8 && cluster_size != 16)) {
+        g_batch_error = "max_tile_side must be >= 0 and cluster_size 0, 1, 2, 4, 8 or 16";
+        return FEWHA_ERR_ARG;
+    }
+    try {
+        std::vector<fewha::HostSetup> hss(count);
+        for (int i = 0; i < count; ++i) {
+            std::string err;
+            if (geoms[i].precision != FEWHA_FP32) {
+                g_batch_error = "instance " + std::to_string(i) + ": batched instances are FP32 only";
+                return FEWHA_ERR_ARG;
+            }
+            int st = fewha::build_setup(geoms[i], profs[i], hss[i], err);
+            if (st) {
+                g_batch_error = "instance " + std::to_string(i) + ": " + err;
+                return st;
+            }
+        }
+        std::string err;
+        int st = FEWHA_OK;
+        fewha::BatchBase* b = fewha::make_batch(hss, (cudaStream_t)stream, max_tile_side, cluster_size, err, st);
+        if (!b) {
+            g_batch_error = err;
+            return st ? st : FEWHA_ERR_CUDA;
+        }
+        fewha_batch* h = new fewha_batch();
+        h->b = b;
+        *out = h;
+        return FEWHA_OK;
+    } catch (const std::bad_alloc&) {
+        g_batch_error = "host out of memory";
+        return FEWHA_ERR_ARG;
+    } catch (...) {
+        g_batch_error = "unexpected host exception";
+        return FEWHA_ERR_ARG;
+    }
+}
+
+int fewha_batch_destroy(fewha_batch* b) {
+    if (!b) return FEWHA_ERR_ARG;
+    delete b->b;
+    delete b;
+    return FEWHA_OK;
+}
+
+const char* fewha_batch_last_error(const fewha_batch* b) {
+    if (!b) return g_batch_error.c_str();
+    return b->msg.c_str();
+}
+
+int fewha_batch_sizes(const fewha_batch* b, int* count, long* coeff_off, long* slope_off) {
+    if (!b) return FEWHA_ERR_ARG;
+    const auto& co = b->b->coeff_off;
+    const auto& so = b->b->slope_off;
+    if (count) *count = (int)co.size() - 1;
+    for (size_t i = 0; i < co.size(); ++i) {
+        if (coeff_off) coeff_off[i] = co[i];
+        if (slope_off) slope_off[i] = so[i];
+    }
+    return FEWHA_OK;
+}
+
+int fewha_batch_set_residual_replacement(fewha_batch* b, int k_rr) {
+    if (!b) return FEWHA_ERR_ARG;
+    if (k_rr < 0) return bfail(b, FEWHA_ERR_ARG, "k_rr must be >= 0");
+    b->b->k_rr = k_rr;
+    return FEWHA_OK;
+}
+
+int fewha_batch_frame(fewha_batch* b, const void* slopes, int n_iter, int warm_start, void* layers_out,
+                      int on_device) {
+    if (!b) return FEWHA_ERR_ARG;
+    return bdone(b, b->b->frame(slopes, n_iter, warm_start, layers_out, on_device));
+}
+
+int fewha_batch_get_state(fewha_batch* b, int inst, void* c, void* bprev, void* r, int on_device) {
+    if (!b) return FEWHA_ERR_ARG;
+    return bdone(b, b->b->get_state(inst, c, bprev, r, on_device));
+}
+
+int fewha_batch_sync(fewha_batch* b) {
+    if (!b) return FEWHA_ERR_ARG;
+    return bdone(b, b->b->sync());
+}
+
+int fewha_batch_describe(fewha_batch* b, char* buf, int len) {
+    if (!b) return FEWHA_ERR_ARG;
+    return bdone(b, b->b->describe(buf, len));
+}
+
+long long fewha_batch_launch_count(const fewha_batch* b) {
+    if (!b) return -1;
+    return b->b->launches;
 }
 
 }  // extern "C"

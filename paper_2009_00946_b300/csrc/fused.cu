@@ -77,6 +77,12 @@ struct FParams {
     const int2* stg;       // Pt staging row ranges per (layer item, rank, sensor)
     double* wpart;         // [n_witems]
     double* lpart;         // [2][n_litems * C][2]
+    // static work lists: sensor tiles of CTA b are wsched[wsched_off[b] ..
+    // wsched_off[b+1]), layer items of cluster k lsched[lsched_off[k] ..)
+    const int* wsched;
+    const int* wsched_off;
+    const int* lsched;
+    const int* lsched_off;
     unsigned* bar;
     int* errw;
     unsigned long long* trace;   // optional: [slot][cta][arrive, depart] globaltimer (ns)
@@ -85,6 +91,7 @@ struct FParams {
     int fcap;
     long long budget;
     int n_inst, n_witems, n_litems;
+    int grid;              // planned grid (the work lists have grid + 1 / grid / C + 1 offsets)
     int n_iter, warm, replace, out_layers;
     int C;
     int stripe_floats, stage_floats, win_floats, tile_nodes, tile_subaps, tile_rows, tile_cols;
@@ -856,11 +863,13 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     cg::cluster_group cl = cg::this_cluster();
     const int C = P.C;
     // every shared-memory address below assumes the planned cluster shape
-    if ((int)cl.num_blocks() != C || (gridDim.x % C) != 0) {
+    if ((int)cl.num_blocks() != C || (int)gridDim.x != P.grid || (gridDim.x % C) != 0) {
         if (threadIdx.x == 0) atomicOr(P.errw, kErrLaunch);
         return;
     }
-    const int cid = blockIdx.x / C, ncl = gridDim.x / C;
+    const int cid = blockIdx.x / C;
+    const int w_lo = P.wsched_off[blockIdx.x], w_hi = P.wsched_off[blockIdx.x + 1];
+    const int l_lo = P.lsched_off[cid], l_hi = P.lsched_off[cid + 1];
     int slot = 0;
     if (threadIdx.x == 0) {
         trace_mark(P, 0, 0);
@@ -879,25 +888,23 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     __syncthreads();
 
     // Alg. 1 RHS: Gamma^T C^{-1} s per sensor tile
-    for (int it = blockIdx.x; it < P.n_witems; it += gridDim.x) sensor_tile(P, it, sm, kModeRhs, false, wdesc, red);
+    for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeRhs, false, wdesc, red);
     grid_barrier(P, target, &s_abort, slot);
     // P^T, W -> b; warm restart (or c -> phi for the replacement); z_0 -> phi
     const int m1 = P.replace ? kLpRhsRepl : kLpRhsStart;
-    for (int li = cid; li < P.n_litems; li += ncl) layer_phase(P, li, m1, 0, sm, rem, cl, red, sh);
+    for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], m1, 0, sm, rem, cl, red, sh);
     grid_barrier(P, target, &s_abort, slot);
     if (P.replace) {
         // r = b - M c: data term of M on phi_c, then the layer phase
-        for (int it = blockIdx.x; it < P.n_witems; it += gridDim.x)
-            sensor_tile(P, it, sm, kModeData, false, wdesc, red);
+        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, false, wdesc, red);
         grid_barrier(P, target, &s_abort, slot);
-        for (int li = cid; li < P.n_litems; li += ncl) layer_phase(P, li, kLpReplStart, 0, sm, rem, cl, red, sh);
+        for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpReplStart, 0, sm, rem, cl, red, sh);
         grid_barrier(P, target, &s_abort, slot);
     }
     for (int k = 0; k < P.n_iter; ++k) {
-        for (int it = blockIdx.x; it < P.n_witems; it += gridDim.x)
-            sensor_tile(P, it, sm, kModeData, true, wdesc, red);
+        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, true, wdesc, red);
         grid_barrier(P, target, &s_abort, slot);
-        for (int li = cid; li < P.n_litems; li += ncl) layer_phase(P, li, kLpIter, k, sm, rem, cl, red, sh);
+        for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpIter, k, sm, rem, cl, red, sh);
         if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort, slot);
     }
     __syncthreads();
@@ -1044,6 +1051,31 @@ bool prep_instance(const HostSetup& hs, InstPrep& ip, std::string& err) {
 }
 
 }  // namespace
+
+// Longest-processing-time-first assignment: items in decreasing cost, each
+// to the least-loaded worker so far (ties: lowest worker index).  With equal
+// costs and no more items than workers this is the plain round-robin.
+static void lpt_schedule(const std::vector<double>& cost, int workers, std::vector<int>& order,
+                         std::vector<int>& off) {
+    std::vector<int> idx(cost.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(workers, 0.0);
+    std::vector<std::vector<int>> lists(workers);
+    for (int it : idx) {
+        int w = 0;
+        for (int k = 1; k < workers; ++k)
+            if (load[k] < load[w]) w = k;
+        load[w] += cost[it];
+        lists[w].push_back(it);
+    }
+    order.clear();
+    off.assign(1, 0);
+    for (auto& l : lists) {
+        order.insert(order.end(), l.begin(), l.end());
+        off.push_back((int)order.size());
+    }
+}
 
 FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const std::vector<DevGeo<float>>& Gs,
                               const std::vector<FusedBuffers>& fbs, int max_tile_side, std::string& err,
@@ -1262,6 +1294,24 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             if (i == 0) pl->psi = I.psi;
             pl->inst.push_back(I);
         }
+        // work lists: a sensor tile costs its nodes times the layers sampled,
+        // a layer item its nodes times (transform + update + one gather per sensor)
+        std::vector<double> wcost, lcost;
+        for (auto& w : witems) {
+            const HostSetup& hs = *hss[w.inst];
+            wcost.push_back((double)(w.i1 - w.i0 + 1) * (w.j1 - w.j0 + 1) * (hs.L + 2));
+        }
+        for (auto& li : litems) {
+            const HostSetup& hs = *hss[li.inst];
+            const double n = hs.lay[li.l].n;
+            lcost.push_back(n * n * (6.0 + hs.G) + 4096.0 * hs.lay[li.l].J);
+        }
+        std::vector<int> wsched, wsched_off, lsched, lsched_off;
+        lpt_schedule(wcost, pl->grid, wsched, wsched_off);
+        lpt_schedule(lcost, pl->nclusters, lsched, lsched_off);
+        int *dws = nullptr, *dwo = nullptr, *dls = nullptr, *dlo = nullptr;
+        ok = ok && dupload(pl, dws, wsched, err) && dupload(pl, dwo, wsched_off, err) &&
+             dupload(pl, dls, lsched, err) && dupload(pl, dlo, lsched_off, err);
         WItem* dw = nullptr;
         LItem* dl = nullptr;
         int2* ds = nullptr;
@@ -1278,6 +1328,11 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         P.witems = dw;
         P.litems = dl;
         P.stg = ds;
+        P.wsched = dws;
+        P.wsched_off = dwo;
+        P.lsched = dls;
+        P.lsched_off = dlo;
+        P.grid = pl->grid;
         P.wpart = wp;
         P.lpart = lp;
         P.bar = bar;

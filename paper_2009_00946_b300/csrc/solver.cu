@@ -1363,4 +1363,174 @@ SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& e
     return out;
 }
 
+// ---------------------------------------------------------------------------
+// batch: independent FP32 instances, one fused launch per frame
+// ---------------------------------------------------------------------------
+
+namespace {
+bool host_pinned(const void* ptr) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+}  // namespace
+
+class Batch : public BatchBase {
+  public:
+    std::vector<std::unique_ptr<Solver<float>>> inst;   // tables and state of each instance
+    FusedPlan* plan = nullptr;
+    float* s_all = nullptr;     // concatenated slopes (the instances read slices)
+    float* phi_all = nullptr;   // concatenated layers (the instances write slices)
+    float* pin_in = nullptr;    // staging for pageable host buffers
+    float* pin_out = nullptr;
+
+    long S_tot() const { return slope_off.back(); }
+    long N_tot() const { return coeff_off.back(); }
+
+    ~Batch() override {
+        if (stream) cudaStreamSynchronize(stream);
+        else cudaDeviceSynchronize();
+        if (plan) fused_destroy(plan);
+        if (s_all) cudaFree(s_all);
+        if (phi_all) cudaFree(phi_all);
+        if (pin_in) cudaFreeHost(pin_in);
+        if (pin_out) cudaFreeHost(pin_out);
+    }
+
+    int frame(const void* sl, int n_iter, int warm, void* lout, int on_device) override {
+        if (!sl) {
+            err = "null slopes";
+            return FEWHA_ERR_ARG;
+        }
+        if (n_iter < 1 || n_iter > 100000) {
+            err = "n_iter must be >= 1";
+            return FEWHA_ERR_ARG;
+        }
+        const size_t sb = (size_t)S_tot() * sizeof(float), nb = (size_t)N_tot() * sizeof(float);
+        if (on_device) {
+            FEWHA_CUDA(cudaMemcpyAsync(s_all, sl, sb, cudaMemcpyDeviceToDevice, stream));
+        } else {
+            const void* src = sl;
+            if (!host_pinned(sl)) {
+                std::memcpy(pin_in, sl, sb);   // the previous host frame has completed
+                src = pin_in;
+            }
+            FEWHA_CUDA(cudaMemcpyAsync(s_all, src, sb, cudaMemcpyHostToDevice, stream));
+        }
+        const bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
+        int st = fused_solve(plan, s_all, n_iter, warm, replace ? 1 : 0, barrier_budget, stream, err, launches);
+        if (st) return st;
+        frame_count += 1;
+        if (on_device) {
+            if (lout) FEWHA_CUDA(cudaMemcpyAsync(lout, phi_all, nb, cudaMemcpyDeviceToDevice, stream));
+            return FEWHA_OK;
+        }
+        void* dst = nullptr;
+        if (lout) {
+            dst = host_pinned(lout) ? lout : (void*)pin_out;
+            FEWHA_CUDA(cudaMemcpyAsync(dst, phi_all, nb, cudaMemcpyDeviceToHost, stream));
+        }
+        st = sync();
+        if (st) return st;
+        if (lout && dst != lout) std::memcpy(lout, pin_out, nb);
+        return FEWHA_OK;
+    }
+
+    int sync() override {
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        const int st = inst[0]->check_err();   // the plan's error word is instance 0's
+        if (st) err = inst[0]->err;
+        return st;
+    }
+
+    int describe(char* buf, int len) override {
+        if (!buf || len <= 0) {
+            err = "null buffer";
+            return FEWHA_ERR_ARG;
+        }
+        int k = snprintf(buf, len, "batch of %d fp32 instances, N %ld, S %ld; ", (int)inst.size(), N_tot(), S_tot());
+        if (k >= 0 && k < len) fused_describe(plan, buf + k, len - k);
+        return FEWHA_OK;
+    }
+
+    int get_state(int i, void* c, void* b, void* r, int on_device) override {
+        if (i < 0 || i >= (int)inst.size()) {
+            err = "instance index out of range";
+            return FEWHA_ERR_ARG;
+        }
+        const int st = inst[i]->get_state(c, b, r, on_device);
+        if (st) err = inst[i]->err;
+        return st;
+    }
+};
+
+BatchBase* make_batch(const std::vector<HostSetup>& hss, cudaStream_t stream, int max_tile_side,
+                      int cluster_size, std::string& err, int& status) {
+    std::unique_ptr<Batch> B(new Batch());
+    B->stream = stream;
+    B->coeff_off.assign(1, 0);
+    B->slope_off.assign(1, 0);
+    for (size_t i = 0; i < hss.size(); ++i) {
+        if (hss[i].prec != FEWHA_FP32) {
+            err = "batched instances are FP32 only";
+            status = FEWHA_ERR_ARG;
+            return nullptr;
+        }
+        std::unique_ptr<Solver<float>> s(new Solver<float>());
+        s->hs = hss[i];
+        s->stream = stream;
+        s->path = FEWHA_PATH_PLAIN;
+        status = s->init();
+        if (status) {
+            err = "instance " + std::to_string(i) + ": " + s->err;
+            return nullptr;
+        }
+        B->coeff_off.push_back(B->coeff_off.back() + hss[i].N);
+        B->slope_off.push_back(B->slope_off.back() + hss[i].S);
+        B->inst.push_back(std::move(s));
+    }
+    const size_t sb = (size_t)B->S_tot() * sizeof(float), nb = (size_t)B->N_tot() * sizeof(float);
+    if (cudaMalloc(&B->s_all, sb) != cudaSuccess || cudaMalloc(&B->phi_all, nb) != cudaSuccess ||
+        cudaMallocHost(&B->pin_in, sb) != cudaSuccess || cudaMallocHost(&B->pin_out, nb) != cudaSuccess ||
+        cudaMemset(B->s_all, 0, sb) != cudaSuccess) {
+        cudaGetLastError();
+        err = "device or pinned host allocation of the batch buffers failed";
+        status = FEWHA_ERR_CUDA;
+        return nullptr;
+    }
+    std::vector<const HostSetup*> hp;
+    std::vector<DevGeo<float>> Gs;
+    std::vector<FusedBuffers> fbs;
+    for (size_t i = 0; i < B->inst.size(); ++i) {
+        Solver<float>& s = *B->inst[i];
+        FusedBuffers fb;
+        fb.c = s.c;
+        fb.r = s.r;
+        fb.p = s.p;
+        fb.q = s.q;
+        fb.b = s.b;
+        fb.bprev = s.bprev;
+        fb.phi = B->phi_all + B->coeff_off[i];
+        fb.Jinv = s.Jinv;
+        fb.aD = s.aD;
+        fb.slopes = B->s_all + B->slope_off[i];
+        fb.sc = s.sc;
+        fb.errw = s.errw;
+        hp.push_back(&s.hs);
+        Gs.push_back(s.G);
+        fbs.push_back(fb);
+    }
+    B->plan = fused_create_multi(hp, Gs, fbs, max_tile_side, err, cluster_size);
+    if (!B->plan) {
+        err = "no fused plan for this batch: " + err;
+        status = FEWHA_ERR_GEOMETRY;
+        return nullptr;
+    }
+    status = FEWHA_OK;
+    return B.release();
+}
+
 }  // namespace fewha

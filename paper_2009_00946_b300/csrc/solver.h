@@ -112,4 +112,26 @@ class SolverBase {
 
 SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& err, int& status);
 
+// Many independent FP32 instances advanced together by one fused launch per
+// frame: slopes and layers are concatenated in instance order.
+class BatchBase {
+  public:
+    virtual ~BatchBase() {}
+    virtual int frame(const void* slopes, int n_iter, int warm, void* layers_out, int on_device) = 0;
+    virtual int sync() = 0;
+    virtual int describe(char* buf, int len) = 0;
+    virtual int get_state(int inst, void* c, void* b, void* r, int on_device) = 0;
+
+    std::vector<long> coeff_off, slope_off;   // count + 1 offsets
+    cudaStream_t stream = 0;
+    int k_rr = 10;
+    long long barrier_budget = (1LL << 31);
+    long long frame_count = 0;
+    long long launches = 0;
+    std::string err;
+};
+
+BatchBase* make_batch(const std::vector<HostSetup>& hss, cudaStream_t stream, int max_tile_side,
+                      int cluster_size, std::string& err, int& status);
+
 }  // namespace fewha

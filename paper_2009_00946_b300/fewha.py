@@ -99,6 +99,17 @@ def lib():
                                       ctypes.POINTER(ci)]),
         "fewha_set_cluster_size": (ci, [vp, ci]),
         "fewha_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
+        "fewha_batch_create": (ci, [ci, ctypes.POINTER(Geometry), ctypes.POINTER(Profile), vp, ci, ci,
+                                    ctypes.POINTER(vp)]),
+        "fewha_batch_destroy": (ci, [vp]),
+        "fewha_batch_last_error": (ctypes.c_char_p, [vp]),
+        "fewha_batch_sizes": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(cl), ctypes.POINTER(cl)]),
+        "fewha_batch_set_residual_replacement": (ci, [vp, ci]),
+        "fewha_batch_frame": (ci, [vp, vp, ci, ci, vp, ci]),
+        "fewha_batch_get_state": (ci, [vp, ci, vp, vp, vp, ci]),
+        "fewha_batch_sync": (ci, [vp]),
+        "fewha_batch_describe": (ci, [vp, ctypes.c_char_p, ci]),
+        "fewha_batch_launch_count": (cll, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -344,3 +355,99 @@ class Solver:
             r = r[r != 0]
             marks.append([(int(v >> np.uint64(56)), int(v & np.uint64(0x00FFFFFFFFFFFFFF))) for v in r])
         return marks
+
+
+class Batch:
+    """Many independent FP32 instances advanced together, one fused launch per
+    frame (a fewha_batch).  Slopes and layers are concatenated in instance
+    order; `slope_off` / `coeff_off` give each instance's slice."""
+
+    def __init__(self, cfgs: list, stream=None, max_tile_side: int = 24, cluster_size: int = 0,
+                 k_rr: int | None = None):
+        import torch
+        L = lib()
+        n = len(cfgs)
+        if n < 1:
+            raise ValueError("empty batch")
+        geoms = (Geometry * n)()
+        profs = (Profile * n)()
+        for i, cfg in enumerate(cfgs):
+            geoms[i], profs[i] = structs_from_config(cfg, FP32)
+        self._stream_obj = torch.cuda.Stream() if stream is None else stream
+        self.stream = self._stream_obj
+        b = ctypes.c_void_p()
+        st = L.fewha_batch_create(n, geoms, profs, ctypes.c_void_p(self._stream_obj.cuda_stream),
+                                  int(max_tile_side), int(cluster_size), ctypes.byref(b))
+        if st != 0:
+            raise FewhaError(st, L.fewha_batch_last_error(None).decode())
+        self.h = b
+        cnt = ctypes.c_int()
+        co = (ctypes.c_long * (n + 1))()
+        so = (ctypes.c_long * (n + 1))()
+        L.fewha_batch_sizes(b, ctypes.byref(cnt), co, so)
+        self.count = cnt.value
+        self.coeff_off = np.array(co[:], np.int64)
+        self.slope_off = np.array(so[:], np.int64)
+        self.N, self.S = int(self.coeff_off[-1]), int(self.slope_off[-1])
+        self.cfgs = cfgs
+        if k_rr is not None:
+            self._check(L.fewha_batch_set_residual_replacement(self.h, int(k_rr)))
+
+    def _check(self, st):
+        if st != 0:
+            raise FewhaError(st, lib().fewha_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fewha_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def concat_slopes(self, per_instance) -> np.ndarray:
+        """One host slope vector from a list of per-instance slope vectors."""
+        return np.concatenate([np.asarray(v, np.float32).ravel() for v in per_instance])
+
+    def split_layers(self, layers) -> list:
+        return [layers[self.coeff_off[i]:self.coeff_off[i + 1]] for i in range(self.count)]
+
+    def frame(self, slopes, n_iter: int, warm: bool = True, layers_out=None):
+        """One frame of every instance.  Host arrays (numpy; the call
+        synchronises) or device tensors (the call only enqueues)."""
+        import torch
+        dt = (np.float32, torch.float32)
+        ps, ds = _ptr(slopes, dt, self.S, None)
+        pl = None
+        if layers_out is not None:
+            pl, dl = _ptr(layers_out, dt, self.N, None)
+            if dl != ds:
+                raise ValueError("slopes and layers_out must both be host or both be device")
+        self._check(lib().fewha_batch_frame(self.h, ps, int(n_iter), 1 if warm else 0, pl, ds))
+
+    def get_state(self, i: int):
+        nn = int(self.coeff_off[i + 1] - self.coeff_off[i])
+        c, b, r = (np.empty(nn, np.float32) for _ in range(3))
+        self._check(lib().fewha_batch_get_state(self.h, int(i), ctypes.c_void_p(c.ctypes.data),
+                                                ctypes.c_void_p(b.ctypes.data), ctypes.c_void_p(r.ctypes.data), 0))
+        return c, b, r
+
+    def sync(self):
+        self._check(lib().fewha_batch_sync(self.h))
+
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        self._check(lib().fewha_batch_describe(self.h, buf, 512))
+        return buf.value.decode()
+
+    def launch_count(self) -> int:
+        return int(lib().fewha_batch_launch_count(self.h))

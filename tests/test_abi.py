@@ -74,3 +74,27 @@ def test_header_documents_every_entry_point():
         # every declaration is preceded by a comment block
         m = re.search(r"\*/\s*\n(?:[^\n]*\n){0,4}[^\n;]*\b" + n + r"\s*\(", hdr)
         assert m, n
+
+
+def test_batch_rejects_invalid_arguments_on_host():
+    """Batch creation checks its arguments before touching the device."""
+    L = fewha.lib()
+    b = ctypes.c_void_p()
+    assert L.fewha_batch_create(0, None, None, None, 0, 0, ctypes.byref(b)) == 1 and not b.value
+    assert "count" in L.fewha_batch_last_error(None).decode()
+    cfgs = [configs.c5_autograd(), configs.c1_plain()]
+    geoms = (fewha.Geometry * 2)()
+    profs = (fewha.Profile * 2)()
+    for i, c in enumerate(cfgs):
+        geoms[i], profs[i] = fewha.structs_from_config(c, fewha.FP32)
+    assert L.fewha_batch_create(2, geoms, profs, None, 0, 3, ctypes.byref(b)) == 1 and not b.value
+    assert "cluster_size" in L.fewha_batch_last_error(None).decode()
+    geoms[1].precision = fewha.FP64
+    assert L.fewha_batch_create(2, geoms, profs, None, 0, 0, ctypes.byref(b)) == 1 and not b.value
+    assert "instance 1" in L.fewha_batch_last_error(None).decode()
+    geoms[1].precision = fewha.FP32
+    profs[0].alpha = -1.0
+    st = L.fewha_batch_create(2, geoms, profs, None, 0, 0, ctypes.byref(b))
+    assert st == 1 and "instance 0" in L.fewha_batch_last_error(None).decode()
+    assert L.fewha_batch_destroy(None) == 1 and L.fewha_batch_frame(None, None, 4, 1, None, 0) == 1
+    assert L.fewha_batch_launch_count(None) == -1
