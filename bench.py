@@ -141,6 +141,20 @@ def cpu_oracle_latency(cfg, n_frames, pool_np):
     return times
 
 
+# DRAM bytes (read + write) of one k_fused_frame launch on this workload from
+# the committed full ncu capture, valid only for the kernel source it was
+# taken on (sha256 prefix of csrc/fused.cu); any other source reports null.
+NCU_TRAFFIC = {"fused_cu_sha256": "7fc80a57a90e1f85", "dram_bytes": 4977152,
+               "summary": "profiles/k_fused_frame_elt_full.md"}
+
+
+def fused_traffic():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2009_00946_b300", "csrc", "fused.cu"), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    return NCU_TRAFFIC["dram_bytes"] if sha.startswith(NCU_TRAFFIC["fused_cu_sha256"]) else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -200,6 +214,91 @@ def time_solve(S, torch, n_iter, K, flush):
     st.synchronize()
     S.sync()
     return float(np.mean([a.elapsed_time(b) * 1e3 for a, b in ev]))
+
+
+def bench_elt_dm_frame(torch, fewha, dev, flush, n_frames):
+    """35-layer ELT frame with the least-squares fit onto 3 mirrors (the whole
+    of Alg. 1 as one captured graph): latency p50/p99 (us), device buffers."""
+    cfg = configs.c3_elt_dm()
+    pool = torch.from_numpy(slope_pool(cfg, 16)).to(dev)
+    S = fewha.Solver(cfg, precision=fewha.FP32, path=fewha.PATH_FUSED, k_rr=K_RR)
+    lay = torch.empty(S.N, dtype=torch.float32, device=dev)
+    dm = torch.empty(S.NA, dtype=torch.float32, device=dev)
+    st = S.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_frames)]
+    for k in range(5):
+        S.frame(pool[k % 16], N_ITER, warm=True, gain=cfg["gain"], n_fit=cfg["n_fit"], layers_out=lay, dm_out=dm)
+    for k in range(n_frames):
+        with torch.cuda.stream(st):
+            flush.fill_(float(k & 7))
+        ev[k][0].record(st)
+        S.frame(pool[k % 16], N_ITER, warm=True, gain=cfg["gain"], n_fit=cfg["n_fit"], layers_out=lay, dm_out=dm)
+        ev[k][1].record(st)
+    st.synchronize()
+    S.sync()
+    t = [a.elapsed_time(b) * 1e3 for a, b in ev]
+    out = {"workload": "ELT with 35 layers 0-25 km (128^2, J=4), 4 iterations, least-squares fit (8 CG steps, "
+                       "5x5 directions) onto 3 mirrors at 0/4/12.7 km, gain 1",
+           "p50_us": float(np.percentile(t, 50)), "p99_us": float(np.percentile(t, 99)), "frames": n_frames,
+           "n_coeff": S.N, "n_act": S.NA, "plan": S.describe()}
+    S.close()
+    return out
+
+
+def bench_batch(torch, fewha, dev, flush, n_frames):
+    """64 uneven instances advanced by one fused launch per frame, against the
+    same 64 instances solved one after another on the plain FP64 path."""
+    cfgs = configs.c4_batch(64)
+    per = [synth.random_slopes(c, 7).astype(np.float32) for c in cfgs]
+    B = fewha.Batch(cfgs, k_rr=K_RR)
+    s = torch.from_numpy(B.concat_slopes(per)).to(dev)
+    lay = torch.empty(B.N, dtype=torch.float32, device=dev)
+    st = B.stream
+    for _ in range(5):
+        B.frame(s, N_ITER, True, lay)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_frames)]
+    for k in range(n_frames):
+        with torch.cuda.stream(st):
+            flush.fill_(float(k & 7))
+        ev[k][0].record(st)
+        B.frame(s, N_ITER, True, lay)
+        ev[k][1].record(st)
+    st.synchronize()
+    B.sync()
+    t = [a.elapsed_time(b) * 1e3 for a, b in ev]
+    p50 = float(np.percentile(t, 50))
+    alg = sum(algorithmic_bytes_per_frame(c, N_ITER) for c in cfgs)
+    plan = B.describe()
+    N, S_tot = B.N, B.S
+    B.close()
+    # sequential: one plain FP64 handle per instance, solved one after another
+    solvers = [fewha.Solver(c, precision=fewha.FP64, path=fewha.PATH_PLAIN, k_rr=K_RR) for c in cfgs]
+    s64 = [torch.from_numpy(x.astype(np.float64)).to(dev) for x in per]
+    reps = 3
+    for S, x in zip(solvers, s64):
+        S.set_frame(x)
+        S.solve(N_ITER, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for S, x in zip(solvers, s64):
+            S.set_frame(x)
+            S.solve(N_ITER, True)
+        for S in solvers:
+            S.sync()
+    seq = (time.perf_counter() - t0) / reps * 1e6
+    for S in solvers:
+        S.close()
+    hbm, _ = measured_peaks()
+    return {"workload": "64 independent instances: D 8-39 m, 16-84 subapertures, 2-9 layers on 32^2-256^2 grids, "
+                        "3-6 LGS, 4 warm-started iterations each, FP32, one fused launch per frame",
+            "n_coeff": N, "n_slopes": S_tot, "p50_us": p50, "p99_us": float(np.percentile(t, 99)),
+            "instance_frames_per_s": 64 * 1e6 / p50, "frames": n_frames,
+            "sequential_fp64_us": seq, "sequential_fp64_instance_frames_per_s": 64 * 1e6 / seq,
+            "speedup_vs_sequential_fp64": seq / p50,
+            "roofline": {"bound": "hbm", "achieved": alg / (p50 * 1e-6) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (p50 * 1e-6) / 1e9 / hbm, "algorithmic_bytes": alg},
+            "plan": plan}
 
 
 def max_over_ranks(values, dist, device):
@@ -279,6 +378,7 @@ def main():
     ap.add_argument("--impl", default="fewha", choices=["fewha", "reference"])
     ap.add_argument("--pool", type=int, default=64, help="distinct synthetic frames, cycled")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 35-layer fit and 64-instance batch lines")
     ap.add_argument("--profile", action="store_true", help="stream launches only (for ncu), no timing")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -373,6 +473,12 @@ def main():
     p64_iter = (p64_t20 - p64_t4) / 16.0
     P64.close()
 
+    # ---- the other workloads: 35-layer frame with the mirror fit, 64-instance batch ----
+    extra = {}
+    if not args.no_extra:
+        extra["elt_dm_frame"] = bench_elt_dm_frame(torch, fewha, dev, flush, min(K, 200))
+        extra["batch64"] = bench_batch(torch, fewha, dev, flush, min(K, 30))
+
     # max over ranks
     p50, p99, mean, per_iter = max_over_ranks([p50, p99, mean, per_iter], dist, dev)
     if rank != 0:
@@ -399,11 +505,14 @@ def main():
                 "how": "fewha_frame with pinned host slopes and layers, host wall clock per frame"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm, "traffic": fused_traffic(),
+                     "traffic_note": "DRAM bytes per launch, ncu full capture (cold caches); the L2 keeps "
+                                     "the state, so traffic is far below the algorithmic bytes",
                      "kernel": "k_fused_frame", "duration_us": t4, "algorithmic_bytes": alg,
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
         "clocks": clocks,
         "phases": phases,
+        **extra,
         "plan": plan,
     }
     if cpu:
