@@ -215,6 +215,45 @@ int fewha_get_trace(fewha_handle* h, unsigned long long* out, int max_entries, i
 int fewha_get_fine_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* per_cta, int* grid);
 
 /* ------------------------------------------------------------------------
+ * Differentiation of the solve (reverse mode).  The reconstruction of Alg. 1
+ * is a fixed, small number of Alg. 2 steps, so its output is a smooth
+ * function of the model parameters of Sec. 2.2: the Cn^2 fractions gamma_l
+ * (through D ~ 1/gamma_l), the regularisation weight alpha and the sensor
+ * weights w_g = 1/sigma_g^2 of C^{-1} (in M and in b).  These calls give the
+ * gradient of a loss on the layers phi = W^T c_K of a cold-started K-step
+ * solve, with the Jacobi preconditioner held fixed (a constant of the
+ * differentiated map).  All array arguments are device pointers in the
+ * handle's precision (gradients: double) ordered on the handle's stream; the
+ * calls only enqueue.  They use the plain operator kernels and do not touch
+ * the frame state (c, r, b) of fewha_solve / fewha_frame.
+ * ------------------------------------------------------------------------ */
+
+/* Replace gamma_l (n_layers values > 0), alpha (> 0) and w_g (n_wfs values
+ * >= 0) for every later call (M, b, the fused and plain paths).  The Jacobi
+ * diagonal keeps its create-time value.  Synchronises the stream.
+ * Errors: ARG. */
+int fewha_set_params(fewha_handle* h, const double* cn2_frac, double alpha, const double* w);
+
+/* Bytes of device memory a taped solve of n_iter iterations records
+ * (5 n_iter vectors of N plus 8 n_iter doubles); -1 on bad arguments. */
+long fewha_tape_bytes(const fewha_handle* h, int n_iter);
+
+/* Differentiable solve: b from the slopes (Alg. 1), c = 0, r = b, n_iter steps
+ * of Alg. 2, every iterate recorded in `tape` (caller-owned device memory of
+ * fewha_tape_bytes bytes, 8-byte aligned); layers_out (may be NULL) = W^T c.
+ * Errors: ARG; BREAKDOWN / INPUT are reported by fewha_sync. */
+int fewha_solve_taped(fewha_handle* h, const void* slopes, int n_iter, void* tape, void* layers_out);
+
+/* Reverse mode of fewha_solve_taped (same slopes, n_iter and tape, and the
+ * parameters the tape was recorded with): for the cotangent layers_bar =
+ * dLoss/dphi it writes dLoss/dgamma (n_layers doubles), dLoss/dalpha (1) and
+ * dLoss/dw (n_wfs) -- overwritten, not accumulated -- and, if grad_slopes is
+ * not NULL, dLoss/dslopes = C^{-1} Gamma P W^T b-bar (slope layout).
+ * Errors: ARG. */
+int fewha_backward(fewha_handle* h, const void* slopes, int n_iter, const void* tape, const void* layers_bar,
+                   double* grad_cn2, double* grad_alpha, double* grad_w, void* grad_slopes);
+
+/* ------------------------------------------------------------------------
  * Batch of independent instances.  Sec. 4 finds the global parallelism of a
  * single reconstruction (a handful of layers and sensors) far too small to
  * fill a GPU; a batch advances many unrelated FP32 instances (different

@@ -214,6 +214,27 @@ int fewha_autotune(fewha_handle* h, int n_iter, int reps, char* report, int len)
     return done(h, h->s->autotune(n_iter, reps, report, len));
 }
 
+int fewha_set_params(fewha_handle* h, const double* cn2_frac, double alpha, const double* w) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->set_params(cn2_frac, alpha, w));
+}
+
+long fewha_tape_bytes(const fewha_handle* h, int n_iter) {
+    if (!h || n_iter < 1) return -1;
+    return (long)h->s->tape_size(n_iter);
+}
+
+int fewha_solve_taped(fewha_handle* h, const void* slopes, int n_iter, void* tape, void* layers_out) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->solve_taped(slopes, n_iter, tape, layers_out));
+}
+
+int fewha_backward(fewha_handle* h, const void* slopes, int n_iter, const void* tape, const void* layers_bar,
+                   double* grad_cn2, double* grad_alpha, double* grad_w, void* grad_slopes) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->backward(slopes, n_iter, tape, layers_bar, grad_cn2, grad_alpha, grad_w, grad_slopes));
+}
+
 long long fewha_launch_count(const fewha_handle* h) {
     if (!h) return -1;
     return h->s->launches;

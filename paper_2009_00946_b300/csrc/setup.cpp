@@ -118,6 +118,10 @@ void db3_taps(double h[6], double g[6]) {
     for (int i = 0; i < 6; ++i) g[i] = ((i & 1) ? -1.0 : 1.0) * h[5 - i];
 }
 
+double reg_diag(double r0, double cn2, double delta, int j) {
+    return std::pow(r0, 5.0 / 3.0) / (cn2 * std::pow(delta, 5.0 / 3.0) * std::pow(2.0, 11.0 * j / 3.0));
+}
+
 int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup& o, std::string& err) {
     char buf[256];
     auto fail = [&](int code, const char* msg) {
@@ -243,8 +247,7 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
         for (int y = 0; y < L.n; ++y)
             for (int x = 0; x < L.n; ++x) {
                 int j = level_of(y, x, L.n, L.J);
-                double Dv = std::pow(o.r0, 5.0 / 3.0) /
-                            (L.cn2 * std::pow(L.delta, 5.0 / 3.0) * std::pow(2.0, 11.0 * j / 3.0));
+                double Dv = reg_diag(o.r0, L.cn2, L.delta, j);
                 long i = L.off + (long)y * L.n + x;
                 o.Dreg[i] = Dv;
                 o.aD[i] = o.alpha * Dv;

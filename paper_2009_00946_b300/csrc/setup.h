@@ -72,6 +72,11 @@ struct HostSetup {
 // FEWHA status; on failure err holds the message.
 int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup& out, std::string& err);
 
+// Diagonal of the regulariser D for a coefficient of wavelet level j on a
+// layer with Cn^2 fraction cn2 and grid spacing delta (Sec. 2.2: the
+// Kolmogorov scaling r0^{5/3} / (cn2 delta^{5/3} 2^{11 j / 3})).
+double reg_diag(double r0, double cn2, double delta, int j);
+
 // db3 taps from the closed form in radicals.
 void db3_taps(double h[6], double g[6]);
 

@@ -498,6 +498,8 @@ static void to_T(const std::vector<double>& v, std::vector<T>& o) {
     for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
 }
 
+#include "adjoint.cuh"
+
 template <typename T>
 class Solver : public SolverBase {
   public:
@@ -1179,6 +1181,173 @@ class Solver : public SolverBase {
         snprintf(buf, sizeof buf, "; chosen C=%d", fused_cluster_size(fused));
         rep_s += buf;
         if (report && len > 0) snprintf(report, len, "%s", rep_s.c_str());
+        return FEWHA_OK;
+    }
+
+    // ---- differentiation: set_params, taped solve, reverse mode ----
+    T *ac = nullptr, *ar = nullptr, *ap = nullptr, *aq = nullptr, *ab = nullptr;   // forward work
+    T *cb = nullptr, *rb = nullptr, *pb = nullptr, *qb = nullptr, *sb = nullptr, *My = nullptr, *psiz = nullptr;
+    double *tsc = nullptr, *asc = nullptr, *apart = nullptr, *alpart = nullptr, *awpart = nullptr, *gam = nullptr;
+    bool adj_ready = false;
+
+    int adj_init() {
+        if (adj_ready) return FEWHA_OK;
+        const size_t N = hs.N;
+        for (T** v : {&ac, &ar, &ap, &aq, &ab, &cb, &rb, &pb, &qb, &sb, &My}) TRY(alloc(*v, N));
+        TRY(alloc(psiz, hs.NW));
+        TRY(alloc(tsc, kNumScalars));
+        TRY(alloc(asc, 8));
+        TRY(alloc(apart, 6 * kRedBlocks));
+        TRY(alloc(alpart, (size_t)hs.L * kRedBlocks));
+        TRY(alloc(awpart, (size_t)hs.G * kRedBlocks));
+        std::vector<double> g(hs.L);
+        for (int l = 0; l < hs.L; ++l) g[l] = hs.lay[l].cn2;
+        TRY(upload(gam, g));
+        FEWHA_CUDA(cudaMemset(tsc, 0, kNumScalars * sizeof(double)));
+        adj_ready = true;
+        return FEWHA_OK;
+    }
+
+    size_t tape_size(int n_iter) const override { return tape_bytes(hs.N, n_iter, sizeof(T)); }
+
+    // New gamma_l, alpha, w_g for M and b; the Jacobi preconditioner keeps
+    // the values of create (it is a constant of the differentiated solve).
+    int set_params(const double* cn2, double alpha, const double* w) override {
+        if (!cn2 || !w || !(alpha > 0) || !std::isfinite(alpha)) {
+            err = "set_params needs cn2 and w arrays and a finite alpha > 0";
+            return FEWHA_ERR_ARG;
+        }
+        for (int l = 0; l < hs.L; ++l)
+            if (!(cn2[l] > 0) || !std::isfinite(cn2[l])) {
+                err = "every Cn^2 fraction must be finite and > 0";
+                return FEWHA_ERR_ARG;
+            }
+        for (int g = 0; g < hs.G; ++g)
+            if (!(w[g] >= 0) || !std::isfinite(w[g])) {
+                err = "every sensor weight must be finite and >= 0";
+                return FEWHA_ERR_ARG;
+            }
+        hs.alpha = alpha;
+        for (int l = 0; l < hs.L; ++l) {
+            HostLayer& L = hs.lay[l];
+            L.cn2 = cn2[l];
+            for (long i = L.off; i < L.off + (long)L.n * L.n; ++i) {
+                hs.Dreg[i] = reg_diag(hs.r0, L.cn2, L.delta, hs.level[i]);
+                hs.aD[i] = alpha * hs.Dreg[i];
+            }
+        }
+        std::vector<double> wv(hs.G);
+        for (int g = 0; g < hs.G; ++g) wv[g] = hs.wfs[g].w = w[g];
+        std::vector<T> t, tw;
+        to_T(hs.aD, t);
+        to_T(wv, tw);
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        FEWHA_CUDA(cudaMemcpy(aD, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice));
+        FEWHA_CUDA(cudaMemcpy((T*)G.wfs_w, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice));
+        if (gam) FEWHA_CUDA(cudaMemcpy(gam, cn2, hs.L * sizeof(double), cudaMemcpyHostToDevice));
+        return FEWHA_OK;
+    }
+
+    // K steps of Alg. 2 from c = 0, r = b(slopes), every iterate on the tape;
+    // the frame state (c, r, b of fewha_solve) is not touched.
+    int solve_taped(const void* sl, int n_iter, void* tape, void* lout) override {
+        if (!sl || !tape || n_iter < 1 || n_iter > 100000) {
+            err = "solve_taped needs slopes, a tape and n_iter >= 1";
+            return FEWHA_ERR_ARG;
+        }
+        TRY(adj_init());
+        fused_layers_ready = false;   // phi is scratch of the operators below
+        const long N = hs.N;
+        T* tv = (T*)tape;
+        double* ts = (double*)((char*)tape + tape_vec_bytes(N, n_iter, sizeof(T)));
+        k_weight_meas<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, (const T*)sl, wsl,
+                                                                                         errw);
+        FEWHA_LAUNCHED();
+        TRY(backproject(wsl, ab));
+        FEWHA_CUDA(cudaMemsetAsync(ac, 0, N * sizeof(T), stream));
+        FEWHA_CUDA(cudaMemcpyAsync(ar, ab, N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+        for (int k = 0; k < n_iter; ++k) {
+            T* v = tv + (size_t)k * kTapeVecs * N;
+            T *rk = v + kTapeR * N, *zk = v + kTapeZ * N, *sk = v + kTapeS * N;
+            FEWHA_CUDA(cudaMemcpyAsync(rk, ar, N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+            k_precond_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, Jinv, ar, zk, part);
+            FEWHA_LAUNCHED();
+            TRY(data_term(zk, sk));
+            k_reg_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, aD, zk, sk, part2);
+            FEWHA_LAUNCHED();
+            k_alg2_scalars<<<1, 256, 0, stream>>>(part, part2, tsc, k, errw);
+            FEWHA_LAUNCHED();
+            k_alg2_update<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, tsc, k == 0, zk, sk, ap, aq, ac, ar);
+            FEWHA_LAUNCHED();
+            FEWHA_CUDA(cudaMemcpyAsync(v + kTapeP * N, ap, N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+            FEWHA_CUDA(cudaMemcpyAsync(v + kTapeQ * N, aq, N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+            k_tape_scalars<<<1, 32, 0, stream>>>(tsc, ts, k);
+            FEWHA_LAUNCHED();
+        }
+        if (lout) TRY(inv_dwt(ac, (T*)lout));
+        return FEWHA_OK;
+    }
+
+    // Reverse mode of solve_taped for the layer cotangent layers_bar:
+    // gradients with respect to gamma_l, alpha, w_g (device doubles,
+    // overwritten) and the slopes (optional).
+    int backward(const void* sl, int n_iter, const void* tape, const void* lbar, double* g_gam, double* g_alpha,
+                 double* g_w, void* g_s) override {
+        if (!sl || !tape || !lbar || !g_gam || !g_alpha || !g_w || n_iter < 1 || n_iter > 100000) {
+            err = "backward needs slopes, the tape, the layer cotangent, gradient outputs and n_iter >= 1";
+            return FEWHA_ERR_ARG;
+        }
+        TRY(adj_init());
+        fused_layers_ready = false;
+        const long N = hs.N;
+        const T* tv = (const T*)tape;
+        const double* ts = (const double*)((const char*)tape + tape_vec_bytes(N, n_iter, sizeof(T)));
+        FEWHA_CUDA(cudaMemsetAsync(g_gam, 0, hs.L * sizeof(double), stream));
+        FEWHA_CUDA(cudaMemsetAsync(g_alpha, 0, sizeof(double), stream));
+        FEWHA_CUDA(cudaMemsetAsync(g_w, 0, hs.G * sizeof(double), stream));
+        FEWHA_CUDA(cudaMemsetAsync(asc, 0, 8 * sizeof(double), stream));
+        for (T* v : {rb, pb, qb}) FEWHA_CUDA(cudaMemsetAsync(v, 0, N * sizeof(T), stream));
+        TRY(fwd_dwt((const T*)lbar, cb));   // phi = W^T c  ->  c-bar = W phi-bar
+        const int np1 = G.nsmax + 1;
+        const dim3 gnodes((np1 * np1 + 255) / 256, G.G);
+        for (int k = n_iter - 1; k >= 0; --k) {
+            const T* v = tv + (size_t)k * kTapeVecs * N;
+            const T* vo = k > 0 ? tv + (size_t)(k - 1) * kTapeVecs * N : nullptr;
+            const T *rk = v + kTapeR * N, *zk = v + kTapeZ * N, *sk = v + kTapeS * N;
+            k_adj_dots<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, cb, rb, pb, qb, v + kTapeP * N, v + kTapeQ * N,
+                                                                  vo ? vo + kTapeP * N : nullptr,
+                                                                  vo ? vo + kTapeQ * N : nullptr, apart);
+            FEWHA_LAUNCHED();
+            k_adj_scalars<<<1, 256, 0, stream>>>(apart, ts, k, asc);
+            FEWHA_LAUNCHED();
+            k_adj_vec1<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, asc, cb, rb, pb, qb, zk, sb);
+            FEWHA_LAUNCHED();
+            TRY(apply_M_dev(sb, My));   // leaves P W^T sb in wpsi
+            // sb^T (dM/dtheta) z_k: alpha D part per layer, C^{-1} part per sensor
+            k_layer_dot<T><<<dim3(kRedBlocks, G.L), kRedThreads, 0, stream>>>(G, sb, aD, zk, alpart);
+            FEWHA_LAUNCHED();
+            TRY(inv_dwt(zk, phi));
+            k_P<T><<<gnodes, 256, 0, stream>>>(G, phi, psiz);
+            FEWHA_LAUNCHED();
+            k_wfs_dot<T><<<dim3(kRedBlocks, G.G), kRedThreads, 0, stream>>>(G, psiz, wpsi, nullptr, awpart);
+            FEWHA_LAUNCHED();
+            k_adj_accum<<<1, 256, 0, stream>>>(alpart, G.L, awpart, G.G, gam, hs.alpha, g_gam, g_alpha, g_w);
+            FEWHA_LAUNCHED();
+            k_adj_vec2<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, asc, pb, qb, rb, zk, sk, rk, My, Jinv);
+            FEWHA_LAUNCHED();
+        }
+        // b-bar = r-bar: b-bar^T (db/dw_g) and the slope gradient C^{-1} Gamma P W^T b-bar
+        TRY(inv_dwt(rb, phi));
+        k_P<T><<<gnodes, 256, 0, stream>>>(G, phi, psiz);
+        FEWHA_LAUNCHED();
+        k_wfs_dot<T><<<dim3(kRedBlocks, G.G), kRedThreads, 0, stream>>>(G, psiz, nullptr, (const T*)sl, awpart);
+        FEWHA_LAUNCHED();
+        k_adj_accum<<<1, 256, 0, stream>>>(nullptr, 0, awpart, G.G, gam, hs.alpha, g_gam, g_alpha, g_w);
+        FEWHA_LAUNCHED();
+        if (g_s) {
+            k_gamma_w<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, psiz, (T*)g_s);
+            FEWHA_LAUNCHED();
+        }
         return FEWHA_OK;
     }
 

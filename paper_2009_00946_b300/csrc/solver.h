@@ -98,6 +98,11 @@ class SolverBase {
     virtual int get_fine_trace(unsigned long long* out, int max_entries, int* per_cta, int* grid) = 0;
     virtual int set_cluster_size(int C) = 0;
     virtual int autotune(int n_iter, int reps, char* report, int len) = 0;
+    virtual int set_params(const double* cn2, double alpha, const double* w) = 0;
+    virtual int solve_taped(const void* slopes, int n_iter, void* tape, void* layers_out) = 0;
+    virtual int backward(const void* slopes, int n_iter, const void* tape, const void* layers_bar, double* g_gam,
+                         double* g_alpha, double* g_w, void* g_slopes) = 0;
+    virtual size_t tape_size(int n_iter) const = 0;
 
     HostSetup hs;
     cudaStream_t stream = 0;

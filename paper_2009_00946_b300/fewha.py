@@ -99,6 +99,10 @@ def lib():
                                       ctypes.POINTER(ci)]),
         "fewha_set_cluster_size": (ci, [vp, ci]),
         "fewha_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
+        "fewha_set_params": (ci, [vp, ctypes.POINTER(cd), cd, ctypes.POINTER(cd)]),
+        "fewha_tape_bytes": (cl, [vp, ci]),
+        "fewha_solve_taped": (ci, [vp, vp, ci, vp, vp]),
+        "fewha_backward": (ci, [vp, vp, ci, vp, vp, vp, vp, vp, vp]),
         "fewha_batch_create": (ci, [ci, ctypes.POINTER(Geometry), ctypes.POINTER(Profile), vp, ci, ci,
                                     ctypes.POINTER(vp)]),
         "fewha_batch_destroy": (ci, [vp]),
@@ -327,6 +331,55 @@ class Solver:
         buf = ctypes.create_string_buffer(512)
         self._check(lib().fewha_describe(self.h, buf, 512))
         return buf.value.decode()
+
+    # -- differentiation (device tensors only) --
+    @property
+    def n_layers(self) -> int:
+        return len(self.cfg["layers"])
+
+    @property
+    def n_wfs(self) -> int:
+        return len(self.cfg["wfs"])
+
+    def set_params(self, cn2, alpha: float, w):
+        """New Cn^2 fractions, alpha and sensor weights for M and b (the
+        Jacobi preconditioner keeps its create-time value)."""
+        cn2 = np.ascontiguousarray(np.asarray(cn2, np.float64).ravel())
+        w = np.ascontiguousarray(np.asarray(w, np.float64).ravel())
+        if cn2.size != self.n_layers or w.size != self.n_wfs:
+            raise ValueError("need %d Cn^2 fractions and %d sensor weights" % (self.n_layers, self.n_wfs))
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(lib().fewha_set_params(self.h, cn2.ctypes.data_as(dp), float(alpha), w.ctypes.data_as(dp)))
+
+    def tape_bytes(self, n_iter: int) -> int:
+        return int(lib().fewha_tape_bytes(self.h, int(n_iter)))
+
+    def solve_taped(self, slopes, n_iter: int, tape, layers_out=None):
+        ps, ds = _ptr(slopes, self._dt(), self.S, None)
+        if not ds or not tape.is_cuda or tape.numel() < self.tape_bytes(n_iter) or tape.data_ptr() % 8:
+            raise ValueError("device slopes and an 8-byte aligned device tape of tape_bytes(n_iter) bytes needed")
+        pl = None
+        if layers_out is not None:
+            pl, dl = _ptr(layers_out, self._dt(), self.N, None)
+            if not dl:
+                raise ValueError("layers_out must be a device tensor")
+        self._check(lib().fewha_solve_taped(self.h, ps, int(n_iter), ctypes.c_void_p(tape.data_ptr()), pl))
+
+    def backward(self, slopes, n_iter: int, tape, layers_bar, g_cn2, g_alpha, g_w, g_slopes=None):
+        import torch
+        ps, ds = _ptr(slopes, self._dt(), self.S, None)
+        pb, db = _ptr(layers_bar, self._dt(), self.N, None)
+        for t, n in ((g_cn2, self.n_layers), (g_alpha, 1), (g_w, self.n_wfs)):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.numel() == n and t.is_contiguous()):
+                raise ValueError("gradients must be contiguous float64 device tensors")
+        pg = None
+        if g_slopes is not None:
+            pg, dg = _ptr(g_slopes, self._dt(), self.S, None)
+        if not (ds and db):
+            raise ValueError("device tensors needed")
+        self._check(lib().fewha_backward(self.h, ps, int(n_iter), ctypes.c_void_p(tape.data_ptr()), pb,
+                                         ctypes.c_void_p(g_cn2.data_ptr()), ctypes.c_void_p(g_alpha.data_ptr()),
+                                         ctypes.c_void_p(g_w.data_ptr()), pg))
 
     def set_trace(self, on: bool = True):
         self._check(lib().fewha_set_trace(self.h, 1 if on else 0))
