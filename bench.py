@@ -127,8 +127,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_latency(cfg, n_frames, pool_np):
-    """The FP64 CPU oracle as it stands, one host core: per-frame latency (us)."""
+def cpu_oracle_latency(cfg, n_frames, pool_np, keep=None):
+    """The FP64 CPU oracle as it stands, one host core: per-frame latency (us).
+    With keep (a list) the layers of every frame are appended to it."""
     from oracle import fewha_oracle as fo
     R = fo.Reconstructor(cfg)
     times = []
@@ -136,9 +137,26 @@ def cpu_oracle_latency(cfg, n_frames, pool_np):
         s = pool_np[k % len(pool_np)].astype(np.float64)
         t0 = time.perf_counter()
         R.frame(s, N_ITER, warm=True, k_rr=K_RR)
-        R.layers()
+        lay = R.layers()
         times.append((time.perf_counter() - t0) * 1e6)
+        if keep is not None:
+            keep.append(lay)
     return times
+
+
+def parity_vs_oracle(fewha, cfg, pool, oracle_layers):
+    """The same frames through a fresh FP32 fused handle (host buffers, one
+    graph per frame): relative L2 error of the layers against the oracle's."""
+    S = fewha.Solver(cfg, precision=fewha.FP32, path=fewha.PATH_FUSED, k_rr=K_RR)
+    out = np.empty(S.N, np.float32)
+    errs = []
+    for k, ref in enumerate(oracle_layers):
+        S.frame(pool[k % len(pool)], N_ITER, warm=True, layers_out=out)
+        errs.append(float(np.linalg.norm(out.astype(np.float64) - ref) / np.linalg.norm(ref)))
+    S.close()
+    return {"layers_rel_l2_max": max(errs), "layers_rel_l2_median": float(np.median(errs)), "frames": len(errs),
+            "tolerance": 1e-4, "against": "FP64 CPU oracle on the same frames (the cpu_baseline run), "
+                                          "warm-started, residual replacement every 10 frames"}
 
 
 # DRAM bytes (read + write) of one k_fused_frame launch on this workload from
@@ -398,8 +416,10 @@ def main():
 
     # CPU oracle baseline first (rank 0, N = 1), before any CUDA call
     cpu = None
+    oracle_layers = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t = cpu_oracle_latency(cfg, 30, pool)[2:]
+        oracle_layers = []
+        t = cpu_oracle_latency(cfg, 30, pool, oracle_layers)[2:]
         cpu = {"value": float(np.percentile(t, 50)), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "28 ELT frames (after 2 warm-up frames), FP64 numpy oracle, one host thread (%d cores "
                          "on the host)" % os.cpu_count()}
@@ -473,6 +493,8 @@ def main():
     p64_iter = (p64_t20 - p64_t4) / 16.0
     P64.close()
 
+    parity = parity_vs_oracle(fewha, cfg, pool, oracle_layers) if oracle_layers else None
+
     # ---- the other workloads: 35-layer frame with the mirror fit, 64-instance batch ----
     extra = {}
     if not args.no_extra:
@@ -517,6 +539,8 @@ def main():
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if parity:
+        line["parity"] = parity
     print(json.dumps(line), flush=True)
     S.close()
     if dist:
