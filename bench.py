@@ -330,7 +330,7 @@ def max_over_ranks(values, dist, device):
     return [float(v) for v in t.cpu().tolist()]
 
 
-def phase_breakdown(S, pool_dev, n_iter=N_ITER):
+def phase_breakdown(S, pool_dev, n_iter=N_ITER, dump=None):
     """One traced non-replacement frame: critical-path time of each phase (the
     latest CTA's work between two barriers) and the barrier latencies (us)."""
     S.set_trace(True)
@@ -340,9 +340,15 @@ def phase_breakdown(S, pool_dev, n_iter=N_ITER):
     tr = S.trace().astype(np.int64)
     fine = S.fine_trace()
     S.set_trace(False)
+    if dump:
+        np.save(dump + "_barriers.npy", tr)
+        np.save(dump + "_fine.npy", np.array([(c, t, v) for c, r in enumerate(fine) for t, v in r], np.int64))
     # sub-phase steps: mean over CTAs and phases of the time between marks
     names = {(10, 11): "layer_stage_rows_us", (11, 12): "layer_PT_us", (12, 13): "layer_fwd_dwt_us",
-             (13, 14): "layer_update_us", (14, 15): "layer_inv_dwt_us", (15, 16): "layer_store_sync_us",
+             (13, 14): "layer_update_us", (14, 15): "layer_inv_dwt_us", (13, 17): "layer_scalars_us",
+             (17, 18): "layer_update_loop_us", (18, 14): "layer_update_reduce_us",
+             (13, 40): "scal_enter_us", (40, 41): "scal_partials_us", (41, 42): "scal_butterfly_us",
+             (42, 43): "scal_fp64_us", (43, 17): "scal_exit_us", (15, 16): "layer_store_sync_us",
              (14, 16): "layer_no_inverse_us", (20, 21): "sensor_stage_windows_us", (21, 22): "sensor_P_us",
              (22, 23): "sensor_slopes_us", (23, 24): "sensor_gammaT_store_us"}
     steps = {}
@@ -384,7 +390,7 @@ def profile_mode(args):
         S.layers(out)
     S.sync()
     print(json.dumps({"profile_mode": True, "frames": args.warmup + args.steps, "plan": S.describe(),
-                      "phases": phase_breakdown(S, pool_dev)}), flush=True)
+                      "phases": phase_breakdown(S, pool_dev, dump=args.trace_out)}), flush=True)
     S.close()
 
 
@@ -398,6 +404,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 35-layer fit and 64-instance batch lines")
     ap.add_argument("--profile", action="store_true", help="stream launches only (for ncu), no timing")
+    ap.add_argument("--trace-out", default=None, help="with --profile: save the raw phase traces (.npy)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -209,7 +209,8 @@ int fewha_get_trace(fewha_handle* h, unsigned long long* out, int max_entries, i
 /* Marks inside the phases of the last traced fused launch (profiling aid):
  * per CTA a row of per_cta values (tag << 56 | globaltimer ns), 0 = unused.
  * Tags: 10..16 layer phase (start, sensor rows staged, P^T done, forward DWT
- * done, update done, inverse DWT done, end); 20..24 sensor tile (start,
+ * done, update done, inverse DWT done, end), 17 / 18 inside the update of an
+ * iteration (scalars known, elementwise loop done); 20..24 sensor tile (start,
  * windows staged, P done, slopes done, end); 30 RHS sensor tile start.
  * Synchronises.  Errors: STATE on the plain path. */
 int fewha_get_fine_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* per_cta, int* grid);

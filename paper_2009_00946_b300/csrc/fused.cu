@@ -39,6 +39,7 @@ constexpr int kMaxC = 16;
 constexpr int kMaxLayersFused = 64;
 constexpr int kMaxWfsFused = 16;
 constexpr int kFineCap = 1024;   // sub-phase marks per CTA per traced launch
+constexpr int kWd = 7;     // ints per layer in a sensor tile's window descriptor
 constexpr int kMaxKG = 4;        // P^T gather entries per layer row / column
 
 enum { kModeRhs = 0, kModeData = 1 };
@@ -75,8 +76,8 @@ struct FParams {
     const WItem* witems;
     const LItem* litems;
     const int2* stg;       // Pt staging row ranges per (layer item, rank, sensor)
-    double* wpart;         // [n_witems]
-    double* lpart;         // [2][n_litems * C][2]
+    float2* wpart;         // [n_witems] data part of mu, double-float (hi, lo)
+    float4* lpart;         // [2][n_litems * C] (rho hi, lo, alpha D z.z hi, lo)
     // static work lists: sensor tiles of CTA b are wsched[wsched_off[b] ..
     // wsched_off[b+1]), layer items of cluster k lsched[lsched_off[k] ..)
     const int* wsched;
@@ -95,6 +96,8 @@ struct FParams {
     int n_iter, warm, replace, out_layers;
     int C;
     int stripe_floats, stage_floats, win_floats, tile_nodes, tile_subaps, tile_rows, tile_cols;
+    int ltab_off, stab_off;   // dynamic shared memory (floats) of the layer / sensor tables
+    int shared_tables;        // 1: the tables lie in the phases' common working area (rebuilt per phase)
     int G_max, n_max;
     float h[6], g[6];
 };
@@ -124,6 +127,15 @@ __device__ __forceinline__ void trace_mark(const FParams& P, int slot, int which
 __device__ int* fmark_counter() {
     __shared__ int cnt;
     return &cnt;
+}
+
+// Mark by thread 0 alone (no block barrier): for steps inside warp 0's work.
+__device__ __forceinline__ void fmark0(const FParams& P, int tag) {
+    if (!P.ftrace || threadIdx.x != 0) return;
+    int* c = fmark_counter();
+    if (*c < P.fcap)
+        P.ftrace[(size_t)blockIdx.x * P.fcap + (*c)++] = ((unsigned long long)tag << 56) |
+                                                         (global_ns() & 0x00FFFFFFFFFFFFFFull);
 }
 
 __device__ __forceinline__ void fmark(const FParams& P, int tag) {
@@ -203,29 +215,100 @@ struct Acc2 {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-__device__ __forceinline__ double block_reduce(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (w == 0) {
-        r = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-    }
-    return r;   // thread 0
+// Double-float sums for the block reductions: the FP64 pipe of this part
+// issues about two FMAs per clock per SM, so FP64 work done by every thread
+// of a block at once (conversions, shuffle-adds) costs microseconds; pairs of
+// floats combined by TwoSum keep about 44 bits and stay on the FP32 pipe.
+// Only thread 0 forms the FP64 result.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
+
+// (h, l) += (bh, bl), renormalised
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+    float s, e;
+    two_sum(h, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(l, bl));
+    h = __fadd_rn(s, e);
+    l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// Block sums of two accumulators as double-float pairs (hi, lo) of A and B
+// (red: 32 float4 of shared memory); valid in thread 0.  Every thread must
+// call it.
+__device__ __forceinline__ float4 block_reduce2(const Acc2& A, const Acc2& B, float4* red) {
+    float ah, al, bh, bl;
+    two_sum(A.hi, A.lo, ah, al);
+    two_sum(B.hi, B.lo, bh, bl);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float x0 = __shfl_down_sync(0xffffffffu, ah, o), x1 = __shfl_down_sync(0xffffffffu, al, o);
+        const float y0 = __shfl_down_sync(0xffffffffu, bh, o), y1 = __shfl_down_sync(0xffffffffu, bl, o);
+        df_add(ah, al, x0, x1);
+        df_add(bh, bl, y0, y1);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = make_float4(ah, al, bh, bl);
+    __syncthreads();
+    if (w == 0) {
+        const float4 v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ah = v.x;
+        al = v.y;
+        bh = v.z;
+        bl = v.w;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float x0 = __shfl_down_sync(0xffffffffu, ah, o), x1 = __shfl_down_sync(0xffffffffu, al, o);
+            const float y0 = __shfl_down_sync(0xffffffffu, bh, o), y1 = __shfl_down_sync(0xffffffffu, bl, o);
+            df_add(ah, al, x0, x1);
+            df_add(bh, bl, y0, y1);
+        }
+    }
+    return make_float4(ah, al, bh, bl);
+}
+
+// Static data of the work items a CTA is on, in shared memory: descriptors,
+// window layout and gather tables are (re)built only when the item changes,
+// so a CTA that owns one sensor tile and one layer item for the whole launch
+// reads them from global memory once.
+struct CtaCache {
+    int wkey, lkey, wtab;       // cached sensor item, layer item; window tables built
+    WItem W;
+    LItem LI;
+    int ns, w_noff, w_soff, w_moff;
+    float w;
+    int n, J, off;
+    FInst IW, IL;
+};
 
 // ---------------------------------------------------------------------------
 // sensor phase: P, Gamma, C^{-1}, Gamma^T on one tile of nodes
 // ---------------------------------------------------------------------------
-__device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, bool want_mu, int* wdesc, double* red) {
-    const WItem W = P.witems[item];
-    const FInst& I = P.inst[W.inst];
-    const int g = W.g, ns = I.wfs_n[g], np1 = ns + 1, L = I.L;
+__device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, bool want_mu, int* wdesc, double* red,
+                            CtaCache* cc) {
     const int tid = threadIdx.x, NT = blockDim.x;
     fmark(P, mode == kModeData ? 20 : 30);
+    if (P.shared_tables && tid == 0) cc->lkey = -1;   // this phase overwrites the layer tables
+    if (cc->wkey != item) {
+        __syncthreads();   // the previous item's data may still be in use
+        if (tid == 0) {
+            cc->W = P.witems[item];
+            cc->IW = P.inst[cc->W.inst];
+            const int gg = cc->W.g;
+            cc->ns = cc->IW.wfs_n[gg];
+            cc->w_noff = cc->IW.wfs_noff[gg];
+            cc->w_soff = cc->IW.wfs_soff[gg];
+            cc->w_moff = cc->IW.wfs_moff[gg];
+            cc->w = cc->IW.wfs_w[gg];
+            cc->wkey = item;
+            cc->wtab = 0;
+        }
+        __syncthreads();
+    }
+    const WItem& W = cc->W;
+    const FInst& I = cc->IW;
+    const int g = W.g, ns = cc->ns, np1 = ns + 1, L = I.L;
     // psi nodes [a_lo, a_hi] x [b_lo, b_hi]; subapertures [a_lo, sa_hi) x [b_lo, sb_hi)
     const int a_lo = max(W.i0 - 1, 0), a_hi = min(W.i1, ns);
     const int b_lo = max(W.j0 - 1, 0), b_hi = min(W.j1, ns);
@@ -237,61 +320,70 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     float* slx = psi + P.tile_nodes;
     float* sly = slx + P.tile_subaps;
     // per-tile interpolation tables: [l][row] window offset / weight, [l][col]
-    int* roff = (int*)(sly + P.tile_subaps);
+    int* roff = (int*)(sm + P.stab_off);
     float* rw = (float*)(roff + L * P.tile_rows);
     int* coff = (int*)(rw + L * P.tile_rows);
     float* cw = (float*)(coff + L * P.tile_cols);
     Acc2 mu;
     const int ns2 = ns * ns;
     if (mode == kModeData) {
-        if (tid < L) {
-            // window of layer tid: rows r0..r1, columns widened to 16-byte
-            // boundaries (c0 down, width up to a multiple of 4 floats; layer
-            // rows are multiples of 4 floats, so the widened window stays inside)
-            const int base = I.tab_off[g * L + tid];
-            const int r0 = I.cy[base + a_lo], r1 = I.cy[base + a_hi] + 1;
-            const int c0 = I.cx[base + b_lo] & ~3, c1 = I.cx[base + b_hi] + 1;
-            wdesc[tid * 5 + 0] = r0;
-            wdesc[tid * 5 + 1] = c0;
-            wdesc[tid * 5 + 2] = r1 - r0 + 1;
-            wdesc[tid * 5 + 3] = (c1 - c0 + 1 + 3) & ~3;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int o = 0;
-            for (int l = 0; l < L; ++l) {
-                wdesc[l * 5 + 4] = o;
-                o += wdesc[l * 5 + 2] * wdesc[l * 5 + 3];
+        const bool build = !cc->wtab;
+        if (build) {
+            if (tid < L) {
+                // window of layer tid: rows r0..r1, columns widened to 16-byte
+                // boundaries (c0 down, width up to a multiple of 4 floats; layer
+                // rows are multiples of 4 floats, so the widened window stays inside)
+                const int base = I.tab_off[g * L + tid];
+                const int r0 = I.cy[base + a_lo], r1 = I.cy[base + a_hi] + 1;
+                const int c0 = I.cx[base + b_lo] & ~3, c1 = I.cx[base + b_hi] + 1;
+                const int n = I.lay_n[tid];
+                wdesc[tid * kWd + 0] = r0;
+                wdesc[tid * kWd + 1] = c0;
+                wdesc[tid * kWd + 2] = r1 - r0 + 1;
+                wdesc[tid * kWd + 3] = (c1 - c0 + 1 + 3) & ~3;
+                wdesc[tid * kWd + 5] = I.lay_off[tid] + r0 * n + c0;
+                wdesc[tid * kWd + 6] = n;
             }
-            wdesc[L * 5 + 4] = o;
+            __syncthreads();
+            if (tid == 0) {
+                int o = 0;
+                for (int l = 0; l < L; ++l) {
+                    wdesc[l * kWd + 4] = o;
+                    o += wdesc[l * kWd + 2] * wdesc[l * kWd + 3];
+                }
+                wdesc[L * kWd + 4] = o;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         // 16-byte asynchronous copies (through L2, not L1): warps over rows,
         // lanes over the float4 columns of a row
         {
             const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
             for (int l = 0; l < L; ++l) {
-                const int nr = wdesc[l * 5 + 2], nc4 = wdesc[l * 5 + 3] >> 2, n = I.lay_n[l];
-                const float* src = I.phi + I.lay_off[l] + (long)wdesc[l * 5] * n + wdesc[l * 5 + 1];
-                float* dst = win + wdesc[l * 5 + 4];
+                const int nr = wdesc[l * kWd + 2], nc4 = wdesc[l * kWd + 3] >> 2, n = wdesc[l * kWd + 6];
+                const float* src = I.phi + wdesc[l * kWd + 5];
+                float* dst = win + wdesc[l * kWd + 4];
                 for (int rr = warp; rr < nr; rr += nwarps)
                     for (int c4 = lane; c4 < nc4; c4 += 32)
                         cp_async16(dst + rr * (nc4 << 2) + (c4 << 2), src + (long)rr * n + (c4 << 2));
             }
             cp_async_wait_all();
         }
-        for (int e = tid; e < L * (pr + pc); e += NT) {
-            const int l = e / (pr + pc), k = e - l * (pr + pc);
-            const int base = I.tab_off[g * L + l];
-            if (k < pr) {
-                roff[l * P.tile_rows + k] = (__ldg(I.cy + base + a_lo + k) - wdesc[l * 5]) * wdesc[l * 5 + 3] +
-                                            wdesc[l * 5 + 4];
-                rw[l * P.tile_rows + k] = __ldg(I.ty + base + a_lo + k);
-            } else {
-                const int kk = k - pr;
-                coff[l * P.tile_cols + kk] = __ldg(I.cx + base + b_lo + kk) - wdesc[l * 5 + 1];
-                cw[l * P.tile_cols + kk] = __ldg(I.tx + base + b_lo + kk);
+        if (build) {
+            for (int e = tid; e < L * (pr + pc); e += NT) {
+                const int l = e / (pr + pc), k = e - l * (pr + pc);
+                const int base = I.tab_off[g * L + l];
+                if (k < pr) {
+                    roff[l * P.tile_rows + k] =
+                        (__ldg(I.cy + base + a_lo + k) - wdesc[l * kWd]) * wdesc[l * kWd + 3] + wdesc[l * kWd + 4];
+                    rw[l * P.tile_rows + k] = __ldg(I.ty + base + a_lo + k);
+                } else {
+                    const int kk = k - pr;
+                    coff[l * P.tile_cols + kk] = __ldg(I.cx + base + b_lo + kk) - wdesc[l * kWd + 1];
+                    cw[l * P.tile_cols + kk] = __ldg(I.tx + base + b_lo + kk);
+                }
             }
+            if (tid == 0) cc->wtab = 1;
         }
         __syncthreads();
         fmark(P, 21);
@@ -299,7 +391,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             const int ii = e / pc, jj = e - ii * pc;
             float acc = 0.f;
             for (int l = 0; l < L; ++l) {
-                const int nc = wdesc[l * 5 + 3];
+                const int nc = wdesc[l * kWd + 3];
                 const float ty = rw[l * P.tile_rows + ii], tx = cw[l * P.tile_cols + jj];
                 const float* f = win + roff[l * P.tile_rows + ii] + coff[l * P.tile_cols + jj];
                 acc += (1.f - ty) * ((1.f - tx) * f[0] + tx * f[1]) + ty * ((1.f - tx) * f[nc] + tx * f[nc + 1]);
@@ -308,14 +400,14 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         }
         __syncthreads();
         fmark(P, 22);
-        const float w = I.wfs_w[g];
+        const float w = cc->w;
         for (int e = tid; e < nsr * nsc; e += NT) {
             const int aa = e / nsc, bb = e - aa * nsc;
             const int a = a_lo + aa, b = b_lo + bb;
             const float* pp = psi + aa * pc + bb;
             const float sx = ((pp[1] - pp[0]) + (pp[pc + 1] - pp[pc])) / 2;
             const float sy = ((pp[pc] - pp[0]) + (pp[pc + 1] - pp[1])) / 2;
-            const float wm = I.mask[I.wfs_moff[g] + a * ns + b] ? w : 0.f;
+            const float wm = I.mask[cc->w_moff + a * ns + b] ? w : 0.f;
             slx[e] = wm * sx;
             sly[e] = wm * sy;
             if (want_mu && a >= W.i0 && b >= W.j0) {
@@ -324,12 +416,12 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             }
         }
     } else {
-        const float w = I.wfs_w[g];
-        const float* S = I.slopes + I.wfs_soff[g];
+        const float w = cc->w;
+        const float* S = I.slopes + cc->w_soff;
         for (int e = tid; e < nsr * nsc; e += NT) {
             const int aa = e / nsc, bb = e - aa * nsc;
             const int a = a_lo + aa, b = b_lo + bb;
-            const bool on = I.mask[I.wfs_moff[g] + a * ns + b] != 0;
+            const bool on = I.mask[cc->w_moff + a * ns + b] != 0;
             const float vx = __ldcg(S + a * ns + b), vy = __ldcg(S + ns2 + a * ns + b);
             const bool fx = isfinite(vx), fy = isfinite(vy);
             if (on && (!fx || !fy) && a >= W.i0 && b >= W.j0) atomicOr(P.errw, kErrInput);
@@ -340,7 +432,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     __syncthreads();
     fmark(P, 23);
     const int ti = W.i1 - W.i0, tj = W.j1 - W.j0;
-    float* out = I.psi + I.wfs_noff[g];
+    float* out = I.psi + cc->w_noff;
     for (int e = tid; e < ti * tj; e += NT) {
         const int ii = e / tj, jj = e - ii * tj;
         const int i = W.i0 + ii, j = W.j0 + jj;
@@ -357,8 +449,8 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         out[i * np1 + j] = acc / 2;
     }
     if (want_mu) {
-        const double s = block_reduce(mu.value(), red);
-        if (tid == 0) P.wpart[item] = s;
+        const float4 s = block_reduce2(mu, Acc2(), (float4*)red);
+        if (tid == 0) P.wpart[item] = make_float2(s.x, s.y);
     }
     __syncthreads();
     fmark(P, 24);
@@ -537,48 +629,82 @@ __device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb
 // ---------------------------------------------------------------------------
 // layer phase
 // ---------------------------------------------------------------------------
-__device__ void alg2_scalars(const FParams& P, const FInst& I, int k, double* sh) {
-    // rho_k and mu_k of the instance, summed in a fixed order; alpha_k, beta_k
-    if (threadIdx.x < 32) {
+// Called by warp 0 alone (no block barrier inside): the caller synchronises
+// the block before sh[] is read.  The partials it reads were all written
+// before the grid barrier that opened this layer phase.
+__device__ void alg2_scalars_warp(const FParams& P, const FInst& I, int k, double* sh) {
+    // rho_k and mu_k of the instance, summed in a fixed order as double-float
+    // pairs; then alpha_k, beta_k in FP64 with two division chains: beta and
+    // rho^2 / (rho_{k-1} alpha_{k-1}) on two lanes at once, then alpha
+    {
         const int lane = threadIdx.x, C = P.C, par = k & 1;
-        const double* lp = P.lpart + (size_t)par * P.n_litems * C * 2;
-        double rho = 0.0, mu = 0.0;
+        double rho_old = 1.0, aold = 1.0;
+        if (k > 0) {   // issued first: independent of the partials
+            const double* so = I.scal + ((k - 1) & 1) * 2;
+            rho_old = __ldcg(so);
+            aold = __ldcg(so + 1);
+        }
+        fmark0(P, 40);
+        const float4* lp = P.lpart + (size_t)par * P.n_litems * C + (size_t)I.l0 * C;
+        float rh = 0.f, rl = 0.f, mh = 0.f, ml = 0.f;
         // written by other CTAs in this launch: read through L2, never L1;
         // up to 8 entries per lane per round, all loads issued before the adds
         const int nlc = I.nl * C;
+        // per round a pairwise tree over the 8 loaded entries (depth 3), then
+        // one add into the running sums
         for (int e0 = lane; e0 < nlc; e0 += 8 * 32) {
-            double2 v[8];
+            float4 v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                v[u] = (e0 + 32 * u < nlc) ? __ldcg((const double2*)(lp + ((size_t)I.l0 * C + e0 + 32 * u) * 2))
-                                           : make_double2(0.0, 0.0);
+                v[u] = (e0 + 32 * u < nlc) ? __ldcg(lp + e0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                rho += v[u].x;
-                mu += v[u].y;
-            }
+            for (int st = 1; st < 8; st <<= 1)
+#pragma unroll
+                for (int u = 0; u < 8; u += 2 * st) {
+                    df_add(v[u].x, v[u].y, v[u + st].x, v[u + st].y);
+                    df_add(v[u].z, v[u].w, v[u + st].z, v[u + st].w);
+                }
+            df_add(rh, rl, v[0].x, v[0].y);
+            df_add(mh, ml, v[0].z, v[0].w);
         }
         for (int e0 = lane; e0 < I.nw; e0 += 8 * 32) {
-            double v[8];
+            float2 v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (e0 + 32 * u < I.nw) ? __ldcg(P.wpart + I.w0 + e0 + 32 * u) : 0.0;
+            for (int u = 0; u < 8; ++u)
+                v[u] = (e0 + 32 * u < I.nw) ? __ldcg(P.wpart + I.w0 + e0 + 32 * u) : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) mu += v[u];
+            for (int st = 1; st < 8; st <<= 1)
+#pragma unroll
+                for (int u = 0; u < 8; u += 2 * st) df_add(v[u].x, v[u].y, v[u + st].x, v[u + st].y);
+            df_add(mh, ml, v[0].x, v[0].y);
         }
+        fmark0(P, 41);
+        // butterfly: df_add is commutative, so every lane ends with the same sums
         for (int o = 16; o > 0; o >>= 1) {
-            rho += __shfl_down_sync(0xffffffffu, rho, o);
-            mu += __shfl_down_sync(0xffffffffu, mu, o);
+            const float a0 = __shfl_xor_sync(0xffffffffu, rh, o), a1 = __shfl_xor_sync(0xffffffffu, rl, o);
+            const float b0 = __shfl_xor_sync(0xffffffffu, mh, o), b1 = __shfl_xor_sync(0xffffffffu, ml, o);
+            df_add(rh, rl, a0, a1);
+            df_add(mh, ml, b0, b1);
         }
+        fmark0(P, 42);
+        // to FP64: lanes 0..3 convert one float each, lanes 0 / 2 add the pairs
+        const float mine = lane == 0 ? rh : lane == 1 ? rl : lane == 2 ? mh : ml;
+        const double dm = (double)mine;
+        const double pr = dm + __shfl_down_sync(0xffffffffu, dm, 1);
+        const double rho = __shfl_sync(0xffffffffu, pr, 0), mu = __shfl_sync(0xffffffffu, pr, 2);
+        double beta = 0.0, denom = mu;
+        if (k > 0) {
+            // beta = rho / rho_{k-1};  mu - rho beta / alpha_{k-1} = mu - rho^2 / (rho_{k-1} alpha_{k-1})
+            const double num = (lane == 1) ? rho * rho : rho;
+            const double den = (lane == 1) ? rho_old * aold : rho_old;
+            const double q = num / den;
+            beta = __shfl_sync(0xffffffffu, q, 0);
+            denom = mu - __shfl_sync(0xffffffffu, q, 1);
+        }
+        double a = rho / denom;
+        fmark0(P, 43);
         if (lane == 0) {
-            double beta = 0.0, denom = mu, aold = 0.0;
-            if (k > 0) {
-                const double* so = I.scal + ((k - 1) & 1) * 2;
-                beta = rho / __ldcg(so);
-                aold = __ldcg(so + 1);
-                denom = mu - rho * beta / aold;
-            }
-            double a = rho / denom;
-            bool bad = !(denom > 0.0) || !isfinite(a) || !isfinite(beta);
+            const bool bad = !(denom > 0.0) || !isfinite(a) || !isfinite(beta);
             if (bad) {
                 a = 0.0;
                 beta = 0.0;
@@ -591,33 +717,48 @@ __device__ void alg2_scalars(const FParams& P, const FInst& I, int k, double* sh
             sh[5] = (a != 0.0) ? a : aold;
         }
     }
-    __syncthreads();
 }
 
 __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm, float* const (*rem)[kMaxC],
-                            cg::cluster_group& cl, double* red, double* sh) {
-    const LItem LI = P.litems[li];
-    const FInst& I = P.inst[LI.inst];
+                            cg::cluster_group& cl, double* red, double* sh, CtaCache* cc) {
+    const int tid = threadIdx.x, NT = blockDim.x;
+    fmark(P, 10);
+    const bool fresh = cc->lkey != li;   // else descriptors, sgi and gather tables are cached
+    if (P.shared_tables && tid == 0) cc->wtab = 0;   // this phase overwrites the window tables
+    if (fresh) {
+        __syncthreads();   // the previous item's tables may still be in use
+        if (tid == 0) {
+            cc->LI = P.litems[li];
+            cc->IL = P.inst[cc->LI.inst];
+            const int ll = cc->LI.l;
+            cc->n = cc->IL.lay_n[ll];
+            cc->J = cc->IL.lay_J[ll];
+            cc->off = cc->IL.lay_off[ll];
+            cc->lkey = li;
+        }
+        __syncthreads();
+    }
+    const LItem& LI = cc->LI;
+    const FInst& I = cc->IL;
     const int l = LI.l, C = P.C, rank = (int)cl.block_rank();
-    const int n = I.lay_n[l], J = I.lay_J[l], off = I.lay_off[l];
+    const int n = cc->n, J = cc->J, off = cc->off;
     const int R = n / C, row0 = rank * R;
-    const int tid = threadIdx.x, NT = blockDim.x, G = I.G, L = I.L;
+    const int G = I.G, L = I.L;
     const int SF = P.stripe_floats;
     __shared__ int sgi[8 * kMaxWfsFused];
-    fmark(P, 10);
     float* Z = sm;
     float* B1 = sm + SF;
     float* B2 = sm + 2 * SF;
     float* B3 = sm + 3 * SF;
     float* stg = sm + 4 * SF;
-    int2* xt = (int2*)(stg + P.stage_floats);          // [g][q][KG]  (j, w)
+    int2* xt = (int2*)(sm + P.ltab_off);                // [g][q][KG]  (j, w)
     int2* yt = xt + P.G_max * P.n_max * I.KG;           // [g][row][KG] (i, w)
     const int ln = 31 - __clz(n), lR = 31 - __clz(R), KG = I.KG;
     Stripe s{n, J, R, row0, ln, lR};
 
     // ---- P^T: gather of the sensor fields into the own rows ----
     {
-        if (tid < G) {
+        if (fresh && tid < G) {
             // staged rows imin..imax-1 of sensor tid are one contiguous range of
             // the field array; it is copied from the 16-byte boundary below its
             // start, so its data begin (start & 3) floats into its staging slot
@@ -644,20 +785,22 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             sgi[tid * 8 + 5] = c4;
             sgi[tid * 8 + 6] = so;
         }
-        __syncthreads();
+        if (fresh) __syncthreads();
         for (int g = 0; g < G; ++g) {
             const int c4 = sgi[g * 8 + 5];
             const float* src = I.psi + sgi[g * 8 + 4];
             float* dst = stg + sgi[g * 8 + 6];
             for (int e = tid; e < c4; e += NT) cp_async16(dst + (e << 2), src + (e << 2));
         }
+        // the CG scalars of this iteration, while the copies are in flight
+        if (mode == kLpIter && tid < 32) alg2_scalars_warp(P, I, k, sh);
         cp_async_wait_all();
         // compact gather tables: columns for every sensor, rows of this stripe
-        for (int e = tid; e < G * n * KG; e += NT) {
+        for (int e = tid; fresh && e < G * n * KG; e += NT) {
             const int g = e / (n * KG), r = e - g * n * KG;
             xt[e] = __ldg(I.gtab + I.gtab_off[g * L + l] + r);
         }
-        for (int e = tid; e < G * R * KG; e += NT) {
+        for (int e = tid; fresh && e < G * R * KG; e += NT) {
             const int g = e / (R * KG), r = e - g * R * KG;
             yt[e] = __ldg(I.gtab + I.gtab_off[g * L + l] + n * KG + row0 * KG + r);
         }
@@ -742,8 +885,8 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
                 }
             }
         };
-        load(tid);
-        alg2_scalars(P, I, k, sh);
+        load(tid);   // sh[] holds the scalars (computed during the staging above)
+        fmark(P, 17);
         const double alpha = sh[0], beta = sh[1];
         if (tid == 0 && li == I.l0 && rank == 0) {
             double* sw = I.scal + (k & 1) * 2;
@@ -822,15 +965,11 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
         }
         Z[e] = zout;
     }
+    if (mode == kLpIter) fmark(P, 18);
     if (make_z) {
         const int par = (mode == kLpIter) ? ((k + 1) & 1) : 0;
-        const double rs = block_reduce(rho_p.value(), red);
-        const double ds = block_reduce(dz_p.value(), red);
-        if (tid == 0) {
-            double* lp = P.lpart + ((size_t)par * P.n_litems * C + (size_t)li * C + rank) * 2;
-            lp[0] = rs;
-            lp[1] = ds;
-        }
+        const float4 rd = block_reduce2(rho_p, dz_p, (float4*)red);
+        if (tid == 0) P.lpart[(size_t)par * P.n_litems * C + (size_t)li * C + rank] = rd;
     }
 
     // ---- inverse DWT -> phi ----
@@ -856,9 +995,10 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     k_fused_frame(const __grid_constant__ FParams P) {
     extern __shared__ __align__(16) float sm[];
     __shared__ float* rem[4][kMaxC];
-    __shared__ double red[32];
+    __shared__ __align__(16) double red[64];   // 32 float4 for the block reductions
     __shared__ double sh[8];
-    __shared__ int wdesc[(kMaxLayersFused + 1) * 5];
+    __shared__ int wdesc[(kMaxLayersFused + 1) * kWd];
+    __shared__ CtaCache cc;
     __shared__ int s_abort;
     cg::cluster_group cl = cg::this_cluster();
     const int C = P.C;
@@ -883,28 +1023,30 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     if (threadIdx.x == 0) {
         s_abort = 0;
         *fmark_counter() = 0;
+        cc.wkey = cc.lkey = -1;
+        cc.wtab = 0;
     }
     unsigned target = 0;
     __syncthreads();
 
     // Alg. 1 RHS: Gamma^T C^{-1} s per sensor tile
-    for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeRhs, false, wdesc, red);
+    for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeRhs, false, wdesc, red, &cc);
     grid_barrier(P, target, &s_abort, slot);
     // P^T, W -> b; warm restart (or c -> phi for the replacement); z_0 -> phi
     const int m1 = P.replace ? kLpRhsRepl : kLpRhsStart;
-    for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], m1, 0, sm, rem, cl, red, sh);
+    for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], m1, 0, sm, rem, cl, red, sh, &cc);
     grid_barrier(P, target, &s_abort, slot);
     if (P.replace) {
         // r = b - M c: data term of M on phi_c, then the layer phase
-        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, false, wdesc, red);
+        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, false, wdesc, red, &cc);
         grid_barrier(P, target, &s_abort, slot);
-        for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpReplStart, 0, sm, rem, cl, red, sh);
+        for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpReplStart, 0, sm, rem, cl, red, sh, &cc);
         grid_barrier(P, target, &s_abort, slot);
     }
     for (int k = 0; k < P.n_iter; ++k) {
-        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, true, wdesc, red);
+        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, true, wdesc, red, &cc);
         grid_barrier(P, target, &s_abort, slot);
-        for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpIter, k, sm, rem, cl, red, sh);
+        for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpIter, k, sm, rem, cl, red, sh, &cc);
         if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort, slot);
     }
     __syncthreads();
@@ -1108,7 +1250,18 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         Gtot += hss[i]->G;
     }
     const int sms = prop.multiProcessorCount;
-    const size_t smem_cap = (size_t)prop.sharedMemPerBlockOptin - 4096;
+    // dynamic shared memory available next to the kernel's static arrays
+    size_t smem_cap = 0;
+    {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fused_kernel_for(8)) != cudaSuccess ||
+            fa.sharedSizeBytes + 1024 >= (size_t)prop.sharedMemPerBlockOptin) {
+            cudaGetLastError();
+            err = "cannot query the fused kernel";
+            return nullptr;
+        }
+        smem_cap = (size_t)prop.sharedMemPerBlockOptin - fa.sharedSizeBytes - 1024;
+    }
 
     FusedPlan* best = nullptr;
     for (int C : {8, 4, 16, 2, 1}) {
@@ -1153,14 +1306,19 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         const int Rmax = nmax / C;
         stage_max = (stage_max + 3) & ~3;
         const size_t gtab_floats = 2 * (size_t)Gmax * nmax * KGmax + 2 * (size_t)Gmax * Rmax * KGmax;
-        const size_t layer_floats = 4 * (size_t)stripe + stage_max + gtab_floats;
+        const size_t layer_floats = 4 * (size_t)stripe + stage_max;   // working set (gather tables apart)
 
         // co-resident clusters: one 512-thread CTA per SM (register-limited),
         // so the answer does not depend on the shared memory below the cap;
         // the attribute is per function: allow the device maximum once
         const FusedKernel kern = fused_kernel_for(C);
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
-        if (C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap) != cudaSuccess ||
+            (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+            cudaGetLastError();
+            if (err.empty()) err = "the fused kernel's launch attributes were refused";
+            delete pl;
+            continue;
+        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C * 1024);
         cfg.blockDim = dim3(kFThreads);
@@ -1227,9 +1385,20 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         tile_nodes = (tile_nodes + 3) & ~3;
         tile_sub = (tile_sub + 3) & ~3;
         win_max = (win_max + 3) & ~3;
-        const size_t sensor_floats = (size_t)win_max + tile_nodes + 2 * (size_t)tile_sub +
-                                     2 * (size_t)Lmax * (tile_rows + tile_cols);
-        const size_t smem = std::max(layer_floats, sensor_floats) * sizeof(float);
+        const size_t sensor_floats = (size_t)win_max + tile_nodes + 2 * (size_t)tile_sub;
+        const size_t stab_floats = 2 * (size_t)Lmax * (tile_rows + tile_cols);
+        // [working set of either phase][layer gather tables][sensor tables]:
+        // the tables persist across phases for a CTA that keeps its items
+        const size_t work_floats = (std::max(layer_floats, sensor_floats) + 3) & ~(size_t)3;
+        size_t smem = (work_floats + gtab_floats + stab_floats) * sizeof(float);
+        bool shared_tables = false;
+        if (smem > smem_cap) {
+            // too big to keep the tables apart: each phase's tables follow its own
+            // working set, and each phase invalidates the other's
+            shared_tables = true;
+            const size_t lw = (layer_floats + 3) & ~(size_t)3;
+            smem = std::max(lw + gtab_floats, sensor_floats + stab_floats) * sizeof(float);
+        }
         if (smem > smem_cap) {
             if (err.empty()) err = "the staged windows do not fit in shared memory";
             delete pl;
@@ -1315,10 +1484,11 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         WItem* dw = nullptr;
         LItem* dl = nullptr;
         int2* ds = nullptr;
-        double *wp = nullptr, *lp = nullptr;
+        float2* wp = nullptr;
+        float4* lp = nullptr;
         unsigned* bar = nullptr;
         ok = ok && dupload(pl, dw, witems, err) && dupload(pl, dl, litems, err) && dupload(pl, ds, stg, err) &&
-             dalloc(pl, wp, witems.size(), err) && dalloc(pl, lp, 2 * litems.size() * C * 2, err) &&
+             dalloc(pl, wp, witems.size(), err) && dalloc(pl, lp, 2 * litems.size() * C, err) &&
              dalloc(pl, bar, 1, err) && dupload(pl, pl->d_inst, pl->inst, err);
         if (!ok) {
             fused_destroy(pl);
@@ -1346,6 +1516,9 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         P.win_floats = win_max;
         P.tile_nodes = tile_nodes;
         P.tile_subaps = tile_sub;
+        P.shared_tables = shared_tables ? 1 : 0;
+        P.ltab_off = shared_tables ? (int)((layer_floats + 3) & ~(size_t)3) : (int)work_floats;
+        P.stab_off = shared_tables ? (int)sensor_floats : (int)(work_floats + gtab_floats);
         P.tile_rows = tile_rows;
         P.tile_cols = tile_cols;
         P.G_max = Gmax;
