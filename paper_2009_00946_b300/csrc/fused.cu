@@ -268,12 +268,132 @@ __device__ __forceinline__ float4 block_reduce2(const Acc2& A, const Acc2& B, fl
     return make_float4(ah, al, bh, bl);
 }
 
+// The CG scalars of iteration k, by warp 0 alone (no block barrier inside;
+// the caller synchronises the block before sh[] is read).  Partials are
+// summed in a fixed order as double-float pairs, so every CTA of an instance
+// obtains bit-identical scalars.
+//  part A needs only the previous layer phase: rho_k, the regulariser part of
+//         mu_k, beta_k = rho_k / rho_{k-1} and t_k = rho_k^2 / (rho_{k-1}
+//         alpha_{k-1}) (two divisions on two lanes at once);
+//  part B adds the sensor part of mu_k (this iteration's sensor phase) and
+//         forms alpha_k = rho_k / (mu_k - t_k).
+struct ScalA {
+    double rho, beta, t, aold;
+    float mh, ml;   // regulariser part of mu, double-float
+};
+
+__device__ __forceinline__ void warp_df_sum(float& h, float& l) {
+    // butterfly: df_add is commutative, so every lane ends with the same sum
+    for (int o = 16; o > 0; o >>= 1) {
+        const float a0 = __shfl_xor_sync(0xffffffffu, h, o), a1 = __shfl_xor_sync(0xffffffffu, l, o);
+        df_add(h, l, a0, a1);
+    }
+}
+
+__device__ __forceinline__ double df_to_double(float h, float l) {
+    // lanes 0 / 1 convert one float each; every lane receives the sum
+    const int lane = threadIdx.x & 31;
+    const double d = (double)(lane == 0 ? h : l);
+    return __shfl_sync(0xffffffffu, d + __shfl_down_sync(0xffffffffu, d, 1), 0);
+}
+
+__device__ void alg2_part_a(const FParams& P, const FInst& I, int k, ScalA& A) {
+    const int lane = threadIdx.x & 31, C = P.C, par = k & 1;
+    double rho_old = 1.0, aold = 1.0;
+    if (k > 0) {   // issued first: independent of the partials
+        const double* so = I.scal + ((k - 1) & 1) * 2;
+        rho_old = __ldcg(so);
+        aold = __ldcg(so + 1);
+    }
+    fmark0(P, 40);
+    const float4* lp = P.lpart + (size_t)par * P.n_litems * C + (size_t)I.l0 * C;
+    float rh = 0.f, rl = 0.f, mh = 0.f, ml = 0.f;
+    // written by other CTAs in this launch: read through L2, never L1; up to
+    // 8 entries per lane per round, all loads issued before the adds, then a
+    // pairwise tree over them (depth 3) and one add into the running sums
+    const int nlc = I.nl * C;
+    for (int e0 = lane; e0 < nlc; e0 += 8 * 32) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = (e0 + 32 * u < nlc) ? __ldcg(lp + e0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int st = 1; st < 8; st <<= 1)
+#pragma unroll
+            for (int u = 0; u < 8; u += 2 * st) {
+                df_add(v[u].x, v[u].y, v[u + st].x, v[u + st].y);
+                df_add(v[u].z, v[u].w, v[u + st].z, v[u + st].w);
+            }
+        df_add(rh, rl, v[0].x, v[0].y);
+        df_add(mh, ml, v[0].z, v[0].w);
+    }
+    warp_df_sum(rh, rl);
+    warp_df_sum(mh, ml);
+    fmark0(P, 41);
+    const double rho = df_to_double(rh, rl);
+    double beta = 0.0, t = 0.0;
+    if (k > 0) {
+        const double num = (lane == 1) ? rho * rho : rho;
+        const double den = (lane == 1) ? rho_old * aold : rho_old;
+        const double q = num / den;
+        beta = __shfl_sync(0xffffffffu, q, 0);
+        t = __shfl_sync(0xffffffffu, q, 1);
+    }
+    A.rho = rho;
+    A.beta = beta;
+    A.t = t;
+    A.aold = (k > 0) ? aold : 0.0;
+    A.mh = mh;
+    A.ml = ml;
+    fmark0(P, 42);
+}
+
+__device__ void alg2_part_b(const FParams& P, const FInst& I, int k, const ScalA& A, double* sh) {
+    const int lane = threadIdx.x & 31;
+    float wh = 0.f, wl = 0.f;
+    for (int e0 = lane; e0 < I.nw; e0 += 8 * 32) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = (e0 + 32 * u < I.nw) ? __ldcg(P.wpart + I.w0 + e0 + 32 * u) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int st = 1; st < 8; st <<= 1)
+#pragma unroll
+            for (int u = 0; u < 8; u += 2 * st) df_add(v[u].x, v[u].y, v[u + st].x, v[u + st].y);
+        df_add(wh, wl, v[0].x, v[0].y);
+    }
+    warp_df_sum(wh, wl);
+    float mh = A.mh, ml = A.ml;
+    df_add(mh, ml, wh, wl);
+    const double mu = df_to_double(mh, ml);
+    const double denom = (k > 0) ? mu - A.t : mu;
+    double a = A.rho / denom;
+    double beta = A.beta;
+    fmark0(P, 43);
+    if (lane == 0) {
+        const bool bad = !(denom > 0.0) || !isfinite(a) || !isfinite(beta);
+        if (bad) {
+            a = 0.0;
+            beta = 0.0;
+        }
+        sh[0] = a;
+        sh[1] = beta;
+        sh[2] = A.rho;
+        sh[3] = mu;
+        sh[4] = bad ? 1.0 : 0.0;
+        sh[5] = (a != 0.0) ? a : A.aold;
+    }
+}
+
 // Static data of the work items a CTA is on, in shared memory: descriptors,
 // window layout and gather tables are (re)built only when the item changes,
 // so a CTA that owns one sensor tile and one layer item for the whole launch
 // reads them from global memory once.
 struct CtaCache {
     int wkey, lkey, wtab;       // cached sensor item, layer item; window tables built
+    int lres, il_valid;         // the CTA has one layer item for the launch; IL holds it
+    int pre_k;                  // iteration whose scalar part A is in pre (-1: none)
+    double pre[6];              // rho, beta, t, alpha_{k-1}, mu part (as two floats)
     WItem W;
     LItem LI;
     int ns, w_noff, w_soff, w_moff;
@@ -286,7 +406,7 @@ struct CtaCache {
 // sensor phase: P, Gamma, C^{-1}, Gamma^T on one tile of nodes
 // ---------------------------------------------------------------------------
 __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, bool want_mu, int* wdesc, double* red,
-                            CtaCache* cc) {
+                            CtaCache* cc, int k) {
     const int tid = threadIdx.x, NT = blockDim.x;
     fmark(P, mode == kModeData ? 20 : 30);
     if (P.shared_tables && tid == 0) cc->lkey = -1;   // this phase overwrites the layer tables
@@ -355,17 +475,31 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             }
             __syncthreads();
         }
-        // 16-byte asynchronous copies (through L2, not L1): warps over rows,
-        // lanes over the float4 columns of a row
+        // 16-byte asynchronous copies (through L2, not L1), every thread on
+        // every layer's window
         {
-            const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
             for (int l = 0; l < L; ++l) {
                 const int nr = wdesc[l * kWd + 2], nc4 = wdesc[l * kWd + 3] >> 2, n = wdesc[l * kWd + 6];
                 const float* src = I.phi + wdesc[l * kWd + 5];
                 float* dst = win + wdesc[l * kWd + 4];
-                for (int rr = warp; rr < nr; rr += nwarps)
-                    for (int c4 = lane; c4 < nc4; c4 += 32)
-                        cp_async16(dst + rr * (nc4 << 2) + (c4 << 2), src + (long)rr * n + (c4 << 2));
+                for (int e = tid; e < nr * nc4; e += NT) {
+                    const int rr = e / nc4, c4 = e - rr * nc4;
+                    cp_async16(dst + (e << 2), src + (long)rr * n + (c4 << 2));
+                }
+            }
+            // part A of the next layer phase's CG scalars while the copies fly
+            if (want_mu && tid < 32 && cc->lres && cc->il_valid) {
+                ScalA A;
+                alg2_part_a(P, cc->IL, k, A);
+                if (tid == 0) {
+                    cc->pre[0] = A.rho;
+                    cc->pre[1] = A.beta;
+                    cc->pre[2] = A.t;
+                    cc->pre[3] = A.aold;
+                    cc->pre[4] = (double)A.mh;
+                    cc->pre[5] = (double)A.ml;
+                    cc->pre_k = k;
+                }
             }
             cp_async_wait_all();
         }
@@ -629,96 +763,6 @@ __device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb
 // ---------------------------------------------------------------------------
 // layer phase
 // ---------------------------------------------------------------------------
-// Called by warp 0 alone (no block barrier inside): the caller synchronises
-// the block before sh[] is read.  The partials it reads were all written
-// before the grid barrier that opened this layer phase.
-__device__ void alg2_scalars_warp(const FParams& P, const FInst& I, int k, double* sh) {
-    // rho_k and mu_k of the instance, summed in a fixed order as double-float
-    // pairs; then alpha_k, beta_k in FP64 with two division chains: beta and
-    // rho^2 / (rho_{k-1} alpha_{k-1}) on two lanes at once, then alpha
-    {
-        const int lane = threadIdx.x, C = P.C, par = k & 1;
-        double rho_old = 1.0, aold = 1.0;
-        if (k > 0) {   // issued first: independent of the partials
-            const double* so = I.scal + ((k - 1) & 1) * 2;
-            rho_old = __ldcg(so);
-            aold = __ldcg(so + 1);
-        }
-        fmark0(P, 40);
-        const float4* lp = P.lpart + (size_t)par * P.n_litems * C + (size_t)I.l0 * C;
-        float rh = 0.f, rl = 0.f, mh = 0.f, ml = 0.f;
-        // written by other CTAs in this launch: read through L2, never L1;
-        // up to 8 entries per lane per round, all loads issued before the adds
-        const int nlc = I.nl * C;
-        // per round a pairwise tree over the 8 loaded entries (depth 3), then
-        // one add into the running sums
-        for (int e0 = lane; e0 < nlc; e0 += 8 * 32) {
-            float4 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                v[u] = (e0 + 32 * u < nlc) ? __ldcg(lp + e0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int st = 1; st < 8; st <<= 1)
-#pragma unroll
-                for (int u = 0; u < 8; u += 2 * st) {
-                    df_add(v[u].x, v[u].y, v[u + st].x, v[u + st].y);
-                    df_add(v[u].z, v[u].w, v[u + st].z, v[u + st].w);
-                }
-            df_add(rh, rl, v[0].x, v[0].y);
-            df_add(mh, ml, v[0].z, v[0].w);
-        }
-        for (int e0 = lane; e0 < I.nw; e0 += 8 * 32) {
-            float2 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                v[u] = (e0 + 32 * u < I.nw) ? __ldcg(P.wpart + I.w0 + e0 + 32 * u) : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int st = 1; st < 8; st <<= 1)
-#pragma unroll
-                for (int u = 0; u < 8; u += 2 * st) df_add(v[u].x, v[u].y, v[u + st].x, v[u + st].y);
-            df_add(mh, ml, v[0].x, v[0].y);
-        }
-        fmark0(P, 41);
-        // butterfly: df_add is commutative, so every lane ends with the same sums
-        for (int o = 16; o > 0; o >>= 1) {
-            const float a0 = __shfl_xor_sync(0xffffffffu, rh, o), a1 = __shfl_xor_sync(0xffffffffu, rl, o);
-            const float b0 = __shfl_xor_sync(0xffffffffu, mh, o), b1 = __shfl_xor_sync(0xffffffffu, ml, o);
-            df_add(rh, rl, a0, a1);
-            df_add(mh, ml, b0, b1);
-        }
-        fmark0(P, 42);
-        // to FP64: lanes 0..3 convert one float each, lanes 0 / 2 add the pairs
-        const float mine = lane == 0 ? rh : lane == 1 ? rl : lane == 2 ? mh : ml;
-        const double dm = (double)mine;
-        const double pr = dm + __shfl_down_sync(0xffffffffu, dm, 1);
-        const double rho = __shfl_sync(0xffffffffu, pr, 0), mu = __shfl_sync(0xffffffffu, pr, 2);
-        double beta = 0.0, denom = mu;
-        if (k > 0) {
-            // beta = rho / rho_{k-1};  mu - rho beta / alpha_{k-1} = mu - rho^2 / (rho_{k-1} alpha_{k-1})
-            const double num = (lane == 1) ? rho * rho : rho;
-            const double den = (lane == 1) ? rho_old * aold : rho_old;
-            const double q = num / den;
-            beta = __shfl_sync(0xffffffffu, q, 0);
-            denom = mu - __shfl_sync(0xffffffffu, q, 1);
-        }
-        double a = rho / denom;
-        fmark0(P, 43);
-        if (lane == 0) {
-            const bool bad = !(denom > 0.0) || !isfinite(a) || !isfinite(beta);
-            if (bad) {
-                a = 0.0;
-                beta = 0.0;
-            }
-            sh[0] = a;
-            sh[1] = beta;
-            sh[2] = rho;
-            sh[3] = mu;
-            sh[4] = bad ? 1.0 : 0.0;
-            sh[5] = (a != 0.0) ? a : aold;
-        }
-    }
-}
-
 __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm, float* const (*rem)[kMaxC],
                             cg::cluster_group& cl, double* red, double* sh, CtaCache* cc) {
     const int tid = threadIdx.x, NT = blockDim.x;
@@ -735,6 +779,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             cc->J = cc->IL.lay_J[ll];
             cc->off = cc->IL.lay_off[ll];
             cc->lkey = li;
+            cc->il_valid = 1;
         }
         __syncthreads();
     }
@@ -793,7 +838,21 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             for (int e = tid; e < c4; e += NT) cp_async16(dst + (e << 2), src + (e << 2));
         }
         // the CG scalars of this iteration, while the copies are in flight
-        if (mode == kLpIter && tid < 32) alg2_scalars_warp(P, I, k, sh);
+        // (part A from the sensor phase when that CTA computed it there)
+        if (mode == kLpIter && tid < 32) {
+            ScalA A;
+            if (cc->pre_k == k) {
+                A.rho = cc->pre[0];
+                A.beta = cc->pre[1];
+                A.t = cc->pre[2];
+                A.aold = cc->pre[3];
+                A.mh = (float)cc->pre[4];   // exact: stored from floats
+                A.ml = (float)cc->pre[5];
+            } else {
+                alg2_part_a(P, I, k, A);
+            }
+            alg2_part_b(P, I, k, A, sh);
+        }
         cp_async_wait_all();
         // compact gather tables: columns for every sensor, rows of this stripe
         for (int e = tid; fresh && e < G * n * KG; e += NT) {
@@ -1025,12 +1084,15 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
         *fmark_counter() = 0;
         cc.wkey = cc.lkey = -1;
         cc.wtab = 0;
+        cc.lres = (l_hi - l_lo == 1) ? 1 : 0;
+        cc.il_valid = 0;
+        cc.pre_k = -1;
     }
     unsigned target = 0;
     __syncthreads();
 
     // Alg. 1 RHS: Gamma^T C^{-1} s per sensor tile
-    for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeRhs, false, wdesc, red, &cc);
+    for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeRhs, false, wdesc, red, &cc, 0);
     grid_barrier(P, target, &s_abort, slot);
     // P^T, W -> b; warm restart (or c -> phi for the replacement); z_0 -> phi
     const int m1 = P.replace ? kLpRhsRepl : kLpRhsStart;
@@ -1038,13 +1100,13 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     grid_barrier(P, target, &s_abort, slot);
     if (P.replace) {
         // r = b - M c: data term of M on phi_c, then the layer phase
-        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, false, wdesc, red, &cc);
+        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, false, wdesc, red, &cc, 0);
         grid_barrier(P, target, &s_abort, slot);
         for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpReplStart, 0, sm, rem, cl, red, sh, &cc);
         grid_barrier(P, target, &s_abort, slot);
     }
     for (int k = 0; k < P.n_iter; ++k) {
-        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, true, wdesc, red, &cc);
+        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, true, wdesc, red, &cc, k);
         grid_barrier(P, target, &s_abort, slot);
         for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpIter, k, sm, rem, cl, red, sh, &cc);
         if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort, slot);
