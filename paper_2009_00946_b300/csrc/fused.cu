@@ -1607,9 +1607,9 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
 int fused_describe(const FusedPlan* pl, char* buf, int len) {
     return snprintf(buf, len,
                     "fused: %d clusters x %d CTAs (grid %d, %d threads), smem %d B, %d sensor tiles, %d layer items, "
-                    "cooperative %d",
+                    "cooperative %d, tables %s",
                     pl->nclusters, pl->C, pl->grid, kFThreads, pl->smem, pl->P.n_witems, pl->P.n_litems,
-                    pl->cooperative ? 1 : 0);
+                    pl->cooperative ? 1 : 0, pl->P.shared_tables ? "shared" : "kept");
 }
 
 void fused_set_trace(FusedPlan* pl, bool on) { pl->trace_on = on; }
