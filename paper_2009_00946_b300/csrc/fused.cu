@@ -66,6 +66,11 @@ struct FInst {
     const int2* gtab;
     const int* gtab_off;
     int KG;
+    // CTA that computes part A of this instance's CG scalars during the
+    // sensor phase and publishes it in preA[2 parities][6] (-1: the layer CTAs
+    // compute it themselves)
+    int preA_cta;
+    double* preA;
 };
 
 struct WItem { int inst, g, i0, i1, j0, j1; };
@@ -93,6 +98,7 @@ struct FParams {
     long long budget;
     int n_inst, n_witems, n_litems;
     int grid;              // planned grid (the work lists have grid + 1 / grid / C + 1 offsets)
+    int res_first, n_res;  // CTAs res_first + i publish part A of instance i's CG scalars
     int n_iter, warm, replace, out_layers;
     int C;
     int stripe_floats, stage_floats, win_floats, tile_nodes, tile_subaps, tile_rows, tile_cols;
@@ -488,7 +494,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 }
             }
             // part A of the next layer phase's CG scalars while the copies fly
-            if (want_mu && tid < 32 && cc->lres && cc->il_valid) {
+            if (want_mu && tid < 32 && cc->lres && cc->il_valid && cc->IL.preA_cta < 0) {
                 ScalA A;
                 alg2_part_a(P, cc->IL, k, A);
                 if (tid == 0) {
@@ -841,7 +847,15 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
         // (part A from the sensor phase when that CTA computed it there)
         if (mode == kLpIter && tid < 32) {
             ScalA A;
-            if (cc->pre_k == k) {
+            if (I.preA_cta >= 0) {   // published by the instance's reserved CTA before the grid barrier
+                const double* pa = I.preA + (k & 1) * 6;
+                A.rho = __ldcg(pa);
+                A.beta = __ldcg(pa + 1);
+                A.t = __ldcg(pa + 2);
+                A.aold = __ldcg(pa + 3);
+                A.mh = (float)__ldcg(pa + 4);   // exact: stored from floats
+                A.ml = (float)__ldcg(pa + 5);
+            } else if (cc->pre_k == k) {
                 A.rho = cc->pre[0];
                 A.beta = cc->pre[1];
                 A.t = cc->pre[2];
@@ -1105,8 +1119,25 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
         for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpReplStart, 0, sm, rem, cl, red, sh, &cc);
         grid_barrier(P, target, &s_abort, slot);
     }
+    const int res_inst = ((int)blockIdx.x >= P.res_first && (int)blockIdx.x < P.res_first + P.n_res)
+                             ? (int)blockIdx.x - P.res_first : -1;
     for (int k = 0; k < P.n_iter; ++k) {
         for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, true, wdesc, red, &cc, k);
+        if (res_inst >= 0 && threadIdx.x < 32) {
+            // part A of instance res_inst's scalars for this iteration's layer phase
+            const FInst& RI = P.inst[res_inst];
+            ScalA A;
+            alg2_part_a(P, RI, k, A);
+            if (threadIdx.x == 0) {
+                double* pa = RI.preA + (k & 1) * 6;
+                pa[0] = A.rho;
+                pa[1] = A.beta;
+                pa[2] = A.t;
+                pa[3] = A.aold;
+                pa[4] = (double)A.mh;
+                pa[5] = (double)A.ml;
+            }
+        }
         grid_barrier(P, target, &s_abort, slot);
         for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpIter, k, sm, rem, cl, red, sh, &cc);
         if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort, slot);
@@ -1400,7 +1431,11 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         // max_tile_side > 0 no side longer than that (bounded windows)
         std::vector<WItem> witems;
         std::vector<int> w0(ninst), nw(ninst);
-        const int per = std::max(1, pl->grid / std::max(1, Gtot));
+        // a few instances: the last CTAs of the grid compute part A of the CG
+        // scalars (one per instance) instead of a sensor tile
+        const int n_res = (ninst <= 4 && ninst * 8 <= pl->grid) ? ninst : 0;
+        const int tile_ctas = pl->grid - n_res;
+        const int per = std::max(1, tile_ctas / std::max(1, Gtot));
         for (int i = 0; i < ninst; ++i) {
             const HostSetup& hs = *hss[i];
             w0[i] = (int)witems.size();
@@ -1517,11 +1552,14 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             int2* d_gtab = nullptr;
             int* d_gtab_off = nullptr;
             // sensor fields (+8 floats: aligned copies may read up to 3 past the end)
-            ok = dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) &&
+            I.preA_cta = (i < n_res) ? tile_ctas + i : -1;
+            I.preA = nullptr;
+            ok = dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) && dalloc(pl, I.preA, 12, err) &&
                  dupload(pl, d_gtab, preps[i].gtab, err) && dupload(pl, d_gtab_off, preps[i].gtab_off, err);
             I.gtab = d_gtab;
             I.gtab_off = d_gtab_off;
             if (ok) cudaMemset(I.scal, 0, 4 * sizeof(double));
+            if (ok) cudaMemset(I.preA, 0, 12 * sizeof(double));
             if (i == 0) pl->psi = I.psi;
             pl->inst.push_back(I);
         }
@@ -1538,7 +1576,8 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             lcost.push_back(n * n * (6.0 + hs.G) + 4096.0 * hs.lay[li.l].J);
         }
         std::vector<int> wsched, wsched_off, lsched, lsched_off;
-        lpt_schedule(wcost, pl->grid, wsched, wsched_off);
+        lpt_schedule(wcost, tile_ctas, wsched, wsched_off);
+        for (int r = 0; r < n_res; ++r) wsched_off.push_back(wsched_off.back());   // reserved: no tiles
         lpt_schedule(lcost, pl->nclusters, lsched, lsched_off);
         int *dws = nullptr, *dwo = nullptr, *dls = nullptr, *dlo = nullptr;
         ok = ok && dupload(pl, dws, wsched, err) && dupload(pl, dwo, wsched_off, err) &&
@@ -1565,6 +1604,8 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         P.lsched = dls;
         P.lsched_off = dlo;
         P.grid = pl->grid;
+        P.res_first = tile_ctas;
+        P.n_res = n_res;
         P.wpart = wp;
         P.lpart = lp;
         P.bar = bar;
