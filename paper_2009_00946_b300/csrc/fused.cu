@@ -71,6 +71,11 @@ struct FInst {
     // compute it themselves)
     int preA_cta;
     double* preA;
+    // the same CTA publishes the finished scalars (sh[0..5] layout) in
+    // preB[2 parities][6] at the start of the layer phase and then sets
+    // flagB = k + 1 (release); the layer CTAs wait for it before the update
+    double* preB;
+    unsigned* flagB;
 };
 
 struct WItem { int inst, g, i0, i1, j0, j1; };
@@ -845,7 +850,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
         }
         // the CG scalars of this iteration, while the copies are in flight
         // (part A from the sensor phase when that CTA computed it there)
-        if (mode == kLpIter && tid < 32) {
+        if (mode == kLpIter && tid < 32 && I.preA_cta < 0) {
             ScalA A;
             if (I.preA_cta >= 0) {   // published by the instance's reserved CTA before the grid barrier
                 const double* pa = I.preA + (k & 1) * 6;
@@ -958,7 +963,28 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
                 }
             }
         };
-        load(tid);   // sh[] holds the scalars (computed during the staging above)
+        // sh[] holds the scalars (computed during the staging above) ...
+        if (I.preA_cta >= 0) {
+            // ... or the instance's reserved CTA publishes them (normally long
+            // before this point); the wait is bounded by the barrier budget
+            if (tid == 0) {
+                const unsigned want = (unsigned)k + 1u;
+                const long long t0 = clock64();
+                bool ok = true;
+                while (ld_acquire_gpu(I.flagB) < want) {
+                    if (clock64() - t0 > P.budget) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                const double* pb = I.preB + (k & 1) * 6;
+                for (int q = 0; q < 6; ++q) sh[q] = ok ? __ldcg(pb + q) : 0.0;
+                if (!ok) atomicOr(P.errw, kErrTimeout);
+            }
+            __syncthreads();
+        }
+        load(tid);
         fmark(P, 17);
         const double alpha = sh[0], beta = sh[1];
         if (tid == 0 && li == I.l0 && rank == 0) {
@@ -1103,6 +1129,11 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
         cc.pre_k = -1;
     }
     unsigned target = 0;
+    const int res_inst = ((int)blockIdx.x >= P.res_first && (int)blockIdx.x < P.res_first + P.n_res)
+                             ? (int)blockIdx.x - P.res_first : -1;
+    // the flag of the published scalars restarts with every launch (read only
+    // after the first grid barrier)
+    if (res_inst >= 0 && threadIdx.x == 0) *P.inst[res_inst].flagB = 0u;
     __syncthreads();
 
     // Alg. 1 RHS: Gamma^T C^{-1} s per sensor tile
@@ -1119,8 +1150,6 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
         for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpReplStart, 0, sm, rem, cl, red, sh, &cc);
         grid_barrier(P, target, &s_abort, slot);
     }
-    const int res_inst = ((int)blockIdx.x >= P.res_first && (int)blockIdx.x < P.res_first + P.n_res)
-                             ? (int)blockIdx.x - P.res_first : -1;
     for (int k = 0; k < P.n_iter; ++k) {
         for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, true, wdesc, red, &cc, k);
         if (res_inst >= 0 && threadIdx.x < 32) {
@@ -1139,6 +1168,26 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
             }
         }
         grid_barrier(P, target, &s_abort, slot);
+        if (res_inst >= 0 && threadIdx.x < 32) {
+            // part B of the reserved instance's scalars: publish, then flag
+            const FInst& RI = P.inst[res_inst];
+            const double* pa = RI.preA + (k & 1) * 6;
+            ScalA A;
+            A.rho = __ldcg(pa);
+            A.beta = __ldcg(pa + 1);
+            A.t = __ldcg(pa + 2);
+            A.aold = __ldcg(pa + 3);
+            A.mh = (float)__ldcg(pa + 4);
+            A.ml = (float)__ldcg(pa + 5);
+            alg2_part_b(P, RI, k, A, sh);
+            __syncwarp();
+            if (threadIdx.x == 0) {
+                double* pb = RI.preB + (k & 1) * 6;
+                for (int q = 0; q < 6; ++q) pb[q] = sh[q];
+                __threadfence();
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(RI.flagB), "r"((unsigned)k + 1u) : "memory");
+            }
+        }
         for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpIter, k, sm, rem, cl, red, sh, &cc);
         if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort, slot);
     }
@@ -1554,7 +1603,10 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             // sensor fields (+8 floats: aligned copies may read up to 3 past the end)
             I.preA_cta = (i < n_res) ? tile_ctas + i : -1;
             I.preA = nullptr;
+            I.preB = nullptr;
+            I.flagB = nullptr;
             ok = dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) && dalloc(pl, I.preA, 12, err) &&
+                 dalloc(pl, I.preB, 12, err) && dalloc(pl, I.flagB, 1, err) &&
                  dupload(pl, d_gtab, preps[i].gtab, err) && dupload(pl, d_gtab_off, preps[i].gtab_off, err);
             I.gtab = d_gtab;
             I.gtab_off = d_gtab_off;
