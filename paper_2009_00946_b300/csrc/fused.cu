@@ -94,7 +94,9 @@ struct FParams {
     const int* wsched_off;
     const int* lsched;
     const int* lsched_off;
-    unsigned* bar;
+    unsigned* bar;         // [0] grid-barrier arrivals, [1] exits (the last CTA out zeroes both)
+    const float* slopes_in;   // single instance: read the frame's slopes here (and copy them to I.slopes)
+    float* phi_out;           // single instance: also write the final layers here
     int* errw;
     unsigned long long* trace;   // optional: [slot][cta][arrive, depart] globaltimer (ns)
     int trace_slots;
@@ -562,12 +564,17 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         }
     } else {
         const float w = cc->w;
-        const float* S = I.slopes + cc->w_soff;
+        const float* S = (P.slopes_in ? P.slopes_in : I.slopes) + cc->w_soff;
+        float* Scopy = P.slopes_in ? const_cast<float*>(I.slopes) + cc->w_soff : nullptr;
         for (int e = tid; e < nsr * nsc; e += NT) {
             const int aa = e / nsc, bb = e - aa * nsc;
             const int a = a_lo + aa, b = b_lo + bb;
             const bool on = I.mask[cc->w_moff + a * ns + b] != 0;
             const float vx = __ldcg(S + a * ns + b), vy = __ldcg(S + ns2 + a * ns + b);
+            if (Scopy) {   // the handle keeps the frame's slopes (tiles may overlap: same values)
+                Scopy[a * ns + b] = vx;
+                Scopy[ns2 + a * ns + b] = vy;
+            }
             const bool fx = isfinite(vx), fy = isfinite(vy);
             if (on && (!fx || !fy) && a >= W.i0 && b >= W.j0) atomicOr(P.errw, kErrInput);
             slx[e] = (on && fx) ? w * vx : 0.f;
@@ -1078,6 +1085,8 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
         float* res = inv_dwt(P, s, Z, B3, B1, B2, rem[0], rem[1], rem[2], cl);
         fmark(P, 15);
         for (int e = tid; e < R * n; e += NT) I.phi[gbase + e] = res[e];
+        if (last && P.phi_out)
+            for (int e = tid; e < R * n; e += NT) P.phi_out[gbase + e] = res[e];
     }
     // the stripes may still be read by the other CTAs of the cluster
     cl.sync();
@@ -1195,6 +1204,14 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     if (threadIdx.x == 0) {
         trace_mark(P, slot, 0);
         trace_mark(P, slot, 1);
+        // every CTA has passed its last barrier read: the last one out resets
+        // the counters for the next launch on this stream
+        __threadfence();
+        if (atomicAdd(P.bar + 1, 1u) == gridDim.x - 1u) {
+            P.bar[0] = 0u;
+            P.bar[1] = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -1227,6 +1244,7 @@ struct FusedPlan {
     FInst* d_inst = nullptr;
     std::vector<FInst> inst;
     float* psi = nullptr;
+    bool bar_dirty = true;   // the barrier counters must be zeroed before the next launch
 };
 
 namespace {
@@ -1642,7 +1660,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         unsigned* bar = nullptr;
         ok = ok && dupload(pl, dw, witems, err) && dupload(pl, dl, litems, err) && dupload(pl, ds, stg, err) &&
              dalloc(pl, wp, witems.size(), err) && dalloc(pl, lp, 2 * litems.size() * C, err) &&
-             dalloc(pl, bar, 1, err) && dupload(pl, pl->d_inst, pl->inst, err);
+             dalloc(pl, bar, 2, err) && dupload(pl, pl->d_inst, pl->inst, err);
         if (!ok) {
             fused_destroy(pl);
             return nullptr;
@@ -1734,15 +1752,25 @@ void fused_destroy(FusedPlan* plan) {
     delete plan;
 }
 
+void fused_mark_dirty(FusedPlan* pl) { pl->bar_dirty = true; }
+
 int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int replace, long long budget,
-                cudaStream_t stream, std::string& err, long long& launches) {
-    (void)slopes;   // the instance reads the solver's slope buffer (fixed at create)
-    cudaError_t e = cudaMemsetAsync(pl->P.bar, 0, sizeof(unsigned), stream);
-    if (e != cudaSuccess) {
-        err = std::string("fused setup copy: ") + cudaGetErrorString(e);
-        return FEWHA_ERR_CUDA;
+                cudaStream_t stream, std::string& err, long long& launches, float* layers_out) {
+    // a completed launch leaves the barrier counters at zero (the last CTA out
+    // resets them); after a failed or first launch they are zeroed here
+    cudaError_t e = cudaSuccess;
+    if (pl->bar_dirty) {
+        e = cudaMemsetAsync(pl->P.bar, 0, 2 * sizeof(unsigned), stream);
+        if (e != cudaSuccess) {
+            err = std::string("fused setup copy: ") + cudaGetErrorString(e);
+            return FEWHA_ERR_CUDA;
+        }
+        pl->bar_dirty = false;
     }
     FParams P = pl->P;
+    // single instance: the frame's slopes and layers may live in the caller's buffers
+    P.slopes_in = (P.n_inst == 1) ? slopes : nullptr;
+    P.phi_out = (P.n_inst == 1) ? layers_out : nullptr;
     P.trace = nullptr;
     P.trace_slots = 0;
     P.ftrace = nullptr;

@@ -40,8 +40,15 @@ void fused_destroy(FusedPlan* plan);
 
 // Enqueue one frame on `stream`: b = W P^T Gamma^T C^{-1} s; warm restart
 // (or replacement r = b - M c, or cold start); n_iter iterations of Alg. 2.
+// One frame (RHS, restart, n_iter iterations) in one launch.  slopes /
+// layers_out (device, may be NULL; single-instance plans only): read the
+// frame's slopes from there instead of the handle's buffer (they are copied
+// into it as they are read), and also write the final layers there.
 int fused_solve(FusedPlan* plan, const float* slopes, int n_iter, int warm, int replace, long long budget,
-                cudaStream_t stream, std::string& err, long long& launches);
+                cudaStream_t stream, std::string& err, long long& launches, float* layers_out = nullptr);
+// After a kernel error the barrier counters may be left set: zero them first
+// at the next launch.
+void fused_mark_dirty(FusedPlan* plan);
 
 // Plan summary (cluster shape, grid, shared memory, work items).
 int fused_describe(const FusedPlan* plan, char* buf, int len);

@@ -519,6 +519,10 @@ class Solver : public SolverBase {
     int* errw_host = nullptr;
     FusedPlan* fused = nullptr;
     FusedBuffers fbuf{};     // state the fused plans point to (FP32 only)
+    // a device-pointer frame on the fused path: the kernel reads the caller's
+    // slopes and writes the caller's layers directly (no copy nodes)
+    const float* ov_slopes = nullptr;
+    float* ov_layers = nullptr;
     // graph cache
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     struct Key {
@@ -904,8 +908,8 @@ class Solver : public SolverBase {
     int solve_enqueue(int n_iter, int warm) {
         if (use_fused()) {
             bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
-            int st = fused_solve(fused, (const float*)slopes, n_iter, warm, replace ? 1 : 0, barrier_budget,
-                                 stream, err, launches);
+            int st = fused_solve(fused, ov_slopes, n_iter, warm, replace ? 1 : 0, barrier_budget, stream, err,
+                                 launches, ov_layers);
             if (st) return st;
             fused_layers_ready = true;
         } else {
@@ -989,6 +993,7 @@ class Solver : public SolverBase {
         FEWHA_CUDA(cudaStreamSynchronize(stream));
         int e = *errw_host;
         if (e) {
+            if (fused) fused_mark_dirty(fused);
             FEWHA_CUDA(cudaMemsetAsync(errw, 0, sizeof(int), stream));
             FEWHA_CUDA(cudaStreamSynchronize(stream));
             if (e & kErrLaunch) {
@@ -1135,7 +1140,7 @@ class Solver : public SolverBase {
                 cudaEventRecord(e0, stream);
                 std::string e;
                 long long dummy = 0;
-                if (fused_solve(pl, (const float*)slopes, n_iter, 1, 0, barrier_budget, stream, e, dummy)) return -1.f;
+                if (fused_solve(pl, nullptr, n_iter, 1, 0, barrier_budget, stream, e, dummy)) return -1.f;
                 cudaEventRecord(e1, stream);
                 cudaEventSynchronize(e1);
                 float ms = 0.f;
@@ -1424,17 +1429,25 @@ class Solver : public SolverBase {
             FEWHA_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
             int st = FEWHA_OK;
             long long l0 = launches;
+            const bool direct = use_fused() && on_device;
             do {
-                cudaError_t e = cudaMemcpyAsync(slopes, sin, hs.S * sizeof(T), kin, stream);
-                if (e != cudaSuccess) {
-                    err = cudaGetErrorString(e);
-                    st = FEWHA_ERR_CUDA;
-                    break;
+                if (!direct) {
+                    cudaError_t e = cudaMemcpyAsync(slopes, sin, hs.S * sizeof(T), kin, stream);
+                    if (e != cudaSuccess) {
+                        err = cudaGetErrorString(e);
+                        st = FEWHA_ERR_CUDA;
+                        break;
+                    }
                 }
-                if ((st = solve_enqueue(n_iter, warm))) break;
+                ov_slopes = direct ? (const float*)sin : nullptr;
+                ov_layers = (direct && lo) ? (float*)lo : nullptr;
+                st = solve_enqueue(n_iter, warm);
+                ov_slopes = nullptr;
+                ov_layers = nullptr;
+                if (st) break;
                 if (dm && (st = fit_dev(gain, n_fit))) break;
-                if (lo && (st = layers_enqueue())) break;
-                if (lo && cudaMemcpyAsync(lo, phi, hs.N * sizeof(T), kout, stream) != cudaSuccess) {
+                if (lo && !direct && (st = layers_enqueue())) break;
+                if (lo && !direct && cudaMemcpyAsync(lo, phi, hs.N * sizeof(T), kout, stream) != cudaSuccess) {
                     st = FEWHA_ERR_CUDA;
                     err = "copy of layers";
                     break;
@@ -1590,7 +1603,7 @@ class Batch : public BatchBase {
             FEWHA_CUDA(cudaMemcpyAsync(s_all, src, sb, cudaMemcpyHostToDevice, stream));
         }
         const bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
-        int st = fused_solve(plan, s_all, n_iter, warm, replace ? 1 : 0, barrier_budget, stream, err, launches);
+        int st = fused_solve(plan, nullptr, n_iter, warm, replace ? 1 : 0, barrier_budget, stream, err, launches);
         if (st) return st;
         frame_count += 1;
         if (on_device) {
@@ -1611,7 +1624,10 @@ class Batch : public BatchBase {
     int sync() override {
         FEWHA_CUDA(cudaStreamSynchronize(stream));
         const int st = inst[0]->check_err();   // the plan's error word is instance 0's
-        if (st) err = inst[0]->err;
+        if (st) {
+            err = inst[0]->err;
+            fused_mark_dirty(plan);
+        }
         return st;
     }
 
