@@ -781,8 +781,11 @@ __device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb
 // ---------------------------------------------------------------------------
 // layer phase
 // ---------------------------------------------------------------------------
+// end_sync: the stripes may still be read by the other CTAs of the cluster,
+// so a CTA waits for them before its shared memory is reused -- unless a grid
+// barrier follows directly (it waits for every CTA).
 __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm, float* const (*rem)[kMaxC],
-                            cg::cluster_group& cl, double* red, double* sh, CtaCache* cc) {
+                            cg::cluster_group& cl, double* red, double* sh, CtaCache* cc, bool end_sync) {
     const int tid = threadIdx.x, NT = blockDim.x;
     fmark(P, 10);
     const bool fresh = cc->lkey != li;   // else descriptors, sgi and gather tables are cached
@@ -1088,8 +1091,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
         if (last && P.phi_out)
             for (int e = tid; e < R * n; e += NT) P.phi_out[gbase + e] = res[e];
     }
-    // the stripes may still be read by the other CTAs of the cluster
-    cl.sync();
+    if (end_sync) cl.sync();
     fmark(P, 16);
 }
 
@@ -1150,13 +1152,14 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     grid_barrier(P, target, &s_abort, slot);
     // P^T, W -> b; warm restart (or c -> phi for the replacement); z_0 -> phi
     const int m1 = P.replace ? kLpRhsRepl : kLpRhsStart;
-    for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], m1, 0, sm, rem, cl, red, sh, &cc);
+    for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], m1, 0, sm, rem, cl, red, sh, &cc, t + 1 < l_hi);
     grid_barrier(P, target, &s_abort, slot);
     if (P.replace) {
         // r = b - M c: data term of M on phi_c, then the layer phase
         for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, false, wdesc, red, &cc, 0);
         grid_barrier(P, target, &s_abort, slot);
-        for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpReplStart, 0, sm, rem, cl, red, sh, &cc);
+        for (int t = l_lo; t < l_hi; ++t)
+            layer_phase(P, P.lsched[t], kLpReplStart, 0, sm, rem, cl, red, sh, &cc, t + 1 < l_hi);
         grid_barrier(P, target, &s_abort, slot);
     }
     for (int k = 0; k < P.n_iter; ++k) {
@@ -1197,7 +1200,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
                 asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(RI.flagB), "r"((unsigned)k + 1u) : "memory");
             }
         }
-        for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], kLpIter, k, sm, rem, cl, red, sh, &cc);
+        for (int t = l_lo; t < l_hi; ++t)
+            layer_phase(P, P.lsched[t], kLpIter, k, sm, rem, cl, red, sh, &cc, t + 1 < l_hi || k + 1 == P.n_iter);
         if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort, slot);
     }
     __syncthreads();
