@@ -16,7 +16,9 @@ What is computed (paper section / equation / algorithm):
     b = W^{-T} A^T C^{-1} s, with W an orthonormal wavelet transform
     (db3, periodic), so W^{-T} = W (forward) and W^{-1} = W^T (inverse).
   * Alg. 2 ("PCG on GPU"): the single-reduction PCG, and textbook PCG beside it.
-  * Alg. 1: RHS, warm restart of the residual, PCG, fitting, open-loop gain.
+  * Alg. 1: RHS, warm restart of the residual, PCG, fitting, open-loop gain;
+    closed loop: pseudo-open-loop slopes s + Gamma P_DM a^(-1) and the gain
+    a^(1) = a^(0) + gain (a~ - a^(-1)).
 
 Readings taken where the paper is silent or garbled (each one also listed in
 the design notes of the repository):
@@ -43,6 +45,11 @@ the design notes of the repository):
   R10 Fitting for L > M: least squares over the fitting directions,
       min sum_t |P^DM_t a - P^lay_t phi|^2 + eps |a|^2, plain CG, n_fit
       iterations warm-started from the previous solution.
+  R13 Closed loop (Alg. 1): the mirrors' contribution to sensor g is
+      Gamma_g sum_m P_{g,m} a_m, P_{g,m} the bilinear mirror m (height h_m)
+      sampled at the sensor's nodes as a layer is (shift theta_g h_m, cone
+      factor 1 - h_m/H_g); every subaperture, active or not, is added (the
+      mask enters only through C^{-1}).
 
 Parity unpinned relative to the paper itself (pinned only by the readings
 above, which the CUDA library implements independently): the constant in D,
@@ -640,6 +647,34 @@ class FitGeometry:
         return np.concatenate([self._interp_T(v, self.dm_tab[t][m], self.na[m]).ravel()
                                for m in range(self.M)])
 
+    def wfs_table(self, g: int, m: int):
+        """Bilinear sample table of mirror m at the nodes of sensor g (R13)."""
+        geom = self.geom
+        w = geom.wfs[g]
+        H = float(w.get("gs_height", 0.0))
+        h = self.hm[m]
+        sc = 1.0 - h / H if H > 0.0 else 1.0
+        x = geom.x_nodes[g]
+        ux = (sc * x + w["theta_x"] * h - self.A0[m]) / self.pitch[m]
+        uy = (sc * x + w["theta_y"] * h - self.A0[m]) / self.pitch[m]
+        cx, tx = _bilinear_table(ux, self.na[m])
+        cy, ty = _bilinear_table(uy, self.na[m])
+        return cy, ty, cx, tx
+
+    def dm_to_wfs(self, a, g: int):
+        """Nodal field sum_m P_{g,m} a_m of the mirrors seen by sensor g."""
+        return sum(self._interp(self.dm(a, m), self.wfs_table(g, m)) for m in range(self.M))
+
+    def dm_slopes(self, a):
+        """Gamma_g sum_m P_{g,m} a_m for every sensor: the measurements the
+        mirrors' shapes add (Alg. 1, closed loop), flat slope vector."""
+        geom = self.geom
+        out = np.empty(geom.S)
+        for g in range(geom.G):
+            sx, sy = Gamma(self.dm_to_wfs(a, g))
+            out[geom.soff[g]:geom.soff[g + 1]] = np.concatenate([sx.ravel(), sy.ravel()])
+        return out
+
     def P_lay(self, phi, t):
         return sum(self._interp(phi[l], self.lay_tab[t][l]) for l in range(self.geom.L))
 
@@ -716,10 +751,18 @@ class Reconstructor:
         return apply_M(self.geom, v, self.params)
 
     def frame(self, s: np.ndarray, n_iter: int, warm: bool = True, k_rr: int = 10,
-              gain: float = 1.0, n_fit: int = 8):
-        """b1 = W P^T Gamma^T C^{-1} s; r = (b1 - b0) + r0 (or b1 - M c0 every
-        k_rr frames); (c1, r1) = PCG(c0, r); a~ = F W^{-1} c1; open-loop gain."""
+              gain: float = 1.0, n_fit: int = 8, loop: str = "open"):
+        """Closed loop: s = s + Gamma P_DM a^(-1) first.  b1 = W P^T Gamma^T
+        C^{-1} s; r = (b1 - b0) + r0 (or b1 - M c0 every k_rr frames);
+        (c1, r1) = PCG(c0, r); a~ = F W^{-1} c1; open-loop gain
+        a1 = (1 - gain) a0 + gain a~, or closed-loop a1 = a0 + gain (a~ - a^(-1))."""
         st = self.state
+        if loop not in ("open", "closed"):
+            raise ValueError("loop must be 'open' or 'closed'")
+        if loop == "closed":
+            if self.fitgeom is None:
+                raise ValueError("closed loop needs deformable mirrors")
+            s = s + self.fitgeom.dm_slopes(st.a_prev)
         b1 = rhs(self.geom, s, self.params)
         if not warm:
             c0 = np.zeros(self.geom.N)
@@ -737,7 +780,10 @@ class Reconstructor:
         if self.fitgeom is not None:
             phi = layers_from_coeffs(self.geom, c1)
             a_fit = self.fitgeom.fit(phi, st.a_fit, n_fit)
-            a_new = (1.0 - gain) * st.a_cur + gain * a_fit
+            if loop == "closed":
+                a_new = st.a_cur + gain * (a_fit - st.a_prev)
+            else:
+                a_new = (1.0 - gain) * st.a_cur + gain * a_fit
             st.a_prev, st.a_cur, st.a_fit = st.a_cur, a_new, a_fit
             out["a"] = a_new
         return out

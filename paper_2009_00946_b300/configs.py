@@ -104,6 +104,22 @@ def c3_elt_dm(frames: int = 2000):
             "precision": "fp32"}
 
 
+def mcao_small(lgs: bool = True):
+    """Small MCAO case for closed-loop checks: D = 8 m, 4 guide stars (LGS at
+    90 km or NGS) on a 30-arcsec ring, 16x16 subapertures, 3 layers 0-8 km on
+    32^2 / 64^2 grids (3 levels), 2 mirrors at 0 / 6 km (pitch 0.5 / 0.8 m),
+    3x3 fitting directions within +-30 arcsec."""
+    h, c = synthetic_profile(3, 8000.0)
+    layers = _layers(h, c, 64, 3)
+    layers[0]["n"] = 32
+    dirs = [(x * ARCSEC, y * ARCSEC) for y in (-30.0, 0.0, 30.0) for x in (-30.0, 0.0, 30.0)]
+    return {"name": "mcao_small", "D": 8.0, "obstruction": 0.0, "r0": R0, "L0": L0, "alpha": ALPHA,
+            "wfs": _wfs(ring(4, 30.0, 45.0), 16, LGS_HEIGHT if lgs else 0.0), "layers": layers,
+            "dms": [{"height": 0.0, "pitch": 0.5}, {"height": 6000.0, "pitch": 0.8}], "fit_dirs": dirs,
+            "n_fit": 8, "gain": 0.5, "n_iter": 4, "warm": True, "k_rr": 10, "frames": 8, "seed": 6,
+            "precision": "fp32"}
+
+
 def c4_instance(i: int):
     """Instance i of the uneven batch: D ~ U[8, 39] m, n_s ~ U{16..84} (even),
     L ~ U{2..9} layers 0-16 km, G ~ U{3..6} LGS on a 60-arcsec ring; layer
