@@ -167,6 +167,17 @@ int fewha_apply_M(fewha_handle* h, const void* x, void* y, int on_device);
 int fewha_frame(fewha_handle* h, const void* slopes, int n_iter, int warm_start,
                 double gain, int n_fit, void* layers_out, void* dm_out, int on_device);
 
+/* Loop mode of Alg. 1 (default open).  closed = 1: every frame first forms
+ * the pseudo-open-loop slopes s + Gamma P_DM a^(-1) -- the measurements the
+ * mirror shapes of two frames back add in every sensor: mirror m (height h_m)
+ * sampled bilinearly at the sensor's nodes with the shift theta_g h_m and,
+ * for a laser guide star, the cone factor 1 - h_m/H_g, then Gamma, added on
+ * every subaperture -- and the fit's gain becomes a^(1) = a^(0) + gain
+ * (a~ - a^(-1)).  The input slopes are the residual measurements.  Errors:
+ * STATE (no mirrors), GEOMETRY (a sensor sees beyond a mirror grid; the
+ * mirrors are sized for the fitting directions), ARG. */
+int fewha_set_loop(fewha_handle* h, int closed);
+
 /* Wait for the handle's stream and return the device error word (OK, INPUT,
  * BREAKDOWN, TIMEOUT).  The word is cleared after it has been read. */
 int fewha_sync(fewha_handle* h);

@@ -214,6 +214,12 @@ int fewha_autotune(fewha_handle* h, int n_iter, int reps, char* report, int len)
     return done(h, h->s->autotune(n_iter, reps, report, len));
 }
 
+int fewha_set_loop(fewha_handle* h, int closed) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (closed != 0 && closed != 1) return fail(h, FEWHA_ERR_ARG, "closed must be 0 or 1");
+    return done(h, h->s->set_loop(closed));
+}
+
 int fewha_set_params(fewha_handle* h, const double* cn2_frac, double alpha, const double* w) {
     if (!h) return FEWHA_ERR_ARG;
     return done(h, h->s->set_params(cn2_frac, alpha, w));

@@ -359,6 +359,29 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
                 gather_ranges(&o.dcy[base], o.fit_n + 1, dm.na, o.dilo, o.dihi);
             }
         }
+        // closed loop (Alg. 1): the mirrors as every sensor sees them -- shift
+        // theta_g h_m and, for a laser guide star, cone factor 1 - h_m/H_g;
+        // unavailable (not an error) when a footprint leaves a mirror grid
+        o.closed_ok = true;
+        o.wdtab_off.resize((size_t)o.G * o.M);
+        for (int g = 0; g < o.G && o.closed_ok; ++g) {
+            const HostWfs& w = o.wfs[g];
+            for (int m = 0; m < o.M && o.closed_ok; ++m) {
+                const HostDm& dm = o.dm[m];
+                const double sc = (w.H > 0) ? 1.0 - dm.h / w.H : 1.0;
+                o.wdtab_off[g * o.M + m] = (int)o.wdcx.size();
+                if (!sample_table(geo.D, w.n, sc, w.tx, dm.h, dm.A0, dm.pitch, dm.na, o.wdcx, o.wdtx) ||
+                    !sample_table(geo.D, w.n, sc, w.ty, dm.h, dm.A0, dm.pitch, dm.na, o.wdcy, o.wdty))
+                    o.closed_ok = false;
+            }
+        }
+        if (!o.closed_ok) {
+            o.wdtab_off.clear();
+            o.wdcx.clear();
+            o.wdcy.clear();
+            o.wdtx.clear();
+            o.wdty.clear();
+        }
         // eps = 1e-6 * mean diagonal of sum_t P_DM_t^T P_DM_t
         double dsum = 0.0;
         for (int t = 0; t < o.T; ++t)

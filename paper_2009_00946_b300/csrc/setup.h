@@ -60,6 +60,11 @@ struct HostSetup {
     std::vector<int> dtab_off, dcx, dcy;     // (T*M): mirror sample tables
     std::vector<double> dtx, dty;
     std::vector<int> dgat_off, djlo, djhi, dilo, dihi;   // (T*M): per actuator index
+    // closed loop: mirror m sampled at the nodes of sensor g (G*M tables, same
+    // layout as the layer tables); closed_ok = every sensor sees inside the mirrors
+    bool closed_ok = false;
+    std::vector<int> wdtab_off, wdcx, wdcy;
+    std::vector<double> wdtx, wdty;
 
     double h[6], g[6];                       // db3 analysis filters
     std::vector<double> aD;                  // alpha * D, N entries

@@ -488,6 +488,49 @@ __global__ void k_gain(int NA, T gain, const T* __restrict__ afit, T* __restrict
     }
 }
 
+// closed-loop gain (Alg. 1): a1 = a0 + gain (a~ - a_{-1}); a_{-1} <- a0
+template <typename T>
+__global__ void k_gain_closed(int NA, T gain, const T* __restrict__ afit, T* __restrict__ acur,
+                              T* __restrict__ aprev) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NA; i += gridDim.x * blockDim.x) {
+        const T a0 = acur[i], am1 = aprev[i];
+        aprev[i] = a0;
+        acur[i] = a0 + gain * (afit[i] - am1);
+    }
+}
+
+// psi_g = sum_m P_{g,m} a_m: the mirrors at the nodes of sensor g (Alg. 1, closed loop)
+template <typename T>
+__global__ void k_dm_wfs(DevGeo<T> G, DevFit<T> F, const T* __restrict__ a, T* __restrict__ psi) {
+    const int g = blockIdx.y, np1 = G.wfs_n[g] + 1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= np1 * np1) return;
+    const int i = idx / np1, jx = idx - i * np1;
+    T acc = 0;
+    for (int m = 0; m < F.M; ++m) {
+        const int base = F.wdtab_off[g * F.M + m], n = F.dm_n[m];
+        const int cy = F.wdcy[base + i], cx = F.wdcx[base + jx];
+        const T ty = F.wdty[base + i], tx = F.wdtx[base + jx];
+        const T* f = a + F.dm_off[m] + (long)cy * n + cx;
+        acc += (1 - ty) * ((1 - tx) * f[0] + tx * f[1]) + ty * ((1 - tx) * f[n] + tx * f[n + 1]);
+    }
+    psi[G.wfs_noff[g] + idx] = acc;
+}
+
+// s += Gamma psi on every subaperture: pseudo-open-loop slopes
+template <typename T>
+__global__ void k_add_gamma(DevGeo<T> G, const T* __restrict__ psi, T* __restrict__ s) {
+    const int g = blockIdx.y, ns = G.wfs_n[g], np1 = ns + 1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ns * ns) return;
+    const int a = idx / ns, b = idx - a * ns;
+    const T* p = psi + G.wfs_noff[g] + (long)a * np1 + b;
+    const T sx = ((p[1] - p[0]) + (p[np1 + 1] - p[np1])) / 2;
+    const T sy = ((p[np1] - p[0]) + (p[np1 + 1] - p[1])) / 2;
+    s[G.wfs_soff[g] + idx] += sx;
+    s[G.wfs_soff[g] + ns * ns + idx] += sy;
+}
+
 // ---------------------------------------------------------------------------
 // solver object
 // ---------------------------------------------------------------------------
@@ -523,6 +566,8 @@ class Solver : public SolverBase {
     // slopes and writes the caller's layers directly (no copy nodes)
     const float* ov_slopes = nullptr;
     float* ov_layers = nullptr;
+    bool closed = false;        // closed loop (Alg. 1): pseudo-open-loop slopes and closed-loop gain
+    bool pol_pending = false;   // the frame's slopes still lack Gamma P_DM a_{-1}
     // graph cache
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     struct Key {
@@ -733,6 +778,20 @@ class Solver : public SolverBase {
         F.djhi = i1;
         F.dilo = j1;
         F.dihi = k1;
+        if (H.closed_ok) {
+            int *w1, *w2, *w3;
+            T *w4, *w5;
+            TRY(upload(w1, H.wdtab_off));
+            TRY(upload(w2, H.wdcx));
+            TRY(upload(w3, H.wdcy));
+            TRY(uploadT(w4, H.wdtx));
+            TRY(uploadT(w5, H.wdty));
+            F.wdtab_off = w1;
+            F.wdcx = w2;
+            F.wdcy = w3;
+            F.wdtx = w4;
+            F.wdty = w5;
+        }
         for (T** v : {&afit, &acur, &aprev, &fr, &fp, &fq, &frhs}) {
             TRY(alloc(*v, H.NA));
             FEWHA_CUDA(cudaMemset(*v, 0, H.NA * sizeof(T)));
@@ -869,7 +928,8 @@ class Solver : public SolverBase {
             k_fit_dir<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, sc, fr, fp);
             FEWHA_LAUNCHED();
         }
-        k_gain<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, (T)gain, afit, acur, aprev);
+        if (closed) k_gain_closed<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, (T)gain, afit, acur, aprev);
+        else k_gain<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, (T)gain, afit, acur, aprev);
         FEWHA_LAUNCHED();
         return FEWHA_OK;
     }
@@ -900,12 +960,40 @@ class Solver : public SolverBase {
     int set_frame(const void* sl, int on_device) override {
         TRY(copy_in(slopes, sl, hs.S, on_device));
         have_frame = true;
+        pol_pending = true;
         return FEWHA_OK;
     }
 
     bool use_fused() const { return path == FEWHA_PATH_FUSED && fused != nullptr; }
 
+    // closed loop: s += Gamma P_DM a_{-1}, once per frame (Alg. 1)
+    int pol_enqueue() {
+        if (!closed || !pol_pending) return FEWHA_OK;
+        const int np1 = G.nsmax + 1;
+        k_dm_wfs<T><<<dim3((np1 * np1 + 255) / 256, G.G), 256, 0, stream>>>(G, F, aprev, wpsi);
+        FEWHA_LAUNCHED();
+        k_add_gamma<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, wpsi, slopes);
+        FEWHA_LAUNCHED();
+        pol_pending = false;
+        return FEWHA_OK;
+    }
+
+    int set_loop(int c) override {
+        if (c && hs.M == 0) {
+            err = "the closed loop needs deformable mirrors";
+            return FEWHA_ERR_STATE;
+        }
+        if (c && !hs.closed_ok) {
+            err = "a sensor sees beyond a mirror grid (mirrors are sized for the fitting directions)";
+            return FEWHA_ERR_GEOMETRY;
+        }
+        closed = c != 0;
+        drop_graphs();
+        return FEWHA_OK;
+    }
+
     int solve_enqueue(int n_iter, int warm) {
+        TRY(pol_enqueue());
         if (use_fused()) {
             bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
             int st = fused_solve(fused, ov_slopes, n_iter, warm, replace ? 1 : 0, barrier_budget, stream, err,
@@ -1429,7 +1517,7 @@ class Solver : public SolverBase {
             FEWHA_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
             int st = FEWHA_OK;
             long long l0 = launches;
-            const bool direct = use_fused() && on_device;
+            const bool direct = use_fused() && on_device && !closed;
             do {
                 if (!direct) {
                     cudaError_t e = cudaMemcpyAsync(slopes, sin, hs.S * sizeof(T), kin, stream);
@@ -1439,6 +1527,7 @@ class Solver : public SolverBase {
                         break;
                     }
                 }
+                pol_pending = true;
                 ov_slopes = direct ? (const float*)sin : nullptr;
                 ov_layers = (direct && lo) ? (float*)lo : nullptr;
                 st = solve_enqueue(n_iter, warm);

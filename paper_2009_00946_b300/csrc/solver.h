@@ -71,6 +71,12 @@ struct DevFit {
     const int* djhi;
     const int* dilo;
     const int* dihi;
+    // closed loop: mirror m at the nodes of sensor g (G*M tables)
+    const int* wdtab_off;
+    const int* wdcx;
+    const int* wdcy;
+    const T* wdtx;
+    const T* wdty;
 };
 
 struct FusedPlan;   // fused.cu
@@ -103,6 +109,7 @@ class SolverBase {
     virtual int backward(const void* slopes, int n_iter, const void* tape, const void* layers_bar, double* g_gam,
                          double* g_alpha, double* g_w, void* g_slopes) = 0;
     virtual size_t tape_size(int n_iter) const = 0;
+    virtual int set_loop(int closed) = 0;
 
     HostSetup hs;
     cudaStream_t stream = 0;

@@ -99,6 +99,7 @@ def lib():
                                       ctypes.POINTER(ci)]),
         "fewha_set_cluster_size": (ci, [vp, ci]),
         "fewha_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
+        "fewha_set_loop": (ci, [vp, ci]),
         "fewha_set_params": (ci, [vp, ctypes.POINTER(cd), cd, ctypes.POINTER(cd)]),
         "fewha_tape_bytes": (cl, [vp, ci]),
         "fewha_solve_taped": (ci, [vp, vp, ci, vp, vp]),
@@ -241,6 +242,10 @@ class Solver:
 
     def set_residual_replacement(self, k_rr: int):
         self._check(lib().fewha_set_residual_replacement(self.h, int(k_rr)))
+
+    def set_loop(self, closed: bool):
+        """Alg. 1 closed loop (pseudo-open-loop slopes, closed-loop gain) or open loop."""
+        self._check(lib().fewha_set_loop(self.h, 1 if closed else 0))
 
     def set_barrier_budget(self, cycles: int):
         self._check(lib().fewha_set_barrier_budget(self.h, int(cycles)))
