@@ -45,6 +45,11 @@ the design notes of the repository):
   R10 Fitting for L > M: least squares over the fitting directions,
       min sum_t |P^DM_t a - P^lay_t phi|^2 + eps |a|^2, plain CG, n_fit
       iterations warm-started from the previous solution.
+  R14 Low-order sensors (n_sub <= 2, the tip-tilt sensors of Sec. 4.1) have
+      every subaperture active.
+  R16 L = M with every mirror at its layer's height (Sec. 4.1): the fit is
+      the bilinear sampling of layer m at mirror m's actuators (no least
+      squares); the layer grid's extent also covers that actuator grid.
   R13 Closed loop (Alg. 1): the mirrors' contribution to sensor g is
       Gamma_g sum_m P_{g,m} a_m, P_{g,m} the bilinear mirror m (height h_m)
       sampled at the sensor's nodes as a layer is (shift theta_g h_m, cone
@@ -235,7 +240,11 @@ def Gamma_T(sx: np.ndarray, sy: np.ndarray) -> np.ndarray:
 
 def subaperture_mask(n: int, obstruction: float) -> np.ndarray:
     """Reading R6: centre of subaperture (i, j) at ((2j+1-n), (2i+1-n)) * d/2;
-    active iff (obstruction*n)^2 <= (2j+1-n)^2 + (2i+1-n)^2 <= n^2."""
+    active iff (obstruction*n)^2 <= (2j+1-n)^2 + (2i+1-n)^2 <= n^2.
+    Reading R14: a low-order (tip-tilt) sensor, n <= 2, has every
+    subaperture active (its subapertures span the whole pupil)."""
+    if n <= 2:
+        return np.ones((n, n))
     c = 2 * np.arange(n) + 1 - n
     r2 = c[:, None] ** 2 + c[None, :] ** 2
     return ((r2 <= n * n) & (r2 >= (obstruction * n) ** 2)).astype(np.float64)
@@ -251,6 +260,13 @@ def _bilinear_table(u: np.ndarray, n: int):
                             % (u.min(), u.max(), n - 1))
     cell = np.clip(np.floor(u).astype(np.int64), 0, n - 2)
     return cell, u - cell
+
+
+def mirror_size(D: float, dirs, h: float, pitch: float) -> tuple:
+    """Actuators per side of a mirror at height h that covers the telescope
+    footprint in every fitting direction: (n_a, pitch)."""
+    half = D / 2.0 + max([max(abs(tx), abs(ty)) for (tx, ty) in dirs] + [0.0]) * h
+    return int(math.ceil(2.0 * half / pitch - 1e-9)) + 1, pitch
 
 
 @dataclass
@@ -282,6 +298,11 @@ class Geometry:
         self.x_nodes = [-self.D / 2.0 + np.arange(n + 1) * (self.D / n) for n in self.n_sub]
         self.mask = [subaperture_mask(n, self.obstruction) for n in self.n_sub]
 
+        # co-located mirrors (R16): L = M, mirror m at layer m's height
+        self.colocated = bool(self.dms) and len(self.dms) == self.L and all(
+            abs(float(d["height"]) - float(l["height"])) <= 1e-6 * max(1.0, float(l["height"]))
+            for d, l in zip(self.dms, self.layers))
+
         # layer grids (R3)
         self.n = [int(l["n"]) for l in self.layers]
         self.J = [int(l["levels"]) for l in self.layers]
@@ -296,6 +317,9 @@ class Geometry:
                 ext = max(ext, 2.0 * (s * self.D / 2.0 + th * h))
             for (tx, ty) in self.fit_dirs:
                 ext = max(ext, 2.0 * (self.D / 2.0 + max(abs(tx), abs(ty)) * h))
+            if self.colocated:
+                na, p = mirror_size(self.D, self.fit_dirs, float(self.dms[l]["height"]), float(self.dms[l]["pitch"]))
+                ext = max(ext, (na - 1) * p)
             self.E.append(ext)
             self.delta.append(ext / (self.n[l] - 1))
             self.X0.append(-ext / 2.0)
@@ -577,8 +601,7 @@ class FitGeometry:
         self.na, self.pitch, self.A0, self.hm = [], [], [], []
         for dm in geom.dms:
             h, p = float(dm["height"]), float(dm["pitch"])
-            half = geom.D / 2.0 + max([max(abs(tx), abs(ty)) for (tx, ty) in self.dirs] + [0.0]) * h
-            na = int(math.ceil(2.0 * half / p - 1e-9)) + 1
+            na, _ = mirror_size(geom.D, self.dirs, h, p)
             self.na.append(na)
             self.pitch.append(p)
             self.A0.append(-(na - 1) * p / 2.0)
@@ -646,6 +669,17 @@ class FitGeometry:
     def P_dm_T(self, v, t):
         return np.concatenate([self._interp_T(v, self.dm_tab[t][m], self.na[m]).ravel()
                                for m in range(self.M)])
+
+    def colocated_fit(self, phi):
+        """R16: mirror m's actuators take layer m's bilinear value at their
+        positions (the layer and the mirror share a height)."""
+        geom = self.geom
+        out = []
+        for m in range(self.M):
+            X = self.A0[m] + np.arange(self.na[m]) * self.pitch[m]
+            c, t = _bilinear_table((X - geom.X0[m]) / geom.delta[m], geom.n[m])
+            out.append(self._interp(phi[m], (c, t, c, t)).ravel())
+        return np.concatenate(out)
 
     def wfs_table(self, g: int, m: int):
         """Bilinear sample table of mirror m at the nodes of sensor g (R13)."""
@@ -779,7 +813,10 @@ class Reconstructor:
         out = {"c": c1, "b": b1, "r": r1}
         if self.fitgeom is not None:
             phi = layers_from_coeffs(self.geom, c1)
-            a_fit = self.fitgeom.fit(phi, st.a_fit, n_fit)
+            if self.geom.colocated:
+                a_fit = self.fitgeom.colocated_fit(phi)
+            else:
+                a_fit = self.fitgeom.fit(phi, st.a_fit, n_fit)
             if loop == "closed":
                 a_new = st.a_cur + gain * (a_fit - st.a_prev)
             else:

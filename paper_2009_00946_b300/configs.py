@@ -120,6 +120,33 @@ def mcao_small(lgs: bool = True):
             "precision": "fp32"}
 
 
+def maory(n_layers: int = 6, n_iter: int = 4):
+    """MAORY-like timing case (Sec. 4.1, Table 2): D = 39 m, 28 % obstructed;
+    6 LGS (90 km) with 80x80 subapertures on a 1-arcmin-radius hexagon and 3
+    NGS tip-tilt sensors (2x2, 1x1, 1x1) on a 80-arcsec-radius ring; L = M
+    layers and mirrors at 0, 4, 8, 12, 16, 20 km (the first n_layers), layer
+    grids 128^2 (4 levels), mirrors of 81^2 (0 km), 48^2 (4-16 km) and 54^2
+    (20 km) actuators covering the 5x5 +-60-arcsec evaluation grid; fit =
+    sampling of each layer at its mirror's actuators; n_iter PCG iterations."""
+    heights = [0.0, 4000.0, 8000.0, 12000.0, 16000.0, 20000.0][:n_layers]
+    n_act = [81, 48, 48, 48, 48, 54][:n_layers]
+    dirs = fit_grid_5x5()
+    thmax = max(max(abs(x), abs(y)) for x, y in dirs)
+    dms = []
+    for h, na in zip(heights, n_act):
+        span = 39.0 + 2.0 * thmax * h          # footprint over the evaluation grid
+        dms.append({"height": h, "pitch": span / (na - 1.5)})   # -> na actuators per side
+    w = np.exp(-np.array(heights) / 3000.0)
+    w = w / w.sum()
+    lgs = _wfs(ring(6, 60.0, 0.0), 80, LGS_HEIGHT)
+    ngs_dirs = ring(3, 80.0, 180.0)
+    ngs = _wfs(ngs_dirs[:1], 2, 0.0) + _wfs(ngs_dirs[1:], 1, 0.0)
+    return {"name": "maory_%dL" % n_layers, "D": 39.0, "obstruction": 0.28, "r0": R0, "L0": L0,
+            "alpha": ALPHA, "wfs": lgs + ngs, "layers": _layers(heights, list(w), 128, 4),
+            "dms": dms, "fit_dirs": dirs, "n_fit": 0, "gain": 0.5, "n_iter": n_iter, "warm": True,
+            "k_rr": 10, "frames": 200, "seed": 7, "precision": "fp32"}
+
+
 def c4_instance(i: int):
     """Instance i of the uneven batch: D ~ U[8, 39] m, n_s ~ U{16..84} (even),
     L ~ U{2..9} layers 0-16 km, G ~ U{3..6} LGS on a 60-arcsec ring; layer
