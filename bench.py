@@ -263,6 +263,38 @@ def bench_elt_dm_frame(torch, fewha, dev, flush, n_frames):
     return out
 
 
+def bench_maory_frame(torch, fewha, dev, flush, n_frames):
+    """The paper's own timing case (Sec. 4.1, Table 2; L = M = 6, 4 iterations):
+    whole frame with the co-located fit through one graph, device buffers."""
+    cfg = configs.maory(6, N_ITER)
+    pool = torch.from_numpy(slope_pool(cfg, 16)).to(dev)
+    S = fewha.Solver(cfg, precision=fewha.FP32, path=fewha.PATH_FUSED, k_rr=K_RR)
+    lay = torch.empty(S.N, dtype=torch.float32, device=dev)
+    dm = torch.empty(S.NA, dtype=torch.float32, device=dev)
+    st = S.stream
+    for k in range(5):
+        S.frame(pool[k % 16], N_ITER, warm=True, gain=cfg["gain"], layers_out=lay, dm_out=dm)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_frames)]
+    for k in range(n_frames):
+        with torch.cuda.stream(st):
+            flush.fill_(float(k & 7))
+        ev[k][0].record(st)
+        S.frame(pool[k % 16], N_ITER, warm=True, gain=cfg["gain"], layers_out=lay, dm_out=dm)
+        ev[k][1].record(st)
+    st.synchronize()
+    S.sync()
+    t = [a.elapsed_time(b) * 1e3 for a, b in ev]
+    out = {"workload": "MAORY-like (Sec. 4.1 / Table 2): D=39 m, 6 LGS 80x80 + NGS tip-tilt 2x2/1x1/1x1, "
+                       "L = M = 6 layers/mirrors (0-20 km, 128^2, J=4; 81^2/48^2/54^2 actuators), 4 iterations, "
+                       "co-located fit, gain 0.5",
+           "p50_us": float(np.percentile(t, 50)), "p99_us": float(np.percentile(t, 99)), "frames": n_frames,
+           "paper_context": "paper (Sec. 4.3): about 3 ms per reconstruction on 2x 8-core Haswell (CPU), 8.6 ms on "
+                            "a V100; other hardware, context only",
+           "plan": S.describe()}
+    S.close()
+    return out
+
+
 def bench_batch(torch, fewha, dev, flush, n_frames):
     """64 uneven instances advanced by one fused launch per frame, against the
     same 64 instances solved one after another on the plain FP64 path."""
@@ -506,6 +538,7 @@ def main():
     extra = {}
     if not args.no_extra:
         extra["elt_dm_frame"] = bench_elt_dm_frame(torch, fewha, dev, flush, min(K, 200))
+        extra["maory_frame"] = bench_maory_frame(torch, fewha, dev, flush, min(K, 200))
         extra["batch64"] = bench_batch(torch, fewha, dev, flush, min(K, 30))
 
     # max over ranks

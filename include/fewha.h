@@ -134,10 +134,14 @@ int fewha_set_frame(fewha_handle* h, const void* slopes, int on_device);
  * BREAKDOWN, TIMEOUT) are reported by the next fewha_sync. */
 int fewha_solve(fewha_handle* h, int n_iter, int warm_start);
 
-/* Alg. 1 fitting and open-loop gain: a~ = F W^{-1} c (least squares over the
- * fitting directions, n_fit CG iterations warm-started from the previous a~),
- * a1 = (1 - gain) a0 + gain a~.  dm_out (A values, may be NULL) receives a1.
- * Errors: STATE if the geometry has no mirrors. */
+/* Alg. 1 fitting and gain: a~ = F W^{-1} c, then a1 = (1 - gain) a0 + gain a~
+ * (open loop) or a1 = a0 + gain (a~ - a^(-1)) (closed loop, fewha_set_loop).
+ * F: least squares over the fitting directions, n_fit CG iterations
+ * warm-started from the previous a~; or, when there are as many mirrors as
+ * layers and mirror m sits at layer m's height (Sec. 4.1, L = M), the
+ * sampling of layer m at mirror m's actuators (n_fit is then ignored).
+ * dm_out (A values, may be NULL) receives a1.  Errors: STATE if the geometry
+ * has no mirrors. */
 int fewha_fit_dm(fewha_handle* h, double gain, int n_fit, void* dm_out, int on_device);
 
 /* phi = W^{-1} c (N values, layers layout). */

@@ -118,6 +118,13 @@ void db3_taps(double h[6], double g[6]) {
     for (int i = 0; i < 6; ++i) g[i] = ((i & 1) ? -1.0 : 1.0) * h[5 - i];
 }
 
+// Actuators per side of a mirror at height h covering the telescope
+// footprint in every fitting direction (|theta| <= thmax).
+static int mirror_actuators(double D, double thmax, double h, double pitch) {
+    const double half = D / 2.0 + thmax * h;
+    return (int)std::ceil(2.0 * half / pitch - 1e-9) + 1;
+}
+
 double reg_diag(double r0, double cn2, double delta, int j) {
     return std::pow(r0, 5.0 / 3.0) / (cn2 * std::pow(delta, 5.0 / 3.0) * std::pow(2.0, 11.0 * j / 3.0));
 }
@@ -170,18 +177,29 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
         noff += (long)(w.n + 1) * (w.n + 1);
         moff += (long)w.n * w.n;
         // pupil mask: centre of subaperture (i, j) at ((2j+1-n), (2i+1-n)) * d/2;
-        // active iff (obstruction*n)^2 <= r^2 <= n^2 in those half-units.
+        // active iff (obstruction*n)^2 <= r^2 <= n^2 in those half-units; a
+        // low-order (tip-tilt) sensor, n <= 2, spans the pupil: all active.
         const double inner = (geo.obstruction * w.n) * (geo.obstruction * w.n);
         for (int i = 0; i < w.n; ++i)
             for (int j = 0; j < w.n; ++j) {
                 long cy = 2L * i + 1 - w.n, cx = 2L * j + 1 - w.n;
                 long r2 = cx * cx + cy * cy;
-                o.mask.push_back((r2 <= (long)w.n * w.n && (double)r2 >= inner) ? 1 : 0);
+                o.mask.push_back((w.n <= 2 || (r2 <= (long)w.n * w.n && (double)r2 >= inner)) ? 1 : 0);
             }
     }
     o.S = soff;
     o.NW = noff;
     o.NS = moff;
+
+    // mirrors co-located with the layers (L = M, mirror m at layer m's
+    // height): the fit samples each layer at its mirror's actuators, and the
+    // layer grid also covers the actuator grid
+    double thfit = 0.0;
+    for (int t = 0; t < o.T; ++t)
+        thfit = std::max(thfit, std::max(std::fabs(geo.fit_theta_x[t]), std::fabs(geo.fit_theta_y[t])));
+    o.colocated = o.M > 0 && o.M == o.L;
+    for (int m = 0; m < o.M && o.colocated; ++m)
+        o.colocated = std::fabs(geo.dm_height[m] - prof.height[m]) <= 1e-6 * std::max(1.0, prof.height[m]);
 
     // layers: extent = union of all footprints (sensors with their cone
     // factor, fitting directions without); spacing E / (n - 1).
@@ -208,6 +226,10 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
         for (int t = 0; t < o.T; ++t) {
             double th = std::max(std::fabs(geo.fit_theta_x[t]), std::fabs(geo.fit_theta_y[t]));
             ext = std::max(ext, 2.0 * (geo.D / 2.0 + th * L.h));
+        }
+        if (o.colocated && geo.dm_pitch[l] > 0) {
+            const int na = mirror_actuators(geo.D, thfit, geo.dm_height[l], geo.dm_pitch[l]);
+            ext = std::max(ext, (na - 1) * geo.dm_pitch[l]);
         }
         L.E = ext;
         L.delta = ext / (L.n - 1);
@@ -327,14 +349,31 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
             dm.h = geo.dm_height[m];
             dm.pitch = geo.dm_pitch[m];
             if (!(dm.pitch > 0) || !(dm.h >= 0)) return fail(FEWHA_ERR_ARG, "mirror pitch must be > 0 and height >= 0");
-            double half = geo.D / 2.0 + thmax * dm.h;
-            dm.na = (int)std::ceil(2.0 * half / dm.pitch - 1e-9) + 1;
+            dm.na = mirror_actuators(geo.D, thmax, dm.h, dm.pitch);
             if (dm.na > 4096) return fail(FEWHA_ERR_ARG, "mirror grid too large");
             dm.A0 = -(dm.na - 1) * dm.pitch / 2.0;
             dm.off = aoff;
             aoff += (long)dm.na * dm.na;
         }
         o.NA = aoff;
+        // co-located fit: actuator k of mirror m on layer m's grid (the grids
+        // are square and centred, so one table serves both axes)
+        if (o.colocated) {
+            o.ctab_off.resize(o.M);
+            for (int m = 0; m < o.M; ++m) {
+                const HostDm& dm = o.dm[m];
+                const HostLayer& L = o.lay[m];
+                o.ctab_off[m] = (int)o.ccx.size();
+                for (int k = 0; k < dm.na; ++k) {
+                    int c;
+                    double w;
+                    if (!bilinear_cell((dm.A0 + k * dm.pitch - L.X0) / L.delta, L.n, c, w))
+                        return fail(FEWHA_ERR_GEOMETRY, "a mirror's actuators leave its layer grid");
+                    o.ccx.push_back(c);
+                    o.ctx.push_back(w);
+                }
+            }
+        }
         o.ftab_off.resize((size_t)o.T * o.L);
         o.dtab_off.resize((size_t)o.T * o.M);
         o.dgat_off.resize((size_t)o.T * o.M);

@@ -62,6 +62,11 @@ struct HostSetup {
     std::vector<int> dgat_off, djlo, djhi, dilo, dihi;   // (T*M): per actuator index
     // closed loop: mirror m sampled at the nodes of sensor g (G*M tables, same
     // layout as the layer tables); closed_ok = every sensor sees inside the mirrors
+    // L = M with co-located mirrors: fit = sampling of layer m at mirror m's
+    // actuators (per mirror na entries: layer cell and weight along one axis)
+    bool colocated = false;
+    std::vector<int> ctab_off, ccx;
+    std::vector<double> ctx;
     bool closed_ok = false;
     std::vector<int> wdtab_off, wdcx, wdcy;
     std::vector<double> wdtx, wdty;

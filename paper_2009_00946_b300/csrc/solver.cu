@@ -488,6 +488,20 @@ __global__ void k_gain(int NA, T gain, const T* __restrict__ afit, T* __restrict
     }
 }
 
+// co-located fit (L = M): actuator (ky, kx) of mirror m takes layer m's
+// bilinear value at its position
+template <typename T>
+__global__ void k_fit_colocated(DevFit<T> F, const T* __restrict__ phi, T* __restrict__ a) {
+    const int m = blockIdx.y, na = F.dm_n[m];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= na * na) return;
+    const int ky = idx / na, kx = idx - ky * na, base = F.ctab_off[m], n = F.lay_n[m];
+    const int cy = F.ccx[base + ky], cx = F.ccx[base + kx];
+    const T ty = F.ctx[base + ky], tx = F.ctx[base + kx];
+    const T* f = phi + F.lay_off[m] + (long)cy * n + cx;
+    a[F.dm_off[m] + idx] = (1 - ty) * ((1 - tx) * f[0] + tx * f[1]) + ty * ((1 - tx) * f[n] + tx * f[n + 1]);
+}
+
 // closed-loop gain (Alg. 1): a1 = a0 + gain (a~ - a_{-1}); a_{-1} <- a0
 template <typename T>
 __global__ void k_gain_closed(int NA, T gain, const T* __restrict__ afit, T* __restrict__ acur,
@@ -778,6 +792,17 @@ class Solver : public SolverBase {
         F.djhi = i1;
         F.dilo = j1;
         F.dihi = k1;
+        F.colocated = H.colocated ? 1 : 0;
+        if (H.colocated) {
+            int *c1, *c2;
+            T* c3;
+            TRY(upload(c1, H.ctab_off));
+            TRY(upload(c2, H.ccx));
+            TRY(uploadT(c3, H.ctx));
+            F.ctab_off = c1;
+            F.ccx = c2;
+            F.ctx = c3;
+        }
         if (H.closed_ok) {
             int *w1, *w2, *w3;
             T *w4, *w5;
@@ -891,7 +916,15 @@ class Solver : public SolverBase {
             err = "the geometry has no deformable mirrors";
             return FEWHA_ERR_STATE;
         }
-        TRY(inv_dwt(c, phi));
+        // phi = W^T c (the fused kernel has just written it)
+        if (!(use_fused() && fused_layers_ready)) TRY(inv_dwt(c, phi));
+        if (F.colocated) {
+            int amax = 0;
+            for (auto& d : hs.dm) amax = std::max(amax, d.na);
+            k_fit_colocated<T><<<dim3((amax * amax + 255) / 256, F.M), 256, 0, stream>>>(F, phi, afit);
+            FEWHA_LAUNCHED();
+            return gain_enqueue(gain);
+        }
         int np1 = F.np1;
         dim3 gdir((np1 * np1 + 255) / 256, F.T_);
         int amax = 0;
@@ -928,6 +961,10 @@ class Solver : public SolverBase {
             k_fit_dir<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, sc, fr, fp);
             FEWHA_LAUNCHED();
         }
+        return gain_enqueue(gain);
+    }
+
+    int gain_enqueue(double gain) {
         if (closed) k_gain_closed<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, (T)gain, afit, acur, aprev);
         else k_gain<T><<<kRedBlocks, kRedThreads, 0, stream>>>(F.NA, (T)gain, afit, acur, aprev);
         FEWHA_LAUNCHED();

@@ -71,6 +71,11 @@ struct DevFit {
     const int* djhi;
     const int* dilo;
     const int* dihi;
+    // L = M co-located mirrors: per mirror, its actuators on its layer's grid
+    int colocated;
+    const int* ctab_off;
+    const int* ccx;
+    const T* ctx;
     // closed loop: mirror m at the nodes of sensor g (G*M tables)
     const int* wdtab_off;
     const int* wdcx;
