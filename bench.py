@@ -405,6 +405,51 @@ def phase_breakdown(S, pool_dev, n_iter=N_ITER, dump=None):
             "steps_max_us": {k: float(np.max(v)) for k, v in sorted(steps.items())}}
 
 
+def sweep_mode(args):
+    """Operator and frame timings against the problem size (the paper's
+    operator figures and its scaling to 300x300 subapertures), one JSON line
+    per point; CUDA events on the handle's stream, warm L2."""
+    from paper_2009_00946_b300 import fewha
+
+    def lines(cfg, tag, ops, precs=(fewha.FP32, fewha.FP64)):
+        for prec in precs:
+            with fewha.Solver(cfg, precision=prec) as S:
+                for op, name in ops:
+                    us = S.time_operator(op, 50)
+                    print(json.dumps({"sweep": tag, "op": name, "precision": "fp64" if prec else "fp32",
+                                      "us": us, "N": S.N, "S": S.S}), flush=True)
+
+    base = configs.c2_elt()
+    for n in (64, 128, 256, 512, 1024):   # W, W^T against the layer side (one layer)
+        cfg = dict(base, layers=[{"height": 0.0, "cn2": 1.0, "n": n, "levels": int(math.log2(n)) - 3}],
+                   wfs=base["wfs"][:1])
+        lines(cfg, "n_lay=%d" % n, [(fewha.OP_W, "W"), (fewha.OP_WT, "WT")])
+    for ns in (16, 32, 64, 84, 128, 200, 300):   # P, P^T, Gamma, Gamma^T against n_s at n_lay = 128
+        cfg = dict(base, wfs=[dict(w, n_sub=ns) for w in base["wfs"]])
+        lines(cfg, "n_s=%d" % ns, [(fewha.OP_P, "P"), (fewha.OP_PT, "PT"), (fewha.OP_GAMMA, "Gamma"),
+                                   (fewha.OP_GAMMA_T, "GammaT")])
+    import torch
+    for ns in (84, 128, 200, 256, 300):   # whole solve (4 iterations) against n_s, n_lay = next power of two
+        nl = 1 << int(math.ceil(math.log2(ns + 1)))
+        cfg = dict(base, wfs=[dict(w, n_sub=ns) for w in base["wfs"]],
+                   layers=[dict(l, n=nl, levels=int(math.log2(nl)) - 3) for l in base["layers"]])
+        for prec in (fewha.FP32, fewha.FP64):
+            S = fewha.Solver(cfg, precision=prec, k_rr=K_RR)
+            S.set_frame(np.asarray(synth.random_slopes(cfg, 3), dtype=S.np_dtype))
+            for _ in range(3):
+                S.solve(N_ITER, warm=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(S.stream)
+            for _ in range(20):
+                S.solve(N_ITER, warm=True)
+            e1.record(S.stream)
+            S.sync()
+            print(json.dumps({"sweep": "frame n_s=%d n_lay=%d" % (ns, nl), "precision": "fp64" if prec else "fp32",
+                              "path": S.describe().split(",")[1].strip(), "us": e0.elapsed_time(e1) * 1e3 / 20,
+                              "N": S.N, "S": S.S}), flush=True)
+            S.close()
+
+
 def profile_mode(args):
     """Stream launches only (no CUDA graph), for ncu: W + K frames of
     set_frame (device) + solve + layers on the fused path."""
@@ -436,6 +481,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 35-layer fit and 64-instance batch lines")
     ap.add_argument("--profile", action="store_true", help="stream launches only (for ncu), no timing")
+    ap.add_argument("--sweep", action="store_true", help="operator and frame timings against the size")
     ap.add_argument("--trace-out", default=None, help="with --profile: save the raw phase traces (.npy)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -445,6 +491,9 @@ def main():
         return
     if args.profile:
         profile_mode(args)
+        return
+    if args.sweep:
+        sweep_mode(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -159,6 +159,30 @@ int fewha_set_state(fewha_handle* h, const void* c, const void* b, const void* r
 /* y = M x (N values each), one operator application (Eq. (fewha) left side). */
 int fewha_apply_M(fewha_handle* h, const void* x, void* y, int on_device);
 
+#define FEWHA_OP_W       0
+#define FEWHA_OP_WT      1
+#define FEWHA_OP_P       2
+#define FEWHA_OP_PT      3
+#define FEWHA_OP_GAMMA   4
+#define FEWHA_OP_GAMMA_T 5
+
+/* The single operators of M (plain kernels, the handle's precision):
+ *   FEWHA_OP_W        coefficients = W layers (periodic db3 analysis, Sec. 2.2), N -> N
+ *   FEWHA_OP_WT       layers = W^T coefficients (synthesis, W^-1 = W^T),           N -> N
+ *   FEWHA_OP_P        sensor nodes = P layers (every sensor, Sec. 2.1),             N -> NW
+ *   FEWHA_OP_PT       layers = P^T sensor nodes (deterministic gather),            NW -> N
+ *   FEWHA_OP_GAMMA    slopes = Gamma nodes (every subaperture, unweighted),        NW -> S
+ *   FEWHA_OP_GAMMA_T  nodes = Gamma^T slopes,                                       S -> NW
+ * with NW the sensor nodes, sum (n_sub + 1)^2, layout [sensor][i][j].
+ * fewha_operator_dims gives the input and output lengths. */
+int fewha_operator_dims(fewha_handle* h, int op, long* n_in, long* n_out);
+int fewha_apply_operator(fewha_handle* h, int op, const void* x, void* y, int on_device);
+
+/* Profiling aid: mean duration (us, CUDA events on the handle's stream) of
+ * one application of operator op over reps back-to-back applications on the
+ * handle's own buffers (after one untimed application).  Synchronises. */
+int fewha_time_operator(fewha_handle* h, int op, int reps, double* us_per_application);
+
 /* One whole frame of Alg. 1 as one CUDA graph: copy in the slopes s, RHS,
  * warm restart, n_iter iterations of Alg. 2, optional fit + gain (dm_out),
  * optional layers phi = W^{-1} c (layers_out), copy out.  on_device = 0: the

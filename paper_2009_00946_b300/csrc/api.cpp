@@ -168,6 +168,21 @@ int fewha_frame(fewha_handle* h, const void* slopes, int n_iter, int warm_start,
     return done(h, h->s->frame(slopes, n_iter, warm_start, gain, n_fit, layers_out, dm_out, on_device));
 }
 
+int fewha_operator_dims(fewha_handle* h, int op, long* n_in, long* n_out) {
+    if (!h || !n_in || !n_out) return FEWHA_ERR_ARG;
+    return done(h, h->s->operator_dims(op, *n_in, *n_out));
+}
+
+int fewha_apply_operator(fewha_handle* h, int op, const void* x, void* y, int on_device) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->apply_operator(op, x, y, on_device));
+}
+
+int fewha_time_operator(fewha_handle* h, int op, int reps, double* us_per_application) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->time_operator(op, reps, us_per_application));
+}
+
 int fewha_sync(fewha_handle* h) {
     if (!h) return FEWHA_ERR_ARG;
     return done(h, h->s->sync());

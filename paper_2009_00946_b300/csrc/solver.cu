@@ -1113,6 +1113,96 @@ class Solver : public SolverBase {
         return copy_out(yout, s, hs.N, on_device);
     }
 
+    // ---- single operators (plain kernels): W, W^T, P, P^T, Gamma, Gamma^T ----
+    int operator_dims(int op, long& n_in, long& n_out) override {
+        const long N = hs.N, NW = hs.NW, S = hs.S;
+        switch (op) {
+            case FEWHA_OP_W: case FEWHA_OP_WT: n_in = N; n_out = N; return FEWHA_OK;
+            case FEWHA_OP_P: n_in = N; n_out = NW; return FEWHA_OK;
+            case FEWHA_OP_PT: n_in = NW; n_out = N; return FEWHA_OK;
+            case FEWHA_OP_GAMMA: n_in = NW; n_out = S; return FEWHA_OK;
+            case FEWHA_OP_GAMMA_T: n_in = S; n_out = NW; return FEWHA_OK;
+            default: err = "unknown operator"; return FEWHA_ERR_ARG;
+        }
+    }
+
+    // input buffer of op, and the enqueue of op from it into its output buffer
+    T* op_in(int op) {
+        switch (op) {
+            case FEWHA_OP_W: case FEWHA_OP_WT: return z;
+            case FEWHA_OP_P: return y;
+            case FEWHA_OP_PT: return wpsi2;
+            case FEWHA_OP_GAMMA: return wpsi;
+            default: return wsl;
+        }
+    }
+    T* op_out(int op) {
+        switch (op) {
+            case FEWHA_OP_W: case FEWHA_OP_WT: return s;
+            case FEWHA_OP_P: return wpsi;
+            case FEWHA_OP_PT: return ext;
+            case FEWHA_OP_GAMMA: return wsl;
+            default: return wpsi2;
+        }
+    }
+    int op_enqueue(int op) {
+        const int np1 = G.nsmax + 1;
+        const dim3 gn((np1 * np1 + 255) / 256, G.G), gs((G.nsmax * G.nsmax + 255) / 256, G.G);
+        switch (op) {
+            case FEWHA_OP_W: return fwd_dwt(z, s);
+            case FEWHA_OP_WT: return inv_dwt(z, s);
+            case FEWHA_OP_P:
+                k_P<T><<<gn, 256, 0, stream>>>(G, y, wpsi);
+                break;
+            case FEWHA_OP_PT:
+                k_PT<T><<<grid_layers(G.nmax * G.nmax), 256, 0, stream>>>(G, wpsi2, ext);
+                break;
+            case FEWHA_OP_GAMMA:
+                FEWHA_CUDA(cudaMemsetAsync(wsl, 0, hs.S * sizeof(T), stream));
+                k_add_gamma<T><<<gs, 256, 0, stream>>>(G, wpsi, wsl);
+                break;
+            default:
+                k_gammaT<T><<<gn, 256, 0, stream>>>(G, wsl, wpsi2);
+                break;
+        }
+        FEWHA_LAUNCHED();
+        return FEWHA_OK;
+    }
+
+    int apply_operator(int op, const void* x, void* yout, int on_device) override {
+        long nin = 0, nout = 0;
+        TRY(operator_dims(op, nin, nout));
+        fused_layers_ready = false;   // the operators' buffers are the plain path's scratch
+        TRY(copy_in(op_in(op), x, nin, on_device));
+        TRY(op_enqueue(op));
+        return copy_out(yout, op_out(op), nout, on_device);
+    }
+
+    int time_operator(int op, int reps, double* us) override {
+        long nin = 0, nout = 0;
+        TRY(operator_dims(op, nin, nout));
+        if (reps < 1 || !us) {
+            err = "reps must be >= 1 and us not NULL";
+            return FEWHA_ERR_ARG;
+        }
+        fused_layers_ready = false;
+        FEWHA_CUDA(cudaMemsetAsync(op_in(op), 0, nin * sizeof(T), stream));
+        TRY(op_enqueue(op));   // warm-up
+        cudaEvent_t e0, e1;
+        FEWHA_CUDA(cudaEventCreate(&e0));
+        FEWHA_CUDA(cudaEventCreate(&e1));
+        cudaEventRecord(e0, stream);
+        for (int i = 0; i < reps; ++i) TRY(op_enqueue(op));
+        cudaEventRecord(e1, stream);
+        FEWHA_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *us = 1e3 * (double)ms / reps;
+        return check_err();
+    }
+
     int check_err() {
         FEWHA_CUDA(cudaMemcpyAsync(errw_host, errw, sizeof(int), cudaMemcpyDeviceToHost, stream));
         FEWHA_CUDA(cudaStreamSynchronize(stream));

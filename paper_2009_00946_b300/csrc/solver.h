@@ -115,6 +115,9 @@ class SolverBase {
                          double* g_alpha, double* g_w, void* g_slopes) = 0;
     virtual size_t tape_size(int n_iter) const = 0;
     virtual int set_loop(int closed) = 0;
+    virtual int operator_dims(int op, long& n_in, long& n_out) = 0;
+    virtual int apply_operator(int op, const void* x, void* y, int on_device) = 0;
+    virtual int time_operator(int op, int reps, double* us) = 0;
 
     HostSetup hs;
     cudaStream_t stream = 0;

@@ -24,6 +24,7 @@ PATH_PLAIN, PATH_FUSED = 0, 1
 ERRORS = {0: "OK", 1: "ARG", 2: "INPUT", 3: "GEOMETRY", 4: "BREAKDOWN", 5: "TIMEOUT", 6: "LAUNCH", 7: "CUDA",
           8: "STATE"}
 VEC_C, VEC_R, VEC_B, VEC_JACOBI, VEC_ALPHA_D = 0, 1, 2, 3, 4
+OP_W, OP_WT, OP_P, OP_PT, OP_GAMMA, OP_GAMMA_T = 0, 1, 2, 3, 4, 5
 
 
 class FewhaError(RuntimeError):
@@ -100,6 +101,9 @@ def lib():
         "fewha_set_cluster_size": (ci, [vp, ci]),
         "fewha_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
         "fewha_set_loop": (ci, [vp, ci]),
+        "fewha_operator_dims": (ci, [vp, ci, ctypes.POINTER(cl), ctypes.POINTER(cl)]),
+        "fewha_apply_operator": (ci, [vp, ci, vp, vp, ci]),
+        "fewha_time_operator": (ci, [vp, ci, ci, ctypes.POINTER(cd)]),
         "fewha_set_params": (ci, [vp, ctypes.POINTER(cd), cd, ctypes.POINTER(cd)]),
         "fewha_tape_bytes": (cl, [vp, ci]),
         "fewha_solve_taped": (ci, [vp, vp, ci, vp, vp]),
@@ -242,6 +246,27 @@ class Solver:
 
     def set_residual_replacement(self, k_rr: int):
         self._check(lib().fewha_set_residual_replacement(self.h, int(k_rr)))
+
+    def operator_dims(self, op: int):
+        ni, no = ctypes.c_long(), ctypes.c_long()
+        self._check(lib().fewha_operator_dims(self.h, int(op), ctypes.byref(ni), ctypes.byref(no)))
+        return ni.value, no.value
+
+    def apply_operator(self, op: int, x):
+        """One of W, W^T, P, P^T, Gamma, Gamma^T on a host array (numpy)."""
+        ni, no = self.operator_dims(op)
+        x = np.ascontiguousarray(x, dtype=self.np_dtype)
+        if x.size != ni:
+            raise ValueError("operator %d takes %d values" % (op, ni))
+        out = np.empty(no, self.np_dtype)
+        self._check(lib().fewha_apply_operator(self.h, int(op), ctypes.c_void_p(x.ctypes.data),
+                                               ctypes.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def time_operator(self, op: int, reps: int = 50) -> float:
+        us = ctypes.c_double()
+        self._check(lib().fewha_time_operator(self.h, int(op), int(reps), ctypes.byref(us)))
+        return us.value
 
     def set_loop(self, closed: bool):
         """Alg. 1 closed loop (pseudo-open-loop slopes, closed-loop gain) or open loop."""
