@@ -1206,7 +1206,11 @@ class Solver : public SolverBase {
     int check_err() {
         FEWHA_CUDA(cudaMemcpyAsync(errw_host, errw, sizeof(int), cudaMemcpyDeviceToHost, stream));
         FEWHA_CUDA(cudaStreamSynchronize(stream));
-        int e = *errw_host;
+        return decode_err(*errw_host);
+    }
+
+    // status of a device error word read back (the word is cleared if set)
+    int decode_err(int e) {
         if (e) {
             if (fused) fused_mark_dirty(fused);
             FEWHA_CUDA(cudaMemsetAsync(errw, 0, sizeof(int), stream));
@@ -1586,14 +1590,7 @@ class Solver : public SolverBase {
             return FEWHA_ERR_STATE;
         }
         // pinned host pointers are captured directly, pageable ones are staged
-        auto pinned = [](const void* ptr) {
-            cudaPointerAttributes at;
-            if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-                cudaGetLastError();
-                return false;
-            }
-            return at.type == cudaMemoryTypeHost;
-        };
+        auto pinned = [&](const void* ptr) { return host_dev_ptr(ptr) != nullptr; };
         const void* sin = s_in;
         void* lo = lout;
         void* dm = dout;
@@ -1618,6 +1615,15 @@ class Solver : public SolverBase {
         }
         const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        // the fused kernel reads the slopes and writes the layers where they
+        // are: device buffers, or pinned host buffers through their device
+        // mapping (the transfers happen inside the kernel, no copy nodes)
+        auto dev_alias = [&](const void* ptr) -> void* {
+            return on_device ? const_cast<void*>(ptr) : host_dev_ptr(ptr);
+        };
+        const void* sin_dev = dev_alias(sin);
+        void* lo_dev = lo ? dev_alias(lo) : nullptr;
+        const bool direct = use_fused() && !closed && sin_dev && (!lo || lo_dev);
         bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
         int slot = replace ? 1 : 0;
         Key key;
@@ -1644,7 +1650,6 @@ class Solver : public SolverBase {
             FEWHA_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
             int st = FEWHA_OK;
             long long l0 = launches;
-            const bool direct = use_fused() && on_device && !closed;
             do {
                 if (!direct) {
                     cudaError_t e = cudaMemcpyAsync(slopes, sin, hs.S * sizeof(T), kin, stream);
@@ -1655,8 +1660,8 @@ class Solver : public SolverBase {
                     }
                 }
                 pol_pending = true;
-                ov_slopes = direct ? (const float*)sin : nullptr;
-                ov_layers = (direct && lo) ? (float*)lo : nullptr;
+                ov_slopes = direct ? (const float*)sin_dev : nullptr;
+                ov_layers = (direct && lo) ? (float*)lo_dev : nullptr;
                 st = solve_enqueue(n_iter, warm);
                 ov_slopes = nullptr;
                 ov_layers = nullptr;
@@ -1666,6 +1671,13 @@ class Solver : public SolverBase {
                 if (lo && !direct && cudaMemcpyAsync(lo, phi, hs.N * sizeof(T), kout, stream) != cudaSuccess) {
                     st = FEWHA_ERR_CUDA;
                     err = "copy of layers";
+                    break;
+                }
+                // a host frame reads the device error word back with its results
+                if (!on_device &&
+                    cudaMemcpyAsync(errw_host, errw, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess) {
+                    st = FEWHA_ERR_CUDA;
+                    err = "copy of the error word";
                     break;
                 }
                 if (dm && cudaMemcpyAsync(dm, acur, hs.NA * sizeof(T), kout, stream) != cudaSuccess) {
@@ -1701,7 +1713,18 @@ class Solver : public SolverBase {
         FEWHA_CUDA(cudaStreamSynchronize(stream));
         if (stage_l) std::memcpy(lout, pinned_out, hs.N * sizeof(T));
         if (stage_d) std::memcpy(dout, pinned_dm, hs.NA * sizeof(T));
-        return check_err();
+        return decode_err(*errw_host);   // copied by the graph
+    }
+
+    // device alias of a pinned host pointer (nullptr for other memory)
+    void* host_dev_ptr(const void* ptr) {
+        if (!ptr) return nullptr;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
     }
 
     // phi = W^T c for output (fused path: already produced by the frame kernel)
