@@ -47,6 +47,11 @@ the design notes of the repository):
       iterations warm-started from the previous solution.
   R14 Low-order sensors (n_sub <= 2, the tip-tilt sensors of Sec. 4.1) have
       every subaperture active.
+  R15 LGS tip-tilt (optional, cfg "lgs_tip_tilt_filter"): a laser guide
+      star cannot sense tip and tilt, so for an LGS sensor
+      C_g^{-1} = w_g (Mk - Mk 1 1^T Mk / n_act) on each slope axis (Mk the
+      mask, n_act its active count): the weighted slopes lose their mean over
+      the active subapertures.
   R16 L = M with every mirror at its layer's height (Sec. 4.1): the fit is
       the bilinear sampling of layer m at mirror m's actuators (no least
       squares); the layer grid's extent also covers that actuator grid.
@@ -297,6 +302,9 @@ class Geometry:
         self.d = [self.D / n for n in self.n_sub]
         self.x_nodes = [-self.D / 2.0 + np.arange(n + 1) * (self.D / n) for n in self.n_sub]
         self.mask = [subaperture_mask(n, self.obstruction) for n in self.n_sub]
+        self.nact = [float(m.sum()) for m in self.mask]
+        tt = bool(cfg.get("lgs_tip_tilt_filter", False))
+        self.tt = [tt and float(w.get("gs_height", 0.0)) > 0.0 for w in self.wfs]
 
         # co-located mirrors (R16): L = M, mirror m at layer m's height
         self.colocated = bool(self.dms) and len(self.dms) == self.L and all(
@@ -422,6 +430,26 @@ def coeffs_from_layers(geom: Geometry, y: list) -> np.ndarray:
     return np.concatenate([fwd_dwt2(y[l], geom.J[l]).ravel() for l in range(geom.L)])
 
 
+def noise_weight(geom: Geometry, params: Params, g: int, sx: np.ndarray, sy: np.ndarray):
+    """C_g^{-1} applied to the slopes of sensor g: w_g mask s, and for a
+    tip-tilt-filtered LGS (R15) minus the active-subaperture mean of each axis."""
+    mk, w = geom.mask[g], params.w[g]
+    if geom.tt[g]:
+        sx = sx - float(np.sum(mk * sx)) / geom.nact[g]
+        sy = sy - float(np.sum(mk * sy)) / geom.nact[g]
+    return w * mk * sx, w * mk * sy
+
+
+def masked_dot(geom: Geometry, g: int, ax, ay, bx, by) -> float:
+    """a^T C_g^{-1} b / w_g for two slope fields of sensor g (R6, R15)."""
+    mk = geom.mask[g]
+    v = float(np.sum(mk * (ax * bx + ay * by)))
+    if geom.tt[g]:
+        v -= (float(np.sum(mk * ax)) * float(np.sum(mk * bx)) + float(np.sum(mk * ay)) * float(np.sum(mk * by))) \
+            / geom.nact[g]
+    return v
+
+
 def apply_data_term(geom: Geometry, c: np.ndarray, params: Params) -> np.ndarray:
     """W P^T Gamma^T C^{-1} Gamma P W^T c (the first term of M)."""
     phi = layers_from_coeffs(geom, c)
@@ -429,8 +457,7 @@ def apply_data_term(geom: Geometry, c: np.ndarray, params: Params) -> np.ndarray
     for g in range(geom.G):
         psi = P_apply(geom, phi, g)
         sx, sy = Gamma(psi)
-        wm = params.w[g] * geom.mask[g]
-        psi_p = Gamma_T(wm * sx, wm * sy)
+        psi_p = Gamma_T(*noise_weight(geom, params, g, sx, sy))
         for l in range(geom.L):
             y[l] += PT_layer(geom, psi_p, g, l)
     return coeffs_from_layers(geom, y)
@@ -448,8 +475,7 @@ def rhs(geom: Geometry, s: np.ndarray, params: Params | None = None) -> np.ndarr
     y = [np.zeros((n, n)) for n in geom.n]
     for g in range(geom.G):
         sx, sy = geom.split_slopes(s, g)
-        wm = params.w[g] * geom.mask[g]
-        psi_p = Gamma_T(wm * sx, wm * sy)
+        psi_p = Gamma_T(*noise_weight(geom, params, g, sx, sy))
         for l in range(geom.L):
             y[l] += PT_layer(geom, psi_p, g, l)
     return coeffs_from_layers(geom, y)
@@ -503,6 +529,8 @@ def jacobi_diag(geom: Geometry, params: Params | None = None) -> np.ndarray:
                 AV, DV = (V[:, :-1] + V[:, 1:]) / 2.0, V[:, 1:] - V[:, :-1]
                 mk = geom.mask[g]
                 Q = (AU ** 2) @ mk @ (DV ** 2).T + (DU ** 2) @ mk @ (AV ** 2).T
+                if geom.tt[g]:   # R15: minus the squared active sums of each slope axis
+                    Q = Q - ((AU @ mk @ DV.T) ** 2 + (DU @ mk @ AV.T) ** 2) / geom.nact[g]
                 acc[sel] += params.w[g] * Q[Y[sel], X[sel]]
         diag[geom.off[l]:geom.off[l + 1]] += acc.ravel()
     return diag
@@ -939,7 +967,7 @@ def dM_contract(geom: Geometry, params: Params, z: np.ndarray, sbar: np.ndarray)
                      for l in range(geom.L)])
     A = _sensor_slopes_of(geom, z)
     B = _sensor_slopes_of(geom, sbar)
-    gw = np.array([float(np.sum(geom.mask[g] * (A[g][0] * B[g][0] + A[g][1] * B[g][1]))) for g in range(geom.G)])
+    gw = np.array([masked_dot(geom, g, A[g][0], A[g][1], B[g][0], B[g][1]) for g in range(geom.G)])
     return ggam, galpha, gw
 
 
@@ -949,7 +977,7 @@ def db_contract(geom: Geometry, s: np.ndarray, bbar: np.ndarray):
     out = []
     for g in range(geom.G):
         sx, sy = geom.split_slopes(s, g)
-        out.append(float(np.sum(geom.mask[g] * (B[g][0] * sx + B[g][1] * sy))))
+        out.append(masked_dot(geom, g, B[g][0], B[g][1], sx, sy))
     return np.array(out)
 
 
