@@ -80,6 +80,10 @@ typedef struct {
     double fit_theta_y[FEWHA_MAX_FIT_DIRS];
     int    fit_n_sub;                      /* pupil sample grid of the fit: fit_n_sub+1 nodes   */
     int    precision;                      /* FEWHA_FP32 or FEWHA_FP64, fixed at create         */
+    int    lgs_tt_filter;                  /* 1: LGS sensors do not sense tip/tilt: their       */
+                                           /* C^{-1} removes each slope axis' mean over active  */
+                                           /* subapertures (plain path only; the fused path,    */
+                                           /* batches and differentiation refuse it)            */
 } fewha_geometry;
 
 /* Turbulence layers reconstructed (Sec. 2.1 layered model; Table 1 sizes). */

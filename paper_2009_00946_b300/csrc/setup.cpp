@@ -186,6 +186,10 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
                 long r2 = cx * cx + cy * cy;
                 o.mask.push_back((w.n <= 2 || (r2 <= (long)w.n * w.n && (double)r2 >= inner)) ? 1 : 0);
             }
+        for (long k = w.moff; k < (long)o.mask.size(); ++k) w.nact += o.mask[k];
+        // an LGS does not sense tip / tilt: optional filter of its slope means
+        w.tt = geo.lgs_tt_filter != 0 && w.H > 0.0 && w.nact > 0;
+        o.any_tt = o.any_tt || w.tt;
     }
     o.S = soff;
     o.NW = noff;
@@ -294,6 +298,7 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
                 const int ns = w.n;
                 const int base = o.tab_off[g * o.L + l];
                 std::vector<double> AU((size_t)m2 * ns), DU((size_t)m2 * ns), AV((size_t)m2 * ns), DV((size_t)m2 * ns);
+                std::vector<double> AUl((size_t)m2 * ns), DUl((size_t)m2 * ns), AVl((size_t)m2 * ns), DVl((size_t)m2 * ns);
                 std::vector<double> U(ns + 1), V(ns + 1);
                 for (int k = 0; k < m2; ++k) {
                     const double* f = &F[(size_t)k * n];
@@ -308,6 +313,10 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
                         DU[(size_t)k * ns + a] = du * du;
                         AV[(size_t)k * ns + a] = av * av;
                         DV[(size_t)k * ns + a] = dv * dv;
+                        AUl[(size_t)k * ns + a] = au;
+                        DUl[(size_t)k * ns + a] = du;
+                        AVl[(size_t)k * ns + a] = av;
+                        DVl[(size_t)k * ns + a] = dv;
                     }
                 }
                 // T1[a][kx] = sum_b mask[a][b] DV[kx][b],  T2 with AV
@@ -324,12 +333,38 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
                         T1[(size_t)a * m2 + kx] = s1;
                         T2[(size_t)a * m2 + kx] = s2;
                     }
+                // LGS tip-tilt filter: minus the squared active sums of each
+                // slope axis, (sum mask (A u)(D v))^2 + (sum mask (D u)(A v))^2, / n_act
+                std::vector<double> T3, T4;
+                if (w.tt) {
+                    T3.assign((size_t)ns * m2, 0.0);
+                    T4.assign((size_t)ns * m2, 0.0);
+                    for (int a = 0; a < ns; ++a)
+                        for (int kx = 0; kx < m2; ++kx) {
+                            double s3 = 0, s4 = 0;
+                            for (int b = 0; b < ns; ++b)
+                                if (mk[a * ns + b]) {
+                                    s3 += DVl[(size_t)kx * ns + b];
+                                    s4 += AVl[(size_t)kx * ns + b];
+                                }
+                            T3[(size_t)a * m2 + kx] = s3;
+                            T4[(size_t)a * m2 + kx] = s4;
+                        }
+                }
                 for (int y = 0; y < m2; ++y)
                     for (int x = 0; x < m2; ++x) {
                         if (level_of(y, x, n, L.J) != j) continue;
                         double q = 0;
                         for (int a = 0; a < ns; ++a)
                             q += AU[(size_t)y * ns + a] * T1[(size_t)a * m2 + x] + DU[(size_t)y * ns + a] * T2[(size_t)a * m2 + x];
+                        if (w.tt) {
+                            double sx = 0, sy = 0;
+                            for (int a = 0; a < ns; ++a) {
+                                sx += AUl[(size_t)y * ns + a] * T3[(size_t)a * m2 + x];
+                                sy += DUl[(size_t)y * ns + a] * T4[(size_t)a * m2 + x];
+                            }
+                            q -= (sx * sx + sy * sy) / w.nact;
+                        }
                         o.Jdiag[L.off + (long)y * n + x] += w.w * q;
                     }
             }

@@ -22,6 +22,8 @@ struct HostWfs {
     long noff = 0;          // node offset ((n+1)^2 per sensor)
     long moff = 0;          // mask / subaperture offset (n^2 per sensor)
     double d = 0, w = 0;    // w = 1 / sigma^2
+    int nact = 0;           // active subapertures
+    bool tt = false;        // LGS tip-tilt filter on this sensor
     double tx = 0, ty = 0, H = 0;
 };
 
@@ -34,6 +36,7 @@ struct HostDm {
 
 struct HostSetup {
     int L = 0, G = 0, M = 0, T = 0;          // layers, sensors, mirrors, fitting directions
+    bool any_tt = false;                     // some sensor has the LGS tip-tilt filter
     long N = 0, S = 0, NW = 0, NS = 0, NA = 0; // coeffs, slopes, sensor nodes, subapertures, actuators
     int prec = FEWHA_FP32;
     double D = 0, obstruction = 0, r0 = 0, alpha = 0;

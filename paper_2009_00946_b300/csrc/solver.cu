@@ -275,6 +275,33 @@ __global__ void k_weight_meas(DevGeo<T> G, const T* __restrict__ s, T* __restric
     sl[G.wfs_soff[g] + ns * ns + idx] = on && isfinite((double)vy) ? w * vy : (T)0;
 }
 
+// LGS tip-tilt filter: per filtered sensor (one block each) the sums of its
+// weighted x and y slopes, reduced in a fixed order
+template <typename T>
+__global__ void k_tt_sums(DevGeo<T> G, const T* __restrict__ sl, double* __restrict__ sums) {
+    __shared__ double sh[32];
+    const int g = blockIdx.x;
+    if (!G.wfs_tt[g]) return;
+    const int ns = G.wfs_n[g], n2 = ns * ns;
+    const T* S = sl + G.wfs_soff[g] + blockIdx.y * n2;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) acc += (double)S[i];
+    const double v = block_sum(acc, sh);
+    if (threadIdx.x == 0) sums[2 * g + blockIdx.y] = v;
+}
+
+// weighted slopes w mask s  ->  w mask (s - mean over active), per axis
+template <typename T>
+__global__ void k_tt_apply(DevGeo<T> G, const double* __restrict__ sums, T* __restrict__ sl) {
+    const int g = blockIdx.y, ns = G.wfs_n[g];
+    if (!G.wfs_tt[g]) return;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ns * ns || !G.mask[G.wfs_moff[g] + idx]) return;
+    const double inv = 1.0 / G.wfs_nact[g];
+    sl[G.wfs_soff[g] + idx] -= (T)(sums[2 * g] * inv);
+    sl[G.wfs_soff[g] + ns * ns + idx] -= (T)(sums[2 * g + 1] * inv);
+}
+
 // psi'(i, j) = (Gamma^T sl)(i, j): gather of the <= 4 adjacent subapertures
 template <typename T>
 __global__ void k_gammaT(DevGeo<T> G, const T* __restrict__ sl, T* __restrict__ psi) {
@@ -571,7 +598,7 @@ class Solver : public SolverBase {
       *wsl = nullptr, *Jinv = nullptr, *aD = nullptr, *Jd = nullptr, *ext = nullptr;
     T *afit = nullptr, *acur = nullptr, *aprev = nullptr, *fr = nullptr, *fp = nullptr, *fq = nullptr, *frhs = nullptr,
       *fv = nullptr;
-    double *part = nullptr, *part2 = nullptr, *sc = nullptr;
+    double *part = nullptr, *part2 = nullptr, *sc = nullptr, *ttsums = nullptr;
     int* errw = nullptr;
     int* errw_host = nullptr;
     FusedPlan* fused = nullptr;
@@ -720,6 +747,20 @@ class Solver : public SolverBase {
         TRY(uploadT(Jd, H.Jdiag));
         G.Jinv = Jinv;
         G.aD = aD;
+        {
+            std::vector<int> tt(H.G), nact(H.G);
+            for (int g = 0; g < H.G; ++g) {
+                tt[g] = H.wfs[g].tt ? 1 : 0;
+                nact[g] = H.wfs[g].nact;
+            }
+            int *d_tt, *d_nact;
+            TRY(upload(d_tt, tt));
+            TRY(upload(d_nact, nact));
+            G.wfs_tt = d_tt;
+            G.wfs_nact = d_nact;
+            G.any_tt = H.any_tt ? 1 : 0;
+            TRY(alloc(ttsums, 2 * (size_t)H.G));
+        }
         const size_t N = H.N;
         for (T** v : {&c, &r, &p, &q, &z, &s, &b, &bprev, &phi, &tmp, &y, &ext}) TRY(alloc(*v, N));
         TRY(alloc(slopes, H.S));
@@ -852,6 +893,16 @@ class Solver : public SolverBase {
         return FEWHA_OK;
     }
 
+    // LGS tip-tilt filter on weighted slopes (no-op without filtered sensors)
+    int tt_filter(T* sl) {
+        if (!G.any_tt) return FEWHA_OK;
+        k_tt_sums<T><<<dim3(G.G, 2), 256, 0, stream>>>(G, sl, ttsums);
+        FEWHA_LAUNCHED();
+        k_tt_apply<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, ttsums, sl);
+        FEWHA_LAUNCHED();
+        return FEWHA_OK;
+    }
+
     int backproject(const T* weighted_slopes, T* out) {   // out = W P^T Gamma^T sl
         int np1 = G.nsmax + 1;
         k_gammaT<T><<<dim3((np1 * np1 + 255) / 256, G.G), 256, 0, stream>>>(G, weighted_slopes, wpsi2);
@@ -868,12 +919,14 @@ class Solver : public SolverBase {
         FEWHA_LAUNCHED();
         k_gamma_w<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, wpsi, wsl);
         FEWHA_LAUNCHED();
+        TRY(tt_filter(wsl));
         return backproject(wsl, out);
     }
 
     int rhs_and_restart(int warm) {
         k_weight_meas<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, slopes, wsl, errw);
         FEWHA_LAUNCHED();
+        TRY(tt_filter(wsl));
         TRY(backproject(wsl, b));
         if (!warm) {
             k_cold<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, b, bprev, r, c);
@@ -1475,6 +1528,10 @@ class Solver : public SolverBase {
     // K steps of Alg. 2 from c = 0, r = b(slopes), every iterate on the tape;
     // the frame state (c, r, b of fewha_solve) is not touched.
     int solve_taped(const void* sl, int n_iter, void* tape, void* lout) override {
+        if (G.any_tt) {
+            err = "differentiation does not model the LGS tip-tilt filter";
+            return FEWHA_ERR_STATE;
+        }
         if (!sl || !tape || n_iter < 1 || n_iter > 100000) {
             err = "solve_taped needs slopes, a tape and n_iter >= 1";
             return FEWHA_ERR_ARG;
@@ -1517,6 +1574,10 @@ class Solver : public SolverBase {
     // overwritten) and the slopes (optional).
     int backward(const void* sl, int n_iter, const void* tape, const void* lbar, double* g_gam, double* g_alpha,
                  double* g_w, void* g_s) override {
+        if (G.any_tt) {
+            err = "differentiation does not model the LGS tip-tilt filter";
+            return FEWHA_ERR_STATE;
+        }
         if (!sl || !tape || !lbar || !g_gam || !g_alpha || !g_w || n_iter < 1 || n_iter > 100000) {
             err = "backward needs slopes, the tape, the layer cotangent, gradient outputs and n_iter >= 1";
             return FEWHA_ERR_ARG;
@@ -1776,7 +1837,7 @@ SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& e
         fb.errw = s->errw;
         std::string ferr;
         s->fbuf = fb;
-        s->fused = fused_create(hs, s->G, fb, ferr);
+        s->fused = hs.any_tt ? nullptr : fused_create(hs, s->G, fb, ferr);
         s->path = s->fused ? FEWHA_PATH_FUSED : FEWHA_PATH_PLAIN;
         out = s;
     }
@@ -1898,6 +1959,11 @@ BatchBase* make_batch(const std::vector<HostSetup>& hss, cudaStream_t stream, in
     B->coeff_off.assign(1, 0);
     B->slope_off.assign(1, 0);
     for (size_t i = 0; i < hss.size(); ++i) {
+        if (hss[i].any_tt) {
+            err = "batched instances do not model the LGS tip-tilt filter";
+            status = FEWHA_ERR_ARG;
+            return nullptr;
+        }
         if (hss[i].prec != FEWHA_FP32) {
             err = "batched instances are FP32 only";
             status = FEWHA_ERR_ARG;

@@ -45,6 +45,9 @@ struct DevGeo {
     const T* Jinv;
     const T* aD;
     T h[6], g[6];
+    int any_tt;                       // LGS tip-tilt filter on some sensor
+    const int* wfs_tt;                // per sensor: 1 = filter its slope means
+    const int* wfs_nact;              // per sensor: active subapertures
 };
 
 // Device fitting tables.

@@ -42,7 +42,7 @@ class Geometry(ctypes.Structure):
                 ("dm_height", ctypes.c_double * MAX_DMS), ("dm_pitch", ctypes.c_double * MAX_DMS),
                 ("n_fit_dir", ctypes.c_int), ("fit_theta_x", ctypes.c_double * MAX_FIT_DIRS),
                 ("fit_theta_y", ctypes.c_double * MAX_FIT_DIRS), ("fit_n_sub", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("lgs_tt_filter", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -157,6 +157,7 @@ def structs_from_config(cfg: dict, precision: int | None = None):
     if precision is None:
         precision = FP64 if cfg.get("precision", "fp32") == "fp64" else FP32
     g.precision = precision
+    g.lgs_tt_filter = 1 if cfg.get("lgs_tip_tilt_filter", False) else 0
     p = Profile()
     lay = cfg["layers"]
     if len(lay) > MAX_LAYERS:
