@@ -781,6 +781,60 @@ __device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb
 // ---------------------------------------------------------------------------
 // layer phase
 // ---------------------------------------------------------------------------
+// P^T gather into the stripe rows: each thread keeps one layer column q and
+// walks rows rr0, rr0 + rstep, ...; per sensor the column entries are read
+// once for all its rows.  KGT = entries per gather row / column of the tables.
+template <int KGT>
+__device__ __forceinline__ void pt_gather(const int* sgi, const float* stg, const int2* xt, const int2* yt, float* Z,
+                                          int G, int n, int R, int ln) {
+    constexpr int kRows = 8;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int qpt = min(n, NT), rstep = NT / qpt;
+    for (int qb = 0; qb < n; qb += qpt) {
+        const int q = qb + tid % qpt, rr0 = tid / qpt;
+        if (rr0 >= rstep) continue;
+        for (int rb = rr0; rb < R; rb += rstep * kRows) {
+            float acc[kRows];
+#pragma unroll
+            for (int u = 0; u < kRows; ++u) acc[u] = 0.f;
+            for (int g = 0; g < G; ++g) {
+                const int imin = sgi[g * 8], imax = sgi[g * 8 + 1];
+                if (imax <= imin) continue;
+                const int np1 = sgi[g * 8 + 3];
+                const float* base = stg + sgi[g * 8 + 2] - imin * np1;
+                int xj[KGT];
+                float xw[KGT];
+#pragma unroll
+                for (int b = 0; b < KGT; ++b) {
+                    const int2 xe = xt[(g * n + q) * KGT + b];
+                    xj[b] = xe.x;
+                    xw[b] = __int_as_float(xe.y);
+                }
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    const int rr = rb + u * rstep;
+                    if (rr >= R) break;
+                    const int2* yr = yt + (g * R + rr) * KGT;
+#pragma unroll
+                    for (int a = 0; a < KGT; ++a) {
+                        const int2 ye = yr[a];
+                        const float* row = base + max(ye.x, imin) * np1;
+                        float racc = 0.f;
+#pragma unroll
+                        for (int b = 0; b < KGT; ++b) racc += xw[b] * row[xj[b]];
+                        acc[u] += __int_as_float(ye.y) * racc;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kRows; ++u) {
+                const int rr = rb + u * rstep;
+                if (rr < R) Z[(rr << ln) + q] = acc[u];
+            }
+        }
+    }
+}
+
 // end_sync: the stripes may still be read by the other CTAs of the cluster,
 // so a CTA waits for them before its shared memory is reused -- unless a grid
 // barrier follows directly (it waits for every CTA).
@@ -894,51 +948,11 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
         }
         __syncthreads();
         fmark(P, 11);
-        // each thread keeps one layer column q and walks rows rr0, rr0 + rstep,
-        // ...; per sensor the column weights are read once for all its rows
-        constexpr int kRows = 8;
-        const int qpt = min(n, NT), rstep = NT / qpt;
-        for (int qb = 0; qb < n; qb += qpt) {
-            const int q = qb + tid % qpt, rr0 = tid / qpt;
-            if (rr0 >= rstep) continue;
-            for (int rb = rr0; rb < R; rb += rstep * kRows) {
-                float acc[kRows];
-#pragma unroll
-                for (int u = 0; u < kRows; ++u) acc[u] = 0.f;
-                for (int g = 0; g < G; ++g) {
-                    const int imin = sgi[g * 8], imax = sgi[g * 8 + 1];
-                    if (imax <= imin) continue;
-                    const int np1 = sgi[g * 8 + 3];
-                    const float* base = stg + sgi[g * 8 + 2] - imin * np1;
-                    int xj[kMaxKG];
-                    float xw[kMaxKG];
-#pragma unroll
-                    for (int b = 0; b < kMaxKG; ++b) {
-                        const int2 xe = b < KG ? xt[(g * n + q) * KG + b] : make_int2(0, 0);
-                        xj[b] = xe.x;
-                        xw[b] = __int_as_float(xe.y);
-                    }
-#pragma unroll
-                    for (int u = 0; u < kRows; ++u) {
-                        const int rr = rb + u * rstep;
-                        if (rr >= R) break;
-                        const int2* yr = yt + (g * R + rr) * KG;
-                        for (int a = 0; a < KG; ++a) {
-                            const int2 ye = yr[a];
-                            const float* row = base + max(ye.x, imin) * np1;
-                            float racc = 0.f;
-#pragma unroll
-                            for (int b = 0; b < kMaxKG; ++b) racc += xw[b] * row[xj[b]];
-                            acc[u] += __int_as_float(ye.y) * racc;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kRows; ++u) {
-                    const int rr = rb + u * rstep;
-                    if (rr < R) Z[(rr << ln) + q] = acc[u];
-                }
-            }
+        switch (KG) {   // the gather loops unrolled over the table's real width
+            case 1: pt_gather<1>(sgi, stg, xt, yt, Z, G, n, R, ln); break;
+            case 2: pt_gather<2>(sgi, stg, xt, yt, Z, G, n, R, ln); break;
+            case 3: pt_gather<3>(sgi, stg, xt, yt, Z, G, n, R, ln); break;
+            default: pt_gather<4>(sgi, stg, xt, yt, Z, G, n, R, ln); break;
         }
     }
 
