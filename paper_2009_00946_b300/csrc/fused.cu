@@ -629,7 +629,7 @@ constexpr int kB = 4;
 
 __device__ void fwd_dwt(const FParams& P, const Stripe& s, float* Z, float* P0, float* P1, float* const* rem0,
                         float* const* rem1, cg::cluster_group& cl) {
-    const int tid = threadIdx.x, NT = blockDim.x, n = s.n, R = s.R, ln = s.ln, lR = s.lR;
+    const int tid = threadIdx.x, NT = blockDim.x, R = s.R, ln = s.ln, lR = s.lR;
     __syncthreads();
     for (int j = 1; j <= s.J; ++j) {
         const int lm = ln - (j - 1), m = 1 << lm, half = m >> 1, mask = m - 1;
@@ -637,7 +637,33 @@ __device__ void fwd_dwt(const FParams& P, const Stripe& s, float* Z, float* P0, 
         float* Pj = (j & 1) ? P0 : P1;
         float* const* rem = (j & 1) ? rem0 : rem1;
         const int nrows = max(0, min(m - s.row0, R));
-        const int cnt_r = nrows << (lm - 1);
+        if (half >= 4) {
+            // a thread makes 4 consecutive pairs of one row from 12 inputs
+            // (three 16-byte loads; 2 k0 is a multiple of 8, the row of m a
+            // multiple of 8 floats, so the wrap keeps them aligned)
+            const int cnt4 = nrows << (lm - 3);
+            for (int e = tid; e < cnt4; e += NT) {
+                const int rr = e >> (lm - 3), k0 = (e & ((half >> 2) - 1)) << 2;
+                const float* x = Z + (rr << ln);
+                const float4 q0 = *reinterpret_cast<const float4*>(x + ((2 * k0) & mask));
+                const float4 q1 = *reinterpret_cast<const float4*>(x + ((2 * k0 + 4) & mask));
+                const float4 q2 = *reinterpret_cast<const float4*>(x + ((2 * k0 + 8) & mask));
+                const float v[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+                float a[4], d[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = d[q] = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) {
+                        a[q] += P.h[t] * v[2 * q + t];
+                        d[q] += P.g[t] * v[2 * q + t];
+                    }
+                }
+                *reinterpret_cast<float4*>(Pj + (rr << ln) + k0) = make_float4(a[0], a[1], a[2], a[3]);
+                *reinterpret_cast<float4*>(Pj + (rr << ln) + half + k0) = make_float4(d[0], d[1], d[2], d[3]);
+            }
+        }
+        const int cnt_r = (half >= 4) ? 0 : nrows << (lm - 1);
         for (int e0 = tid; e0 < cnt_r; e0 += kB * NT) {
             float a[kB], d[kB];
 #pragma unroll
@@ -675,8 +701,11 @@ __device__ void fwd_dwt(const FParams& P, const Stripe& s, float* Z, float* P0, 
             for (int e = tid; e < items; e += NT) {
                 const int x = e & mask, grp = e >> lm;
                 const int row = s.row0 + (grp << lkR);
-                const int k0 = row < half ? row : row - half;
-                const float* f = row < half ? P.h : P.g;
+                const bool lo = row < half;
+                const int k0 = lo ? row : row - half;
+                float f[6];   // h or g, selected per coefficient (no indexing of the parameters)
+#pragma unroll
+                for (int t = 0; t < 6; ++t) f[t] = lo ? P.h[t] : P.g[t];
                 float v[12];
 #pragma unroll
                 for (int i = 0; i < 12; ++i) {
@@ -712,7 +741,6 @@ __device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb
         float* const* remLL = (j == s.J) ? remZ : (((j + 1) & 1) ? remQ1 : remQ0);
         float* Qj = (j & 1) ? Q1 : Q0;
         const int nrows = max(0, min(m - s.row0, R));
-        const int cnt = nrows << lm;
         // column pass: output rows i0 .. i0 + kR - 1 (i0 even) of one column
         // need the a and d rows k0 - 2 .. k0 + kR/2 - 1 (k0 = i0 / 2); output
         // i0 + u takes taps t = e + 2 s (e = u & 1) from rows k0 + u/2 - s
@@ -747,28 +775,32 @@ __device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb
             }
         }
         __syncthreads();
-        for (int e0 = tid; e0 < cnt; e0 += kB * NT) {
-            float acc[kB];
+        // row pass: entries 2kk and 2kk+1 of a row share the a and d entries
+        // kk - s (s = 0..2, periodic) with taps 2s and 2s+1; one item makes both
+        const int hmask2 = half - 1, cntp = nrows << (lm - 1);
+        for (int e0 = tid; e0 < cntp; e0 += kB * NT) {
+            float2 o[kB];
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
                 const int e = e0 + u * NT;
-                acc[u] = 0.f;
-                if (e < cnt) {
-                    const int x = e & mask;
-                    const float* pr = Pb + ((e >> lm) << ln);
+                o[u] = make_float2(0.f, 0.f);
+                if (e < cntp) {
+                    const float* pr = Pb + ((e >> (lm - 1)) << ln);
+                    const int kk = e & hmask2;
 #pragma unroll
-                    for (int t = 0; t < 6; ++t) {
-                        const int r = (x - t) & mask;
-                        if (r & 1) continue;
-                        const int k = r >> 1;
-                        acc[u] += P.h[t] * pr[k] + P.g[t] * pr[half + k];
+                    for (int sg = 0; sg < 3; ++sg) {
+                        const int k = (kk - sg) & hmask2;
+                        const float av = pr[k], dv = pr[half + k];
+                        o[u].x += P.h[2 * sg] * av + P.g[2 * sg] * dv;
+                        o[u].y += P.h[2 * sg + 1] * av + P.g[2 * sg + 1] * dv;
                     }
                 }
             }
 #pragma unroll
             for (int u = 0; u < kB; ++u) {
                 const int e = e0 + u * NT;
-                if (e < cnt) Qj[((e >> lm) << ln) + (e & mask)] = acc[u];
+                if (e < cntp)
+                    *reinterpret_cast<float2*>(Qj + ((e >> (lm - 1)) << ln) + 2 * (e & hmask2)) = o[u];
             }
         }
         out = Qj;
