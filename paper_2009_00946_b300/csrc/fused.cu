@@ -162,16 +162,18 @@ __device__ __forceinline__ void fmark(const FParams& P, int tag) {
     }
 }
 
-// Arrive: one fenced atomic per CTA; wait: thread 0 polls with acquire loads
-// and a short back-off (fewer polls on the counter's line leave the L2 slice
-// free for the arrivals), bounded by the clock budget.
+// Arrive: one release reduction per CTA (cumulative over the CTA's writes,
+// which the block barrier orders before it); wait: thread 0 polls with
+// acquire loads and a short back-off (fewer polls on the counter's line leave
+// the L2 slice free for the arrivals), bounded by the clock budget.  The
+// acquire load that sees the last arrival orders everything after it, and the
+// block barrier passes that on to the CTA's other threads.
 __device__ void grid_barrier(const FParams& P, unsigned& target, int* s_abort, int& slot) {
     __syncthreads();
     if (threadIdx.x == 0) {
         trace_mark(P, slot, 0);
         target += gridDim.x;
-        __threadfence();
-        atomicAdd(P.bar, 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(P.bar), "r"(1u) : "memory");
         if (!*s_abort) {
             long long t0 = clock64();
             while ((int)(ld_acquire_gpu(P.bar) - target) < 0) {
@@ -183,7 +185,6 @@ __device__ void grid_barrier(const FParams& P, unsigned& target, int* s_abort, i
                 __nanosleep(32);
             }
         }
-        __threadfence();
         trace_mark(P, slot, 1);
     }
     ++slot;
@@ -1242,7 +1243,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
             if (threadIdx.x == 0) {
                 double* pb = RI.preB + (k & 1) * 6;
                 for (int q = 0; q < 6; ++q) pb[q] = sh[q];
-                __threadfence();
+                // the release store orders this thread's stores above before the flag
                 asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(RI.flagB), "r"((unsigned)k + 1u) : "memory");
             }
         }
