@@ -39,7 +39,7 @@ constexpr int kMaxC = 16;
 constexpr int kMaxLayersFused = 64;
 constexpr int kMaxWfsFused = 16;
 constexpr int kFineCap = 1024;   // sub-phase marks per CTA per traced launch
-constexpr int kWd = 7;     // ints per layer in a sensor tile's window descriptor
+constexpr int kWd = 8;     // ints per layer in a sensor tile's window descriptor
 constexpr int kMaxKG = 4;        // P^T gather entries per layer row / column
 
 enum { kModeRhs = 0, kModeData = 1 };
@@ -477,6 +477,11 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 wdesc[tid * kWd + 3] = (c1 - c0 + 1 + 3) & ~3;
                 wdesc[tid * kWd + 5] = I.lay_off[tid] + r0 * n + c0;
                 wdesc[tid * kWd + 6] = n;
+                // row of a window float4 by multiply-high with ceil(2^32 / nc4)
+                // (Granlund-Montgomery, round-up multiplier: exact for q * nc4 < 2^32);
+                // nc4 = 1 (multiplier 2^32) is marked 0 and takes the row directly
+                const unsigned nc4 = (unsigned)wdesc[tid * kWd + 3] >> 2;
+                wdesc[tid * kWd + 7] = nc4 > 1 ? (int)(unsigned)(((1ull << 32) + nc4 - 1) / nc4) : 0;
             }
             __syncthreads();
             if (tid == 0) {
@@ -489,17 +494,20 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             }
             __syncthreads();
         }
-        // 16-byte asynchronous copies (through L2, not L1), every thread on
-        // every layer's window
+        // 16-byte asynchronous copies (through L2, not L1): the windows of all
+        // layers are one run of float4s (window l starts at float4
+        // wdesc[l].off / 4), spread evenly over the threads; a thread's layer
+        // index only grows along its run
         {
-            for (int l = 0; l < L; ++l) {
-                const int nr = wdesc[l * kWd + 2], nc4 = wdesc[l * kWd + 3] >> 2, n = wdesc[l * kWd + 6];
-                const float* src = I.phi + wdesc[l * kWd + 5];
-                float* dst = win + wdesc[l * kWd + 4];
-                for (int e = tid; e < nr * nc4; e += NT) {
-                    const int rr = e / nc4, c4 = e - rr * nc4;
-                    cp_async16(dst + (e << 2), src + (long)rr * n + (c4 << 2));
-                }
+            const int tot4 = wdesc[L * kWd + 4] >> 2;
+            int l = 0;
+            for (int e4 = tid; e4 < tot4; e4 += NT) {
+                while (e4 >= (wdesc[(l + 1) * kWd + 4] >> 2)) ++l;
+                const int nc4 = wdesc[l * kWd + 3] >> 2;
+                const unsigned loc = (unsigned)(e4 - (wdesc[l * kWd + 4] >> 2));
+                const unsigned mg = (unsigned)wdesc[l * kWd + 7];
+                const int rr = mg ? (int)__umulhi(loc, mg) : (int)loc, c4 = (int)loc - rr * nc4;
+                cp_async16(win + (e4 << 2), I.phi + wdesc[l * kWd + 5] + (long)rr * wdesc[l * kWd + 6] + (c4 << 2));
             }
             // part A of the next layer phase's CG scalars while the copies fly
             if (want_mu && tid < 32 && cc->lres && cc->il_valid && cc->IL.preA_cta < 0) {

@@ -1698,10 +1698,6 @@ class Solver : public SolverBase {
         key.path = path * 2 + (on_device ? 1 : 0);
         key.k_rr = k_rr;
         if (!gexec[slot] || !(gkey[slot] == key)) {
-            if (gexec[slot]) {
-                cudaGraphExecDestroy(gexec[slot]);
-                gexec[slot] = nullptr;
-            }
             if (stream == 0) {
                 err = "fewha_frame needs a non-default stream (graph capture)";
                 return FEWHA_ERR_STATE;
@@ -1747,16 +1743,32 @@ class Solver : public SolverBase {
                     break;
                 }
             } while (0);
+            graph = nullptr;
             cudaError_t ec = cudaStreamEndCapture(stream, &graph);
             frame_count = fc;              // the capture only recorded the work
             long long gl = launches - l0;
             launches = l0;
-            if (st) return st;
-            if (ec != cudaSuccess) {
+            if (st || ec != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                if (st) return st;
                 err = std::string("graph capture: ") + cudaGetErrorString(ec);
                 return FEWHA_ERR_CUDA;
             }
-            cudaError_t ei = cudaGraphInstantiate(&gexec[slot], graph, 0);
+            // the same work on other buffers (a new slopes or layers pointer
+            // every frame) updates the instantiated graph in place: no
+            // re-instantiation on the host, launches already enqueued keep
+            // their parameters; any other change instantiates anew
+            cudaError_t ei = cudaErrorUnknown;
+            if (gexec[slot]) {
+                cudaGraphExecUpdateResultInfo info;
+                ei = cudaGraphExecUpdate(gexec[slot], graph, &info);
+                if (ei != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(gexec[slot]);
+                    gexec[slot] = nullptr;
+                }
+            }
+            if (!gexec[slot]) ei = cudaGraphInstantiate(&gexec[slot], graph, 0);
             cudaGraphDestroy(graph);
             if (ei != cudaSuccess) {
                 err = std::string("graph instantiate: ") + cudaGetErrorString(ei);

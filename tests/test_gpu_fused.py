@@ -152,6 +152,34 @@ def test_fused_graph_frame_host_and_device(fw, elt_frames):
             assert np.array_equal(lb, dev_l.cpu().numpy()), k
 
 
+def test_fused_graph_frames_on_rotating_buffers(fw, elt_frames):
+    """A new slopes and layers buffer every frame, enqueued back to back (the
+    cached graph is updated in place, not re-instantiated): the layers are
+    bit-identical to frames through fixed buffers, one launch per frame."""
+    import torch
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as A, _fused(fw, cfg, k_rr=10) as B:
+        fixed_s = torch.empty(A.S, dtype=torch.float32, device="cuda")
+        fixed_l = torch.empty(A.N, dtype=torch.float32, device="cuda")
+        pool = torch.from_numpy(S_in[:12]).cuda()              # one slopes buffer per frame
+        outs = torch.empty(12, B.N, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        l0 = B.launch_count()
+        with torch.cuda.stream(B.stream):
+            for k in range(12):
+                B.frame(pool[k], 4, warm=True, layers_out=outs[k])
+        B.sync()
+        assert B.launch_count() - l0 == 12
+        for k in range(12):
+            with torch.cuda.stream(A.stream):
+                fixed_s.copy_(pool[k])
+            A.frame(fixed_s, 4, warm=True, layers_out=fixed_l)
+            A.sync()
+            got = outs[k].cpu().numpy()
+            assert np.array_equal(got, fixed_l.cpu().numpy()), k
+            assert rel(got, ref[k][0]) < 1e-4, k
+
+
 @pytest.mark.parametrize("C", [1, 2, 4, 8, 16])
 def test_fused_every_cluster_shape_matches_oracle(fw, elt_frames, C):
     """Each thread-block-cluster shape of the fused plan (row stripes of n/C
