@@ -1230,62 +1230,67 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     __syncthreads();
     if (P.pf && (int)threadIdx.x >= (int)blockDim.x - 32) prefetch_plan_data(P);   // the last warp
 
-    // Alg. 1 RHS: Gamma^T C^{-1} s per sensor tile
-    for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeRhs, false, wdesc, red, &cc, 0);
-    grid_barrier(P, target, &s_abort, slot);
-    // P^T, W -> b; warm restart (or c -> phi for the replacement); z_0 -> phi
-    const int m1 = P.replace ? kLpRhsRepl : kLpRhsStart;
-    for (int t = l_lo; t < l_hi; ++t) layer_phase(P, P.lsched[t], m1, 0, sm, rem, cl, red, sh, &cc, t + 1 < l_hi);
-    grid_barrier(P, target, &s_abort, slot);
-    if (P.replace) {
-        // r = b - M c: data term of M on phi_c, then the layer phase
-        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, false, wdesc, red, &cc, 0);
-        grid_barrier(P, target, &s_abort, slot);
-        for (int t = l_lo; t < l_hi; ++t)
-            layer_phase(P, P.lsched[t], kLpReplStart, 0, sm, rem, cl, red, sh, &cc, t + 1 < l_hi);
-        grid_barrier(P, target, &s_abort, slot);
-    }
-    for (int k = 0; k < P.n_iter; ++k) {
-        for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, kModeData, true, wdesc, red, &cc, k);
-        if (res_inst >= 0 && threadIdx.x < 32) {
-            // part A of instance res_inst's scalars for this iteration's layer phase
-            const FInst& RI = P.inst[res_inst];
-            ScalA A;
-            alg2_part_a(P, RI, k, A);
-            if (threadIdx.x == 0) {
-                double* pa = RI.preA + (k & 1) * 6;
-                pa[0] = A.rho;
-                pa[1] = A.beta;
-                pa[2] = A.t;
-                pa[3] = A.aold;
-                pa[4] = (double)A.mh;
-                pa[5] = (double)A.ml;
+    // One loop over the phases of the frame, each phase function called from
+    // a single site (one copy of its code, warm in the instruction caches and
+    // the L2 from the first phase of its kind on).  Phases, a grid barrier
+    // after every one but the last:
+    //   0: Alg. 1 RHS, Gamma^T C^{-1} s per sensor tile
+    //   1: P^T, W -> b; warm restart (or c -> phi for the replacement); z_0 -> phi
+    //   [2, 3: replacement r = b - M c: data term of M on phi_c, then the layer phase]
+    //   then per Alg. 2 iteration k: the data term (sensor tiles; the reserved
+    //   CTA computes part A of the scalars), then the layer phase (the reserved
+    //   CTA first publishes part B)
+    const int base = P.replace ? 4 : 2, nph = base + 2 * P.n_iter;
+    for (int ph = 0; ph < nph; ++ph) {
+        const bool it = ph >= base;
+        const int k = it ? (ph - base) >> 1 : 0;
+        const bool sensor_ph = it ? ((ph - base) & 1) == 0 : (ph & 1) == 0;
+        if (sensor_ph) {
+            const int smode = (ph == 0) ? kModeRhs : kModeData;
+            for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, smode, it, wdesc, red, &cc, k);
+            if (it && res_inst >= 0 && threadIdx.x < 32) {
+                // part A of instance res_inst's scalars for this iteration's layer phase
+                const FInst& RI = P.inst[res_inst];
+                ScalA A;
+                alg2_part_a(P, RI, k, A);
+                if (threadIdx.x == 0) {
+                    double* pa = RI.preA + (k & 1) * 6;
+                    pa[0] = A.rho;
+                    pa[1] = A.beta;
+                    pa[2] = A.t;
+                    pa[3] = A.aold;
+                    pa[4] = (double)A.mh;
+                    pa[5] = (double)A.ml;
+                }
             }
-        }
-        grid_barrier(P, target, &s_abort, slot);
-        if (res_inst >= 0 && threadIdx.x < 32) {
-            // part B of the reserved instance's scalars: publish, then flag
-            const FInst& RI = P.inst[res_inst];
-            const double* pa = RI.preA + (k & 1) * 6;
-            ScalA A;
-            A.rho = __ldcg(pa);
-            A.beta = __ldcg(pa + 1);
-            A.t = __ldcg(pa + 2);
-            A.aold = __ldcg(pa + 3);
-            A.mh = (float)__ldcg(pa + 4);
-            A.ml = (float)__ldcg(pa + 5);
-            alg2_part_b(P, RI, k, A, sh);
-            __syncwarp();
-            if (threadIdx.x == 0) {
-                double* pb = RI.preB + (k & 1) * 6;
-                for (int q = 0; q < 6; ++q) pb[q] = sh[q];
-                // the release store orders this thread's stores above before the flag
-                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(RI.flagB), "r"((unsigned)k + 1u) : "memory");
+        } else {
+            if (it && res_inst >= 0 && threadIdx.x < 32) {
+                // part B of the reserved instance's scalars: publish, then flag
+                const FInst& RI = P.inst[res_inst];
+                const double* pa = RI.preA + (k & 1) * 6;
+                ScalA A;
+                A.rho = __ldcg(pa);
+                A.beta = __ldcg(pa + 1);
+                A.t = __ldcg(pa + 2);
+                A.aold = __ldcg(pa + 3);
+                A.mh = (float)__ldcg(pa + 4);
+                A.ml = (float)__ldcg(pa + 5);
+                alg2_part_b(P, RI, k, A, sh);
+                __syncwarp();
+                if (threadIdx.x == 0) {
+                    double* pb = RI.preB + (k & 1) * 6;
+                    for (int q = 0; q < 6; ++q) pb[q] = sh[q];
+                    // the release store orders this thread's stores above before the flag
+                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(RI.flagB), "r"((unsigned)k + 1u)
+                                 : "memory");
+                }
             }
+            const int lmode = it ? kLpIter : (ph == 1 ? (P.replace ? kLpRhsRepl : kLpRhsStart) : kLpReplStart);
+            const bool last_ph = it && k + 1 == P.n_iter;
+            for (int t = l_lo; t < l_hi; ++t)
+                layer_phase(P, P.lsched[t], lmode, k, sm, rem, cl, red, sh, &cc, t + 1 < l_hi || last_ph);
         }
-        for (int t = l_lo; t < l_hi; ++t)
-            layer_phase(P, P.lsched[t], kLpIter, k, sm, rem, cl, red, sh, &cc, t + 1 < l_hi || k + 1 == P.n_iter);
-        if (k + 1 < P.n_iter) grid_barrier(P, target, &s_abort, slot);
+        if (ph + 1 < nph) grid_barrier(P, target, &s_abort, slot);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1907,6 +1912,30 @@ void fused_destroy(FusedPlan* plan) {
 }
 
 void fused_mark_dirty(FusedPlan* pl) { pl->bar_dirty = true; }
+
+int fused_repoint_node(cudaGraphExec_t exec, cudaGraphNode_t node, const float* slopes, float* layers_out) {
+    cudaKernelNodeParams kp;
+    if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess || !kp.kernelParams || !kp.kernelParams[0]) {
+        cudaGetLastError();
+        return -1;
+    }
+    bool ours = false;
+    for (int C : {1, 2, 4, 8, 16}) ours = ours || kp.func == (void*)fused_kernel_for(C);
+    if (!ours) return -1;
+    FParams P = *static_cast<const FParams*>(kp.kernelParams[0]);
+    if (P.n_inst != 1) return -1;
+    P.slopes_in = slopes;
+    P.phi_out = layers_out;
+    void* args[1] = {&P};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    if (cudaGraphExecKernelNodeSetParams(exec, node, &kp) != cudaSuccess ||
+        cudaGraphKernelNodeSetParams(node, &kp) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return 0;
+}
 
 int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int replace, long long budget,
                 cudaStream_t stream, std::string& err, long long& launches, float* layers_out) {

@@ -49,6 +49,11 @@ int fused_solve(FusedPlan* plan, const float* slopes, int n_iter, int warm, int 
 // After a kernel error the barrier counters may be left set: zero them first
 // at the next launch.
 void fused_mark_dirty(FusedPlan* plan);
+// A captured single-instance frame launch (kernel node `node` of the graph
+// `exec` was instantiated from) re-pointed at other slopes / layers buffers,
+// in the executable graph and in the node: no re-capture, no instantiation.
+// Returns 0, or -1 when the node is not a fused frame launch.
+int fused_repoint_node(cudaGraphExec_t exec, cudaGraphNode_t node, const float* slopes, float* layers_out);
 
 // Plan summary (cluster shape, grid, shared memory, work items).
 int fused_describe(const FusedPlan* plan, char* buf, int len);

@@ -611,23 +611,33 @@ class Solver : public SolverBase {
     bool pol_pending = false;   // the frame's slopes still lack Gamma P_DM a_{-1}
     // graph cache
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraph_t gsrc[2] = {nullptr, nullptr};          // graph each exec was instantiated from
+    cudaGraphNode_t gknode[2] = {nullptr, nullptr};    // its lone fused kernel node (direct frames)
     struct Key {
         int n_iter = -1, warm = -1, n_fit = -1, path = -1, k_rr = -1;
         double gain = -1;
         const void* sin = nullptr;
         void* lout = nullptr;
         void* dout = nullptr;
-        bool operator==(const Key& o) const {
-            return n_iter == o.n_iter && warm == o.warm && n_fit == o.n_fit && gain == o.gain && sin == o.sin &&
-                   lout == o.lout && dout == o.dout && path == o.path && k_rr == o.k_rr;
+        bool same_work(const Key& o) const {   // all but the slopes / layers buffers
+            return n_iter == o.n_iter && warm == o.warm && n_fit == o.n_fit && gain == o.gain && dout == o.dout &&
+                   path == o.path && k_rr == o.k_rr && (lout == nullptr) == (o.lout == nullptr);
         }
+        bool operator==(const Key& o) const { return same_work(o) && sin == o.sin && lout == o.lout; }
     } gkey[2];
+
+    void drop_graph(int i) {
+        if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+        if (gsrc[i]) cudaGraphDestroy(gsrc[i]);
+        gexec[i] = nullptr;
+        gsrc[i] = nullptr;
+        gknode[i] = nullptr;
+    }
 
     ~Solver() override {
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
-        for (int i = 0; i < 2; ++i)
-            if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+        for (int i = 0; i < 2; ++i) drop_graph(i);
         if (fused) fused_destroy(fused);
         for (void* a : allocs) cudaFree(a);
         if (pinned_in) cudaFreeHost(pinned_in);
@@ -1266,6 +1276,7 @@ class Solver : public SolverBase {
     int decode_err(int e) {
         if (e) {
             if (fused) fused_mark_dirty(fused);
+            drop_graphs();   // captured frames would skip the counter reset the next launch needs
             FEWHA_CUDA(cudaMemsetAsync(errw, 0, sizeof(int), stream));
             FEWHA_CUDA(cudaStreamSynchronize(stream));
             if (e & kErrLaunch) {
@@ -1351,11 +1362,7 @@ class Solver : public SolverBase {
 
     // captured frame graphs hold the old plan's launch: drop them
     void drop_graphs() {
-        for (int i = 0; i < 2; ++i)
-            if (gexec[i]) {
-                cudaGraphExecDestroy(gexec[i]);
-                gexec[i] = nullptr;
-            }
+        for (int i = 0; i < 2; ++i) drop_graph(i);
     }
 
     int set_cluster_size(int C) override {
@@ -1697,6 +1704,9 @@ class Solver : public SolverBase {
         key.dout = dm;
         key.path = path * 2 + (on_device ? 1 : 0);
         key.k_rr = k_rr;
+        if (gexec[slot] && !(gkey[slot] == key) && gknode[slot] && direct && gkey[slot].same_work(key) &&
+            fused_repoint_node(gexec[slot], gknode[slot], (const float*)sin_dev, (float*)lo_dev) == 0)
+            gkey[slot] = key;   // the same frame on other buffers: re-pointed in place
         if (!gexec[slot] || !(gkey[slot] == key)) {
             if (stream == 0) {
                 err = "fewha_frame needs a non-default stream (graph capture)";
@@ -1754,27 +1764,26 @@ class Solver : public SolverBase {
                 err = std::string("graph capture: ") + cudaGetErrorString(ec);
                 return FEWHA_ERR_CUDA;
             }
-            // the same work on other buffers (a new slopes or layers pointer
-            // every frame) updates the instantiated graph in place: no
-            // re-instantiation on the host, launches already enqueued keep
-            // their parameters; any other change instantiates anew
-            cudaError_t ei = cudaErrorUnknown;
-            if (gexec[slot]) {
-                cudaGraphExecUpdateResultInfo info;
-                ei = cudaGraphExecUpdate(gexec[slot], graph, &info);
-                if (ei != cudaSuccess) {
-                    cudaGetLastError();
-                    cudaGraphExecDestroy(gexec[slot]);
-                    gexec[slot] = nullptr;
-                }
-            }
-            if (!gexec[slot]) ei = cudaGraphInstantiate(&gexec[slot], graph, 0);
-            cudaGraphDestroy(graph);
+            drop_graph(slot);
+            cudaError_t ei = cudaGraphInstantiate(&gexec[slot], graph, 0);
             if (ei != cudaSuccess) {
+                cudaGraphDestroy(graph);
                 err = std::string("graph instantiate: ") + cudaGetErrorString(ei);
                 gexec[slot] = nullptr;
                 return FEWHA_ERR_CUDA;
             }
+            // a direct frame whose graph is the fused launch alone can later be
+            // re-pointed at other buffers (kept: the graph and its node)
+            gsrc[slot] = graph;
+            size_t nn = 0;
+            if (direct && cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn == 1) {
+                cudaGraphNode_t nd;
+                cudaGraphNodeType ty;
+                if (cudaGraphGetNodes(graph, &nd, &nn) == cudaSuccess && cudaGraphNodeGetType(nd, &ty) == cudaSuccess &&
+                    ty == cudaGraphNodeTypeKernel)
+                    gknode[slot] = nd;
+            }
+            cudaGetLastError();
             gkey[slot] = key;
             graph_launch_count[slot] = gl;
         }
