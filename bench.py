@@ -162,7 +162,7 @@ def parity_vs_oracle(fewha, cfg, pool, oracle_layers):
 # DRAM bytes (read + write) of one k_fused_frame launch on this workload from
 # the committed full ncu capture, valid only for the kernel source it was
 # taken on (sha256 prefix of csrc/fused.cu); any other source reports null.
-NCU_TRAFFIC = {"fused_cu_sha256": "51c5ccc305cb9355", "dram_bytes": 5008896,
+NCU_TRAFFIC = {"fused_cu_sha256": "a286d4b1b407e6f8", "dram_bytes": 5549312,
                "summary": "profiles/k_fused_frame_elt_full.md"}
 
 
