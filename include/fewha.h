@@ -119,7 +119,11 @@ const char* fewha_last_error(const fewha_handle* h);
 int fewha_sizes(const fewha_handle* h, long* n_coeff, long* n_slopes, long* n_act);
 
 /* Select the execution path for FP32 handles (FP64 handles always use the
- * plain path).  Default: FEWHA_PATH_FUSED for FP32. */
+ * plain path).  Default: FEWHA_PATH_FUSED for FP32 when a fused plan exists
+ * for the geometry, else FEWHA_PATH_PLAIN.  Requesting FEWHA_PATH_FUSED
+ * without a plan returns FEWHA_ERR_GEOMETRY (fewha_last_error says why: the
+ * LGS tip-tilt filter, too many layers or sensors, shared memory) and keeps
+ * the current path. */
 int fewha_set_path(fewha_handle* h, int path);
 
 /* Residual replacement period k_rr (Alg. 1 warm restart, reading: every

@@ -474,26 +474,35 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 const int r0 = I.cy[base + a_lo], r1 = I.cy[base + a_hi] + 1;
                 const int c0 = I.cx[base + b_lo] & ~3, c1 = I.cx[base + b_hi] + 1;
                 const int n = I.lay_n[tid];
-                wdesc[tid * kWd + 0] = r0;
+                const int nr = r1 - r0 + 1, nc = (c1 - c0 + 1 + 3) & ~3;
+                // a sparse sensor (nodes several layer cells apart, e.g. a 1x1
+                // tip-tilt sensor) stages only the 2 x 2 cells under each node
+                // (gathered window: row 2 ii + dr, column 2 jj + dc; marked by
+                // r0 = -1); nodes up to ~4 cells apart keep the dense window,
+                // which stages faster at a similar size
+                const bool gath = nr * nc > 16 * pr * pc;
+                wdesc[tid * kWd + 0] = gath ? -1 : r0;
                 wdesc[tid * kWd + 1] = c0;
-                wdesc[tid * kWd + 2] = r1 - r0 + 1;
-                wdesc[tid * kWd + 3] = (c1 - c0 + 1 + 3) & ~3;
-                wdesc[tid * kWd + 5] = I.lay_off[tid] + r0 * n + c0;
+                wdesc[tid * kWd + 2] = gath ? 2 * pr : nr;
+                wdesc[tid * kWd + 3] = gath ? 2 * pc : nc;
+                wdesc[tid * kWd + 5] = gath ? I.lay_off[tid] : I.lay_off[tid] + r0 * n + c0;
                 wdesc[tid * kWd + 6] = n;
                 // row of a window float4 by multiply-high with ceil(2^32 / nc4)
                 // (Granlund-Montgomery, round-up multiplier: exact for q * nc4 < 2^32);
                 // nc4 = 1 (multiplier 2^32) is marked 0 and takes the row directly
-                const unsigned nc4 = (unsigned)wdesc[tid * kWd + 3] >> 2;
+                const unsigned nc4 = (unsigned)nc >> 2;
                 wdesc[tid * kWd + 7] = nc4 > 1 ? (int)(unsigned)(((1ull << 32) + nc4 - 1) / nc4) : 0;
             }
             __syncthreads();
             if (tid == 0) {
-                int o = 0;
+                int o = 0, anyg = 0;
                 for (int l = 0; l < L; ++l) {
                     wdesc[l * kWd + 4] = o;
                     o += wdesc[l * kWd + 2] * wdesc[l * kWd + 3];
+                    anyg |= wdesc[l * kWd] < 0;
                 }
                 wdesc[L * kWd + 4] = o;
+                wdesc[L * kWd + 0] = anyg;   // some layer of the tile has a gathered window
             }
             __syncthreads();
         }
@@ -503,14 +512,40 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         // index only grows along its run
         {
             const int tot4 = wdesc[L * kWd + 4] >> 2;
-            int l = 0;
-            for (int e4 = tid; e4 < tot4; e4 += NT) {
-                while (e4 >= (wdesc[(l + 1) * kWd + 4] >> 2)) ++l;
+            const bool anyg = wdesc[L * kWd + 0] != 0;
+            auto dense4 = [&](int l, int e4) {
                 const int nc4 = wdesc[l * kWd + 3] >> 2;
                 const unsigned loc = (unsigned)(e4 - (wdesc[l * kWd + 4] >> 2));
                 const unsigned mg = (unsigned)wdesc[l * kWd + 7];
                 const int rr = mg ? (int)__umulhi(loc, mg) : (int)loc, c4 = (int)loc - rr * nc4;
                 cp_async16(win + (e4 << 2), I.phi + wdesc[l * kWd + 5] + (long)rr * wdesc[l * kWd + 6] + (c4 << 2));
+            };
+            int l = 0;
+            if (!anyg) {
+                for (int e4 = tid; e4 < tot4; e4 += NT) {
+                    while (e4 >= (wdesc[(l + 1) * kWd + 4] >> 2)) ++l;
+                    dense4(l, e4);
+                }
+            } else {
+                for (int e4 = tid; e4 < tot4; e4 += NT) {
+                    while (e4 >= (wdesc[(l + 1) * kWd + 4] >> 2)) ++l;
+                    if (wdesc[l * kWd] >= 0) dense4(l, e4);   // gathered layers below
+                }
+            }
+            // gathered windows: 4-byte reads through L2 (the layers were written
+            // by other SMs in this launch)
+            for (int ll = 0; anyg && ll < L; ++ll) {
+                if (wdesc[ll * kWd] >= 0) continue;
+                const int tb = I.tab_off[g * L + ll], nc = wdesc[ll * kWd + 3], n = wdesc[ll * kWd + 6];
+                const int cnt = wdesc[ll * kWd + 2] * nc;
+                const float* src = I.phi + wdesc[ll * kWd + 5];
+                float* dst = win + wdesc[ll * kWd + 4];
+                for (int e = tid; e < cnt; e += NT) {
+                    const int rp = e / nc, cq = e - rp * nc;
+                    const int row = __ldg(I.cy + tb + a_lo + (rp >> 1)) + (rp & 1);
+                    const int col = __ldg(I.cx + tb + b_lo + (cq >> 1)) + (cq & 1);
+                    dst[e] = __ldcg(src + (long)row * n + col);
+                }
             }
             // part A of the next layer phase's CG scalars while the copies fly
             if (want_mu && tid < 32 && cc->lres && cc->il_valid && cc->IL.preA_cta < 0) {
@@ -532,13 +567,14 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             for (int e = tid; e < L * (pr + pc); e += NT) {
                 const int l = e / (pr + pc), k = e - l * (pr + pc);
                 const int base = I.tab_off[g * L + l];
+                const bool gath = wdesc[l * kWd] < 0;
                 if (k < pr) {
-                    roff[l * P.tile_rows + k] =
-                        (__ldg(I.cy + base + a_lo + k) - wdesc[l * kWd]) * wdesc[l * kWd + 3] + wdesc[l * kWd + 4];
+                    const int rr = gath ? 2 * k : __ldg(I.cy + base + a_lo + k) - wdesc[l * kWd];
+                    roff[l * P.tile_rows + k] = rr * wdesc[l * kWd + 3] + wdesc[l * kWd + 4];
                     rw[l * P.tile_rows + k] = __ldg(I.ty + base + a_lo + k);
                 } else {
                     const int kk = k - pr;
-                    coff[l * P.tile_cols + kk] = __ldg(I.cx + base + b_lo + kk) - wdesc[l * kWd + 1];
+                    coff[l * P.tile_cols + kk] = gath ? 2 * kk : __ldg(I.cx + base + b_lo + kk) - wdesc[l * kWd + 1];
                     cw[l * P.tile_cols + kk] = __ldg(I.tx + base + b_lo + kk);
                 }
             }
@@ -1413,7 +1449,7 @@ bool prep_instance(const HostSetup& hs, InstPrep& ip, std::string& err) {
             }
         }
     if (ip.KG > kMaxKG) {
-        err = "layer grid much finer than the sensor grid (more than 4 samples per layer cell pair)";
+        err = "sensor grid much finer than the layer grid (more than 4 sensor nodes per layer cell pair)";
         return false;
     }
     auto fbits = [](float f) {
@@ -1629,12 +1665,13 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             tile_nodes = std::max(tile_nodes, (a_hi - a_lo + 1) * (b_hi - b_lo + 1));
             tile_sub = std::max(tile_sub, (std::min(w.i1, ns) - a_lo) * (std::min(w.j1, ns) - b_lo));
             int win = 0;
+            const int pr = a_hi - a_lo + 1, pc = b_hi - b_lo + 1;
             for (int l = 0; l < hs.L; ++l) {
                 const int base = hs.tab_off[w.g * hs.L + l];
                 const int nr = hs.cy[base + a_hi] + 1 - hs.cy[base + a_lo] + 1;
                 const int c0 = hs.cx[base + b_lo] & ~3;   // as in the kernel: 16-byte aligned
                 const int nc = (hs.cx[base + b_hi] + 1 - c0 + 1 + 3) & ~3;
-                win += nr * nc;
+                win += nr * nc > 16 * pr * pc ? 4 * pr * pc : nr * nc;   // dense, or 2 x 2 cells per node
             }
             win_max = std::max(win_max, win);
         }

@@ -130,6 +130,8 @@ class SolverBase {
     long long frame_count = 0;
     long long launches = 0;
     bool have_frame = false;
+    bool fused_available = false;   // a fused plan exists for this geometry
+    std::string fused_reason;       // else why not (set when the handle is created)
     std::string err;
 };
 

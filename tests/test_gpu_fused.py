@@ -180,6 +180,20 @@ def test_fused_graph_frames_on_rotating_buffers(fw, elt_frames):
             assert rel(got, ref[k][0]) < 1e-4, k
 
 
+def test_fused_request_without_plan_refused(fw):
+    """A 64 x 64 sensor on 8 x 8 layer grids puts about 8 sensor nodes in every
+    layer cell pair, beyond the fused P^T gather's width: the handle runs the
+    plain path, and asking for the fused one fails with the reason instead of
+    silently keeping the plain path."""
+    cfg = configs.tiny(n_sub=64, n=8, levels=(1, 1), G=2, lgs=False, obstruction=0.0, D=4.0)
+    with fw.Solver(cfg, precision=fw.FP32) as S:
+        assert "path plain" in S.describe()
+        with pytest.raises(fw.FewhaError) as ei:
+            S.set_path(fw.PATH_FUSED)
+        assert ei.value.name == "GEOMETRY" and "sensor grid much finer" in str(ei.value)
+        assert "path plain" in S.describe()
+
+
 @pytest.mark.parametrize("C", [1, 2, 4, 8, 16])
 def test_fused_every_cluster_shape_matches_oracle(fw, elt_frames, C):
     """Each thread-block-cluster shape of the fused plan (row stripes of n/C
