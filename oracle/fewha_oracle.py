@@ -55,6 +55,13 @@ the design notes of the repository):
   R16 L = M with every mirror at its layer's height (Sec. 4.1): the fit is
       the bilinear sampling of layer m at mirror m's actuators (no least
       squares); the layer grid's extent also covers that actuator grid.
+  R17 Operating modes of the fit (Sec. 1, Sec. 4.3): MCAO fits every mirror
+      over every fitting direction (R10); LTAO is the case of one mirror and
+      one direction (the object); MOAO (cfg "fit_mode": "moao") gives each
+      fitting direction t its own mirror m = t, fitted in that direction
+      alone: min sum_t |P^DM_{t,t} a_t - P^lay_t phi|^2 + eps |a|^2, eps from
+      the same diagonal restricted to the pairs (t, t).  MOAO mirrors are not
+      seen by the sensors, so MOAO runs open loop.
   R13 Closed loop (Alg. 1): the mirrors' contribution to sensor g is
       Gamma_g sum_m P_{g,m} a_m, P_{g,m} the bilinear mirror m (height h_m)
       sampled at the sensor's nodes as a layer is (shift theta_g h_m, cone
@@ -296,6 +303,12 @@ class Geometry:
         self.L = len(self.layers)
         self.fit_dirs = [tuple(t) for t in cfg.get("fit_dirs", [])]
         self.dms = cfg.get("dms", [])
+        self.fit_mode = str(cfg.get("fit_mode", "mcao")).lower()   # R17
+        if self.fit_mode not in ("mcao", "moao"):
+            raise ValueError("fit_mode must be 'mcao' or 'moao'")
+        self.moao = self.fit_mode == "moao"
+        if self.moao and len(self.dms) != len(self.fit_dirs):
+            raise ValueError("MOAO needs one mirror per fitting direction")
 
         # WFS grids (R1)
         self.n_sub = [int(w["n_sub"]) for w in self.wfs]
@@ -306,8 +319,9 @@ class Geometry:
         tt = bool(cfg.get("lgs_tip_tilt_filter", False))
         self.tt = [tt and float(w.get("gs_height", 0.0)) > 0.0 for w in self.wfs]
 
-        # co-located mirrors (R16): L = M, mirror m at layer m's height
-        self.colocated = bool(self.dms) and len(self.dms) == self.L and all(
+        # co-located mirrors (R16): L = M, mirror m at layer m's height (not
+        # for MOAO, whose mirrors each belong to one direction, R17)
+        self.colocated = bool(self.dms) and not self.moao and len(self.dms) == self.L and all(
             abs(float(d["height"]) - float(l["height"])) <= 1e-6 * max(1.0, float(l["height"]))
             for d, l in zip(self.dms, self.layers))
 
@@ -640,7 +654,7 @@ class FitGeometry:
         self.dm_tab = [[self._dm(t, m) for m in range(self.M)] for t in range(len(self.dirs))]
         diag = np.zeros(self.NA)
         for t in range(len(self.dirs)):
-            for m in range(self.M):
+            for m in self.mirrors(t):
                 cy, ty, cx, tx = self.dm_tab[t][m]
                 wy = np.stack([1 - ty, ty]) ** 2
                 wx = np.stack([1 - tx, tx]) ** 2
@@ -691,12 +705,17 @@ class FitGeometry:
     def dm(self, a, m):
         return a[self.aoff[m]:self.aoff[m + 1]].reshape(self.na[m], self.na[m])
 
+    def mirrors(self, t):
+        """Mirrors fitted in direction t: all (MCAO, LTAO) or mirror t (MOAO, R17)."""
+        return [t] if self.geom.moao else list(range(self.M))
+
     def P_dm(self, a, t):
-        return sum(self._interp(self.dm(a, m), self.dm_tab[t][m]) for m in range(self.M))
+        return sum(self._interp(self.dm(a, m), self.dm_tab[t][m]) for m in self.mirrors(t))
 
     def P_dm_T(self, v, t):
-        return np.concatenate([self._interp_T(v, self.dm_tab[t][m], self.na[m]).ravel()
-                               for m in range(self.M)])
+        ms = self.mirrors(t)
+        return np.concatenate([self._interp_T(v, self.dm_tab[t][m], self.na[m]).ravel() if m in ms
+                               else np.zeros(self.na[m] * self.na[m]) for m in range(self.M)])
 
     def colocated_fit(self, phi):
         """R16: mirror m's actuators take layer m's bilinear value at their
@@ -824,6 +843,8 @@ class Reconstructor:
         if loop == "closed":
             if self.fitgeom is None:
                 raise ValueError("closed loop needs deformable mirrors")
+            if self.geom.moao:
+                raise ValueError("MOAO mirrors are not seen by the sensors: open loop only (R17)")
             s = s + self.fitgeom.dm_slopes(st.a_prev)
         b1 = rhs(self.geom, s, self.params)
         if not warm:

@@ -147,6 +147,47 @@ def maory(n_layers: int = 6, n_iter: int = 4):
             "k_rr": 10, "frames": 200, "seed": 7, "precision": "fp32"}
 
 
+def ao_mode_small(mode: str = "moao"):
+    """Small LTAO / MOAO case (Sec. 1 and 4.3 operating modes): the mcao_small
+    asterism and layers (4 LGS 16x16 on a 30-arcsec ring, 3 layers 0-8 km on
+    32^2 / 64^2 grids), open loop, 8 fitting CG steps.  LTAO: one mirror at
+    0 km (pitch 0.5 m) fitted on axis.  MOAO: three objects at (0, 0),
+    (20, 0) and (-15, 15) arcsec, each with its own mirror at 0 km."""
+    cfg = dict(mcao_small(True))
+    if mode == "ltao":
+        cfg.update(name="ltao_small", dms=[{"height": 0.0, "pitch": 0.5}], fit_dirs=[(0.0, 0.0)])
+    elif mode == "moao":
+        dirs = [(0.0, 0.0), (20.0 * ARCSEC, 0.0), (-15.0 * ARCSEC, 15.0 * ARCSEC)]
+        cfg.update(name="moao_small", dms=[{"height": 0.0, "pitch": 0.5} for _ in dirs], fit_dirs=dirs,
+                   fit_mode="moao")
+    else:
+        raise ValueError("mode must be 'ltao' or 'moao'")
+    cfg.update(gain=0.5, n_fit=8)
+    return cfg
+
+
+def maory_mode(mode: str = "moao", n_layers: int = 6, n_obj: int = 5):
+    """The MAORY-like asterism and layers (maory()) in the LTAO or MOAO
+    operating mode (Sec. 4.3 times all three): LTAO, one mirror at 0 km with
+    the 81-actuator pitch fitted on axis; MOAO, n_obj objects on the 5x5
+    evaluation grid (centre first, then the corners), one such mirror each.
+    Least-squares fit with 8 CG steps, open loop."""
+    cfg = dict(maory(n_layers, 4))
+    pitch = 39.0 / (81 - 1.5)
+    grid = fit_grid_5x5()
+    order = [12, 0, 4, 20, 24, 2, 10, 14, 22]
+    if mode == "ltao":
+        cfg.update(name="maory_ltao", dms=[{"height": 0.0, "pitch": pitch}], fit_dirs=[(0.0, 0.0)])
+    elif mode == "moao":
+        dirs = [grid[i] for i in order[:n_obj]]
+        cfg.update(name="maory_moao_%d" % n_obj, dms=[{"height": 0.0, "pitch": pitch} for _ in dirs],
+                   fit_dirs=dirs, fit_mode="moao")
+    else:
+        raise ValueError("mode must be 'ltao' or 'moao'")
+    cfg.update(n_fit=8, gain=0.5)
+    return cfg
+
+
 def c4_instance(i: int):
     """Instance i of the uneven batch: D ~ U[8, 39] m, n_s ~ U{16..84} (even),
     L ~ U{2..9} layers 0-16 km, G ~ U{3..6} LGS on a 60-arcsec ring; layer
