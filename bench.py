@@ -295,6 +295,38 @@ def bench_maory_frame(torch, fewha, dev, flush, n_frames):
     return out
 
 
+def bench_mode_frame(torch, fewha, dev, flush, n_frames, mode):
+    """The MAORY-like asterism and layers in the LTAO or MOAO operating mode
+    (Sec. 4.3 times LTAO, MOAO and MCAO): whole frame with the least-squares
+    mirror fit (8 CG steps) through one graph, device buffers, open loop."""
+    cfg = configs.maory_mode(mode)
+    pool = torch.from_numpy(slope_pool(cfg, 16)).to(dev)
+    S = fewha.Solver(cfg, precision=fewha.FP32, path=fewha.PATH_FUSED, k_rr=K_RR)
+    lay = torch.empty(S.N, dtype=torch.float32, device=dev)
+    dm = torch.empty(S.NA, dtype=torch.float32, device=dev)
+    st = S.stream
+    for k in range(5):
+        S.frame(pool[k % 16], N_ITER, warm=True, gain=cfg["gain"], n_fit=cfg["n_fit"], layers_out=lay, dm_out=dm)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_frames)]
+    for k in range(n_frames):
+        with torch.cuda.stream(st):
+            flush.fill_(float(k & 7))
+        ev[k][0].record(st)
+        S.frame(pool[k % 16], N_ITER, warm=True, gain=cfg["gain"], n_fit=cfg["n_fit"], layers_out=lay, dm_out=dm)
+        ev[k][1].record(st)
+    st.synchronize()
+    S.sync()
+    t = [a.elapsed_time(b) * 1e3 for a, b in ev]
+    what = ("one ground mirror (81^2) fitted on axis" if mode == "ltao" else
+            "%d objects on the 5x5 grid, one ground mirror (81^2) each" % len(cfg["dms"]))
+    out = {"workload": "MAORY-like asterism and layers (6 LGS 80x80 + 3 tip-tilt NGS, 6 layers 0-20 km, 128^2, "
+                       "J=4), %s, %s, 4 iterations + 8 fitting CG steps, open loop" % (mode.upper(), what),
+           "p50_us": float(np.percentile(t, 50)), "p99_us": float(np.percentile(t, 99)), "frames": n_frames,
+           "plan": S.describe()}
+    S.close()
+    return out
+
+
 def bench_batch(torch, fewha, dev, flush, n_frames):
     """64 uneven instances advanced by one fused launch per frame, against the
     same 64 instances solved one after another on the plain FP64 path."""
@@ -588,6 +620,8 @@ def main():
     if not args.no_extra:
         extra["elt_dm_frame"] = bench_elt_dm_frame(torch, fewha, dev, flush, min(K, 200))
         extra["maory_frame"] = bench_maory_frame(torch, fewha, dev, flush, min(K, 200))
+        extra["ltao_frame"] = bench_mode_frame(torch, fewha, dev, flush, min(K, 200), "ltao")
+        extra["moao_frame"] = bench_mode_frame(torch, fewha, dev, flush, min(K, 200), "moao")
         extra["batch64"] = bench_batch(torch, fewha, dev, flush, min(K, 30))
 
     # max over ranks

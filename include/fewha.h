@@ -61,6 +61,10 @@ extern "C" {
 #define FEWHA_MAX_DMS      8
 #define FEWHA_MAX_FIT_DIRS 64
 
+/* Operating modes of the mirror fit (Sec. 1, Sec. 4.3). */
+#define FEWHA_FIT_MCAO 0
+#define FEWHA_FIT_MOAO 1
+
 /* Telescope, guide stars / wavefront sensors, mirrors, fitting directions.
  * Angles in radians, heights and lengths in metres (Sec. 2.1, Sec. 4.1). */
 typedef struct {
@@ -84,6 +88,10 @@ typedef struct {
                                            /* C^{-1} removes each slope axis' mean over active  */
                                            /* subapertures (plain path only; the fused path,    */
                                            /* batches and differentiation refuse it)            */
+    int    fit_mode;                       /* FEWHA_FIT_MCAO: every mirror over every fitting   */
+                                           /* direction (one mirror, one direction: LTAO);      */
+                                           /* FEWHA_FIT_MOAO: mirror t fitted in direction t    */
+                                           /* alone (n_dm == n_fit_dir; open loop only)         */
 } fewha_geometry;
 
 /* Turbulence layers reconstructed (Sec. 2.1 layered model; Table 1 sizes). */

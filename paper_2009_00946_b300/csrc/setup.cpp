@@ -144,6 +144,10 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
     if (geo.n_dm < 0 || geo.n_dm > FEWHA_MAX_DMS) return fail(FEWHA_ERR_ARG, "n_dm out of range");
     if (geo.n_fit_dir < 0 || geo.n_fit_dir > FEWHA_MAX_FIT_DIRS) return fail(FEWHA_ERR_ARG, "n_fit_dir out of range");
     if (geo.n_dm > 0 && geo.n_fit_dir < 1) return fail(FEWHA_ERR_ARG, "mirrors need at least one fitting direction");
+    if (geo.fit_mode != FEWHA_FIT_MCAO && geo.fit_mode != FEWHA_FIT_MOAO)
+        return fail(FEWHA_ERR_ARG, "fit_mode must be FEWHA_FIT_MCAO or FEWHA_FIT_MOAO");
+    if (geo.fit_mode == FEWHA_FIT_MOAO && geo.n_dm != geo.n_fit_dir)
+        return fail(FEWHA_ERR_ARG, "MOAO needs one mirror per fitting direction");
 
     o.prec = geo.precision;
     o.D = geo.D;
@@ -154,6 +158,7 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
     o.G = geo.n_wfs;
     o.M = geo.n_dm;
     o.T = geo.n_fit_dir;
+    o.moao = geo.fit_mode == FEWHA_FIT_MOAO;
     db3_taps(o.h, o.g);
 
     // sensors
@@ -201,7 +206,7 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
     double thfit = 0.0;
     for (int t = 0; t < o.T; ++t)
         thfit = std::max(thfit, std::max(std::fabs(geo.fit_theta_x[t]), std::fabs(geo.fit_theta_y[t])));
-    o.colocated = o.M > 0 && o.M == o.L;
+    o.colocated = o.M > 0 && o.M == o.L && !o.moao;   // MOAO mirrors belong to directions
     for (int m = 0; m < o.M && o.colocated; ++m)
         o.colocated = std::fabs(geo.dm_height[m] - prof.height[m]) <= 1e-6 * std::max(1.0, prof.height[m]);
 
@@ -436,7 +441,7 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
         // closed loop (Alg. 1): the mirrors as every sensor sees them -- shift
         // theta_g h_m and, for a laser guide star, cone factor 1 - h_m/H_g;
         // unavailable (not an error) when a footprint leaves a mirror grid
-        o.closed_ok = true;
+        o.closed_ok = !o.moao;   // the sensors do not see MOAO mirrors: open loop
         o.wdtab_off.resize((size_t)o.G * o.M);
         for (int g = 0; g < o.G && o.closed_ok; ++g) {
             const HostWfs& w = o.wfs[g];
@@ -456,10 +461,11 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
             o.wdtx.clear();
             o.wdty.clear();
         }
-        // eps = 1e-6 * mean diagonal of sum_t P_DM_t^T P_DM_t
+        // eps = 1e-6 * mean diagonal of sum_t P_DM_t^T P_DM_t (MOAO: pairs t = m)
         double dsum = 0.0;
         for (int t = 0; t < o.T; ++t)
             for (int m = 0; m < o.M; ++m) {
+                if (o.moao && m != t) continue;
                 int base = o.dtab_off[t * o.M + m];
                 double sx[2] = {0, 0};
                 (void)sx;

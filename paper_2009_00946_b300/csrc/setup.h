@@ -71,6 +71,7 @@ struct HostSetup {
     std::vector<int> ctab_off, ccx;
     std::vector<double> ctx;
     bool closed_ok = false;
+    bool moao = false;                       // mirror t is fitted in direction t alone
     std::vector<int> wdtab_off, wdcx, wdcy;
     std::vector<double> wdtx, wdty;
 

@@ -408,7 +408,7 @@ __global__ void k_fit_lay(DevFit<T> F, const T* __restrict__ phi, T* __restrict_
     v[(long)t * np1 * np1 + idx] = acc;
 }
 
-// v_t(node) = sum_m bilinear(a_m) along direction t
+// v_t(node) = sum_m bilinear(a_m) along direction t (MOAO: m = t only)
 template <typename T>
 __global__ void k_fit_dm(DevFit<T> F, const T* __restrict__ a, T* __restrict__ v) {
     int t = blockIdx.y, np1 = F.np1;
@@ -416,7 +416,7 @@ __global__ void k_fit_dm(DevFit<T> F, const T* __restrict__ a, T* __restrict__ v
     if (idx >= np1 * np1) return;
     int i = idx / np1, jx = idx - i * np1;
     T acc = 0;
-    for (int m = 0; m < F.M; ++m) {
+    for (int m = F.moao ? t : 0; m < (F.moao ? t + 1 : F.M); ++m) {
         int base = F.dtab_off[t * F.M + m], n = F.dm_n[m];
         int cy = F.dcy[base + i], cx = F.dcx[base + jx];
         T ty = F.dty[base + i], tx = F.dtx[base + jx];
@@ -426,8 +426,8 @@ __global__ void k_fit_dm(DevFit<T> F, const T* __restrict__ a, T* __restrict__ v
     v[(long)t * np1 * np1 + idx] = acc;
 }
 
-// out(actuator) = sum_t (P_DM_t^T v_t)(actuator) [+ eps * x(actuator)] ;
-// optional partial dot (x, out)
+// out(actuator) = sum_t (P_DM_t^T v_t)(actuator) [+ eps * x(actuator)]
+// (MOAO: t = m only)
 template <typename T>
 __global__ void k_fit_dmT(DevFit<T> F, const T* __restrict__ v, const T* __restrict__ x, T eps, T* __restrict__ out) {
     int m = blockIdx.y, n = F.dm_n[m];
@@ -435,7 +435,7 @@ __global__ void k_fit_dmT(DevFit<T> F, const T* __restrict__ v, const T* __restr
     if (idx >= n * n) return;
     int p = idx / n, q = idx - p * n, np1 = F.np1;
     T acc = 0;
-    for (int t = 0; t < F.T_; ++t) {
+    for (int t = F.moao ? m : 0; t < (F.moao ? m + 1 : F.T_); ++t) {
         int base = F.dtab_off[t * F.M + m], gb = F.dgat_off[t * F.M + m];
         int i0 = F.dilo[gb + p], i1 = F.dihi[gb + p], j0 = F.djlo[gb + q], j1 = F.djhi[gb + q];
         const T* V = v + (long)t * np1 * np1;
@@ -796,6 +796,7 @@ class Solver : public SolverBase {
         F.L = H.L;
         F.M = H.M;
         F.T_ = H.T;
+        F.moao = H.moao ? 1 : 0;
         F.NA = (int)H.NA;
         F.np1 = H.fit_n + 1;
         F.eps = (T)H.fit_eps;
@@ -1081,6 +1082,10 @@ class Solver : public SolverBase {
     int set_loop(int c) override {
         if (c && hs.M == 0) {
             err = "the closed loop needs deformable mirrors";
+            return FEWHA_ERR_STATE;
+        }
+        if (c && hs.moao) {
+            err = "MOAO mirrors are not seen by the sensors: open loop only";
             return FEWHA_ERR_STATE;
         }
         if (c && !hs.closed_ok) {

@@ -54,6 +54,7 @@ struct DevGeo {
 template <typename T>
 struct DevFit {
     int L, M, T_, NA, np1;   // np1 = pupil nodes per side
+    int moao;                // 1: mirror t enters direction t only
     T eps;
     const int* lay_n;
     const int* lay_off;

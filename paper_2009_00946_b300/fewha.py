@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "fewha.h")
 MAX_WFS, MAX_LAYERS, MAX_DMS, MAX_FIT_DIRS = 16, 64, 8, 64
 FP32, FP64 = 0, 1
 PATH_PLAIN, PATH_FUSED = 0, 1
+FIT_MCAO, FIT_MOAO = 0, 1
 ERRORS = {0: "OK", 1: "ARG", 2: "INPUT", 3: "GEOMETRY", 4: "BREAKDOWN", 5: "TIMEOUT", 6: "LAUNCH", 7: "CUDA",
           8: "STATE"}
 VEC_C, VEC_R, VEC_B, VEC_JACOBI, VEC_ALPHA_D = 0, 1, 2, 3, 4
@@ -42,7 +43,7 @@ class Geometry(ctypes.Structure):
                 ("dm_height", ctypes.c_double * MAX_DMS), ("dm_pitch", ctypes.c_double * MAX_DMS),
                 ("n_fit_dir", ctypes.c_int), ("fit_theta_x", ctypes.c_double * MAX_FIT_DIRS),
                 ("fit_theta_y", ctypes.c_double * MAX_FIT_DIRS), ("fit_n_sub", ctypes.c_int),
-                ("precision", ctypes.c_int), ("lgs_tt_filter", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("lgs_tt_filter", ctypes.c_int), ("fit_mode", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -158,6 +159,10 @@ def structs_from_config(cfg: dict, precision: int | None = None):
         precision = FP64 if cfg.get("precision", "fp32") == "fp64" else FP32
     g.precision = precision
     g.lgs_tt_filter = 1 if cfg.get("lgs_tip_tilt_filter", False) else 0
+    mode = str(cfg.get("fit_mode", "mcao")).lower()
+    if mode not in ("mcao", "moao"):
+        raise ValueError("fit_mode must be 'mcao' or 'moao'")
+    g.fit_mode = FIT_MOAO if mode == "moao" else FIT_MCAO
     p = Profile()
     lay = cfg["layers"]
     if len(lay) > MAX_LAYERS:

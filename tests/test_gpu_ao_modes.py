@@ -1,0 +1,88 @@
+"""LTAO and MOAO fitting modes on the GPU (Sec. 1 and 4.3; the oracle's reading
+R17): the small LTAO (one ground mirror, on axis) and MOAO (three objects, one
+ground mirror each) cases over several open-loop frames against the FP64
+oracle -- FP64 plain path <= 1e-10, FP32 fused frame graph <= 1e-4 on the
+mirror commands and the layers -- and the MOAO refusals (closed loop, a
+mirror count that differs from the object count)."""
+
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import fewha_oracle as fo
+from paper_2009_00946_b300 import configs, synth
+
+pytestmark = pytest.mark.gpu
+N_FR = 6
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def fw():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2009_00946_b300 import fewha
+    return fewha
+
+
+def _reference(mode):
+    cfg = configs.ao_mode_small(mode)
+    S_in, _ = synth.frames(cfg, N_FR)
+    R = fo.Reconstructor(cfg)
+    ref = []
+    for k in range(N_FR):
+        o = R.frame(S_in[k], 4, warm=True, k_rr=10, gain=0.5, n_fit=8)
+        ref.append((o["a"].copy(), R.layers()))
+    return cfg, S_in, ref
+
+
+@pytest.fixture(scope="module", params=["ltao", "moao"])
+def mode_ref(request):
+    return (request.param,) + _reference(request.param)
+
+
+def test_fp64_plain_matches_oracle(fw, mode_ref):
+    mode, cfg, S_in, ref = mode_ref
+    with fw.Solver(cfg, precision=fw.FP64, path=fw.PATH_PLAIN, k_rr=10) as S:
+        assert S.NA == (1 if mode == "ltao" else 3) * 17 ** 2
+        for k in range(N_FR):
+            a = np.empty(S.NA)
+            lay = np.empty(S.N)
+            S.frame(S_in[k], 4, warm=True, gain=0.5, n_fit=8, layers_out=lay, dm_out=a)
+            assert rel(a, ref[k][0]) < 1e-10, (mode, k)
+            assert rel(lay, ref[k][1]) < 1e-10, (mode, k)
+
+
+def test_fp32_fused_frame_graph_matches_oracle(fw, mode_ref):
+    import torch
+    mode, cfg, S_in, ref = mode_ref
+    with fw.Solver(cfg, precision=fw.FP32, k_rr=10) as S:
+        S.set_path(fw.PATH_FUSED)
+        ds = torch.empty(S.S, dtype=torch.float32, device="cuda")
+        dl = torch.empty(S.N, dtype=torch.float32, device="cuda")
+        da = torch.empty(S.NA, dtype=torch.float32, device="cuda")
+        for k in range(N_FR):
+            with torch.cuda.stream(S.stream):
+                ds.copy_(torch.from_numpy(S_in[k].astype(np.float32)).cuda())
+            S.stream.synchronize()
+            S.frame(ds, 4, warm=True, gain=0.5, n_fit=8, layers_out=dl, dm_out=da)
+            S.sync()
+            assert rel(da.cpu().numpy(), ref[k][0]) < 1e-4, (mode, k)
+            assert rel(dl.cpu().numpy(), ref[k][1]) < 1e-4, (mode, k)
+
+
+def test_moao_refusals(fw):
+    cfg = configs.ao_mode_small("moao")
+    with fw.Solver(cfg, precision=fw.FP32) as S:
+        with pytest.raises(fw.FewhaError) as ei:
+            S.set_loop(True)
+        assert ei.value.name == "STATE"
+    bad = copy.deepcopy(cfg)
+    bad["dms"] = bad["dms"][:2]
+    with pytest.raises(fw.FewhaError) as ei:
+        fw.Solver(bad, precision=fw.FP32)
+    assert ei.value.name == "ARG"
