@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libfewha.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["solver.cu", "fused.cu", "noalloc.cu"]
+CU_SOURCES = ["solver.cu", "fused.cu", "fitcg.cu", "noalloc.cu"]
 CPP_SOURCES = ["setup.cpp", "api.cpp"]
 HEADERS = ["setup.h", "solver.h", "fused.h"]
 

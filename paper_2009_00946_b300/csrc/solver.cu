@@ -10,6 +10,7 @@
 #include <memory>
 #include <type_traits>
 
+#include "fitcg.h"
 #include "fused.h"
 #include "solver.h"
 
@@ -602,6 +603,10 @@ class Solver : public SolverBase {
     int* errw = nullptr;
     int* errw_host = nullptr;
     FusedPlan* fused = nullptr;
+    FitCgPlan* fitcg = nullptr;     // persistent FP32 fit (fused path)
+    T* fu = nullptr;                // its second search direction [NA]
+    double* fpart = nullptr;        // its partial sums [3][grid]
+    unsigned* fbar = nullptr;       // its barrier counters
     FusedBuffers fbuf{};     // state the fused plans point to (FP32 only)
     // a device-pointer frame on the fused path: the kernel reads the caller's
     // slopes and writes the caller's layers directly (no copy nodes)
@@ -639,6 +644,7 @@ class Solver : public SolverBase {
         else cudaDeviceSynchronize();
         for (int i = 0; i < 2; ++i) drop_graph(i);
         if (fused) fused_destroy(fused);
+        if (fitcg) fitcg_destroy(fitcg);
         for (void* a : allocs) cudaFree(a);
         if (pinned_in) cudaFreeHost(pinned_in);
         if (pinned_out) cudaFreeHost(pinned_out);
@@ -874,6 +880,16 @@ class Solver : public SolverBase {
             FEWHA_CUDA(cudaMemset(*v, 0, H.NA * sizeof(T)));
         }
         TRY(alloc(fv, (size_t)H.T * F.np1 * F.np1));
+        if constexpr (std::is_same<T, float>::value) {
+            // the persistent fit of the fused path (none: the plain kernels)
+            std::string ferr;
+            if (!F.colocated && (fitcg = fitcg_create(H, F, ferr)) != nullptr) {
+                TRY(alloc(fu, (size_t)H.NA));
+                TRY(alloc(fpart, fitcg_part_doubles(fitcg)));
+                TRY(alloc(fbar, 2));
+                FEWHA_CUDA(cudaMemset(fbar, 0, 2 * sizeof(unsigned)));
+            }
+        }
         return FEWHA_OK;
     }
 
@@ -988,6 +1004,13 @@ class Solver : public SolverBase {
             k_fit_colocated<T><<<dim3((amax * amax + 255) / 256, F.M), 256, 0, stream>>>(F, phi, afit);
             FEWHA_LAUNCHED();
             return gain_enqueue(gain);
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            if (fitcg && use_fused()) {
+                FitCgBuffers fb{fv, afit, fr, fp, fu, fq, acur, aprev, fpart, fbar, errw};
+                return fitcg_launch(fitcg, F, phi, fb, n_fit, (float)gain, closed ? 1 : 0, barrier_budget, stream,
+                                    err, launches);
+            }
         }
         int np1 = F.np1;
         dim3 gdir((np1 * np1 + 255) / 256, F.T_);
@@ -1281,6 +1304,7 @@ class Solver : public SolverBase {
     int decode_err(int e) {
         if (e) {
             if (fused) fused_mark_dirty(fused);
+            fitcg_mark_dirty(fitcg);
             drop_graphs();   // captured frames would skip the counter reset the next launch needs
             FEWHA_CUDA(cudaMemsetAsync(errw, 0, sizeof(int), stream));
             FEWHA_CUDA(cudaStreamSynchronize(stream));
@@ -1317,6 +1341,9 @@ class Solver : public SolverBase {
         int k = snprintf(buf, len, "precision %s, path %s, N %ld, S %ld, A %ld; ", sizeof(T) == 8 ? "fp64" : "fp32",
                          use_fused() ? "fused" : "plain", hs.N, hs.S, hs.NA);
         if (fused && k >= 0 && k < len) fused_describe(fused, buf + k, len - k);
+        const int used = (int)strnlen(buf, len);
+        if (fitcg && use_fused() && used + 1 < len)
+            snprintf(buf + used, len - used, "; fit: one launch, normal matrix %ld non-zeros", fitcg_nnz(fitcg));
         return FEWHA_OK;
     }
 
