@@ -86,3 +86,45 @@ def test_moao_refusals(fw):
     with pytest.raises(fw.FewhaError) as ei:
         fw.Solver(bad, precision=fw.FP32)
     assert ei.value.name == "ARG"
+
+
+@pytest.mark.parametrize("mode", ["mcao", "moao"])
+def test_fit_kernel_bit_deterministic(fw, mode):
+    """The one-launch fit (every CTA sums the same partials in the same order)
+    gives bit-identical mirror commands on two fresh handles."""
+    cfg = configs.mcao_small(True) if mode == "mcao" else configs.ao_mode_small("moao")
+    S_in, _ = synth.frames(cfg, 3)
+    outs = []
+    for _ in range(2):
+        with fw.Solver(cfg, precision=fw.FP32, k_rr=10) as S:
+            assert "fit: one launch" in S.describe()
+            got = []
+            for k in range(3):
+                a = np.empty(S.NA, np.float32)
+                S.frame(np.ascontiguousarray(S_in[k], dtype=np.float32), 4, warm=True, gain=0.5, n_fit=8,
+                        dm_out=a)
+                got.append(a)
+            outs.append(got)
+    for k in range(3):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+def test_fit_kernel_timeout_reported_and_recoverable(fw):
+    """Barrier budget 0: the fit kernel's grid barriers expire at once, it runs
+    to its end and TIMEOUT is returned; with the budget restored the handle's
+    next fit runs normally (its barrier counters are zeroed first)."""
+    cfg = configs.ao_mode_small("ltao")
+    S_in, _ = synth.frames(cfg, 2)
+    with fw.Solver(cfg, precision=fw.FP32, k_rr=10) as S:
+        S.set_frame(np.ascontiguousarray(S_in[0], dtype=np.float32))
+        S.solve(4, warm=True)
+        S.sync()
+        S.set_barrier_budget(0)
+        S.fit_dm(0.5, 8)   # enqueues; device errors surface at sync
+        with pytest.raises(fw.FewhaError) as ei:
+            S.sync()
+        assert ei.value.name == "TIMEOUT"
+        S.set_barrier_budget(1 << 31)
+        a = S.fit_dm(0.5, 8)   # the next launch zeroes the counters and completes
+        S.sync()
+        assert np.isfinite(a).all()
