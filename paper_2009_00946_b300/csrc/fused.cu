@@ -1551,8 +1551,41 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         smem_cap = (size_t)prop.sharedMemPerBlockOptin - fa.sharedSizeBytes - 1024;
     }
 
+    // cluster shape: clusters of 8 unless they leave layer items for a second
+    // round of the layer phase and a smaller shape runs every item at once
+    // (e.g. 35 layers: 15 clusters of 8 on this part, 37 of 4)
+    std::vector<int> order = {8, 4, 16, 2, 1};
+    if (forced_C == 0) {
+        int items = 0;
+        for (const HostSetup* h : hss) items += h->L;
+        auto clusters_for = [&](int C) {
+            const FusedKernel k = fused_kernel_for(C);
+            if (!k || 2 * C > nmin || (size_t)nmax * nmax / C * 4 * sizeof(float) > smem_cap) return 0;
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3(C * 1024);
+            q.blockDim = dim3(kFThreads);
+            q.dynamicSmemBytes = std::min(smem_cap, (size_t)nmax * nmax / C * 4 * sizeof(float));
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, k, &q) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            return std::min(n, sms / C);
+        };
+        if (items > clusters_for(8))
+            for (int C : {4, 2})
+                if (items <= clusters_for(C)) {
+                    order.erase(std::find(order.begin(), order.end(), C));
+                    order.insert(order.begin(), C);
+                    break;
+                }
+    }
     FusedPlan* best = nullptr;
-    for (int C : {8, 4, 16, 2, 1}) {
+    for (int C : order) {
         if (forced_C > 0 && C != forced_C) continue;
         if (2 * C > nmin) continue;   // stripes of at least 2 rows
         if ((size_t)nmax * nmax / C * 4 * sizeof(float) > smem_cap) continue;
