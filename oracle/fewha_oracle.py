@@ -62,6 +62,13 @@ the design notes of the repository):
       alone: min sum_t |P^DM_{t,t} a_t - P^lay_t phi|^2 + eps |a|^2, eps from
       the same diagonal restricted to the pairs (t, t).  MOAO mirrors are not
       seen by the sensors, so MOAO runs open loop.
+  R18 Modified Jacobi (Sec. 3.3 names a Jacobi preconditioner with different
+      weights for low and high frequencies, after a reference not available
+      here): J_i = omega_{j(i)} diag(M)_i, j(i) the DWT level of coefficient i
+      (1 = finest, J_l = the LL block), omega_j > 0 from cfg
+      "jacobi_level_weights" (a list over j = 1, 2, ...; levels past its end
+      take 1).  All omega_j = 1 is the plain Jacobi of R7; the weights
+      themselves are parameters, not the paper's.
   R13 Closed loop (Alg. 1): the mirrors' contribution to sensor g is
       Gamma_g sum_m P_{g,m} a_m, P_{g,m} the bilinear mirror m (height h_m)
       sampled at the sensor's nodes as a layer is (shift theta_g h_m, cone
@@ -550,6 +557,23 @@ def jacobi_diag(geom: Geometry, params: Params | None = None) -> np.ndarray:
     return diag
 
 
+def level_weights(geom: Geometry) -> np.ndarray:
+    """omega_{j(i)} for every coefficient (R18): all ones without weights."""
+    w = [float(x) for x in geom.cfg.get("jacobi_level_weights", [])]
+    if any(not (x > 0.0) for x in w):
+        raise ValueError("jacobi_level_weights must be > 0")
+    out = np.ones(geom.N)
+    for l in range(geom.L):
+        lev = level_map(geom.n[l], geom.J[l]).ravel()
+        out[geom.off[l]:geom.off[l + 1]] = [w[j - 1] if j <= len(w) else 1.0 for j in lev]
+    return out
+
+
+def preconditioner_diag(geom: Geometry, params: Params | None = None) -> np.ndarray:
+    """The Jacobi preconditioner of Alg. 2: diag(M), level-weighted (R7, R18)."""
+    return level_weights(geom) * jacobi_diag(geom, params)
+
+
 def assemble_M_dense(geom: Geometry, params: Params | None = None) -> np.ndarray:
     """Dense M, one column per unit vector (small grids only)."""
     params = geom.default_params() if params is None else params
@@ -817,7 +841,7 @@ class Reconstructor:
     def __init__(self, cfg: dict, params: Params | None = None):
         self.geom = Geometry(cfg)
         self.params = self.geom.default_params() if params is None else params
-        self.Jdiag = jacobi_diag(self.geom, self.params)
+        self.Jdiag = preconditioner_diag(self.geom, self.params)
         self.Jinv = 1.0 / self.Jdiag
         self.fitgeom = FitGeometry(self.geom) if self.geom.dms else None
         self.reset()
