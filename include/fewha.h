@@ -60,6 +60,7 @@ extern "C" {
 #define FEWHA_MAX_LAYERS   64
 #define FEWHA_MAX_DMS      8
 #define FEWHA_MAX_FIT_DIRS 64
+#define FEWHA_MAX_JACOBI_LEVELS 16
 
 /* Operating modes of the mirror fit (Sec. 1, Sec. 4.3). */
 #define FEWHA_FIT_MCAO 0
@@ -103,6 +104,10 @@ typedef struct {
     int    levels[FEWHA_MAX_LAYERS];       /* db3 levels J_l, 1 <= J_l, n_l >> J_l >= 2         */
     double r0;                             /* Fried parameter at 500 nm (m)                     */
     double alpha;                          /* regularisation weight alpha (> 0), Eq. (fewha)    */
+    double jacobi_level_weight[FEWHA_MAX_JACOBI_LEVELS];
+                                           /* modified Jacobi: the preconditioner's diagonal of */
+                                           /* a level-j coefficient (j = 1 finest) is          */
+                                           /* weight[j-1] * diag(M); 0 (the default) means 1    */
 } fewha_profile;
 
 typedef struct fewha_handle fewha_handle;

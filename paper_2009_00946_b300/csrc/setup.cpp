@@ -141,6 +141,9 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
     if (prof.n_layers < 1 || prof.n_layers > FEWHA_MAX_LAYERS) return fail(FEWHA_ERR_ARG, "n_layers out of range");
     if (geo.precision != FEWHA_FP32 && geo.precision != FEWHA_FP64) return fail(FEWHA_ERR_ARG, "precision must be FP32 or FP64");
     if (!(prof.alpha > 0) || !(prof.r0 > 0)) return fail(FEWHA_ERR_ARG, "alpha and r0 must be > 0");
+    for (int j = 0; j < FEWHA_MAX_JACOBI_LEVELS; ++j)
+        if (!(prof.jacobi_level_weight[j] >= 0.0))
+            return fail(FEWHA_ERR_ARG, "jacobi_level_weight must be >= 0 (0: unweighted)");
     if (geo.n_dm < 0 || geo.n_dm > FEWHA_MAX_DMS) return fail(FEWHA_ERR_ARG, "n_dm out of range");
     if (geo.n_fit_dir < 0 || geo.n_fit_dir > FEWHA_MAX_FIT_DIRS) return fail(FEWHA_ERR_ARG, "n_fit_dir out of range");
     if (geo.n_dm > 0 && geo.n_fit_dir < 1) return fail(FEWHA_ERR_ARG, "mirrors need at least one fitting direction");
@@ -374,6 +377,13 @@ int build_setup(const fewha_geometry& geo, const fewha_profile& prof, HostSetup&
                     }
             }
         }
+    }
+
+    // modified Jacobi: each coefficient's diagonal times its level's weight
+    for (long i = 0; i < o.N; ++i) {
+        const int j = o.level[i];
+        const double w = (j >= 1 && j <= FEWHA_MAX_JACOBI_LEVELS) ? prof.jacobi_level_weight[j - 1] : 0.0;
+        if (w > 0.0) o.Jdiag[i] *= w;
     }
 
     // ---- mirrors and fitting directions ----

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfewha.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "fewha.h")
 
-MAX_WFS, MAX_LAYERS, MAX_DMS, MAX_FIT_DIRS = 16, 64, 8, 64
+MAX_WFS, MAX_LAYERS, MAX_DMS, MAX_FIT_DIRS, MAX_JACOBI_LEVELS = 16, 64, 8, 64, 16
 FP32, FP64 = 0, 1
 PATH_PLAIN, PATH_FUSED = 0, 1
 FIT_MCAO, FIT_MOAO = 0, 1
@@ -49,7 +49,8 @@ class Geometry(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int), ("height", ctypes.c_double * MAX_LAYERS),
                 ("cn2", ctypes.c_double * MAX_LAYERS), ("n_side", ctypes.c_int * MAX_LAYERS),
-                ("levels", ctypes.c_int * MAX_LAYERS), ("r0", ctypes.c_double), ("alpha", ctypes.c_double)]
+                ("levels", ctypes.c_int * MAX_LAYERS), ("r0", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("jacobi_level_weight", ctypes.c_double * MAX_JACOBI_LEVELS)]
 
 
 _lib = None
@@ -175,6 +176,11 @@ def structs_from_config(cfg: dict, precision: int | None = None):
         p.levels[i] = int(l["levels"])
     p.r0 = cfg["r0"]
     p.alpha = cfg["alpha"]
+    jw = [float(x) for x in cfg.get("jacobi_level_weights", [])]
+    if len(jw) > MAX_JACOBI_LEVELS or any(not (x > 0.0) for x in jw):
+        raise ValueError("jacobi_level_weights: at most %d weights, each > 0" % MAX_JACOBI_LEVELS)
+    for j, x in enumerate(jw):
+        p.jacobi_level_weight[j] = x
     return g, p
 
 
