@@ -365,6 +365,14 @@ int fewha_batch_sync(fewha_batch* b);
 int fewha_batch_describe(fewha_batch* b, char* buf, int len);
 long long fewha_batch_launch_count(const fewha_batch* b);
 
+/* Autotuner of the batch's launch: builds the plan for every cluster size
+ * (8, 4, 16) and sensor-tile bound (none, 32, 24, 20, 16) that fits shared
+ * memory, times each on the current slopes (n_iter warm-started iterations
+ * from the same state, CUDA events, median of reps launches after one
+ * warm-up), keeps the fastest and restores the instances' state.  report:
+ * the timings (NUL-terminated, truncated to len).  Synchronises. */
+int fewha_batch_autotune(fewha_batch* b, int n_iter, int reps, char* report, int len);
+
 /* The paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory (a control loop that reserves all memory at start-up
  * and allows no allocation while it runs, code inside a framework that owns

@@ -371,4 +371,9 @@ long long fewha_batch_launch_count(const fewha_batch* b) {
     return b->b->launches;
 }
 
+int fewha_batch_autotune(fewha_batch* b, int n_iter, int reps, char* report, int len) {
+    if (!b) return FEWHA_ERR_ARG;
+    return bdone(b, b->b->autotune(n_iter, reps, report, len));
+}
+
 }  // extern "C"

@@ -1919,6 +1919,9 @@ class Batch : public BatchBase {
   public:
     std::vector<std::unique_ptr<Solver<float>>> inst;   // tables and state of each instance
     FusedPlan* plan = nullptr;
+    std::vector<const HostSetup*> hp;   // what a plan is built from (the autotuner rebuilds it)
+    std::vector<DevGeo<float>> Gs;
+    std::vector<FusedBuffers> fbs;
     float* s_all = nullptr;     // concatenated slopes (the instances read slices)
     float* phi_all = nullptr;   // concatenated layers (the instances write slices)
     float* pin_in = nullptr;    // staging for pageable host buffers
@@ -1986,6 +1989,108 @@ class Batch : public BatchBase {
         return st;
     }
 
+    // Plans for every cluster shape and sensor-tile bound that fit, timed on the
+    // current slopes (n_iter warm-started iterations from the same state per
+    // launch, CUDA events, median of reps); the fastest is kept and the
+    // instances' state is restored.
+    int autotune(int n_iter, int reps, char* report, int len) override {
+        if (n_iter < 1 || reps < 1 || !report || len <= 0) {
+            err = "autotune needs n_iter >= 1, reps >= 1 and a report buffer";
+            return FEWHA_ERR_ARG;
+        }
+        const long N = N_tot();
+        float* saved = nullptr;
+        if (cudaMalloc(&saved, 4 * (size_t)N * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            err = "autotune: no device memory for the saved state";
+            return FEWHA_ERR_CUDA;
+        }
+        auto copy_state = [&](bool save) {
+            for (size_t i = 0; i < inst.size(); ++i) {
+                Solver<float>& s = *inst[i];
+                const size_t n = (size_t)s.hs.N * sizeof(float);
+                float* base = saved + coeff_off[i];
+                float* vs[4] = {s.c, s.r, s.b, s.bprev};
+                for (int v = 0; v < 4; ++v) {
+                    float* slot = base + (size_t)v * N;
+                    if (cudaMemcpyAsync(save ? slot : vs[v], save ? vs[v] : slot, n, cudaMemcpyDeviceToDevice,
+                                        stream) != cudaSuccess)
+                        return false;
+                }
+            }
+            return true;
+        };
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int st = FEWHA_OK;
+        FusedPlan* best = plan;
+        float best_t = -1.f;
+        std::string rep;
+        auto time_plan = [&](FusedPlan* pl) -> float {
+            std::vector<float> ts;
+            long long dummy = 0;
+            for (int r = 0; r <= reps && st == FEWHA_OK; ++r) {
+                if (!copy_state(false)) st = FEWHA_ERR_CUDA;
+                cudaEventRecord(e0, stream);
+                if (st == FEWHA_OK) st = fused_solve(pl, nullptr, n_iter, 1, 0, barrier_budget, stream, err, dummy);
+                cudaEventRecord(e1, stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) st = FEWHA_ERR_CUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) ts.push_back(ms * 1e3f);   // the first launch warms up
+            }
+            if (st == FEWHA_OK && (st = inst[0]->check_err()) != FEWHA_OK) err = inst[0]->err;
+            if (ts.empty()) return -1.f;
+            std::sort(ts.begin(), ts.end());
+            return ts[ts.size() / 2];
+        };
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess || !copy_state(true)) {
+            cudaGetLastError();
+            st = FEWHA_ERR_CUDA;
+            err = "autotune: events or state copy";
+        }
+        if (st == FEWHA_OK) {
+            best_t = time_plan(plan);
+            char b[96];
+            snprintf(b, sizeof b, "current: %.1f us", best_t);
+            rep = b;
+        }
+        for (int C : {8, 4, 16}) {
+            for (int tile : {0, 32, 24, 20, 16}) {
+                if (st != FEWHA_OK) break;
+                std::string e;
+                FusedPlan* pl = fused_create_multi(hp, Gs, fbs, tile, e, C);
+                if (!pl) continue;
+                const float t = time_plan(pl);
+                char b[96];
+                snprintf(b, sizeof b, "; C=%d tile<=%d: %.1f us", C, tile, t);
+                rep += b;
+                if (t > 0.f && (best_t <= 0.f || t < best_t)) {
+                    if (best != plan) fused_destroy(best);
+                    best = pl;
+                    best_t = t;
+                } else {
+                    fused_destroy(pl);
+                }
+            }
+        }
+        if (best != plan) {
+            if (st == FEWHA_OK) {
+                fused_destroy(plan);
+                plan = best;
+                rep += "; chosen: the fastest above";
+            } else {
+                fused_destroy(best);
+            }
+        }
+        if (!copy_state(false)) st = st ? st : FEWHA_ERR_CUDA;
+        cudaStreamSynchronize(stream);
+        cudaFree(saved);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        snprintf(report, len, "%s", rep.c_str());
+        return st;
+    }
+
     int describe(char* buf, int len) override {
         if (!buf || len <= 0) {
             err = "null buffer";
@@ -2046,9 +2151,9 @@ BatchBase* make_batch(const std::vector<HostSetup>& hss, cudaStream_t stream, in
         status = FEWHA_ERR_CUDA;
         return nullptr;
     }
-    std::vector<const HostSetup*> hp;
-    std::vector<DevGeo<float>> Gs;
-    std::vector<FusedBuffers> fbs;
+    std::vector<const HostSetup*>& hp = B->hp;
+    std::vector<DevGeo<float>>& Gs = B->Gs;
+    std::vector<FusedBuffers>& fbs = B->fbs;
     for (size_t i = 0; i < B->inst.size(); ++i) {
         Solver<float>& s = *B->inst[i];
         FusedBuffers fb;

@@ -121,6 +121,7 @@ def lib():
         "fewha_batch_sync": (ci, [vp]),
         "fewha_batch_describe": (ci, [vp, ctypes.c_char_p, ci]),
         "fewha_batch_launch_count": (cll, [vp]),
+        "fewha_batch_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -546,3 +547,10 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(lib().fewha_batch_launch_count(self.h))
+
+    def autotune(self, n_iter: int = 4, reps: int = 3) -> str:
+        """Time the feasible cluster shapes and sensor-tile bounds on the
+        current slopes (after a frame), keep the fastest."""
+        buf = ctypes.create_string_buffer(1024)
+        self._check(lib().fewha_batch_autotune(self.h, int(n_iter), int(reps), buf, 1024))
+        return buf.value.decode()

@@ -99,6 +99,22 @@ def test_batch_device_buffers_and_state(fw, subset_frames):
         assert c.size == B.coeff_off[4] - B.coeff_off[3] and np.isfinite(c).all()
 
 
+def test_batch_autotune_keeps_state_and_parity(fw, subset_frames):
+    """The batch autotuner times the feasible cluster shapes and tile bounds on
+    the current frame, keeps the fastest and restores the state: the frames
+    that follow still match the oracle."""
+    cfgs, slopes, ref = subset_frames
+    with fw.Batch(cfgs, k_rr=10) as B:
+        out = np.empty(B.N, np.float32)
+        B.frame(B.concat_slopes([s[0] for s in slopes]), 4, warm=True, layers_out=out)
+        report = B.autotune(4, 2)
+        assert report.startswith("current:") and "C=8" in report, report
+        for k in range(1, 4):
+            B.frame(B.concat_slopes([s[k] for s in slopes]), 4, warm=True, layers_out=out)
+            for i, lay in enumerate(B.split_layers(out)):
+                assert rel(lay, ref[i][k]) < 1e-4, (SUBSET[i], k)
+
+
 def test_batch_nan_in_one_instance_reported(fw, subset_frames):
     cfgs, slopes, ref = subset_frames
     g = fo.Geometry(cfgs[2])
