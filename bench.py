@@ -162,7 +162,7 @@ def parity_vs_oracle(fewha, cfg, pool, oracle_layers):
 # DRAM bytes (read + write) of one k_fused_frame launch on this workload from
 # the committed full ncu capture, valid only for the kernel source it was
 # taken on (sha256 prefix of csrc/fused.cu); any other source reports null.
-NCU_TRAFFIC = {"fused_cu_sha256": "a286d4b1b407e6f8", "dram_bytes": 5549312,
+NCU_TRAFFIC = {"fused_cu_sha256": "2ca7ac431480232c", "dram_bytes": 5550848,
                "summary": "profiles/k_fused_frame_elt_full.md"}
 
 
@@ -178,8 +178,8 @@ def measured_peaks():
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    return 6400.0, "fallback"
+        return float(d["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6400.0, "of fallback (6.4 TB/s; no MEASURED_PEAKS.json)"
 
 
 def run_reference(args):
@@ -661,7 +661,7 @@ def main():
                      "traffic_note": "DRAM bytes per launch, ncu full capture (cold caches); the L2 keeps "
                                      "the state, so traffic is far below the algorithmic bytes",
                      "kernel": "k_fused_frame", "duration_us": t4, "algorithmic_bytes": alg,
-                     "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+                     "peak_kind": peak_kind},
         "clocks": clocks,
         "phases": phases,
         **extra,
