@@ -71,11 +71,12 @@ struct FInst {
     // compute it themselves)
     int preA_cta;
     double* preA;
-    // the same CTA publishes the finished scalars (sh[0..5] layout) in
-    // preB[2 parities][6] at the start of the layer phase and then sets
-    // flagB = k + 1 (release); the layer CTAs wait for it before the update
-    double* preB;
-    unsigned* flagB;
+    // the same CTA finishes the scalars at the start of the layer phase,
+    // writes the instance's outputs, and publishes alpha_k and beta_k as two
+    // 64-bit words {FP32 bits, tag k + 1} in pubAB[2 parities][2]: a word is
+    // read whole, so a layer CTA takes a value once its tag matches, with no
+    // flag and no release / acquire round trip (zeroed at launch start)
+    unsigned long long* pubAB;
 };
 
 struct WItem { int inst, g, i0, i1, j0, j1; };
@@ -125,6 +126,15 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Two 64-bit words, each read / written whole (relaxed, GPU scope).
+__device__ __forceinline__ void st_relaxed_v2(unsigned long long* p, unsigned long long a, unsigned long long b) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long* p, unsigned long long& a,
+                                              unsigned long long& b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -1037,6 +1047,11 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     }
 
     // ---- forward DWT ----
+    // alpha_k, beta_k from the instance's reserved CTA: the first look is
+    // issued here and lands while the transform runs
+    const bool pub = (mode == kLpIter) && I.preA_cta >= 0;
+    unsigned long long wa = 0ull, wb = 0ull;
+    if (pub && tid == 0) ld_relaxed_v2(I.pubAB + (k & 1) * 2, wa, wb);
     fmark(P, 12);
     fwd_dwt(P, s, Z, B1, B2, rem[1], rem[2], cl);
     fmark(P, 13);
@@ -1068,30 +1083,31 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             }
         };
         // sh[] holds the scalars (computed during the staging above) ...
-        if (I.preA_cta >= 0) {
+        load(tid);
+        if (pub) {
             // ... or the instance's reserved CTA publishes them (normally long
             // before this point); the wait is bounded by the barrier budget
             if (tid == 0) {
                 const unsigned want = (unsigned)k + 1u;
                 const long long t0 = clock64();
                 bool ok = true;
-                while (ld_acquire_gpu(I.flagB) < want) {
+                while ((unsigned)(wa >> 32) != want || (unsigned)(wb >> 32) != want) {
                     if (clock64() - t0 > P.budget) {
                         ok = false;
                         break;
                     }
                     __nanosleep(32);
+                    ld_relaxed_v2(I.pubAB + (k & 1) * 2, wa, wb);
                 }
-                const double* pb = I.preB + (k & 1) * 6;
-                for (int q = 0; q < 6; ++q) sh[q] = ok ? __ldcg(pb + q) : 0.0;
+                sh[0] = ok ? (double)__uint_as_float((unsigned)wa) : 0.0;
+                sh[1] = ok ? (double)__uint_as_float((unsigned)wb) : 0.0;
                 if (!ok) atomicOr(P.errw, kErrTimeout);
             }
             __syncthreads();
         }
-        load(tid);
         fmark(P, 17);
         const double alpha = sh[0], beta = sh[1];
-        if (tid == 0 && li == I.l0 && rank == 0) {
+        if (!pub && tid == 0 && li == I.l0 && rank == 0) {
             double* sw = I.scal + (k & 1) * 2;
             sw[0] = sh[2];
             sw[1] = sh[5];
@@ -1260,9 +1276,9 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     unsigned target = 0;
     const int res_inst = ((int)blockIdx.x >= P.res_first && (int)blockIdx.x < P.res_first + P.n_res)
                              ? (int)blockIdx.x - P.res_first : -1;
-    // the flag of the published scalars restarts with every launch (read only
-    // after the first grid barrier)
-    if (res_inst >= 0 && threadIdx.x == 0) *P.inst[res_inst].flagB = 0u;
+    // the published alpha / beta words restart at tag 0 with every launch
+    // (read only after the first grid barrier)
+    if (res_inst >= 0 && threadIdx.x < 4) P.inst[res_inst].pubAB[threadIdx.x] = 0ull;
     __syncthreads();
     if (P.pf && (int)threadIdx.x >= (int)blockDim.x - 32) prefetch_plan_data(P);   // the last warp
 
@@ -1314,11 +1330,22 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
                 alg2_part_b(P, RI, k, A, sh);
                 __syncwarp();
                 if (threadIdx.x == 0) {
-                    double* pb = RI.preB + (k & 1) * 6;
-                    for (int q = 0; q < 6; ++q) pb[q] = sh[q];
-                    // the release store orders this thread's stores above before the flag
-                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(RI.flagB), "r"((unsigned)k + 1u)
-                                 : "memory");
+                    // alpha_k, beta_k for the layer CTAs first (tagged words) ...
+                    const unsigned long long tag = (unsigned long long)(k + 1) << 32;
+                    st_relaxed_v2(RI.pubAB + (k & 1) * 2, tag | __float_as_uint((float)sh[0]),
+                                  tag | __float_as_uint((float)sh[1]));
+                    // ... then the instance's outputs (rho_k and the last
+                    // nonzero alpha feed part A of the next iteration here)
+                    double* sw = RI.scal + (k & 1) * 2;
+                    sw[0] = sh[2];
+                    sw[1] = sh[5];
+                    if (sh[4] != 0.0) atomicOr(P.errw, kErrBreakdown);
+                    if (RI.sc_out) {
+                        RI.sc_out[kRho] = sh[2];
+                        RI.sc_out[kMu] = sh[3];
+                        RI.sc_out[kBeta] = sh[1];
+                        RI.sc_out[kAlphaK] = sh[0];
+                    }
                 }
             }
             const int lmode = it ? kLpIter : (ph == 1 ? (P.replace ? kLpRhsRepl : kLpRhsStart) : kLpReplStart);
@@ -1783,10 +1810,9 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             // sensor fields (+8 floats: aligned copies may read up to 3 past the end)
             I.preA_cta = (i < n_res) ? tile_ctas + i : -1;
             I.preA = nullptr;
-            I.preB = nullptr;
-            I.flagB = nullptr;
+            I.pubAB = nullptr;
             ok = dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) && dalloc(pl, I.preA, 12, err) &&
-                 dalloc(pl, I.preB, 12, err) && dalloc(pl, I.flagB, 1, err) &&
+                 dalloc(pl, I.pubAB, 4, err) &&
                  dupload(pl, d_gtab, preps[i].gtab, err) && dupload(pl, d_gtab_off, preps[i].gtab_off, err);
             I.gtab = d_gtab;
             I.gtab_off = d_gtab_off;
