@@ -654,7 +654,7 @@ def main():
                        "frames": n64},
         "e2e": {"value": float(np.percentile(e2e, 50)), "unit": UNIT, "p99": float(np.percentile(e2e, 99)),
                 "h2d_bytes_per_step": S.S * 4, "d2h_bytes_per_step": S.N * 4, "frames": n_e2e,
-                "how": "fewha_frame with pinned host slopes and layers, host wall clock per frame"},
+                "how": "fewha_frame with pinned host slopes and layers (read and written by the kernel through their device mapping; the host waits on the mapped completion word), host wall clock per frame"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": fused_traffic(),

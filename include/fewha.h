@@ -209,7 +209,12 @@ int fewha_time_operator(fewha_handle* h, int op, int reps, double* us_per_applic
  * optional layers phi = W^{-1} c (layers_out), copy out.  on_device = 0: the
  * three pointers are host memory (pinned memory is used in place, pageable
  * memory is staged) and the call synchronises; on_device = 1: device
- * pointers, the call only enqueues.  The graph is captured on the first call
+ * pointers, the call only enqueues.  A host frame on the fused path without
+ * dm_out returns as soon as the kernel has set the handle's completion word
+ * (mapped pinned memory, written after every result is visible to the host):
+ * the results and the error status are final then, while the launch may
+ * still be retiring on the stream (later calls are ordered after it).  The
+ * graph is captured on the first call
  * and re-captured when n_iter, the flags or the pointers change; frames that
  * fall on the residual-replacement period use a second graph.
  * layers_out / dm_out may be NULL. */

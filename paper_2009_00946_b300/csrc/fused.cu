@@ -99,6 +99,10 @@ struct FParams {
     unsigned* bar;         // [0] grid-barrier arrivals, [1] exits (the last CTA out zeroes both)
     const float* slopes_in;   // single instance: read the frame's slopes here (and copy them to I.slopes)
     float* phi_out;           // single instance: also write the final layers here
+    // single instance, may be NULL: a word in mapped pinned host memory that
+    // the last CTA out sets to (1 << 32) | error word once every result of
+    // the launch (host-mapped layers included) is visible to the host
+    unsigned long long* done_host;
     int* errw;
     unsigned long long* trace;   // optional: [slot][cta][arrive, depart] globaltimer (ns)
     int trace_slots;
@@ -1361,11 +1365,18 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
         trace_mark(P, slot, 1);
         // every CTA has passed its last barrier read: the last one out resets
         // the counters for the next launch on this stream
-        __threadfence();
+        if (P.done_host) __threadfence_system();   // this CTA's results, host-mapped ones too
+        else __threadfence();
         if (atomicAdd(P.bar + 1, 1u) == gridDim.x - 1u) {
             P.bar[0] = 0u;
             P.bar[1] = 0u;
-            __threadfence();
+            if (P.done_host) {
+                __threadfence_system();
+                const unsigned e = (unsigned)atomicOr(P.errw, 0);
+                *(volatile unsigned long long*)P.done_host = (1ull << 32) | e;
+            } else {
+                __threadfence();
+            }
         }
     }
 }
@@ -2034,7 +2045,8 @@ int fused_repoint_node(cudaGraphExec_t exec, cudaGraphNode_t node, const float* 
 }
 
 int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int replace, long long budget,
-                cudaStream_t stream, std::string& err, long long& launches, float* layers_out) {
+                cudaStream_t stream, std::string& err, long long& launches, float* layers_out,
+                unsigned long long* done_host) {
     // a completed launch leaves the barrier counters at zero (the last CTA out
     // resets them); after a failed or first launch they are zeroed here
     cudaError_t e = cudaSuccess;
@@ -2050,6 +2062,7 @@ int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int re
     // single instance: the frame's slopes and layers may live in the caller's buffers
     P.slopes_in = (P.n_inst == 1) ? slopes : nullptr;
     P.phi_out = (P.n_inst == 1) ? layers_out : nullptr;
+    P.done_host = (P.n_inst == 1) ? done_host : nullptr;
     P.trace = nullptr;
     P.trace_slots = 0;
     P.ftrace = nullptr;

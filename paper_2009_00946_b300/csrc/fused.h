@@ -44,8 +44,12 @@ void fused_destroy(FusedPlan* plan);
 // layers_out (device, may be NULL; single-instance plans only): read the
 // frame's slopes from there instead of the handle's buffer (they are copied
 // into it as they are read), and also write the final layers there.
+// done_host (device alias of a mapped pinned host word, may be NULL; single
+// instance): set to (1 << 32) | error word by the launch once all of its
+// results are visible to the host, so a host caller can wait on the word.
 int fused_solve(FusedPlan* plan, const float* slopes, int n_iter, int warm, int replace, long long budget,
-                cudaStream_t stream, std::string& err, long long& launches, float* layers_out = nullptr);
+                cudaStream_t stream, std::string& err, long long& launches, float* layers_out = nullptr,
+                unsigned long long* done_host = nullptr);
 // After a kernel error the barrier counters may be left set: zero them first
 // at the next launch.
 void fused_mark_dirty(FusedPlan* plan);

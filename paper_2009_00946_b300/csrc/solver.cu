@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -602,6 +604,12 @@ class Solver : public SolverBase {
     double *part = nullptr, *part2 = nullptr, *sc = nullptr, *ttsums = nullptr;
     int* errw = nullptr;
     int* errw_host = nullptr;
+    // completion word of a host frame on the fused path (mapped pinned host
+    // memory; the kernel sets it to (1 << 32) | error word when the frame's
+    // results are visible, so the host waits on it instead of the stream)
+    unsigned long long* done_host = nullptr;
+    unsigned long long* done_dev = nullptr;
+    unsigned long long* ov_done = nullptr;
     FusedPlan* fused = nullptr;
     FitCgPlan* fitcg = nullptr;     // persistent FP32 fit (fused path)
     T* fu = nullptr;                // its second search direction [NA]
@@ -650,6 +658,7 @@ class Solver : public SolverBase {
         if (pinned_out) cudaFreeHost(pinned_out);
         if (pinned_dm) cudaFreeHost(pinned_dm);
         if (errw_host) cudaFreeHost(errw_host);
+        if (done_host) cudaFreeHost(done_host);
     }
 
     template <typename U>
@@ -788,6 +797,9 @@ class Solver : public SolverBase {
         TRY(alloc(sc, kNumScalars));
         TRY(alloc(errw, 1));
         FEWHA_CUDA(cudaMallocHost((void**)&errw_host, sizeof(int)));
+        FEWHA_CUDA(cudaHostAlloc((void**)&done_host, sizeof(unsigned long long), cudaHostAllocMapped));
+        *done_host = 0ull;
+        FEWHA_CUDA(cudaHostGetDevicePointer((void**)&done_dev, done_host, 0));
         for (T* v : {c, r, p, q, z, s, b, bprev, phi, tmp, y, ext}) FEWHA_CUDA(cudaMemset(v, 0, N * sizeof(T)));
         FEWHA_CUDA(cudaMemset(slopes, 0, H.S * sizeof(T)));
         FEWHA_CUDA(cudaMemset(sc, 0, kNumScalars * sizeof(double)));
@@ -1125,7 +1137,7 @@ class Solver : public SolverBase {
         if (use_fused()) {
             bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
             int st = fused_solve(fused, ov_slopes, n_iter, warm, replace ? 1 : 0, barrier_budget, stream, err,
-                                 launches, ov_layers);
+                                 launches, ov_layers, ov_done);
             if (st) return st;
             fused_layers_ready = true;
         } else {
@@ -1690,15 +1702,16 @@ class Solver : public SolverBase {
             return FEWHA_ERR_STATE;
         }
         // pinned host pointers are captured directly, pageable ones are staged
-        auto pinned = [&](const void* ptr) { return host_dev_ptr(ptr) != nullptr; };
         const void* sin = s_in;
         void* lo = lout;
         void* dm = dout;
+        void* sin_map = on_device ? nullptr : host_dev_ptr(s_in);
+        void* lo_map = (on_device || !lout) ? nullptr : host_dev_ptr(lout);
         bool stage_in = false, stage_l = false, stage_d = false;
         if (!on_device) {
-            stage_in = !pinned(s_in);
-            stage_l = lout && !pinned(lout);
-            stage_d = dout && !pinned(dout);
+            stage_in = !sin_map;
+            stage_l = lout && !lo_map;
+            stage_d = dout && !host_dev_ptr(dout);
             if (stage_in) {
                 if (!pinned_in) FEWHA_CUDA(cudaMallocHost(&pinned_in, hs.S * sizeof(T)));
                 std::memcpy(pinned_in, s_in, hs.S * sizeof(T));
@@ -1718,12 +1731,12 @@ class Solver : public SolverBase {
         // the fused kernel reads the slopes and writes the layers where they
         // are: device buffers, or pinned host buffers through their device
         // mapping (the transfers happen inside the kernel, no copy nodes)
-        auto dev_alias = [&](const void* ptr) -> void* {
-            return on_device ? const_cast<void*>(ptr) : host_dev_ptr(ptr);
-        };
-        const void* sin_dev = dev_alias(sin);
-        void* lo_dev = lo ? dev_alias(lo) : nullptr;
+        const void* sin_dev = on_device ? sin : (stage_in ? host_dev_ptr(sin) : sin_map);
+        void* lo_dev = !lo ? nullptr : on_device ? lo : (stage_l ? host_dev_ptr(lo) : lo_map);
         const bool direct = use_fused() && !closed && sin_dev && (!lo || lo_dev);
+        // a host frame that is the fused launch alone reports through the
+        // completion word (no error-word copy node, no stream wait)
+        const bool use_done = direct && !on_device && !dm && done_dev;
         bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
         int slot = replace ? 1 : 0;
         Key key;
@@ -1761,9 +1774,11 @@ class Solver : public SolverBase {
                 pol_pending = true;
                 ov_slopes = direct ? (const float*)sin_dev : nullptr;
                 ov_layers = (direct && lo) ? (float*)lo_dev : nullptr;
+                ov_done = use_done ? done_dev : nullptr;
                 st = solve_enqueue(n_iter, warm);
                 ov_slopes = nullptr;
                 ov_layers = nullptr;
+                ov_done = nullptr;
                 if (st) break;
                 if (dm && (st = fit_dev(gain, n_fit))) break;
                 if (lo && !direct && (st = layers_enqueue())) break;
@@ -1773,7 +1788,7 @@ class Solver : public SolverBase {
                     break;
                 }
                 // a host frame reads the device error word back with its results
-                if (!on_device &&
+                if (!on_device && !use_done &&
                     cudaMemcpyAsync(errw_host, errw, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess) {
                     st = FEWHA_ERR_CUDA;
                     err = "copy of the error word";
@@ -1819,11 +1834,37 @@ class Solver : public SolverBase {
             gkey[slot] = key;
             graph_launch_count[slot] = gl;
         }
+        if (use_done) {
+            *(volatile unsigned long long*)done_host = 0ull;   // before the launch that sets it
+            std::atomic_thread_fence(std::memory_order_seq_cst);
+        }
         FEWHA_CUDA(cudaGraphLaunch(gexec[slot], stream));
         launches += graph_launch_count[slot];
         frame_count += 1;
         have_frame = true;
         if (on_device) return FEWHA_OK;
+        if (use_done) {
+            // the kernel's last CTA sets the word after every result is
+            // visible here; a launch that never gets there is caught by the
+            // stream wait after the deadline
+            unsigned long long v = 0ull;
+            const auto t0 = std::chrono::steady_clock::now();
+            for (long it = 0;; ++it) {
+                v = *(volatile unsigned long long*)done_host;
+                if (v >> 32) break;
+                if ((it & 1023) == 1023 && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) break;
+            }
+            if (!(v >> 32)) {
+                FEWHA_CUDA(cudaStreamSynchronize(stream));
+                v = *(volatile unsigned long long*)done_host;
+                if (!(v >> 32)) {
+                    FEWHA_CUDA(cudaMemcpy(errw_host, errw, sizeof(int), cudaMemcpyDeviceToHost));
+                    v = (unsigned)*errw_host;
+                }
+            }
+            if (stage_l) std::memcpy(lout, pinned_out, hs.N * sizeof(T));
+            return decode_err((int)(unsigned)(v & 0xffffffffull));
+        }
         FEWHA_CUDA(cudaStreamSynchronize(stream));
         if (stage_l) std::memcpy(lout, pinned_out, hs.N * sizeof(T));
         if (stage_d) std::memcpy(dout, pinned_dm, hs.NA * sizeof(T));

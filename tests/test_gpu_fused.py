@@ -152,6 +152,50 @@ def test_fused_graph_frame_host_and_device(fw, elt_frames):
             assert np.array_equal(lb, dev_l.cpu().numpy()), k
 
 
+def test_fused_host_frames_pinned_and_completion_word(fw, elt_frames):
+    """Host frames with pinned slopes and pinned layers (the kernel reads and
+    writes them through their device mapping and reports through the mapped
+    completion word, no stream wait): bit-identical to device frames, the
+    replacement frames included, and errors come back through the word: the
+    INPUT status for non-finite slopes, TIMEOUT for expired barriers, after
+    which the handle recovers."""
+    import torch
+    cfg, S_in, ref = elt_frames
+    g = fo.Geometry(cfg)
+    with _fused(fw, cfg, k_rr=10) as A, _fused(fw, cfg, k_rr=10) as B:
+        pin_s = torch.empty(A.S, dtype=torch.float32).pin_memory()
+        pin_l = torch.empty(A.N, dtype=torch.float32).pin_memory()
+        dev_s = torch.empty(A.S, dtype=torch.float32, device="cuda")
+        dev_l = torch.empty(A.N, dtype=torch.float32, device="cuda")
+        for k in range(11):
+            pin_s.numpy()[:] = S_in[k]
+            A.frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy())
+            dev_s.copy_(torch.from_numpy(S_in[k]).cuda())
+            torch.cuda.synchronize()
+            B.frame(dev_s, 4, warm=True, layers_out=dev_l)
+            B.sync()
+            assert np.array_equal(pin_l.numpy(), dev_l.cpu().numpy()), k
+            assert rel(pin_l.numpy(), ref[k][0]) < 1e-4, k
+        state = A.get_state()
+        bad = S_in[11].copy()
+        active = int(np.flatnonzero(g.mask[2].ravel() == 1)[5])
+        bad[g.soff[2] + active] = np.inf
+        pin_s.numpy()[:] = bad
+        with pytest.raises(fw.FewhaError) as ei:
+            A.frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy())
+        assert ei.value.name == "INPUT"
+        A.set_barrier_budget(0)
+        pin_s.numpy()[:] = S_in[11]
+        A.set_state(*state, frame_count=11)
+        with pytest.raises(fw.FewhaError) as ei:
+            A.frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy())
+        assert ei.value.name == "TIMEOUT"
+        A.set_barrier_budget(1 << 31)
+        A.set_state(*state, frame_count=11)
+        A.frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy())
+        assert rel(pin_l.numpy(), ref[11][0]) < 1e-4
+
+
 def test_fused_graph_frames_on_rotating_buffers(fw, elt_frames):
     """A new slopes and layers buffer every frame, enqueued back to back (the
     cached graph is updated in place, not re-instantiated): the layers are
