@@ -217,6 +217,11 @@ __device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+
 // Dot-product partials without per-element FP64 work (FP64 runs at a small
 // fraction of the FP32 rate on this part): a*b = p + e exactly (p = fl(a*b),
 // e = fma(a, b, -p)), and the running sum is kept as an unevaluated pair
@@ -422,6 +427,7 @@ __device__ void alg2_part_b(const FParams& P, const FInst& I, int k, const ScalA
 // reads them from global memory once.
 struct CtaCache {
     int wkey, lkey, wtab;       // cached sensor item, layer item; window tables built
+    int ltkey;                  // layer item whose staging ranges and gather tables are built
     int lres, il_valid;         // the CTA has one layer item for the launch; IL holds it
     int pre_k;                  // iteration whose scalar part A is in pre (-1: none)
     double pre[6];              // rho, beta, t, alpha_{k-1}, mu part (as two floats)
@@ -433,6 +439,87 @@ struct CtaCache {
     FInst IW, IL;
 };
 
+// Descriptors of sensor item `item` into the CTA cache (one thread).
+__device__ __forceinline__ void sensor_desc(const FParams& P, int item, CtaCache* cc) {
+    cc->W = P.witems[item];
+    cc->IW = P.inst[cc->W.inst];
+    const int gg = cc->W.g;
+    cc->ns = cc->IW.wfs_n[gg];
+    cc->w_noff = cc->IW.wfs_noff[gg];
+    cc->w_soff = cc->IW.wfs_soff[gg];
+    cc->w_moff = cc->IW.wfs_moff[gg];
+    cc->w = cc->IW.wfs_w[gg];
+    cc->wkey = item;
+    cc->wtab = 0;
+}
+
+// Descriptors of layer item `li` into the CTA cache (one thread).
+__device__ __forceinline__ void layer_desc(const FParams& P, int li, CtaCache* cc) {
+    cc->LI = P.litems[li];
+    cc->IL = P.inst[cc->LI.inst];
+    const int ll = cc->LI.l;
+    cc->n = cc->IL.lay_n[ll];
+    cc->J = cc->IL.lay_J[ll];
+    cc->off = cc->IL.lay_off[ll];
+    cc->lkey = li;
+    cc->il_valid = 1;
+}
+
+// Per-sensor staging ranges of the P^T gather, [sensor][8] ints.
+__device__ int* sgi_buf() {
+    __shared__ int sgi[8 * kMaxWfsFused];
+    return sgi;
+}
+
+// Staging ranges (threads < G) and gather tables (cp.async by every thread)
+// of the cached layer item for this rank.  The caller waits for the copies
+// and synchronises the CTA before the tables or ranges are read.
+__device__ void layer_tables(const FParams& P, int rank, const CtaCache* cc, float* sm) {
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const LItem& LI = cc->LI;
+    const FInst& I = cc->IL;
+    const int n = cc->n, R = n / P.C, row0 = rank * R, G = I.G, L = I.L, l = LI.l, KG = I.KG;
+    int* sgi = sgi_buf();
+    if (tid < G) {
+        // staged rows imin..imax-1 of sensor tid are one contiguous range of
+        // the field array; it is copied from the 16-byte boundary below its
+        // start, so its data begin (start & 3) floats into its staging slot
+        auto range = [&](int g, int& a0, int& c4, int& s0) {
+            const int2 r2 = P.stg[LI.stg + rank * G + g];
+            const int np1 = I.wfs_n[g] + 1;
+            s0 = I.wfs_noff[g] + r2.x * np1;
+            const int e0 = I.wfs_noff[g] + r2.y * np1;
+            a0 = s0 & ~3;
+            c4 = (r2.y > r2.x) ? (e0 - a0 + 3) >> 2 : 0;
+        };
+        int so = 0, a0, c4, s0;
+        for (int g = 0; g < tid; ++g) {
+            range(g, a0, c4, s0);
+            so += c4 << 2;
+        }
+        range(tid, a0, c4, s0);
+        const int2 rg = P.stg[LI.stg + rank * G + tid];
+        sgi[tid * 8 + 0] = rg.x;
+        sgi[tid * 8 + 1] = rg.y;
+        sgi[tid * 8 + 2] = so + (s0 - a0);
+        sgi[tid * 8 + 3] = I.wfs_n[tid] + 1;
+        sgi[tid * 8 + 4] = a0;
+        sgi[tid * 8 + 5] = c4;
+        sgi[tid * 8 + 6] = so;
+    }
+    // compact gather tables: columns for every sensor, rows of this stripe
+    int2* xt = (int2*)(sm + P.ltab_off);        // [g][q][KG]  (j, w)
+    int2* yt = xt + P.G_max * P.n_max * KG;     // [g][row][KG] (i, w)
+    for (int e = tid; e < G * n * KG; e += NT) {
+        const int g = e / (n * KG), r = e - g * n * KG;
+        cp_async8(xt + e, I.gtab + I.gtab_off[g * L + l] + r);
+    }
+    for (int e = tid; e < G * R * KG; e += NT) {
+        const int g = e / (R * KG), r = e - g * R * KG;
+        cp_async8(yt + e, I.gtab + I.gtab_off[g * L + l] + n * KG + row0 * KG + r);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // sensor phase: P, Gamma, C^{-1}, Gamma^T on one tile of nodes
 // ---------------------------------------------------------------------------
@@ -440,21 +527,10 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                             CtaCache* cc, int k) {
     const int tid = threadIdx.x, NT = blockDim.x;
     fmark(P, mode == kModeData ? 20 : 30);
-    if (P.shared_tables && tid == 0) cc->lkey = -1;   // this phase overwrites the layer tables
+    if (P.shared_tables && tid == 0) cc->lkey = cc->ltkey = -1;   // this phase overwrites the layer tables
     if (cc->wkey != item) {
         __syncthreads();   // the previous item's data may still be in use
-        if (tid == 0) {
-            cc->W = P.witems[item];
-            cc->IW = P.inst[cc->W.inst];
-            const int gg = cc->W.g;
-            cc->ns = cc->IW.wfs_n[gg];
-            cc->w_noff = cc->IW.wfs_noff[gg];
-            cc->w_soff = cc->IW.wfs_soff[gg];
-            cc->w_moff = cc->IW.wfs_moff[gg];
-            cc->w = cc->IW.wfs_w[gg];
-            cc->wkey = item;
-            cc->wtab = 0;
-        }
+        if (tid == 0) sensor_desc(P, item, cc);
         __syncthreads();
     }
     const WItem& W = cc->W;
@@ -936,30 +1012,23 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
                             cg::cluster_group& cl, double* red, double* sh, CtaCache* cc, bool end_sync) {
     const int tid = threadIdx.x, NT = blockDim.x;
     fmark(P, 10);
-    const bool fresh = cc->lkey != li;   // else descriptors, sgi and gather tables are cached
+    const bool fresh = cc->lkey != li;   // else the descriptors are cached
     if (P.shared_tables && tid == 0) cc->wtab = 0;   // this phase overwrites the window tables
     if (fresh) {
         __syncthreads();   // the previous item's tables may still be in use
-        if (tid == 0) {
-            cc->LI = P.litems[li];
-            cc->IL = P.inst[cc->LI.inst];
-            const int ll = cc->LI.l;
-            cc->n = cc->IL.lay_n[ll];
-            cc->J = cc->IL.lay_J[ll];
-            cc->off = cc->IL.lay_off[ll];
-            cc->lkey = li;
-            cc->il_valid = 1;
-        }
+        if (tid == 0) layer_desc(P, li, cc);
         __syncthreads();
     }
-    const LItem& LI = cc->LI;
+    // staging ranges and gather tables: built at launch start for the first
+    // item (next to the first sensor phase), here for any other
+    const bool tabs = cc->ltkey != li;
     const FInst& I = cc->IL;
-    const int l = LI.l, C = P.C, rank = (int)cl.block_rank();
+    const int C = P.C, rank = (int)cl.block_rank();
     const int n = cc->n, J = cc->J, off = cc->off;
     const int R = n / C, row0 = rank * R;
-    const int G = I.G, L = I.L;
+    const int G = I.G;
     const int SF = P.stripe_floats;
-    __shared__ int sgi[8 * kMaxWfsFused];
+    const int* sgi = sgi_buf();
     float* Z = sm;
     float* B1 = sm + SF;
     float* B2 = sm + 2 * SF;
@@ -972,34 +1041,10 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
 
     // ---- P^T: gather of the sensor fields into the own rows ----
     {
-        if (fresh && tid < G) {
-            // staged rows imin..imax-1 of sensor tid are one contiguous range of
-            // the field array; it is copied from the 16-byte boundary below its
-            // start, so its data begin (start & 3) floats into its staging slot
-            auto range = [&](int g, int& a0, int& c4, int& s0) {
-                const int2 r2 = P.stg[LI.stg + rank * G + g];
-                const int np1 = I.wfs_n[g] + 1;
-                s0 = I.wfs_noff[g] + r2.x * np1;
-                const int e0 = I.wfs_noff[g] + r2.y * np1;
-                a0 = s0 & ~3;
-                c4 = (r2.y > r2.x) ? (e0 - a0 + 3) >> 2 : 0;
-            };
-            int so = 0, a0, c4, s0;
-            for (int g = 0; g < tid; ++g) {
-                range(g, a0, c4, s0);
-                so += c4 << 2;
-            }
-            range(tid, a0, c4, s0);
-            const int2 rg = P.stg[LI.stg + rank * G + tid];
-            sgi[tid * 8 + 0] = rg.x;
-            sgi[tid * 8 + 1] = rg.y;
-            sgi[tid * 8 + 2] = so + (s0 - a0);
-            sgi[tid * 8 + 3] = I.wfs_n[tid] + 1;
-            sgi[tid * 8 + 4] = a0;
-            sgi[tid * 8 + 5] = c4;
-            sgi[tid * 8 + 6] = so;
+        if (tabs) {
+            layer_tables(P, rank, cc, sm);
+            __syncthreads();   // the staging ranges
         }
-        if (fresh) __syncthreads();
         for (int g = 0; g < G; ++g) {
             const int c4 = sgi[g * 8 + 5];
             const float* src = I.psi + sgi[g * 8 + 4];
@@ -1030,16 +1075,8 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             }
             alg2_part_b(P, I, k, A, sh);
         }
-        cp_async_wait_all();
-        // compact gather tables: columns for every sensor, rows of this stripe
-        for (int e = tid; fresh && e < G * n * KG; e += NT) {
-            const int g = e / (n * KG), r = e - g * n * KG;
-            xt[e] = __ldg(I.gtab + I.gtab_off[g * L + l] + r);
-        }
-        for (int e = tid; fresh && e < G * R * KG; e += NT) {
-            const int g = e / (R * KG), r = e - g * R * KG;
-            yt[e] = __ldg(I.gtab + I.gtab_off[g * L + l] + n * KG + row0 * KG + r);
-        }
+        cp_async_wait_all();   // the fields (and gather tables, if just issued)
+        if (tabs && tid == 0) cc->ltkey = li;
         __syncthreads();
         fmark(P, 11);
         switch (KG) {   // the gather loops unrolled over the table's real width
@@ -1271,7 +1308,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     if (threadIdx.x == 0) {
         s_abort = 0;
         *fmark_counter() = 0;
-        cc.wkey = cc.lkey = -1;
+        cc.wkey = cc.lkey = cc.ltkey = -1;
         cc.wtab = 0;
         cc.lres = (l_hi - l_lo == 1) ? 1 : 0;
         cc.il_valid = 0;
@@ -1285,6 +1322,20 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     if (res_inst >= 0 && threadIdx.x < 4) P.inst[res_inst].pubAB[threadIdx.x] = 0ull;
     __syncthreads();
     if (P.pf && (int)threadIdx.x >= (int)blockDim.x - 32) prefetch_plan_data(P);   // the last warp
+    // Descriptors of the CTA's first sensor and layer items, fetched side by
+    // side (two dependent chains at once, not one at the top of each phase),
+    // then the first layer item's staging ranges and gather tables, whose
+    // copies land while the first sensor phase runs (separate shared memory)
+    if (!P.shared_tables) {
+        if (threadIdx.x == 0 && w_lo < w_hi) sensor_desc(P, P.wsched[w_lo], &cc);
+        if (threadIdx.x == 32 && l_lo < l_hi) layer_desc(P, P.lsched[l_lo], &cc);
+        __syncthreads();
+        if (l_lo < l_hi) {
+            layer_tables(P, (int)cl.block_rank(), &cc, sm);
+            if (threadIdx.x == 0) cc.ltkey = cc.lkey;
+        }
+        __syncthreads();
+    }
 
     // One loop over the phases of the frame, each phase function called from
     // a single site (one copy of its code, warm in the instruction caches and
