@@ -162,7 +162,7 @@ def parity_vs_oracle(fewha, cfg, pool, oracle_layers):
 # DRAM bytes (read + write) of one k_fused_frame launch on this workload from
 # the committed full ncu capture, valid only for the kernel source it was
 # taken on (sha256 prefix of csrc/fused.cu); any other source reports null.
-NCU_TRAFFIC = {"fused_cu_sha256": "2ca7ac431480232c", "dram_bytes": 5550848,
+NCU_TRAFFIC = {"fused_cu_sha256": "6a19b73df3f994f9", "dram_bytes": 5561344,
                "summary": "profiles/k_fused_frame_elt_full.md"}
 
 
