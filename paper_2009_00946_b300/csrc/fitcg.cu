@@ -166,38 +166,78 @@ __device__ double sum_partials(const FitCgParams& P, int s, double* sh) {
     return r;
 }
 
-// sum_l bilinear(phi_l) along direction t at pupil node (i, jx)
-__device__ __forceinline__ float lay_sample(const DevFit<float>& F, const float* phi, int t, int i, int jx) {
+// Layers per round of lay_sample: the table and layer loads of kFitLU layers
+// are in flight together (a 35-layer sample is 5 rounds of two dependent
+// loads, not 35 of three); the sum still runs over l in order.
+constexpr int kFitLU = 8;
+// direction-layer table offsets, layer sides and offsets staged in shared
+// memory when T * L fits
+constexpr int kFitTabMax = 2048;
+
+// sum_l bilinear(phi_l) along direction t at pupil node (i, jx); toff, ln,
+// loff: the direction-layer table offsets [T][L], layer sides and offsets
+__device__ __forceinline__ float lay_sample(const DevFit<float>& F, const float* phi, const int* toff, const int* ln,
+                                            const int* loff, int t, int i, int jx) {
     float acc = 0.f;
-    for (int l = 0; l < F.L; ++l) {
-        const int base = F.ftab_off[t * F.L + l], n = F.lay_n[l];
-        const int cy = __ldg(F.fcy + base + i), cx = __ldg(F.fcx + base + jx);
-        const float ty = __ldg(F.fty + base + i), tx = __ldg(F.ftx + base + jx);
-        const float* f = phi + F.lay_off[l] + (long)cy * n + cx;
-        acc += (1 - ty) * ((1 - tx) * f[0] + tx * f[1]) + ty * ((1 - tx) * f[n] + tx * f[n + 1]);
+    for (int l0 = 0; l0 < F.L; l0 += kFitLU) {
+        int cy[kFitLU], cx[kFitLU], n[kFitLU], o[kFitLU];
+        float ty[kFitLU], tx[kFitLU], v[kFitLU][4];
+#pragma unroll
+        for (int u = 0; u < kFitLU; ++u) {
+            const int l = l0 + u;
+            if (l < F.L) {
+                const int base = toff[t * F.L + l];
+                n[u] = ln[l];
+                o[u] = loff[l];
+                cy[u] = __ldg(F.fcy + base + i);
+                cx[u] = __ldg(F.fcx + base + jx);
+                ty[u] = __ldg(F.fty + base + i);
+                tx[u] = __ldg(F.ftx + base + jx);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kFitLU; ++u) {
+            if (l0 + u < F.L) {
+                const float* f = phi + o[u] + (long)cy[u] * n[u] + cx[u];
+                v[u][0] = f[0];
+                v[u][1] = f[1];
+                v[u][2] = f[n[u]];
+                v[u][3] = f[n[u] + 1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kFitLU; ++u)
+            if (l0 + u < F.L)
+                acc += (1 - ty[u]) * ((1 - tx[u]) * v[u][0] + tx[u] * v[u][1]) +
+                       ty[u] * ((1 - tx[u]) * v[u][2] + tx[u] * v[u][3]);
     }
     return acc;
 }
 
-// A lane's share of row i of a CSR matrix times x: entries sub, sub + gsz, ...,
-// four per round with their loads issued before the adds.
+// Entries of a row a lane takes per round of a sparse product: all their
+// index, value and gathered loads are issued before the adds, so a row of up
+// to kFitU * 32 entries (the 35-layer fit averages 183) costs two dependent
+// L2 round trips.
+constexpr int kFitU = 8;
+
+// A lane's share of row i of a CSR matrix times x: entries sub, sub + gsz, ...
 __device__ __forceinline__ float csr_dot(const int* row, const int* col, const float* val, const float* x, int i,
                                          int sub, int gsz) {
     float s = 0.f;
     const int j1 = row[i + 1];
-    for (int j0 = row[i] + sub; j0 < j1; j0 += 4 * gsz) {
-        int c[4];
-        float a[4], xv[4];
+    for (int j0 = row[i] + sub; j0 < j1; j0 += kFitU * gsz) {
+        int c[kFitU];
+        float a[kFitU], xv[kFitU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kFitU; ++u) {
             const int j = j0 + u * gsz;
             c[u] = j < j1 ? __ldg(col + j) : 0;
             a[u] = j < j1 ? __ldg(val + j) : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) xv[u] = x[c[u]];
+        for (int u = 0; u < kFitU; ++u) xv[u] = x[c[u]];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s += a[u] * xv[u];
+        for (int u = 0; u < kFitU; ++u) s += a[u] * xv[u];
     }
     return s;
 }
@@ -227,9 +267,22 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_cg(const __grid_constant
     float beta = 0.f;
     if (P.n_fit > 0) {
         // 1: the layers at every pupil node of every direction
+        __shared__ int s_toff[kFitTabMax], s_ln[64], s_loff[64];
+        const bool staged = F.T_ * F.L <= kFitTabMax && F.L <= 64;
+        if (staged) {
+            for (int e = threadIdx.x; e < F.T_ * F.L; e += blockDim.x) s_toff[e] = __ldg(F.ftab_off + e);
+            for (int e = threadIdx.x; e < F.L; e += blockDim.x) {
+                s_ln[e] = __ldg(F.lay_n + e);
+                s_loff[e] = __ldg(F.lay_off + e);
+            }
+        }
+        __syncthreads();
+        const int* toff = staged ? s_toff : F.ftab_off;
+        const int* lns = staged ? s_ln : F.lay_n;
+        const int* loff = staged ? s_loff : F.lay_off;
         for (int e = gtid; e < Tn; e += nthr) {
             const int t = e / nn, idx = e - t * nn, i = idx / np1, jx = idx - i * np1;
-            B.v[e] = lay_sample(F, P.phi, t, i, jx);
+            B.v[e] = lay_sample(F, P.phi, toff, lns, loff, t, i, jx);
         }
         fit_barrier(P, target, &s_abort);
         // 2: r = sum_t P^DM_t^T v_t - A x, p = r (groups of lanes per row, as in A)
@@ -266,24 +319,24 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_cg(const __grid_constant
             const int i = i0 + (lane >> lg);
             float s = 0.f;
             if (i < NA) {
-                // four entries per round: their loads issued before the adds
+                // kFitU entries per round: their loads issued before the adds
                 const int j1 = P.row[i + 1];
-                for (int j0 = P.row[i] + sub; j0 < j1; j0 += 4 * gsz) {
-                    int c[4];
-                    float a[4], rv[4], pv[4];
+                for (int j0 = P.row[i] + sub; j0 < j1; j0 += kFitU * gsz) {
+                    int c[kFitU];
+                    float a[kFitU], rv[kFitU], pv[kFitU];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < kFitU; ++u) {
                         const int j = j0 + u * gsz;
                         c[u] = j < j1 ? __ldg(P.col + j) : 0;
                         a[u] = j < j1 ? __ldg(P.val + j) : 0.f;
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < kFitU; ++u) {
                         rv[u] = B.r[c[u]];
                         pv[u] = pc[c[u]];
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) s += a[u] * (rv[u] + fb * pv[u]);
+                    for (int u = 0; u < kFitU; ++u) s += a[u] * (rv[u] + fb * pv[u]);
                 }
             }
             s = group_sum(s, lg);
