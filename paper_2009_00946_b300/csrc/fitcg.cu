@@ -48,6 +48,7 @@ struct FitCgParams {
     const int* pcol;
     const float* pval;
     int gp_log;        // P^T rows are reduced by groups of 2^gp_log lanes
+    long long nnz, pnnz;   // entries of A and of sum_t P^DM_t^T
     long long budget;
     float gain;
     int closed, n_fit, gs_log;   // rows of A are reduced by groups of 2^gs_log lanes
@@ -266,6 +267,22 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_cg(const __grid_constant
     double rr = 0.0;
     float beta = 0.f;
     if (P.n_fit > 0) {
+        // the matrices of step 2 and the CG steps (static; evicted when other
+        // work ran since the last frame) are requested into L2 first, so they
+        // arrive while the layers are sampled: each CTA takes a share of the
+        // 128-byte lines of each array
+        {
+            const char* arr[6] = {(const char*)P.col, (const char*)P.val, (const char*)P.pcol,
+                                  (const char*)P.pval, (const char*)P.row, (const char*)P.prow};
+            const long long bytes[6] = {P.nnz * 4, P.nnz * 4, P.pnnz * 4, P.pnnz * 4, (long long)(NA + 1) * 4,
+                                        (long long)(NA + 1) * 4};
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                const long long lines = (bytes[a] + 127) >> 7;
+                for (long long q = gtid; q < lines; q += nthr)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(arr[a] + (q << 7)));
+            }
+        }
         // 1: the layers at every pupil node of every direction
         __shared__ int s_toff[kFitTabMax], s_ln[64], s_loff[64];
         const bool staged = F.T_ * F.L <= kFitTabMax && F.L <= 64;
@@ -427,7 +444,7 @@ Factor make_factor(const int* cm, const double* tm, int na_m, const int* cn, con
 
 struct FitCgPlan {
     int grid = 0, gs_log = 5, gp_log = 5;
-    long nnz = 0;
+    long nnz = 0, pnnz = 0;
     bool dirty = true;
     int* row = nullptr;
     int* col = nullptr;
@@ -541,6 +558,7 @@ FitCgPlan* fitcg_create(const HostSetup& hs, const DevFit<float>& F, std::string
     auto* pl = new FitCgPlan();
     pl->grid = std::min(sms, 256);   // the partial sums are read 8 per lane
     pl->nnz = (long)col.size();
+    pl->pnnz = (long)pcol.size();
     auto group_log = [&](double avg) { return avg > 48 ? 5 : avg > 24 ? 4 : avg > 12 ? 3 : 2; };
     pl->gs_log = group_log((double)pl->nnz / (double)hs.NA);
     pl->gp_log = group_log((double)pcol.size() / (double)hs.NA);
@@ -598,6 +616,8 @@ int fitcg_launch(FitCgPlan* pl, const DevFit<float>& F, const float* phi, const 
     P.pcol = pl->pcol;
     P.pval = pl->pval;
     P.gp_log = pl->gp_log;
+    P.nnz = pl->nnz;
+    P.pnnz = pl->pnnz;
     P.budget = budget;
     P.gain = gain;
     P.closed = closed;
