@@ -331,14 +331,45 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_cg(const __grid_constant
         const float fb = (float)beta;
         Pair pq_acc;
         // a warp takes 32 / 2^lg consecutive rows per pass (the trip count is the
-        // same for the whole warp, so every shuffle has all its lanes)
-        for (int i0 = gwarp << (5 - lg); i0 < NA; i0 += nwarps << (5 - lg)) {
+        // same for the whole warp, so every shuffle has all its lanes).  Software
+        // pipeline: the gathers of the current rows' first round are issued,
+        // then the next rows' bounds and first round of entries are loaded
+        // while those gathers are in flight
+        const int stride = nwarps << (5 - lg);
+        int nb = 0, ne = 0, nc[kFitU];
+        float na[kFitU];
+        auto first_round = [&](int i0x) {
+            const int ix = i0x + (lane >> lg);
+            nb = ne = 0;
+            if (i0x < NA && ix < NA) {
+                nb = __ldg(P.row + ix) + sub;
+                ne = __ldg(P.row + ix + 1);
+            }
+#pragma unroll
+            for (int u = 0; u < kFitU; ++u) {
+                const int j = nb + u * gsz;
+                nc[u] = j < ne ? __ldg(P.col + j) : 0;
+                na[u] = j < ne ? __ldg(P.val + j) : 0.f;
+            }
+        };
+        first_round(gwarp << (5 - lg));
+        for (int i0 = gwarp << (5 - lg); i0 < NA; i0 += stride) {
             const int i = i0 + (lane >> lg);
             float s = 0.f;
+            const int j0f = nb, j1 = ne;
+            float a0[kFitU], rv0[kFitU], pv0[kFitU];
+#pragma unroll
+            for (int u = 0; u < kFitU; ++u) {   // index 0 (a valid entry, weight 0) past the row
+                a0[u] = na[u];
+                rv0[u] = B.r[nc[u]];
+                pv0[u] = pc[nc[u]];
+            }
+            first_round(i0 + stride);
             if (i < NA) {
-                // kFitU entries per round: their loads issued before the adds
-                const int j1 = P.row[i + 1];
-                for (int j0 = P.row[i] + sub; j0 < j1; j0 += kFitU * gsz) {
+#pragma unroll
+                for (int u = 0; u < kFitU; ++u) s += a0[u] * (rv0[u] + fb * pv0[u]);
+                // rows longer than one round: the rest, round by round
+                for (int j0 = j0f + kFitU * gsz; j0 < j1; j0 += kFitU * gsz) {
                     int c[kFitU];
                     float a[kFitU], rv[kFitU], pv[kFitU];
 #pragma unroll
