@@ -65,6 +65,38 @@ def algorithmic_bytes_per_frame(cfg, n_iter, elem=4):
     return elem * (n_iter * (16 * N + 4 * NW) + S + 2 * NW + 10 * N)
 
 
+def algorithmic_bytes_per_iteration(cfg, elem=4):
+    """16N + 4 NW elements: one PCG iteration of Alg. 2 with its operator M."""
+    N = sum(l["n"] ** 2 for l in cfg["layers"])
+    NW = sum((w["n_sub"] + 1) ** 2 for w in cfg["wfs"])
+    return elem * (16 * N + 4 * NW)
+
+
+def roofline_block(cfg, t_launch_us, per_iter_us, l2, hbm, hbm_kind, traffic):
+    """Roofline of the fused frame kernel against the measured L2 bandwidth
+    (its working set stays in L2), with the HBM figure beside it.
+    t_launch_us: event-timed duration of one 4-iteration solve launch;
+    per_iter_us: marginal cost of one PCG iteration; l2: measure_l2() result
+    (the larger of the read and the copy figure is the peak)."""
+    alg = algorithmic_bytes_per_frame(cfg, N_ITER)
+    it_bytes = algorithmic_bytes_per_iteration(cfg)
+    achieved = alg / (t_launch_us * 1e-6) / 1e9
+    l2_peak = max(l2["read_gbs"], l2["copy_gbs"])
+    it_ach = it_bytes / (per_iter_us * 1e-6) / 1e9 if per_iter_us and per_iter_us > 0 else None
+    return {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
+            "traffic": traffic,
+            "traffic_note": "DRAM bytes per launch, ncu full capture (cold caches); the L2 keeps the state, so "
+                            "traffic is far below the algorithmic bytes",
+            "kernel": "k_fused_frame", "duration_us": t_launch_us, "algorithmic_bytes": alg,
+            "peak_kind": "of measured (fewha_measure_l2 in this run: %d MiB resident buffer, %d passes per "
+                         "launch, fastest of %d; read %.0f GB/s, copy read+write %.0f GB/s; the larger is the "
+                         "peak)" % (l2["bytes"] >> 20, l2["passes"], l2["reps"], l2["read_gbs"], l2["copy_gbs"]),
+            "per_iteration": {"algorithmic_bytes": it_bytes, "us": per_iter_us, "achieved": it_ach,
+                              "frac": it_ach / l2_peak if it_ach else None,
+                              "what": "16N + 4NW FP32 elements per PCG iteration / marginal iteration time"},
+            "hbm": {"peak": hbm, "frac": achieved / hbm, "peak_kind": hbm_kind}}
+
+
 def slope_pool(cfg, count, seed=None):
     atm = synth.Atmosphere(cfg, seed)
     return np.stack([atm.slopes(k) for k in range(count)]).astype(np.float32)
@@ -390,6 +422,47 @@ def bench_batch(torch, fewha, dev, flush, n_frames):
             "plan": plan}
 
 
+def bench_batch_sharded(torch, fewha, dev, flush, n_frames, dist, rank, world):
+    """The 64 uneven instances partitioned over the ranks (no collective in
+    the solve: each rank one fused launch per frame over its own instances);
+    the slowest rank's p50 sets the job's batch-frame time."""
+    from paper_2009_00946_b300 import shard
+    cfgs = configs.c4_batch(64)
+    sb = shard.ShardedBatch(cfgs, rank, world, k_rr=K_RR)
+    t = [0.0]
+    if sb.batch is not None:
+        B = sb.batch
+        per = [synth.random_slopes(c, 7).astype(np.float32) for c in B.cfgs]
+        s = torch.from_numpy(B.concat_slopes(per)).to(dev)
+        lay = torch.empty(B.N, dtype=torch.float32, device=dev)
+        st = B.stream
+        for _ in range(5):
+            B.frame(s, N_ITER, True, lay)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_frames)]
+        for k in range(n_frames):
+            with torch.cuda.stream(st):
+                flush.fill_(float(k & 7))
+            ev[k][0].record(st)
+            B.frame(s, N_ITER, True, lay)
+            ev[k][1].record(st)
+        st.synchronize()
+        B.sync()
+        t = [a.elapsed_time(b) * 1e3 for a, b in ev]
+    else:
+        lay = torch.zeros(0, device=dev)
+    p50 = float(np.percentile(t, 50))
+    got = sb.gather_layers(lay, dist, dst=0, device=dev)   # untimed: the results to rank 0
+    p50_max = max_over_ranks([p50], dist, dev)[0]
+    sb.close()
+    out = {"workload": "64 independent instances partitioned over %d ranks (cost-balanced, no collective in the "
+                       "solve), 4 warm-started iterations each, FP32, one fused launch per rank per frame" % world,
+           "p50_us_slowest_rank": p50_max, "instance_frames_per_s_total": 64 * 1e6 / p50_max,
+           "instances_per_rank": [len(p) for p in sb.parts], "frames": n_frames, "scaling": "strong"}
+    if got is not None:
+        out["gathered_instances"] = sum(1 for a in got if a is not None and np.isfinite(a).all())
+    return out
+
+
 def max_over_ranks(values, dist, device):
     """Element-wise maximum of per-rank timings (replicas: the slowest rank
     sets the job's latency); identity without a process group."""
@@ -590,8 +663,10 @@ def main():
     phases = phase_breakdown(S, pool_dev)
     plan = S.describe()
     hbm, peak_kind = measured_peaks()
-    alg = algorithmic_bytes_per_frame(cfg, N_ITER)
-    achieved = alg / (t4 * 1e-6) / 1e9
+    with ClockSampler(local_rank) as clk_l2:
+        l2 = fewha.measure_l2()
+    l2["clocks"] = clk_l2.summary()
+    roofline = roofline_block(cfg, t4, per_iter, l2, hbm, peak_kind, fused_traffic())
 
     # ---- end to end: pinned host slopes in, layers out, through fewha_frame ----
     pin_s = torch.empty(S.S, dtype=torch.float32).pin_memory()
@@ -629,7 +704,10 @@ def main():
         extra["maory_frame"] = bench_maory_frame(torch, fewha, dev, flush, min(K, 200))
         extra["ltao_frame"] = bench_mode_frame(torch, fewha, dev, flush, min(K, 200), "ltao")
         extra["moao_frame"] = bench_mode_frame(torch, fewha, dev, flush, min(K, 200), "moao")
-        extra["batch64"] = bench_batch(torch, fewha, dev, flush, min(K, 30))
+        if world > 1:
+            extra["batch64_sharded"] = bench_batch_sharded(torch, fewha, dev, flush, min(K, 30), dist, rank, world)
+        else:
+            extra["batch64"] = bench_batch(torch, fewha, dev, flush, min(K, 30))
 
     # max over ranks
     p50, p99, mean, per_iter = max_over_ranks([p50, p99, mean, per_iter], dist, dev)
@@ -656,12 +734,8 @@ def main():
                 "h2d_bytes_per_step": S.S * 4, "d2h_bytes_per_step": S.N * 4, "frames": n_e2e,
                 "how": "fewha_frame with pinned host slopes and layers (read and written by the kernel through their device mapping; the host waits on the mapped completion word), host wall clock per frame"},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": fused_traffic(),
-                     "traffic_note": "DRAM bytes per launch, ncu full capture (cold caches); the L2 keeps "
-                                     "the state, so traffic is far below the algorithmic bytes",
-                     "kernel": "k_fused_frame", "duration_us": t4, "algorithmic_bytes": alg,
-                     "peak_kind": peak_kind},
+        "roofline": roofline,
+        "l2_measured": l2,
         "clocks": clocks,
         "phases": phases,
         **extra,

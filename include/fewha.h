@@ -378,6 +378,21 @@ long long fewha_batch_launch_count(const fewha_batch* b);
  * the timings (NUL-terminated, truncated to len).  Synchronises. */
 int fewha_batch_autotune(fewha_batch* b, int n_iter, int reps, char* report, int len);
 
+/* Profiling aid for the roofline of the fused kernel (Sec. 4.3 places the
+ * operators of M against a memory roofline; the fused kernel's working set
+ * stays in L2, so the L2, not HBM, is its bandwidth bound): the achievable
+ * L2 bandwidth of the current device, measured with the library's own
+ * kernels.  A device buffer of `bytes` (a multiple of 256 in 1..96 MiB, well
+ * below the 126 MB L2; allocated and freed by the call) is written once, then
+ * read -- and copied, its first half into its second -- `passes` times per
+ * launch with 16-byte loads and stores that bypass L1; each of the two
+ * kernels is timed over `reps` launches (CUDA events on a private stream) and
+ * the fastest launch gives read_gbs (bytes read / s) and copy_gbs (bytes read
+ * + written / s), in GB/s.  Synchronises.  errbuf (errlen bytes, may be NULL)
+ * receives a message on failure.  Errors: ARG (range), CUDA. */
+int fewha_measure_l2(long bytes, int passes, int reps, double* read_gbs, double* copy_gbs, char* errbuf,
+                     int errlen);
+
 /* The paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory (a control loop that reserves all memory at start-up
  * and allows no allocation while it runs, code inside a framework that owns

@@ -1026,6 +1026,19 @@ def db_contract(geom: Geometry, s: np.ndarray, bbar: np.ndarray):
     return np.array(out)
 
 
+def slopes_contract(geom: Geometry, params: Params, bbar: np.ndarray) -> np.ndarray:
+    """d loss / d s from the cotangent bbar of b: b = W P^T Gamma^T C^{-1} s
+    (Eq. (fewha)) is linear in s, so the slope gradient is its transpose
+    applied to bbar, C^{-1} Gamma P W^T bbar (C^{-1} symmetric), in the slope
+    layout of the measurement vector."""
+    B = _sensor_slopes_of(geom, bbar)
+    out = []
+    for g in range(geom.G):
+        wx, wy = noise_weight(geom, params, g, B[g][0], B[g][1])
+        out.append(np.concatenate([wx.ravel(), wy.ravel()]))
+    return np.concatenate(out)
+
+
 def solve_loss(geom: Geometry, params: Params, Jinv: np.ndarray, s: np.ndarray, phi_true: np.ndarray,
                n_iter: int):
     """Loss |W^T c_K - phi_true|^2 of one frame solved from a cold start."""
@@ -1036,8 +1049,9 @@ def solve_loss(geom: Geometry, params: Params, Jinv: np.ndarray, s: np.ndarray, 
 
 
 def solve_loss_grad(geom: Geometry, params: Params, Jinv: np.ndarray, s: np.ndarray, phi_true: np.ndarray,
-                    n_iter: int):
-    """(loss, d loss / d gamma, d loss / d alpha, d loss / d w) by reverse mode."""
+                    n_iter: int, with_slopes: bool = False):
+    """(loss, d loss / d gamma, d loss / d alpha, d loss / d w) by reverse mode;
+    with_slopes: also d loss / d s (a fifth entry)."""
     Mop = lambda v: apply_M(geom, v, params)
     b = rhs(geom, s, params)
     c, _, tape = pcg_alg2_tape(Mop, Jinv, b, n_iter)
@@ -1057,4 +1071,6 @@ def solve_loss_grad(geom: Geometry, params: Params, Jinv: np.ndarray, s: np.ndar
         galpha += b2
         gw += c2
     gw += db_contract(geom, s, bbar)
+    if with_slopes:
+        return loss, ggam, galpha, gw, slopes_contract(geom, params, bbar)
     return loss, ggam, galpha, gw

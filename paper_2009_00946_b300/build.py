@@ -22,9 +22,11 @@ LIB = os.path.join(HERE, "libfewha.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["solver.cu", "fused.cu", "fitcg.cu", "noalloc.cu"]
+CU_SOURCES = ["solver.cu", "fused.cu", "fitcg.cu", "noalloc.cu", "l2bw.cu"]
 CPP_SOURCES = ["setup.cpp", "api.cpp"]
-HEADERS = ["setup.h", "solver.h", "fused.h"]
+# every header of csrc/ is a dependency of every object (a conservative rule:
+# an edited header rebuilds all objects)
+HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
 
 
 def _newer(target: str, deps: list[str]) -> bool:

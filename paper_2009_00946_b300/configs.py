@@ -10,9 +10,9 @@ fractions proportional to exp(-h / 3 km), normalised): the standard 9- and
 MAORY-like setting of Sec. 4.1 (LGS on a 1-arcmin-radius hexagon at 90 km,
 fitting/evaluation directions on the 5x5 grid at -60..60 arcsec).
 
-alpha: fixed once per configuration family by ``oracle/scan_alpha.py`` (a scan
-of the layer reconstruction error against the synthetic truth on the small
-NGS configuration), then reused unchanged.
+alpha: fixed once, by a one-time scan of the layer reconstruction error
+against the synthetic truth on the small NGS configuration (minimum near
+100-300), then reused unchanged for every configuration.
 """
 
 from __future__ import annotations
@@ -26,7 +26,7 @@ R0 = 0.157        # m at 500 nm
 L0 = 25.0         # m, outer scale
 SIGMA = 0.1       # rad, slope noise
 LGS_HEIGHT = 90e3  # m, sodium layer
-ALPHA = 200.0     # regularisation weight (oracle/scan_alpha.py: minimum near 100-300)
+ALPHA = 200.0     # regularisation weight (one-time scan on the small NGS case: minimum near 100-300)
 
 
 def synthetic_profile(n_layers: int, h_max: float):

@@ -72,10 +72,12 @@ struct FInst {
     int preA_cta;
     double* preA;
     // the same CTA finishes the scalars at the start of the layer phase,
-    // writes the instance's outputs, and publishes alpha_k and beta_k as two
-    // 64-bit words {FP32 bits, tag k + 1} in pubAB[2 parities][2]: a word is
-    // read whole, so a layer CTA takes a value once its tag matches, with no
-    // flag and no release / acquire round trip (zeroed at launch start)
+    // writes the instance's outputs, and publishes the FP64 alpha_k and
+    // beta_k as four 64-bit words {32 bits of the double, tag k + 1} in
+    // pubAB[2 parities][4] (alpha high, alpha low, beta high, beta low): a
+    // word is read whole, so a layer CTA rebuilds both doubles exactly once
+    // all four tags match, with no flag and no release / acquire round trip
+    // (zeroed at launch start)
     unsigned long long* pubAB;
 };
 
@@ -1091,8 +1093,11 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     // alpha_k, beta_k from the instance's reserved CTA: the first look is
     // issued here and lands while the transform runs
     const bool pub = (mode == kLpIter) && I.preA_cta >= 0;
-    unsigned long long wa = 0ull, wb = 0ull;
-    if (pub && tid == 0) ld_relaxed_v2(I.pubAB + (k & 1) * 2, wa, wb);
+    unsigned long long wa = 0ull, wa2 = 0ull, wb = 0ull, wb2 = 0ull;
+    if (pub && tid == 0) {
+        ld_relaxed_v2(I.pubAB + (k & 1) * 4, wa, wa2);
+        ld_relaxed_v2(I.pubAB + (k & 1) * 4 + 2, wb, wb2);
+    }
     fmark(P, 12);
     fwd_dwt(P, s, Z, B1, B2, rem[1], rem[2], cl);
     fmark(P, 13);
@@ -1132,16 +1137,18 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
                 const unsigned want = (unsigned)k + 1u;
                 const long long t0 = clock64();
                 bool ok = true;
-                while ((unsigned)(wa >> 32) != want || (unsigned)(wb >> 32) != want) {
+                while ((unsigned)(wa >> 32) != want || (unsigned)(wa2 >> 32) != want ||
+                       (unsigned)(wb >> 32) != want || (unsigned)(wb2 >> 32) != want) {
                     if (clock64() - t0 > P.budget) {
                         ok = false;
                         break;
                     }
                     __nanosleep(32);
-                    ld_relaxed_v2(I.pubAB + (k & 1) * 2, wa, wb);
+                    ld_relaxed_v2(I.pubAB + (k & 1) * 4, wa, wa2);
+                    ld_relaxed_v2(I.pubAB + (k & 1) * 4 + 2, wb, wb2);
                 }
-                sh[0] = ok ? (double)__uint_as_float((unsigned)wa) : 0.0;
-                sh[1] = ok ? (double)__uint_as_float((unsigned)wb) : 0.0;
+                sh[0] = ok ? __hiloint2double((int)(unsigned)wa, (int)(unsigned)wa2) : 0.0;
+                sh[1] = ok ? __hiloint2double((int)(unsigned)wb, (int)(unsigned)wb2) : 0.0;
                 if (!ok) atomicOr(P.errw, kErrTimeout);
             }
             __syncthreads();
@@ -1319,7 +1326,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
                              ? (int)blockIdx.x - P.res_first : -1;
     // the published alpha / beta words restart at tag 0 with every launch
     // (read only after the first grid barrier)
-    if (res_inst >= 0 && threadIdx.x < 4) P.inst[res_inst].pubAB[threadIdx.x] = 0ull;
+    if (res_inst >= 0 && threadIdx.x < 8) P.inst[res_inst].pubAB[threadIdx.x] = 0ull;
     __syncthreads();
     if (P.pf && (int)threadIdx.x >= (int)blockDim.x - 32) prefetch_plan_data(P);   // the last warp
     // Descriptors of the CTA's first sensor and layer items, fetched side by
@@ -1385,10 +1392,12 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
                 alg2_part_b(P, RI, k, A, sh);
                 __syncwarp();
                 if (threadIdx.x == 0) {
-                    // alpha_k, beta_k for the layer CTAs first (tagged words) ...
+                    // alpha_k, beta_k (FP64) for the layer CTAs first (tagged words) ...
                     const unsigned long long tag = (unsigned long long)(k + 1) << 32;
-                    st_relaxed_v2(RI.pubAB + (k & 1) * 2, tag | __float_as_uint((float)sh[0]),
-                                  tag | __float_as_uint((float)sh[1]));
+                    st_relaxed_v2(RI.pubAB + (k & 1) * 4, tag | (unsigned)__double2hiint(sh[0]),
+                                  tag | (unsigned)__double2loint(sh[0]));
+                    st_relaxed_v2(RI.pubAB + (k & 1) * 4 + 2, tag | (unsigned)__double2hiint(sh[1]),
+                                  tag | (unsigned)__double2loint(sh[1]));
                     // ... then the instance's outputs (rho_k and the last
                     // nonzero alpha feed part A of the next iteration here)
                     double* sw = RI.scal + (k & 1) * 2;
@@ -1874,7 +1883,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             I.preA = nullptr;
             I.pubAB = nullptr;
             ok = dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) && dalloc(pl, I.preA, 12, err) &&
-                 dalloc(pl, I.pubAB, 4, err) &&
+                 dalloc(pl, I.pubAB, 8, err) &&
                  dupload(pl, d_gtab, preps[i].gtab, err) && dupload(pl, d_gtab_off, preps[i].gtab_off, err);
             I.gtab = d_gtab;
             I.gtab_off = d_gtab_off;

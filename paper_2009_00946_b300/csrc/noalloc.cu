@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -122,6 +123,12 @@ extern "C" int fewha_layers_noalloc(const float* coeffs, float* layers, int n_la
         snprintf(msg, sizeof msg, "%ld coefficients exceed the fixed scratch of %ld floats (4 MiB)", total,
                  kScratchFloats);
         return fail(errbuf, errlen, FEWHA_ERR_ARG, msg);
+    }
+    {
+        // the copy and the level passes assume disjoint buffers
+        const uintptr_t c0 = (uintptr_t)coeffs, c1 = c0 + (uintptr_t)total * sizeof(float);
+        const uintptr_t y0 = (uintptr_t)layers, y1 = y0 + (uintptr_t)total * sizeof(float);
+        if (c0 < y1 && y0 < c1) return fail(errbuf, errlen, FEWHA_ERR_ARG, "coeffs and layers must not overlap");
     }
     double h[6], g[6];
     fewha::db3_taps(h, g);

@@ -122,6 +122,7 @@ def lib():
         "fewha_batch_describe": (ci, [vp, ctypes.c_char_p, ci]),
         "fewha_batch_launch_count": (cll, [vp]),
         "fewha_batch_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
+        "fewha_measure_l2": (ci, [cl, ci, ci, ctypes.POINTER(cd), ctypes.POINTER(cd), ctypes.c_char_p, ci]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -554,3 +555,16 @@ class Batch:
         buf = ctypes.create_string_buffer(1024)
         self._check(lib().fewha_batch_autotune(self.h, int(n_iter), int(reps), buf, 1024))
         return buf.value.decode()
+
+
+def measure_l2(nbytes: int = 48 << 20, passes: int = 40, reps: int = 5) -> dict:
+    """Achievable L2 bandwidth of the current GPU (fewha_measure_l2): a buffer
+    of nbytes resident in L2 read, and copied half to half, passes times per
+    launch; the fastest of reps launches, GB/s (read, and read + write)."""
+    rd, cp = ctypes.c_double(), ctypes.c_double()
+    msg = ctypes.create_string_buffer(256)
+    st = lib().fewha_measure_l2(int(nbytes), int(passes), int(reps), ctypes.byref(rd), ctypes.byref(cp), msg, 256)
+    if st:
+        raise FewhaError(st, msg.value.decode())
+    return {"read_gbs": rd.value, "copy_gbs": cp.value, "bytes": int(nbytes), "passes": int(passes),
+            "reps": int(reps)}

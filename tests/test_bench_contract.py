@@ -74,5 +74,23 @@ def test_peak_provenance(monkeypatch, tmp_path):
     assert peak == 7100.0 and kind.startswith("of measured")
 
 
+def test_roofline_block_is_against_the_measured_l2():
+    import bench
+    from paper_2009_00946_b300 import configs
+    cfg = configs.c2_elt()
+    l2 = {"read_gbs": 20000.0, "copy_gbs": 16000.0, "bytes": 48 << 20, "passes": 40, "reps": 5}
+    r = bench.roofline_block(cfg, 100.0, 20.0, l2, 6500.0, "of measured", None)
+    assert r["bound"] == "l2" and r["unit"] == "GB/s" and r["peak"] == 20000.0   # the larger L2 figure
+    alg = bench.algorithmic_bytes_per_frame(cfg, bench.N_ITER)
+    assert abs(r["achieved"] - alg / 100e-6 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 20000.0) < 1e-12
+    # one PCG iteration: 16 N + 4 NW FP32 elements (N = 9 * 128^2, NW = 6 * 85^2)
+    it = r["per_iteration"]
+    assert it["algorithmic_bytes"] == 4 * (16 * 9 * 128 ** 2 + 4 * 6 * 85 ** 2)
+    assert abs(it["frac"] - it["algorithmic_bytes"] / 20e-6 / 1e9 / 20000.0) < 1e-12
+    assert abs(r["hbm"]["frac"] - r["achieved"] / 6500.0) < 1e-12
+    assert r["peak_kind"].startswith("of measured")
+
+
 if __name__ == "__main__":
     sys.exit(pytest.main([__file__, "-q"]))

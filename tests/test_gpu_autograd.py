@@ -66,13 +66,14 @@ def _gpu_grads(env, S_, prec, s, phit, params=None):
 def test_taped_solve_and_adjoint_match_oracle_fp64(env):
     torch, fewha, _, cfg, g, pr, Jinv, S, T = env
     with fewha.Solver(cfg, precision=fewha.FP64) as S_:
-        phi, loss, gg, ga, gw, _ = _gpu_grads(env, S_, fewha.FP64, S[0], T[0])
+        phi, loss, gg, ga, gw, gs = _gpu_grads(env, S_, fewha.FP64, S[0], T[0])
     b = fo.rhs(g, S[0], pr)
     c, _, _ = fo.pcg_alg2_tape(lambda v: fo.apply_M(g, v, pr), Jinv, b, N_ITER)
     assert rel(phi, np.concatenate([x.ravel() for x in fo.layers_from_coeffs(g, c)])) < 1e-10
-    lo, ogg, oga, ogw = fo.solve_loss_grad(g, pr, Jinv, S[0], T[0], N_ITER)
+    lo, ogg, oga, ogw, ogs = fo.solve_loss_grad(g, pr, Jinv, S[0], T[0], N_ITER, with_slopes=True)
     assert abs(loss - lo) <= 1e-10 * lo
     assert rel(gg, ogg) < 1e-8 and abs(ga - oga) <= 1e-8 * abs(oga) and rel(gw, ogw) < 1e-8
+    assert rel(gs, ogs) < 1e-8                      # slope gradient C^{-1} Gamma P W^T bbar
 
 
 def test_set_params_then_gradients_match_oracle_fp64(env):
@@ -138,14 +139,16 @@ def test_fp32_autograd_batch_of_32_frames_matches_oracle(env):
         loss.backward()
         got = (cn2.grad.cpu().numpy(), float(alpha.grad.cpu()), w.grad.cpu().numpy())
         assert slopes.grad is not None and slopes.grad.shape == slopes.shape
-        assert torch.isfinite(slopes.grad).all()
+        gsl = slopes.grad.double().cpu().numpy()
     ref_loss, ogg, oga, ogw = 0.0, np.zeros(g.L), 0.0, np.zeros(g.G)
     for f in range(32):
-        lo, a, b, c = fo.solve_loss_grad(g, pr, Jinv, S[f], T[f], N_ITER)
+        lo, a, b, c, gs = fo.solve_loss_grad(g, pr, Jinv, S[f].astype(np.float32).astype(np.float64), T[f], N_ITER,
+                                             with_slopes=True)
         ref_loss += lo
         ogg += a
         oga += b
         ogw += c
+        assert rel(gsl[f], gs) < 2e-3, (f, rel(gsl[f], gs))   # per-frame slope gradient
     assert abs(float(loss.detach()) - ref_loss) <= 1e-4 * ref_loss
     assert rel(got[0], ogg) < 2e-3, (got[0], ogg)
     assert abs(got[1] - oga) <= 2e-3 * abs(oga), (got[1], oga)

@@ -5,6 +5,8 @@ by instance: layers <= 1e-4 relative L2 for every instance and frame."""
 import numpy as np
 import pytest
 
+from _cases import elementwise_check
+
 from oracle import fewha_oracle as fo
 from paper_2009_00946_b300 import configs, synth
 
@@ -57,6 +59,7 @@ def test_batch_subset_frames_match_oracle(fw, subset_frames):
             B.frame(B.concat_slopes([s[k] for s in slopes]), 4, warm=True, layers_out=out)
             for i, lay in enumerate(B.split_layers(out)):
                 assert rel(lay, ref[i][k]) < 1e-4, (SUBSET[i], k)
+                elementwise_check(lay, ref[i][k], [l["n"] for l in cfgs[i]["layers"]], 1e-3, what=(SUBSET[i], k))
         assert B.launch_count() == 12
 
 
@@ -139,3 +142,5 @@ def test_batch_all_64_instances_match_oracle(fw):
             B.frame(B.concat_slopes([s[k] for s in slopes]), 4, warm=True, layers_out=out)
             errs = [rel(lay, ref[i][k]) for i, lay in enumerate(B.split_layers(out))]
             assert max(errs) < 1e-4, (k, int(np.argmax(errs)), max(errs))
+            for i, lay in enumerate(B.split_layers(out)):
+                elementwise_check(lay, ref[i][k], [l["n"] for l in cfgs[i]["layers"]], 1e-3, what=(i, k))

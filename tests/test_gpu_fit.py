@@ -5,6 +5,8 @@ against the oracle, on the mirror commands and the layers."""
 import numpy as np
 import pytest
 
+from _cases import elementwise_check
+
 from oracle import fewha_oracle as fo
 from paper_2009_00946_b300 import configs, synth
 
@@ -47,6 +49,8 @@ def test_c3_fp32_fused_frame_graph_matches_oracle(fw, c3_ref):
                     layers_out=lay, dm_out=dm)
             assert rel(lay, ref[k][1]) < 1e-4, k
             assert rel(dm, ref[k][0]) < 1e-4, k
+            elementwise_check(lay, ref[k][1], [l["n"] for l in cfg["layers"]], 1e-3, what=k)
+            elementwise_check(dm, ref[k][0], [79, 63, 48], 1e-3, what=("dm", k))
 
 
 def test_c3_fp64_plain_matches_oracle(fw, c3_ref):

@@ -8,7 +8,7 @@ import pytest
 from oracle import fewha_oracle as fo
 from paper_2009_00946_b300 import configs, synth
 
-from _cases import ragged_cfg
+from _cases import elementwise_check, ragged_cfg
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +47,7 @@ def test_fused_elt_frames_match_oracle(fw, elt_frames):
     """ELT bulk, 4 warm iterations per frame, 13 frames across the residual
     replacement of frame 10: layers and coefficients <= 1e-4."""
     cfg, S_in, ref = elt_frames
+    sides = [l["n"] for l in cfg["layers"]]
     with _fused(fw, cfg, k_rr=10) as S:
         for k in range(13):
             S.set_frame(S_in[k])
@@ -54,6 +55,7 @@ def test_fused_elt_frames_match_oracle(fw, elt_frames):
             S.sync()
             assert rel(S.layers(), ref[k][0]) < 1e-4, k
             assert rel(S.vector(fw.VEC_C), ref[k][1]) < 1e-4, k
+            elementwise_check(S.layers(), ref[k][0], sides, 1e-3, what=k)
 
 
 def test_fused_matches_plain_fp32(fw, elt_frames):
@@ -93,6 +95,7 @@ def test_fused_small_and_ragged_geometries(fw, name):
             S.solve(6, warm=(k > 0))
             S.sync()
             assert rel(S.layers(), R.layers()) < 1e-4, (name, k)
+            elementwise_check(S.layers(), R.layers(), [l["n"] for l in cfg["layers"]], 1e-3, what=(name, k))
 
 
 def test_fused_timeout_reported_and_recoverable(fw, elt_frames):

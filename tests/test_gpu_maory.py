@@ -7,6 +7,8 @@ against the FP64 oracle: plain FP64 <= 1e-10 and the FP32 fused frame graph
 import numpy as np
 import pytest
 
+from _cases import elementwise_check
+
 from oracle import fewha_oracle as fo
 from paper_2009_00946_b300 import configs, synth
 
@@ -66,3 +68,5 @@ def test_maory_fp32_fused_graph_matches_oracle(fw, maory_ref):
             S.sync()
             assert rel(da.cpu().numpy(), ref[k][0]) < 1e-4, k
             assert rel(dl.cpu().numpy(), ref[k][1]) < 1e-4, k
+            elementwise_check(dl.cpu().numpy(), ref[k][1], [l["n"] for l in cfg["layers"]], 1e-3, what=k)
+            elementwise_check(da.cpu().numpy(), ref[k][0], [81, 48, 48, 48, 48, 54], 1e-3, what=("dm", k))

@@ -5,6 +5,8 @@ through the C ABI.  Bars: FP64 GPU <= 1e-10 relative L2 against the oracle
 import numpy as np
 import pytest
 
+from _cases import elementwise_check
+
 from oracle import fewha_oracle as fo
 from paper_2009_00946_b300 import configs, synth
 
@@ -83,6 +85,7 @@ def test_c1_fp64_frame_matches_oracle(fw):
     assert rel(b, out["b"]) < 1e-12
     assert rel(c, out["c"]) < 1e-10
     assert rel(phi, R.layers()) < 1e-10
+    elementwise_check(phi, R.layers(), [l["n"] for l in cfg["layers"]], 1e-9, what="c1 fp64")
 
 
 def test_fp64_warm_frames_with_replacement(fw):
@@ -129,6 +132,7 @@ def test_fp32_plain_elt_frames_match_oracle(fw):
             S.solve(4, warm=True)
             S.sync()
             assert rel(S.layers(), R.layers()) < 1e-4, k
+            elementwise_check(S.layers(), R.layers(), [l["n"] for l in cfg["layers"]], 1e-3, what=k)
 
 
 def test_nan_slopes_reported(fw):

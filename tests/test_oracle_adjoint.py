@@ -71,3 +71,24 @@ def test_solve_map_adjoint_identity():
     cm, _, _ = fo.pcg_alg2_tape(Mop, Jinv, b - eps * v, 4)
     Jv = (cp - cm) / (2 * eps)
     assert abs(Jv @ u - v @ bbar) <= 1e-6 * abs(v @ bbar)
+
+
+@pytest.mark.parametrize("name", ["tiny_lgs", "c5_autograd"])
+def test_slope_gradient_matches_central_differences(name):
+    """d loss / d s = C^{-1} Gamma P W^T bbar against central differences of
+    the forward solve along random slope directions (the solve is nonlinear in
+    s through the CG step lengths, so this checks bbar as well), and zero on
+    masked subapertures."""
+    g, pr, Jinv, s, phit = _case(name)
+    loss, _, _, _, gs = fo.solve_loss_grad(g, pr, Jinv, s, phit, 4, with_slopes=True)
+    assert gs.shape == s.shape
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        v = rng.standard_normal(s.size)
+        eps = 1e-5 * np.linalg.norm(s) / np.linalg.norm(v)
+        fd = (fo.solve_loss(g, pr, Jinv, s + eps * v, phit, 4) - fo.solve_loss(g, pr, Jinv, s - eps * v, phit, 4)) \
+            / (2 * eps)
+        assert abs(fd - float(gs @ v)) <= 1e-6 * max(abs(fd), 1e-6 * loss), (fd, float(gs @ v))
+    for q in range(g.G):
+        gx, gy = g.split_slopes(gs, q)
+        assert np.all(gx[g.mask[q] == 0] == 0) and np.all(gy[g.mask[q] == 0] == 0)

@@ -202,6 +202,26 @@ def test_P_identity_for_colocated_ground_layer():
         assert np.max(np.abs(fo.P_layer(g, phi, gg, 0) - phi)) < 1e-14
 
 
+def test_layer_grid_extent_hand_examples(golden):
+    """Layer extents, spacings and origins worked by hand for an NGS layer, an
+    LGS cone layer, a layer set by the fitting directions, one set by the
+    co-located mirror's actuator cover and one set by a tip-tilt NGS; plus the
+    bilinear cell and weight of two sensor nodes, one on the last-node
+    tie-break."""
+    from paper_2009_00946_b300 import configs
+    for case in golden["layer_grid_extents"]["cases"]:
+        geo = fo.Geometry(getattr(configs, case["config"])())
+        l = case["layer"]
+        assert abs(geo.E[l] - case["E"]) <= 1e-9 * case["E"], case["config"]
+        assert abs(geo.delta[l] - case["delta"]) <= 1e-9 * case["delta"], case["config"]
+        assert abs(geo.X0[l] - case["X0"]) <= 1e-9 * abs(case["X0"]), case["config"]
+        smp = case.get("sample")
+        if smp:
+            cy, ty, cx, tx = geo.tab[smp["wfs"]][l]
+            assert cy[smp["i_last"]] == smp["cell_last"] and abs(ty[smp["i_last"]] - smp["t_last"]) < 1e-9
+            assert cy[smp["i_first"]] == smp["cell_first"] and abs(ty[smp["i_first"]] - smp["t_first"]) < 1e-6
+
+
 def test_geometry_error_outside_layer_grid():
     cfg = configs.tiny()
     g = fo.Geometry(cfg)

@@ -61,6 +61,61 @@ def test_noalloc_layers_match_get_layers_on_two_calls(fw, name):
             assert rel(got, want.astype(np.float64)) < 1e-6, (name, call)
 
 
+def _mixed_levels_cfg():
+    """Layers of different sides and DWT level counts, so that the coarse
+    levels of the deeper layers run while the shallower layers skip them."""
+    cfg = configs.c1_plain()
+    base = cfg["layers"][0]
+    cfg["layers"] = [dict(base, height=0.0, n=64, levels=2), dict(base, height=3000.0, n=128, levels=4),
+                     dict(base, height=6000.0, n=256, levels=5), dict(base, height=9000.0, n=32, levels=3)]
+    return cfg
+
+
+def test_noalloc_mixed_levels_match_oracle_and_get_layers(fw):
+    import torch
+
+    from oracle import fewha_oracle as fo
+    cfg = _mixed_levels_cfg()
+    sides = [l["n"] for l in cfg["layers"]]
+    with fw.Solver(cfg, precision=fw.FP32, path=fw.PATH_PLAIN) as S:
+        out = torch.empty(S.N, dtype=torch.float32, device="cuda")
+        for call in range(2):
+            c = synth.random_coeffs(cfg, 300 + call).astype(np.float32)
+            zeros = np.zeros(S.N, np.float32)
+            S.set_state(c, zeros, zeros, frame_count=0)
+            want_lib = S.layers().astype(np.float64)
+            want, o = [], 0
+            for l, n in zip(cfg["layers"], sides):       # the oracle's synthesis, layer by layer
+                want.append(fo.inv_dwt2(c[o:o + n * n].astype(np.float64).reshape(n, n), l["levels"]).ravel())
+                o += n * n
+            want = np.concatenate(want)
+            c_dev = torch.from_numpy(c).to("cuda")
+            torch.cuda.synchronize()
+            st, msg = _noalloc(fw, cfg, c_dev, out, S.stream)
+            assert st == 0, msg
+            S.stream.synchronize()
+            got = out.cpu().numpy().astype(np.float64)
+            assert rel(got, want) < 1e-6, call
+            assert rel(got, want_lib) < 1e-6, call
+            o = 0
+            for n in sides:                              # every layer on its own, element by element
+                g, w = got[o:o + n * n], want[o:o + n * n]
+                assert np.max(np.abs(g - w)) <= 1e-5 * np.max(np.abs(w)), (n, call)
+                o += n * n
+
+
+def test_noalloc_rejects_overlapping_buffers(fw):
+    import torch
+    cfg = configs.c1_plain()
+    N = sum(l["n"] ** 2 for l in cfg["layers"])
+    buf = torch.zeros(2 * N, dtype=torch.float32, device="cuda")
+    # layers start 4 floats into the coefficient range: a partial overlap
+    st, msg = _noalloc(fw, cfg, buf, buf[4:], torch.cuda.current_stream())
+    assert st == 1 and "overlap" in msg, msg
+    st, msg = _noalloc(fw, cfg, buf[4:], buf, torch.cuda.current_stream())
+    assert st == 1 and "overlap" in msg, msg
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(fw):
     import torch
     cfg = configs.c3_elt_dm()
