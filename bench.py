@@ -494,7 +494,9 @@ def phase_breakdown(S, pool_dev, n_iter=N_ITER, dump=None):
              (13, 40): "scal_enter_us", (40, 41): "scal_partials_us", (41, 42): "scal_butterfly_us",
              (42, 43): "scal_fp64_us", (43, 17): "scal_exit_us", (15, 16): "layer_store_sync_us",
              (14, 16): "layer_no_inverse_us", (20, 21): "sensor_stage_windows_us", (21, 22): "sensor_P_us",
-             (22, 23): "sensor_slopes_us", (23, 24): "sensor_gammaT_store_us"}
+             (22, 23): "sensor_slopes_us", (23, 24): "sensor_gammaT_store_us",
+             (12, 50): "casc_cols_fwd_us", (50, 51): "casc_sync1_us", (51, 13): "casc_rows_fwd_us",
+             (14, 53): "casc_rows_inv_us", (53, 54): "casc_sync2_us", (54, 15): "casc_cols_inv_us"}
     steps = {}
     for row in fine:
         for (ta, a), (tb, b) in zip(row[:-1], row[1:]):

@@ -245,7 +245,20 @@ int fewha_set_barrier_budget(fewha_handle* h, long long cycles);
  * if no plan of that size fits the geometry or the device. */
 int fewha_set_cluster_size(fewha_handle* h, int cluster_size);
 
-/* Autotuner of the fused path: times every feasible cluster shape on the
+/* Fused-path layer phase (FP32 handles): form = 0 keeps each layer in row
+ * stripes of its cluster and runs the 2D DWT of Sec. 2.2 level by level (one
+ * cluster barrier per level whose block spans CTAs); form = 1 runs it
+ * level-stacked: every column of the CTA's column stripe through the whole 1D
+ * cascade, one exchange of the stacked rows through distributed shared
+ * memory, then a 1D cascade per row (and the transposes in reverse for W^T),
+ * the same coefficients in Mallat layout; form = -1 (the default) takes the
+ * level-stacked form wherever it fits shared memory.  The plan is rebuilt
+ * (with the current cluster size when that size supports the form).
+ * Errors: ARG (no plan of that form fits), STATE (FP64 handle). */
+int fewha_set_layer_transform(fewha_handle* h, int form);
+
+/* Autotuner of the fused path: times every feasible cluster shape (and, unless
+ * fewha_set_layer_transform fixed it, both layer-phase forms) on the
  * current frame (set_frame first) for n_iter warm-started iterations, reps
  * timed launches each (CUDA events, median), keeps the fastest and restores
  * the solver state (c, r, b) it found.  report (len bytes, may be NULL)
@@ -276,7 +289,10 @@ int fewha_get_trace(fewha_handle* h, unsigned long long* out, int max_entries, i
  * Tags: 10..16 layer phase (start, sensor rows staged, P^T done, forward DWT
  * done, update done, inverse DWT done, end), 17 / 18 inside the update of an
  * iteration (scalars known, elementwise loop done); 20..24 sensor tile (start,
- * windows staged, P done, slopes done, end); 30 RHS sensor tile start.
+ * windows staged, P done, slopes done, end); 30 RHS sensor tile start;
+ * level-stacked layer phase: 50 column cascade (and its stores into the rows'
+ * owners) done, 51 first cluster barrier passed, 53 row synthesis done, 54
+ * second cluster barrier passed.
  * Synchronises.  Errors: STATE on the plain path. */
 int fewha_get_fine_trace(fewha_handle* h, unsigned long long* out, int max_entries, int* per_cta, int* grid);
 

@@ -228,6 +228,12 @@ int fewha_set_cluster_size(fewha_handle* h, int cluster_size) {
     return done(h, h->s->set_cluster_size(cluster_size));
 }
 
+int fewha_set_layer_transform(fewha_handle* h, int form) {
+    if (!h) return FEWHA_ERR_ARG;
+    if (form < -1 || form > 1) return fail(h, FEWHA_ERR_ARG, "layer transform must be -1, 0 or 1");
+    return done(h, h->s->set_layer_transform(form));
+}
+
 int fewha_autotune(fewha_handle* h, int n_iter, int reps, char* report, int len) {
     if (!h) return FEWHA_ERR_ARG;
     return done(h, h->s->autotune(n_iter, reps, report, len));

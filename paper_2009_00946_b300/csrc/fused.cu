@@ -42,7 +42,10 @@ constexpr int kFineCap = 1024;   // sub-phase marks per CTA per traced launch
 constexpr int kWd = 8;     // ints per layer in a sensor tile's window descriptor
 constexpr int kMaxKG = 4;        // P^T gather entries per layer row / column
 
-enum { kModeRhs = 0, kModeData = 1 };
+// sensor phases: the RHS (weighted slopes), the data term of M on the
+// current layers, and the data residual s - Gamma P phi of a residual
+// replacement (weighted, then Gamma^T)
+enum { kModeRhs = 0, kModeData = 1, kModeResid = 2 };
 enum { kLpRhsStart = 0, kLpRhsRepl = 1, kLpReplStart = 2, kLpIter = 3 };
 
 // One instance's device tables and state.
@@ -83,7 +86,7 @@ struct FInst {
 
 struct WItem { int inst, g, i0, i1, j0, j1; };
 struct PfChunk { const char* p; int bytes, pad; };   // <= 4 KB of data to bring into L2
-struct LItem { int inst, l, stg; };
+struct LItem { int inst, l, stg, csh; };   // csh: offset of the layer shape's cascade tables
 
 struct FParams {
     const FInst* inst;
@@ -123,6 +126,12 @@ struct FParams {
     int pf_per_cta;
     int G_max, n_max;
     float h[6], g[6];
+    // level-stacked layer phase (variant 1; see fused_cascade.cuh)
+    const int* cshape;        // ownership tables, one block per layer shape (n, J)
+    const int4* stg4;         // staging boxes per (layer item, rank, sensor): rows [x, y), columns [z, w)
+    int v_z, v_t, v_u, v_r, v_c, v_tab;   // shared-memory offsets (floats)
+    int v_rmax, v_smax;       // widest column stripe, most slots of a rank
+    int v_tumax;              // own-map capacity (a multiple of 4)
 };
 
 // ---------------------------------------------------------------------------
@@ -218,6 +227,11 @@ __device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -528,7 +542,7 @@ __device__ void layer_tables(const FParams& P, int rank, const CtaCache* cc, flo
 __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, bool want_mu, int* wdesc, double* red,
                             CtaCache* cc, int k) {
     const int tid = threadIdx.x, NT = blockDim.x;
-    fmark(P, mode == kModeData ? 20 : 30);
+    fmark(P, mode == kModeRhs ? 30 : 20);
     if (P.shared_tables && tid == 0) cc->lkey = cc->ltkey = -1;   // this phase overwrites the layer tables
     if (cc->wkey != item) {
         __syncthreads();   // the previous item's data may still be in use
@@ -555,7 +569,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     float* cw = (float*)(coff + L * P.tile_cols);
     Acc2 mu;
     const int ns2 = ns * ns;
-    if (mode == kModeData) {
+    if (mode != kModeRhs) {
         const bool build = !cc->wtab;
         if (build) {
             if (tid < L) {
@@ -688,12 +702,21 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         __syncthreads();
         fmark(P, 22);
         const float w = cc->w;
+        const float* Sm = I.slopes + cc->w_soff;   // the frame's slopes (residual mode)
         for (int e = tid; e < nsr * nsc; e += NT) {
             const int aa = e / nsc, bb = e - aa * nsc;
             const int a = a_lo + aa, b = b_lo + bb;
             const float* pp = psi + aa * pc + bb;
-            const float sx = ((pp[1] - pp[0]) + (pp[pc + 1] - pp[pc])) / 2;
-            const float sy = ((pp[pc] - pp[0]) + (pp[pc + 1] - pp[1])) / 2;
+            float sx = ((pp[1] - pp[0]) + (pp[pc + 1] - pp[pc])) / 2;
+            float sy = ((pp[pc] - pp[0]) + (pp[pc + 1] - pp[1])) / 2;
+            if (mode == kModeResid) {
+                // measured minus modelled slopes: the residual of a replacement
+                // frame without the cancellation of b - M c (b and M c agree to
+                // a few per cent, their difference loses the digits)
+                const float mx = __ldcg(Sm + a * ns + b), my = __ldcg(Sm + ns2 + a * ns + b);
+                sx = (isfinite(mx) ? mx : 0.f) - sx;
+                sy = (isfinite(my) ? my : 0.f) - sy;
+            }
             const float wm = I.mask[cc->w_moff + a * ns + b] ? w : 0.f;
             slx[e] = wm * sx;
             sly[e] = wm * sy;
@@ -1220,11 +1243,11 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             I.b[i] = Z[e];
             zout = I.c[i];
         } else if (mode == kLpReplStart) {
+            // r = b - M c = W P^T Gamma^T C^{-1} (s - Gamma P W^T c) - alpha D c
+            // (the data part arrives as the transformed slope residual)
             const float cv = I.c[i];
-            const float Mc = Z[e] + ad * cv;
-            const float bv = I.b[i];
-            const float rv = (float)((double)bv - (double)Mc);
-            I.bprev[i] = bv;
+            const float rv = (float)((double)Z[e] - (double)ad * (double)cv);
+            I.bprev[i] = I.b[i];
             I.r[i] = rv;
             zout = jinv * rv;
             rho_p.add_prod(rv, zout);
@@ -1252,6 +1275,8 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     if (end_sync) cl.sync();
     fmark(P, 16);
 }
+
+#include "fused_cascade.cuh"
 
 // ---------------------------------------------------------------------------
 // L2 prefetch of the launch's static data and state
@@ -1281,8 +1306,10 @@ __device__ void prefetch_plan_data(const FParams& P) {
 // the frame kernel
 // ---------------------------------------------------------------------------
 // The cluster shape is compiled into each instance (one per cluster size), so
-// it belongs to the kernel and not to the launch configuration.
-template <int CS>
+// it belongs to the kernel and not to the launch configuration.  V selects the
+// layer phase: 0 row stripes (one cluster barrier per DWT level), 1 the
+// level-stacked form (one exchange per transform, fused_cascade.cuh).
+template <int CS, int V>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     k_fused_frame(const __grid_constant__ FParams P) {
     extern __shared__ __align__(16) float sm[];
@@ -1310,7 +1337,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     ++slot;
     if (threadIdx.x < 4 * C) {
         const int b = threadIdx.x / C, r = threadIdx.x % C;
-        rem[b][r] = cl.map_shared_rank(sm + b * P.stripe_floats, r);
+        if (V == 0) rem[b][r] = cl.map_shared_rank(sm + b * P.stripe_floats, r);
+        else if (b < 2) rem[b][r] = cl.map_shared_rank(sm + (b == 0 ? P.v_r : P.v_u), r);   // Urow, Ucol
     }
     if (threadIdx.x == 0) {
         s_abort = 0;
@@ -1338,7 +1366,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
         if (threadIdx.x == 32 && l_lo < l_hi) layer_desc(P, P.lsched[l_lo], &cc);
         __syncthreads();
         if (l_lo < l_hi) {
-            layer_tables(P, (int)cl.block_rank(), &cc, sm);
+            if (V == 0) layer_tables(P, (int)cl.block_rank(), &cc, sm);
+            else layer_tables_v1(P, (int)cl.block_rank(), &cc, sm);
             if (threadIdx.x == 0) cc.ltkey = cc.lkey;
         }
         __syncthreads();
@@ -1350,7 +1379,9 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     // after every one but the last:
     //   0: Alg. 1 RHS, Gamma^T C^{-1} s per sensor tile
     //   1: P^T, W -> b; warm restart (or c -> phi for the replacement); z_0 -> phi
-    //   [2, 3: replacement r = b - M c: data term of M on phi_c, then the layer phase]
+    //   [2, 3: replacement r = b - M c: the weighted slope residual
+    //    Gamma^T C^{-1} (s - Gamma P phi_c), then the layer phase
+    //    r = W P^T (...) - alpha D c]
     //   then per Alg. 2 iteration k: the data term (sensor tiles; the reserved
     //   CTA computes part A of the scalars), then the layer phase (the reserved
     //   CTA first publishes part B)
@@ -1360,7 +1391,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
         const int k = it ? (ph - base) >> 1 : 0;
         const bool sensor_ph = it ? ((ph - base) & 1) == 0 : (ph & 1) == 0;
         if (sensor_ph) {
-            const int smode = (ph == 0) ? kModeRhs : kModeData;
+            const int smode = (ph == 0) ? kModeRhs : (!it && ph == 2) ? kModeResid : kModeData;
             for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, smode, it, wdesc, red, &cc, k);
             if (it && res_inst >= 0 && threadIdx.x < 32) {
                 // part A of instance res_inst's scalars for this iteration's layer phase
@@ -1415,7 +1446,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
             const int lmode = it ? kLpIter : (ph == 1 ? (P.replace ? kLpRhsRepl : kLpRhsStart) : kLpReplStart);
             const bool last_ph = it && k + 1 == P.n_iter;
             for (int t = l_lo; t < l_hi; ++t)
-                layer_phase(P, P.lsched[t], lmode, k, sm, rem, cl, red, sh, &cc, t + 1 < l_hi || last_ph);
+                if (V == 0) layer_phase(P, P.lsched[t], lmode, k, sm, rem, cl, red, sh, &cc, t + 1 < l_hi || last_ph);
+                else layer_phase_v1(P, P.lsched[t], lmode, k, sm, rem, cl, red, sh, &cc, false);
         }
         if (ph + 1 < nph) grid_barrier(P, target, &s_abort, slot);
     }
@@ -1443,13 +1475,23 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
 
 using FusedKernel = void (*)(FParams);
 
-FusedKernel fused_kernel_for(int C) {
+FusedKernel fused_kernel_for(int C, int V) {
+    if (V == 1) {
+        switch (C) {
+            case 1: return k_fused_frame<1, 1>;
+            case 2: return k_fused_frame<2, 1>;
+            case 4: return k_fused_frame<4, 1>;
+            case 8: return k_fused_frame<8, 1>;
+            case 16: return k_fused_frame<16, 1>;
+            default: return nullptr;
+        }
+    }
     switch (C) {
-        case 1: return k_fused_frame<1>;
-        case 2: return k_fused_frame<2>;
-        case 4: return k_fused_frame<4>;
-        case 8: return k_fused_frame<8>;
-        case 16: return k_fused_frame<16>;
+        case 1: return k_fused_frame<1, 0>;
+        case 2: return k_fused_frame<2, 0>;
+        case 4: return k_fused_frame<4, 0>;
+        case 8: return k_fused_frame<8, 0>;
+        case 16: return k_fused_frame<16, 0>;
         default: return nullptr;
     }
 }
@@ -1458,7 +1500,7 @@ FusedKernel fused_kernel_for(int C) {
 // host plan
 // ---------------------------------------------------------------------------
 struct FusedPlan {
-    int C = 1, nclusters = 0, grid = 0, smem = 0;
+    int C = 1, V = 0, nclusters = 0, grid = 0, smem = 0;
     bool cooperative = true;
     bool trace_on = false;
     unsigned long long* ftrace = nullptr;
@@ -1605,9 +1647,86 @@ static void lpt_schedule(const std::vector<double>& cost, int workers, std::vect
     }
 }
 
+// Ownership tables of the level-stacked layer phase for layers of side n with
+// J levels on clusters of C CTAs (layout in fused_cascade.cuh), appended to
+// blob; returns the block's offset.  The T_U = 2n(1 - 2^-J) rows of the
+// stacked column transform are dealt to the CTAs longest-processing-time
+// first, a row costing n/2 (its share of the exchange and the cascade) plus
+// twice its coefficients (the elementwise update); a CTA's rows are ordered
+// by depth, deepest first, so the rows active at a level form a prefix.
+struct CascStats { int smax = 0, ncoef_max = 0, tu_max = 0; };
+
+static int build_casc_shape(int n, int J, int C, std::vector<int>& blob, CascStats& st) {
+    struct Row { int u, j, isA, goff, ncoef; double cost; };
+    std::vector<Row> rows;
+    int base = 0;
+    for (int j = 1; j <= J; ++j) {
+        const int half = n >> j;
+        for (int k = 0; k < half; ++k) {   // Lo_j rows: Hi_j (j < J), Lo_J and Hi_J (j = J)
+            const bool A = j < J;
+            rows.push_back(Row{base + k, j, A ? 1 : 0, k * n + (A ? half : 0), A ? half : 2 * half, 0.0});
+        }
+        for (int k = 0; k < half; ++k)     // Hi_j rows: Lo_j and Hi_j, Mallat row half + k
+            rows.push_back(Row{base + half + k, j, 0, (half + k) * n, 2 * half, 0.0});
+        base += 2 * half;
+    }
+    const int TU = base;
+    std::vector<double> cost;
+    for (auto& r : rows) cost.push_back(0.5 * n + 2.0 * r.ncoef);
+    std::vector<int> order, off;
+    lpt_schedule(cost, C, order, off);
+    const int hdr = (5 + C + 3) & ~3;
+    const int start = (int)blob.size();
+    blob.resize(start + hdr, 0);
+    blob[start + 0] = TU;
+    blob[start + 1] = J;
+    blob[start + 2] = n;
+    blob[start + 3] = C;
+    std::vector<int> own(TU, 0);
+    for (int r = 0; r < C; ++r) {
+        std::vector<Row> mine;
+        for (int i = off[r]; i < off[r + 1]; ++i) mine.push_back(rows[order[i]]);
+        std::sort(mine.begin(), mine.end(), [](const Row& a, const Row& b) { return a.j != b.j ? a.j > b.j : a.u < b.u; });
+        const int rb = (int)blob.size();
+        blob[start + 4 + r] = rb - start;
+        blob.resize(rb + 20 + 4 * mine.size(), 0);
+        int zoff = 0;
+        std::vector<int> gidx;   // Mallat offset in the layer of every owned coefficient
+        for (size_t s = 0; s < mine.size(); ++s) {
+            const Row& w = mine[s];
+            int* e = &blob[rb + 20 + 4 * s];
+            e[0] = w.u;
+            e[1] = w.j | (w.isA << 8);
+            e[2] = w.goff;
+            e[3] = zoff;
+            own[w.u] = (r << 16) | (int)s;
+            zoff += w.ncoef;
+            for (int x = 0; x < w.ncoef; ++x) gidx.push_back(w.goff + x);
+        }
+        blob.insert(blob.end(), gidx.begin(), gidx.end());
+        blob.resize((blob.size() + 3) & ~(size_t)3, 0);
+        blob[rb + 0] = (int)mine.size();
+        blob[rb + 1] = zoff;
+        blob[rb + 2] = TU;
+        blob[rb + 3] = J;
+        for (int i = 1; i <= 16; ++i) {
+            int c = 0;
+            for (auto& w : mine) c += w.j >= i;
+            blob[rb + 4 + i - 1] = c;
+        }
+        st.smax = std::max(st.smax, (int)mine.size());
+        st.ncoef_max = std::max(st.ncoef_max, zoff);
+    }
+    blob[start + 4 + C] = (int)blob.size() - start;
+    blob.insert(blob.end(), own.begin(), own.end());
+    blob.resize((blob.size() + 3) & ~(size_t)3, 0);
+    st.tu_max = std::max(st.tu_max, TU);
+    return start;
+}
+
 FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const std::vector<DevGeo<float>>& Gs,
                               const std::vector<FusedBuffers>& fbs, int max_tile_side, std::string& err,
-                              int forced_C) {
+                              int forced_C, int forced_V) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceProp prop;
@@ -1640,7 +1759,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
     size_t smem_cap = 0;
     {
         cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, fused_kernel_for(8)) != cudaSuccess ||
+        if (cudaFuncGetAttributes(&fa, fused_kernel_for(8, 0)) != cudaSuccess ||
             fa.sharedSizeBytes + 1024 >= (size_t)prop.sharedMemPerBlockOptin) {
             cudaGetLastError();
             err = "cannot query the fused kernel";
@@ -1657,7 +1776,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         int items = 0;
         for (const HostSetup* h : hss) items += h->L;
         auto clusters_for = [&](int C) {
-            const FusedKernel k = fused_kernel_for(C);
+            const FusedKernel k = fused_kernel_for(C, 0);
             if (!k || 2 * C > nmin || (size_t)nmax * nmax / C * 4 * sizeof(float) > smem_cap) return 0;
             if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap) != cudaSuccess) {
                 cudaGetLastError();
@@ -1682,38 +1801,85 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
                     break;
                 }
     }
+    // candidates: every cluster shape in order of preference, the level-stacked
+    // layer phase (V = 1) before the row stripes (V = 0) for each
+    std::vector<std::pair<int, int>> cand;
+    for (int C : order)
+        for (int V : {1, 0}) cand.push_back({C, V});
     FusedPlan* best = nullptr;
-    for (int C : order) {
+    for (auto [C, V] : cand) {
         if (forced_C > 0 && C != forced_C) continue;
-        if (2 * C > nmin) continue;   // stripes of at least 2 rows
-        if ((size_t)nmax * nmax / C * 4 * sizeof(float) > smem_cap) continue;
+        if (forced_V >= 0 && V != forced_V) continue;
+        if (V == 0) {
+            if (2 * C > nmin) continue;   // stripes of at least 2 rows
+            if ((size_t)nmax * nmax / C * 4 * sizeof(float) > smem_cap) continue;
+        } else if (C > nmin || nmax / C > kFThreads) {
+            continue;                     // column stripes of 1 .. 512 columns
+        }
         auto* pl = new FusedPlan();
         pl->C = C;
-        // layer items (instance, layer) with the staged sensor rows per rank
+        pl->V = V;
+        // layer items (instance, layer) with the staged sensor rows (V = 0) or
+        // boxes (V = 1) per rank, and for V = 1 the ownership tables per shape
         std::vector<LItem> litems;
         std::vector<int2> stg;
+        std::vector<int4> stg4;
+        std::vector<int> cshape;
+        CascStats cst;
+        std::vector<std::pair<std::pair<int, int>, int>> shape_off;
         std::vector<int> l0(ninst), nl(ninst);
         int stage_max = 0;
         for (int i = 0; i < ninst; ++i) {
             const HostSetup& hs = *hss[i];
             l0[i] = (int)litems.size();
             for (int l = 0; l < hs.L; ++l) {
-                LItem li{i, l, (int)stg.size()};
                 const int n = hs.lay[l].n, R = n / C;
+                LItem li{i, l, V == 0 ? (int)stg.size() : (int)stg4.size(), 0};
+                if (V == 1) {
+                    const std::pair<int, int> key{n, hs.lay[l].J};
+                    int o = -1;
+                    for (auto& so : shape_off)
+                        if (so.first == key) o = so.second;
+                    if (o < 0) {
+                        o = build_casc_shape(n, hs.lay[l].J, C, cshape, cst);
+                        shape_off.push_back({key, o});
+                    }
+                    li.csh = o;
+                }
                 for (int rank = 0; rank < C; ++rank) {
                     int tot = 0;
                     for (int g = 0; g < hs.G; ++g) {
                         const int gb = hs.gat_off[g * hs.L + l];
-                        int lo = 1 << 30, hi = 0;
-                        for (int p = rank * R; p < (rank + 1) * R; ++p) {
-                            if (hs.ihi[gb + p] > hs.ilo[gb + p]) {
-                                lo = std::min(lo, hs.ilo[gb + p]);
-                                hi = std::max(hi, hs.ihi[gb + p]);
+                        if (V == 0) {
+                            int lo = 1 << 30, hi = 0;
+                            for (int p = rank * R; p < (rank + 1) * R; ++p) {
+                                if (hs.ihi[gb + p] > hs.ilo[gb + p]) {
+                                    lo = std::min(lo, hs.ilo[gb + p]);
+                                    hi = std::max(hi, hs.ihi[gb + p]);
+                                }
                             }
+                            if (lo >= hi) lo = hi = 0;
+                            stg.push_back(make_int2(lo, hi));
+                            tot += (hi - lo) * (hs.wfs[g].n + 1) + 8;   // + 16-byte alignment slack
+                        } else {
+                            // every sensor row any layer row gathers from, the sensor
+                            // columns of this rank's layer columns
+                            int ilo = 1 << 30, ihi = 0, jlo = 1 << 30, jhi = 0;
+                            for (int p = 0; p < n; ++p)
+                                if (hs.ihi[gb + p] > hs.ilo[gb + p]) {
+                                    ilo = std::min(ilo, hs.ilo[gb + p]);
+                                    ihi = std::max(ihi, hs.ihi[gb + p]);
+                                }
+                            for (int q = rank * R; q < (rank + 1) * R; ++q)
+                                if (hs.jhi[gb + q] > hs.jlo[gb + q]) {
+                                    jlo = std::min(jlo, hs.jlo[gb + q]);
+                                    jhi = std::max(jhi, hs.jhi[gb + q]);
+                                }
+                            if (ilo >= ihi || jlo >= jhi) ilo = ihi = jlo = jhi = 0;
+                            stg4.push_back(make_int4(ilo, ihi, jlo, jhi));
+                            const int W = (ihi > ilo && jhi > jlo) ? ((jhi - jlo + 6) & ~3) : 0;   // as the kernel
+                            tot += (ihi - ilo) * W;
                         }
-                        if (lo >= hi) lo = hi = 0;
-                        stg.push_back(make_int2(lo, hi));
-                        tot += (hi - lo) * (hs.wfs[g].n + 1) + 8;   // + 16-byte alignment slack
                     }
                     stage_max = std::max(stage_max, tot);
                 }
@@ -1724,13 +1890,27 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         const int stripe = nmax * nmax / C;
         const int Rmax = nmax / C;
         stage_max = (stage_max + 3) & ~3;
-        const size_t gtab_floats = 2 * (size_t)Gmax * nmax * KGmax + 2 * (size_t)Gmax * Rmax * KGmax;
-        const size_t layer_floats = 4 * (size_t)stripe + stage_max;   // working set (gather tables apart)
+        auto r4 = [](size_t x) { return (x + 3) & ~(size_t)3; };
+        size_t gtab_floats, layer_floats;
+        size_t vz = 0, vt = 0, vu = 0, vr = 0, vc = 0;
+        if (V == 0) {
+            gtab_floats = 2 * (size_t)Gmax * nmax * KGmax + 2 * (size_t)Gmax * Rmax * KGmax;
+            layer_floats = 4 * (size_t)stripe + stage_max;   // working set (gather tables apart)
+        } else {
+            // Z | T | Ucol (staged fields alias it) | Urow | Zc; tables: xt, yt, cascade tables
+            vt = r4((size_t)nmax * Rmax);
+            vu = vt + r4(std::max((size_t)cst.smax * (nmax / 2), (size_t)(nmax / 2) * Rmax));
+            vr = vu + r4(std::max({(size_t)cst.tu_max * Rmax, (size_t)stage_max, (size_t)nmax * Rmax}));
+            vc = vr + r4((size_t)cst.smax * nmax);
+            layer_floats = vc + r4((size_t)cst.ncoef_max);
+            gtab_floats = 2 * (size_t)Gmax * (Rmax + nmax) * KGmax +
+                          r4(20 + 4 * (size_t)cst.smax + r4(cst.tu_max) + cst.ncoef_max);
+        }
 
         // co-resident clusters: one 512-thread CTA per SM (register-limited),
         // so the answer does not depend on the shared memory below the cap;
         // the attribute is per function: allow the device maximum once
-        const FusedKernel kern = fused_kernel_for(C);
+        const FusedKernel kern = fused_kernel_for(C, V);
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap) != cudaSuccess ||
             (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
             cudaGetLastError();
@@ -1914,10 +2094,13 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         WItem* dw = nullptr;
         LItem* dl = nullptr;
         int2* ds = nullptr;
+        int4* ds4 = nullptr;
+        int* dcs = nullptr;
         float2* wp = nullptr;
         float4* lp = nullptr;
         unsigned* bar = nullptr;
         ok = ok && dupload(pl, dw, witems, err) && dupload(pl, dl, litems, err) && dupload(pl, ds, stg, err) &&
+             dupload(pl, ds4, stg4, err) && dupload(pl, dcs, cshape, err) &&
              dalloc(pl, wp, witems.size(), err) && dalloc(pl, lp, 2 * litems.size() * C, err) &&
              dalloc(pl, bar, 2, err) && dupload(pl, pl->d_inst, pl->inst, err);
         if (!ok) {
@@ -1928,6 +2111,8 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         P.witems = dw;
         P.litems = dl;
         P.stg = ds;
+        P.stg4 = ds4;
+        P.cshape = dcs;
         P.wsched = dws;
         P.wsched_off = dwo;
         P.lsched = dls;
@@ -1955,6 +2140,15 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         P.tile_cols = tile_cols;
         P.G_max = Gmax;
         P.n_max = nmax;
+        P.v_z = (int)vz;
+        P.v_t = (int)vt;
+        P.v_u = (int)vu;
+        P.v_r = (int)vr;
+        P.v_c = (int)vc;
+        P.v_rmax = Rmax;
+        P.v_smax = cst.smax;
+        P.v_tumax = (int)r4(cst.tu_max);
+        P.v_tab = P.ltab_off + (int)(2 * (size_t)Gmax * (Rmax + nmax) * KGmax);
         for (int i = 0; i < 6; ++i) {
             P.h[i] = (float)hss[0]->h[i];
             P.g[i] = (float)hss[0]->g[i];
@@ -1974,6 +2168,8 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             add(dw, witems.size() * sizeof(WItem));
             add(dl, litems.size() * sizeof(LItem));
             add(ds, stg.size() * sizeof(int2));
+            add(ds4, stg4.size() * sizeof(int4));
+            add(dcs, cshape.size() * sizeof(int));
             add(dws, wsched.size() * sizeof(int));
             add(dwo, wsched_off.size() * sizeof(int));
             add(dls, lsched.size() * sizeof(int));
@@ -2038,20 +2234,23 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
 }
 
 FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const FusedBuffers& fb, std::string& err) {
-    return fused_create_multi({&hs}, {G}, {fb}, 0, err, 0);
+    return fused_create_multi({&hs}, {G}, {fb}, 0, err, 0, -1);
 }
 
 int fused_describe(const FusedPlan* pl, char* buf, int len) {
     return snprintf(buf, len,
                     "fused: %d clusters x %d CTAs (grid %d, %d threads), smem %d B, %d sensor tiles, %d layer items, "
-                    "cooperative %d, tables %s",
+                    "cooperative %d, tables %s, layer transform %s",
                     pl->nclusters, pl->C, pl->grid, kFThreads, pl->smem, pl->P.n_witems, pl->P.n_litems,
-                    pl->cooperative ? 1 : 0, pl->P.shared_tables ? "shared" : "kept");
+                    pl->cooperative ? 1 : 0, pl->P.shared_tables ? "shared" : "kept",
+                    pl->V ? "level-stacked" : "row stripes");
 }
 
 void fused_set_trace(FusedPlan* pl, bool on) { pl->trace_on = on; }
 
 int fused_cluster_size(const FusedPlan* pl) { return pl->C; }
+
+int fused_layer_form(const FusedPlan* pl) { return pl->V; }
 
 int fused_get_trace(FusedPlan* pl, unsigned long long* out, int max_entries, int* slots, int* grid) {
     *slots = pl->trace ? pl->last_slots : 0;
@@ -2087,7 +2286,8 @@ int fused_repoint_node(cudaGraphExec_t exec, cudaGraphNode_t node, const float* 
         return -1;
     }
     bool ours = false;
-    for (int C : {1, 2, 4, 8, 16}) ours = ours || kp.func == (void*)fused_kernel_for(C);
+    for (int C : {1, 2, 4, 8, 16})
+        for (int V : {0, 1}) ours = ours || kp.func == (void*)fused_kernel_for(C, V);
     if (!ours) return -1;
     FParams P = *static_cast<const FParams*>(kp.kernelParams[0]);
     if (P.n_inst != 1) return -1;
@@ -2155,7 +2355,7 @@ int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int re
     P.replace = replace;
     P.out_layers = 1;
     P.budget = budget;
-    const FusedKernel kern = fused_kernel_for(pl->C);
+    const FusedKernel kern = fused_kernel_for(pl->C, pl->V);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3(pl->grid);

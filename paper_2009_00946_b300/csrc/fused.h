@@ -30,12 +30,15 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
 // One plan over several independent instances (solved together in one
 // launch; every instance has its own tables, state and scalars).
 // max_tile_side > 0 bounds the sensor tiles (and so the staged windows).
-// forced_C > 0 builds only that cluster size (the autotuner's candidates).
+// forced_C > 0 builds only that cluster size (the autotuner's candidates);
+// forced_V >= 0 only that layer-phase form (0 row stripes, 1 level-stacked),
+// else the level-stacked form wherever it fits.
 FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hs, const std::vector<DevGeo<float>>& G,
                               const std::vector<FusedBuffers>& fb, int max_tile_side, std::string& err,
-                              int forced_C);
-// Cluster size of a plan.
+                              int forced_C, int forced_V = -1);
+// Cluster size and layer-phase form of a plan.
 int fused_cluster_size(const FusedPlan* plan);
+int fused_layer_form(const FusedPlan* plan);
 void fused_destroy(FusedPlan* plan);
 
 // Enqueue one frame on `stream`: b = W P^T Gamma^T C^{-1} s; warm restart

@@ -263,6 +263,26 @@ __global__ void k_gamma_w(DevGeo<T> G, const T* __restrict__ psi, T* __restrict_
     sl[G.wfs_soff[g] + ns * ns + idx] = wm * sy;
 }
 
+// weighted slope residual w mask (s - Gamma psi) of a residual replacement
+// (measured minus modelled slopes; non-finite measured slopes count as 0, as
+// in the right-hand side)
+template <typename T>
+__global__ void k_resid_w(DevGeo<T> G, const T* __restrict__ s, const T* __restrict__ psi, T* __restrict__ sl) {
+    int g = blockIdx.y, ns = G.wfs_n[g], np1 = ns + 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ns * ns) return;
+    int a = idx / ns, b = idx - a * ns;
+    const T* p = psi + G.wfs_noff[g] + (long)a * np1 + b;
+    T sx = ((p[1] - p[0]) + (p[np1 + 1] - p[np1])) / 2;
+    T sy = ((p[np1] - p[0]) + (p[np1 + 1] - p[1])) / 2;
+    T mx = s[G.wfs_soff[g] + idx], my = s[G.wfs_soff[g] + ns * ns + idx];
+    mx = isfinite((double)mx) ? mx : (T)0;
+    my = isfinite((double)my) ? my : (T)0;
+    T wm = G.mask[G.wfs_moff[g] + idx] ? G.wfs_w[g] : (T)0;
+    sl[G.wfs_soff[g] + idx] = wm * (mx - sx);
+    sl[G.wfs_soff[g] + ns * ns + idx] = wm * (my - sy);
+}
+
 // weighted measurement slopes for the right-hand side; non-finite active
 // slopes raise the INPUT error bit, inactive ones are ignored
 template <typename T>
@@ -367,14 +387,16 @@ __global__ void k_warm(int N, const T* __restrict__ b, T* __restrict__ bprev, T*
     }
 }
 
-// residual replacement r = b1 - M c0 (accumulated in FP64) ; b0 = b1
+// residual replacement r = b1 - M c0 = d - alpha D c0 with d = W P^T Gamma^T
+// C^{-1} (s - Gamma P W^T c0), the data residual formed in the slope domain
+// (b1 and M c0 agree to a few per cent, so their difference would lose the
+// digits of the working precision); the subtraction in FP64 ; b0 = b1
 template <typename T>
-__global__ void k_replace(int N, const T* __restrict__ b, const T* __restrict__ Mc, T* __restrict__ bprev,
-                          T* __restrict__ r) {
+__global__ void k_replace(int N, const T* __restrict__ b, const T* __restrict__ d, const T* __restrict__ aD,
+                          const T* __restrict__ c, T* __restrict__ bprev, T* __restrict__ r) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        T bi = b[i];
-        r[i] = (T)((double)bi - (double)Mc[i]);
-        bprev[i] = bi;
+        r[i] = (T)((double)d[i] - (double)aD[i] * (double)c[i]);
+        bprev[i] = b[i];
     }
 }
 
@@ -971,8 +993,15 @@ class Solver : public SolverBase {
             k_cold<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, b, bprev, r, c);
             FEWHA_LAUNCHED();
         } else if (k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0) {
-            TRY(apply_M_dev(c, ext));
-            k_replace<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, b, ext, bprev, r);
+            TRY(inv_dwt(c, phi));
+            const int np1 = G.nsmax + 1;
+            k_P<T><<<dim3((np1 * np1 + 255) / 256, G.G), 256, 0, stream>>>(G, phi, wpsi);
+            FEWHA_LAUNCHED();
+            k_resid_w<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, slopes, wpsi, wsl);
+            FEWHA_LAUNCHED();
+            TRY(tt_filter(wsl));
+            TRY(backproject(wsl, ext));
+            k_replace<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, b, ext, aD, c, bprev, r);
             FEWHA_LAUNCHED();
         } else {
             k_warm<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, b, bprev, r);
@@ -1394,10 +1423,13 @@ class Solver : public SolverBase {
         return FEWHA_OK;
     }
 
+    // layer-phase form of the fused plan: -1 automatic, 0 row stripes, 1 level-stacked
+    int layer_form = -1;
+
     // a fused plan with cluster size C (FP32 instances only)
-    FusedPlan* make_plan(int C, std::string& e) {
+    FusedPlan* make_plan(int C, std::string& e, int form = -2) {
         if constexpr (std::is_same<T, float>::value) {
-            return fused_create_multi({&hs}, {G}, {fbuf}, 0, e, C);
+            return fused_create_multi({&hs}, {G}, {fbuf}, 0, e, C, form == -2 ? layer_form : form);
         } else {
             e = "the fused path is FP32 only";
             return nullptr;
@@ -1407,6 +1439,26 @@ class Solver : public SolverBase {
     // captured frame graphs hold the old plan's launch: drop them
     void drop_graphs() {
         for (int i = 0; i < 2; ++i) drop_graph(i);
+    }
+
+    int set_layer_transform(int form) override {
+        if (sizeof(T) != 4) {
+            err = "the fused path is FP32 only";
+            return FEWHA_ERR_STATE;
+        }
+        std::string e;
+        FusedPlan* pl = make_plan(fused ? fused_cluster_size(fused) : 0, e, form);
+        if (!pl && fused) pl = make_plan(0, e, form);
+        if (!pl) {
+            err = "no fused plan with this layer transform: " + e;
+            return FEWHA_ERR_ARG;
+        }
+        layer_form = form;
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        if (fused) fused_destroy(fused);
+        fused = pl;
+        drop_graphs();
+        return FEWHA_OK;
     }
 
     int set_cluster_size(int C) override {
@@ -1478,15 +1530,21 @@ class Solver : public SolverBase {
         char buf[96];
         FusedPlan* best = fused;
         float best_t = time_plan(fused);
-        snprintf(buf, sizeof buf, "C=%d: %.1f us (current)", fused_cluster_size(fused), best_t * 1e3f);
+        const int C0 = fused_cluster_size(fused), V0 = fused_layer_form(fused);
+        snprintf(buf, sizeof buf, "C=%d V=%d: %.1f us (current)", C0, V0, best_t * 1e3f);
         rep_s += buf;
-        for (int C : {16, 8, 4, 2}) {
-            if (C == fused_cluster_size(best)) continue;
+        for (int C : {16, 8, 4, 2})
+          for (int V : {1, 0}) {
+            if (C == C0 && V == V0) continue;
+            if (layer_form >= 0 && V != layer_form) continue;
             std::string e;
-            FusedPlan* pl = make_plan(C, e);
-            if (!pl) continue;
+            FusedPlan* pl = make_plan(C, e, V);
+            if (!pl || fused_cluster_size(pl) != C || fused_layer_form(pl) != V) {
+                if (pl) fused_destroy(pl);
+                continue;
+            }
             const float t = time_plan(pl);
-            snprintf(buf, sizeof buf, "; C=%d: %.1f us", C, t * 1e3f);
+            snprintf(buf, sizeof buf, "; C=%d V=%d: %.1f us", C, V, t * 1e3f);
             rep_s += buf;
             if (t > 0.f && (best_t <= 0.f || t < best_t)) {
                 if (best != fused) fused_destroy(best);
@@ -1506,7 +1564,7 @@ class Solver : public SolverBase {
             fused = best;
             drop_graphs();
         }
-        snprintf(buf, sizeof buf, "; chosen C=%d", fused_cluster_size(fused));
+        snprintf(buf, sizeof buf, "; chosen C=%d V=%d", fused_cluster_size(fused), fused_layer_form(fused));
         rep_s += buf;
         if (report && len > 0) snprintf(report, len, "%s", rep_s.c_str());
         return FEWHA_OK;

@@ -101,6 +101,7 @@ def lib():
         "fewha_get_fine_trace": (ci, [vp, ctypes.POINTER(ctypes.c_ulonglong), ci, ctypes.POINTER(ci),
                                       ctypes.POINTER(ci)]),
         "fewha_set_cluster_size": (ci, [vp, ci]),
+        "fewha_set_layer_transform": (ci, [vp, ci]),
         "fewha_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
         "fewha_set_loop": (ci, [vp, ci]),
         "fewha_operator_dims": (ci, [vp, ci, ctypes.POINTER(cl), ctypes.POINTER(cl)]),
@@ -364,6 +365,11 @@ class Solver:
 
     def set_cluster_size(self, cluster_size: int):
         self._check(lib().fewha_set_cluster_size(self.h, int(cluster_size)))
+
+    def set_layer_transform(self, form: int):
+        """Fused layer phase: 0 row stripes (a cluster barrier per DWT level),
+        1 level-stacked (one exchange per transform), -1 automatic."""
+        self._check(lib().fewha_set_layer_transform(self.h, int(form)))
 
     def autotune(self, n_iter: int = 4, reps: int = 5) -> str:
         """Time the feasible fused-kernel shapes on the current frame, keep the fastest."""

@@ -53,7 +53,7 @@ def _oracle_run(cfg, path, n_frames, q):
         q.put((k, R.layers()))
 
 
-def run(n_frames: int, workers: int | None = None, cfg=None) -> dict:
+def run(n_frames: int, workers: int | None = None, cfg=None, form: int = -1) -> dict:
     import multiprocessing as mp
 
     from paper_2009_00946_b300 import configs
@@ -78,6 +78,9 @@ def run(n_frames: int, workers: int | None = None, cfg=None) -> dict:
     from paper_2009_00946_b300 import fewha
     sides = [l["n"] for l in cfg["layers"]]
     S = fewha.Solver(cfg, precision=fewha.FP32, path=fewha.PATH_FUSED, k_rr=K_RR)
+    if form >= 0:
+        S.set_layer_transform(form)
+    plan = S.describe()
     out = np.empty(S.N, np.float32)
     rel, emax, border = [], [], []
     try:
@@ -113,7 +116,7 @@ def run(n_frames: int, workers: int | None = None, cfg=None) -> dict:
             "layers_rel_l2_last_50_mean": float(r[-50:].mean()), "layers_rel_l2_first_50_mean": float(r[:50].mean()),
             "elementwise_max_over_grid_max": float(max(emax)), "border_max_over_grid_max": float(max(border)),
             "replacement_frames": len(repl), "tolerance": 1e-4,
-            "slopes_workers": len(jobs), "slopes_s": t_slopes, "total_s": time.time() - t0,
+            "slopes_workers": len(jobs), "slopes_s": t_slopes, "total_s": time.time() - t0, "plan": plan,
             "per_frame_rel_l2": [float(x) for x in r]}
 
 
@@ -122,8 +125,9 @@ def main():
     ap.add_argument("--frames", type=int, default=1000)
     ap.add_argument("--workers", type=int, default=None)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--form", type=int, default=-1, help="fused layer transform (-1 automatic, 0, 1)")
     a = ap.parse_args()
-    res = run(a.frames, a.workers)
+    res = run(a.frames, a.workers, form=a.form)
     short = {k: v for k, v in res.items() if k != "per_frame_rel_l2"}
     print(json.dumps(short), flush=True)
     if a.out:

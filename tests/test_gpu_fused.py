@@ -59,6 +59,9 @@ def test_fused_elt_frames_match_oracle(fw, elt_frames):
 
 
 def test_fused_matches_plain_fp32(fw, elt_frames):
+    """The fused and the plain FP32 paths evaluate the same recurrence with
+    different summation orders (the fused DWT is distributed), each within a
+    few 1e-5 of the FP64 oracle, so they agree to the sum of their errors."""
     cfg, S_in, _ = elt_frames
     with _fused(fw, cfg, k_rr=10) as A, fw.Solver(cfg, precision=fw.FP32, path=fw.PATH_PLAIN, k_rr=10) as B:
         for k in range(12):
@@ -66,7 +69,7 @@ def test_fused_matches_plain_fp32(fw, elt_frames):
                 S.set_frame(S_in[k])
                 S.solve(4, warm=True)
                 S.sync()
-            assert rel(A.vector(fw.VEC_C), B.vector(fw.VEC_C).astype(np.float64)) < 2e-5, k
+            assert rel(A.vector(fw.VEC_C), B.vector(fw.VEC_C).astype(np.float64)) < 5e-5, k
             assert rel(A.vector(fw.VEC_R), B.vector(fw.VEC_R).astype(np.float64)) < 1e-3, k
 
 
@@ -276,3 +279,46 @@ def test_fused_autotune_keeps_state_and_parity(fw, elt_frames):
             S.solve(4, warm=True)
             S.sync()
             assert rel(S.layers(), ref[k][0]) < 1e-4, (k, rep)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("name", ["c2_elt", "c1_plain", "ragged"])
+def test_both_layer_transforms_match_oracle(fw, name, form):
+    """The fused layer phase in each form -- row stripes with a cluster barrier
+    per DWT level, and the level-stacked transform with one exchange each way
+    -- against the oracle over frames across a residual replacement."""
+    cfg = ragged_cfg() if name == "ragged" else configs.ALL[name]()
+    nf = 4
+    S_in, _ = synth.frames(cfg, nf)
+    R = fo.Reconstructor(cfg)
+    sides = [l["n"] for l in cfg["layers"]]
+    with _fused(fw, cfg, k_rr=3) as S:
+        S.set_layer_transform(form)
+        assert ("level-stacked" if form else "row stripes") in S.describe()
+        for k in range(nf):
+            R.frame(S_in[k], 4, warm=True, k_rr=3)
+            S.set_frame(S_in[k].astype(np.float32))
+            S.solve(4, warm=True)
+            S.sync()
+            assert rel(S.layers(), R.layers()) < 1e-4, (name, form, k)
+            assert rel(S.vector(fw.VEC_C), R.state.c) < 1e-4, (name, form, k)
+            elementwise_check(S.layers(), R.layers(), sides, 1e-3, what=(name, form, k))
+
+
+@pytest.mark.parametrize("C", [4, 8, 16])
+def test_level_stacked_transform_every_cluster_shape(fw, elt_frames, C):
+    """The level-stacked layer phase on clusters of 4, 8 and 16 (column
+    stripes of 32, 16 and 8 columns, different row ownership tables)."""
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as S:
+        S.set_layer_transform(1)
+        try:
+            S.set_cluster_size(C)
+        except fw.FewhaError as e:
+            pytest.skip("no plan with clusters of %d: %s" % (C, e))
+        assert "level-stacked" in S.describe() and (" x %d CTAs" % C) in S.describe()
+        for k in range(3):
+            S.set_frame(S_in[k])
+            S.solve(4, warm=True)
+            S.sync()
+            assert rel(S.layers(), ref[k][0]) < 1e-4, (C, k)
