@@ -167,20 +167,45 @@ __device__ __forceinline__ void casc_cols_fwd(const FParams& P, const float* Z, 
         const float* in = (j == 1) ? Z : A + (n - (n >> (j - 2))) * R;
         float* oa = A + (n - (n >> (j - 1))) * R;
         const int ub = casc_base(n, j);
-        const int items = half << lR;
-        for (int e = tid; e < items; e += NT) {
-            const int k = e >> lR, c = e & (R - 1);
-            float a = 0.f, d = 0.f;
+        if (lR >= 2) {
+            // four neighbouring columns per thread: 16-byte loads and stores
+            const int l4 = lR - 2, items = half << l4;
+            for (int e = tid; e < items; e += NT) {
+                const int k = e >> l4, c = (e & ((1 << l4) - 1)) << 2;
+                float4 a = make_float4(0.f, 0.f, 0.f, 0.f), d = a;
 #pragma unroll
-            for (int t = 0; t < 6; ++t) {
-                const float v = in[((2 * k + t) & mask) * R + c];
-                a += P.h[t] * v;
-                d += P.g[t] * v;
+                for (int t = 0; t < 6; ++t) {
+                    const float4 v = *reinterpret_cast<const float4*>(in + ((2 * k + t) & mask) * R + c);
+                    a.x += P.h[t] * v.x;
+                    a.y += P.h[t] * v.y;
+                    a.z += P.h[t] * v.z;
+                    a.w += P.h[t] * v.w;
+                    d.x += P.g[t] * v.x;
+                    d.y += P.g[t] * v.y;
+                    d.z += P.g[t] * v.z;
+                    d.w += P.g[t] * v.w;
+                }
+                if (j < J) *reinterpret_cast<float4*>(oa + k * R + c) = a;
+                const int wa = own[ub + k], wd = own[ub + half + k];
+                *reinterpret_cast<float4*>(rUrow[wa >> 16] + (wa & 0xffff) * n + c0 + c) = a;
+                *reinterpret_cast<float4*>(rUrow[wd >> 16] + (wd & 0xffff) * n + c0 + c) = d;
             }
-            if (j < J) oa[e] = a;
-            const int wa = own[ub + k], wd = own[ub + half + k];
-            rUrow[wa >> 16][(wa & 0xffff) * n + c0 + c] = a;
-            rUrow[wd >> 16][(wd & 0xffff) * n + c0 + c] = d;
+        } else {
+            const int items = half << lR;
+            for (int e = tid; e < items; e += NT) {
+                const int k = e >> lR, c = e & (R - 1);
+                float a = 0.f, d = 0.f;
+#pragma unroll
+                for (int t = 0; t < 6; ++t) {
+                    const float v = in[((2 * k + t) & mask) * R + c];
+                    a += P.h[t] * v;
+                    d += P.g[t] * v;
+                }
+                if (j < J) oa[e] = a;
+                const int wa = own[ub + k], wd = own[ub + half + k];
+                rUrow[wa >> 16][(wa & 0xffff) * n + c0 + c] = a;
+                rUrow[wd >> 16][(wd & 0xffff) * n + c0 + c] = d;
+            }
         }
         __syncthreads();
     }
@@ -215,35 +240,42 @@ __device__ __forceinline__ void casc_rows_fwd(const FParams& P, const int* tab, 
     const int4* slots = reinterpret_cast<const int4*>(tab + 20);
     const int depth = tab[0] > 0 ? (slots[0].y & 255) : 0;
     for (int i = 1; i <= depth; ++i) {
+        // outputs k0, k0 + 1 (k0 even) per thread from inputs 2 k0 .. 2 k0 + 7
+        // (two 16-byte loads; half >= 2 at every level a row reaches)
         const int m = n >> (i - 1), half = m >> 1, mask = m - 1, lh = 31 - __clz(half);
         const float* in = (i & 1) ? Urow : T;
         const int ins = (i & 1) ? n : (n >> 1);
         float* out = (i & 1) ? T : Urow;
         const int outs = (i & 1) ? (n >> 1) : n;
-        const int items = tab[4 + i - 1] << lh;
+        const int items = tab[4 + i - 1] << (lh - 1);
         for (int e = tid; e < items; e += NT) {
-            const int s = e >> lh, k = e & (half - 1);
+            const int s = e >> (lh - 1), k0 = (e & ((half >> 1) - 1)) << 1;
             const int4 sl = slots[s];
             const float* x = in + s * ins;
-            const float2 v0 = *reinterpret_cast<const float2*>(x + 2 * k);
-            const float2 v1 = *reinterpret_cast<const float2*>(x + ((2 * k + 2) & mask));
-            const float2 v2 = *reinterpret_cast<const float2*>(x + ((2 * k + 4) & mask));
-            const float v[6] = {v0.x, v0.y, v1.x, v1.y, v2.x, v2.y};
-            float lo = 0.f;
+            const float4 q0 = *reinterpret_cast<const float4*>(x + 2 * k0);
+            const float4 q1 = *reinterpret_cast<const float4*>(x + ((2 * k0 + 4) & mask));
+            const float v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+            float lo0 = 0.f, lo1 = 0.f;
 #pragma unroll
-            for (int t = 0; t < 6; ++t) lo += P.h[t] * v[t];
+            for (int t = 0; t < 6; ++t) {
+                lo0 += P.h[t] * v[t];
+                lo1 += P.h[t] * v[t + 2];
+            }
             const int j = sl.y & 255;
             if (j > i) {
-                out[s * outs + k] = lo;
+                *reinterpret_cast<float2*>(out + s * outs + k0) = make_float2(lo0, lo1);
             } else {
-                float hi = 0.f;
+                float hi0 = 0.f, hi1 = 0.f;
 #pragma unroll
-                for (int t = 0; t < 6; ++t) hi += P.g[t] * v[t];
+                for (int t = 0; t < 6; ++t) {
+                    hi0 += P.g[t] * v[t];
+                    hi1 += P.g[t] * v[t + 2];
+                }
                 if (sl.y >> 8) {
-                    Zc[sl.w + k] = hi;
+                    *reinterpret_cast<float2*>(Zc + sl.w + k0) = make_float2(hi0, hi1);
                 } else {
-                    Zc[sl.w + k] = lo;
-                    Zc[sl.w + half + k] = hi;
+                    *reinterpret_cast<float2*>(Zc + sl.w + k0) = make_float2(lo0, lo1);
+                    *reinterpret_cast<float2*>(Zc + sl.w + half + k0) = make_float2(hi0, hi1);
                 }
             }
         }
@@ -261,40 +293,49 @@ __device__ __forceinline__ void casc_rows_inv(const FParams& P, const int* tab, 
     const int4* slots = reinterpret_cast<const int4*>(tab + 20);
     const int depth = tab[0] > 0 ? (slots[0].y & 255) : 0;
     for (int i = depth; i >= 1; --i) {
-        const int half = n >> i, lh = 31 - __clz(half);
+        // outputs 2 k0 .. 2 k0 + 3 (k0 even) per thread from the a and d
+        // entries k0 - 2 .. k0 + 1 (periodic)
+        const int half = n >> i, hmask = half - 1, lh = 31 - __clz(half);
         const float* prev = ((i + 1) & 1) ? Urow : T;   // level i + 1's output
         const int ps = ((i + 1) & 1) ? n : (n >> 1);
         float* out = (i & 1) ? Urow : T;
         const int outs = (i & 1) ? n : (n >> 1);
-        const int items = tab[4 + i - 1] << lh;
+        const int items = tab[4 + i - 1] << (lh - 1);
         for (int e = tid; e < items; e += NT) {
-            const int s = e >> lh, kk = e & (half - 1);
+            const int s = e >> (lh - 1), k0 = (e & ((half >> 1) - 1)) << 1;
             const int4 sl = slots[s];
             const int j = sl.y & 255;
             const bool isA = (sl.y >> 8) != 0;
-            float2 o = make_float2(0.f, 0.f);
+            float a[4], d[4];   // entries k0 - 2 + t
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = (k0 - 2 + t) & hmask;
+                if (j == i) {
+                    a[t] = isA ? 0.f : Zc[sl.w + k];
+                    d[t] = Zc[sl.w + (isA ? 0 : half) + k];
+                } else {
+                    a[t] = prev[s * ps + k];
+                    d[t] = 0.f;
+                }
+            }
+            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int sg = 0; sg < 3; ++sg) {
-                const int k = (kk - sg) & (half - 1);
-                float a, d;
-                if (j == i) {
-                    a = isA ? 0.f : Zc[sl.w + k];
-                    d = Zc[sl.w + (isA ? 0 : half) + k];
-                } else {
-                    a = prev[s * ps + k];
-                    d = 0.f;
-                }
-                o.x += P.h[2 * sg] * a + P.g[2 * sg] * d;
-                o.y += P.h[2 * sg + 1] * a + P.g[2 * sg + 1] * d;
+                // output pair k0 takes entry k0 - sg (index 2 - sg), pair k0 + 1 entry k0 + 1 - sg
+                o.x += P.h[2 * sg] * a[2 - sg] + P.g[2 * sg] * d[2 - sg];
+                o.y += P.h[2 * sg + 1] * a[2 - sg] + P.g[2 * sg + 1] * d[2 - sg];
+                o.z += P.h[2 * sg] * a[3 - sg] + P.g[2 * sg] * d[3 - sg];
+                o.w += P.h[2 * sg + 1] * a[3 - sg] + P.g[2 * sg + 1] * d[3 - sg];
             }
+            const int x = 2 * k0;
             if (i > 1) {
-                *reinterpret_cast<float2*>(out + s * outs + 2 * kk) = o;
-            } else if (R >= 2) {
-                const int x = 2 * kk;
-                *reinterpret_cast<float2*>(rUcol[x >> lR] + sl.x * R + (x & (R - 1))) = o;
+                *reinterpret_cast<float4*>(out + s * outs + x) = o;
+            } else if (lR >= 2) {
+                *reinterpret_cast<float4*>(rUcol[x >> lR] + sl.x * R + (x & (R - 1))) = o;
             } else {
-                rUcol[2 * kk][sl.x] = o.x;
-                rUcol[2 * kk + 1][sl.x] = o.y;
+                const float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) rUcol[(x + t) >> lR][sl.x * R + ((x + t) & (R - 1))] = ov[t];
             }
         }
         __syncthreads();
