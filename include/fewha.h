@@ -87,8 +87,9 @@ typedef struct {
     int    precision;                      /* FEWHA_FP32 or FEWHA_FP64, fixed at create         */
     int    lgs_tt_filter;                  /* 1: LGS sensors do not sense tip/tilt: their       */
                                            /* C^{-1} removes each slope axis' mean over active  */
-                                           /* subapertures (plain path only; the fused path,    */
-                                           /* batches and differentiation refuse it)            */
+                                           /* subapertures (plain path, and the fused path with */
+                                           /* the level-stacked layer phase; batches and        */
+                                           /* differentiation refuse it)                        */
     int    fit_mode;                       /* FEWHA_FIT_MCAO: every mirror over every fitting   */
                                            /* direction (one mirror, one direction: LTAO);      */
                                            /* FEWHA_FIT_MOAO: mirror t fitted in direction t    */
@@ -134,9 +135,9 @@ int fewha_sizes(const fewha_handle* h, long* n_coeff, long* n_slopes, long* n_ac
 /* Select the execution path for FP32 handles (FP64 handles always use the
  * plain path).  Default: FEWHA_PATH_FUSED for FP32 when a fused plan exists
  * for the geometry, else FEWHA_PATH_PLAIN.  Requesting FEWHA_PATH_FUSED
- * without a plan returns FEWHA_ERR_GEOMETRY (fewha_last_error says why: the
- * LGS tip-tilt filter, too many layers or sensors, shared memory) and keeps
- * the current path. */
+ * without a plan returns FEWHA_ERR_GEOMETRY (fewha_last_error says why: too
+ * many layers or sensors, shared memory, the LGS tip-tilt filter on a plan
+ * that only fits the row-stripe layer phase) and keeps the current path. */
 int fewha_set_path(fewha_handle* h, int path);
 
 /* Residual replacement period k_rr (Alg. 1 warm restart, reading: every

@@ -106,8 +106,6 @@ int fewha_set_path(fewha_handle* h, int path) {
     if (path != FEWHA_PATH_PLAIN && path != FEWHA_PATH_FUSED) return fail(h, FEWHA_ERR_ARG, "unknown path");
     if (path == FEWHA_PATH_FUSED && h->s->hs.prec != FEWHA_FP32)
         return fail(h, FEWHA_ERR_ARG, "the fused path is FP32 only");
-    if (path == FEWHA_PATH_FUSED && h->s->hs.any_tt)
-        return fail(h, FEWHA_ERR_ARG, "the fused path does not model the LGS tip-tilt filter");
     if (path == FEWHA_PATH_FUSED && !h->s->fused_available)
         return fail(h, FEWHA_ERR_GEOMETRY, "no fused plan for this geometry: " + h->s->fused_reason);
     h->s->path = path;

@@ -82,6 +82,14 @@ struct FInst {
     // all four tags match, with no flag and no release / acquire round trip
     // (zeroed at launch start)
     unsigned long long* pubAB;
+    // LGS tip-tilt filter (reading R15; level-stacked plans): per sensor the
+    // flag, its active subapertures, its tiles [x, x + y) in the item list,
+    // and the node fields Gamma^T (mask 1_x), Gamma^T (mask 1_y) ([2][NW])
+    int tt_any;
+    const int* tt;
+    const int* nact;
+    const int2* tt_tiles;
+    const float* ttv;
 };
 
 struct WItem { int inst, g, i0, i1, j0, j1; };
@@ -94,6 +102,7 @@ struct FParams {
     const LItem* litems;
     const int2* stg;       // Pt staging row ranges per (layer item, rank, sensor)
     float2* wpart;         // [n_witems] data part of mu, double-float (hi, lo)
+    float4* tpart;         // [n_witems] tip-tilt filtered sensors: sums of the masked x and y slopes (df pairs)
     float4* lpart;         // [2][n_litems * C] (rho hi, lo, alpha D z.z hi, lo)
     // static work lists: sensor tiles of CTA b are wsched[wsched_off[b] ..
     // wsched_off[b+1]), layer items of cluster k lsched[lsched_off[k] ..)
@@ -417,7 +426,27 @@ __device__ void alg2_part_b(const FParams& P, const FInst& I, int k, const ScalA
     warp_df_sum(wh, wl);
     float mh = A.mh, ml = A.ml;
     df_add(mh, ml, wh, wl);
-    const double mu = df_to_double(mh, ml);
+    double mu = df_to_double(mh, ml);
+    if (I.tt_any) {
+        // filtered sensors: s^T C^{-1} s = w (sum mask s^2 - (sum mask s)^2 / n_act)
+        // per axis; the tiles summed the masked slopes, here the square terms go
+        double corr = 0.0;
+        for (int g = 0; g < I.G; ++g) {
+            if (!I.tt[g]) continue;
+            const int2 tr = I.tt_tiles[g];
+            float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
+            for (int e = lane; e < tr.y; e += 32) {
+                const float4 v = __ldcg(P.tpart + tr.x + e);
+                df_add(xh, xl, v.x, v.y);
+                df_add(yh, yl, v.z, v.w);
+            }
+            warp_df_sum(xh, xl);
+            warp_df_sum(yh, yl);
+            const double Mx = df_to_double(xh, xl), My = df_to_double(yh, yl);
+            corr += (double)I.wfs_w[g] * (Mx * Mx + My * My) / (double)I.nact[g];
+        }
+        mu -= corr;
+    }
     const double denom = (k > 0) ? mu - A.t : mu;
     double a = A.rho / denom;
     double beta = A.beta;
@@ -567,7 +596,8 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     float* rw = (float*)(roff + L * P.tile_rows);
     int* coff = (int*)(rw + L * P.tile_rows);
     float* cw = (float*)(coff + L * P.tile_cols);
-    Acc2 mu;
+    Acc2 mu, tmx, tmy;   // tmx, tmy: masked slope sums of a tip-tilt filtered sensor
+    const bool ttg = I.tt_any && I.tt[g];
     const int ns2 = ns * ns;
     if (mode != kModeRhs) {
         const bool build = !cc->wtab;
@@ -724,6 +754,10 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 mu.add_prod3(wm, sx, sx);
                 mu.add_prod3(wm, sy, sy);
             }
+            if (ttg && wm != 0.f && a >= W.i0 && b >= W.j0) {
+                tmx.add(sx);
+                tmy.add(sy);
+            }
         }
     } else {
         const float w = cc->w;
@@ -742,6 +776,10 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
             if (on && (!fx || !fy) && a >= W.i0 && b >= W.j0) atomicOr(P.errw, kErrInput);
             slx[e] = (on && fx) ? w * vx : 0.f;
             sly[e] = (on && fy) ? w * vy : 0.f;
+            if (ttg && on && a >= W.i0 && b >= W.j0) {
+                tmx.add(fx ? vx : 0.f);
+                tmy.add(fy ? vy : 0.f);
+            }
         }
     }
     __syncthreads();
@@ -766,6 +804,11 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     if (want_mu) {
         const float4 s = block_reduce2(mu, Acc2(), (float4*)red);
         if (tid == 0) P.wpart[item] = make_float2(s.x, s.y);
+    }
+    if (ttg) {
+        __syncthreads();   // red is reused
+        const float4 s = block_reduce2(tmx, tmy, (float4*)red);
+        if (tid == 0) P.tpart[item] = s;
     }
     __syncthreads();
     fmark(P, 24);
@@ -1810,6 +1853,12 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
     for (auto [C, V] : cand) {
         if (forced_C > 0 && C != forced_C) continue;
         if (forced_V >= 0 && V != forced_V) continue;
+        bool any_tt = false;
+        for (const HostSetup* h : hss) any_tt = any_tt || h->any_tt;
+        if (V == 0 && any_tt) {
+            if (err.empty()) err = "the row-stripe layer phase does not model the LGS tip-tilt filter";
+            continue;
+        }
         if (V == 0) {
             if (2 * C > nmin) continue;   // stripes of at least 2 rows
             if ((size_t)nmax * nmax / C * 4 * sizeof(float) > smem_cap) continue;
@@ -1937,6 +1986,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         // max_tile_side > 0 no side longer than that (bounded windows)
         std::vector<WItem> witems;
         std::vector<int> w0(ninst), nw(ninst);
+        std::vector<std::vector<int2>> tt_tiles(ninst);   // per instance, per sensor: its tiles
         // a few instances: the last CTAs of the grid compute part A of the CG
         // scalars (one per instance) instead of a sensor tile
         const int n_res = (ninst <= 4 && ninst * 8 <= pl->grid) ? ninst : 0;
@@ -1961,7 +2011,9 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
                             best_tx = tx;
                         }
                     }
+                const int t0 = (int)witems.size();
                 make_tiles(i, g, np1, best_ty, best_tx, witems);
+                tt_tiles[i].push_back(make_int2(t0, (int)witems.size() - t0));
             }
             nw[i] = (int)witems.size() - w0[i];
         }
@@ -2062,7 +2114,37 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             I.preA_cta = (i < n_res) ? tile_ctas + i : -1;
             I.preA = nullptr;
             I.pubAB = nullptr;
-            ok = dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) && dalloc(pl, I.preA, 12, err) &&
+            // LGS tip-tilt filter: per sensor flag, active count, tile range, and
+            // the node fields Gamma^T (mask 1_x), Gamma^T (mask 1_y) (exact halves)
+            I.tt_any = hs.any_tt ? 1 : 0;
+            I.tt = G.wfs_tt;
+            I.nact = G.wfs_nact;
+            int2* d_ttt = nullptr;
+            float* d_ttv = nullptr;
+            if (hs.any_tt) {
+                std::vector<float> ttv(2 * (size_t)hs.NW, 0.f);
+                for (int g = 0; g < hs.G; ++g) {
+                    if (!hs.wfs[g].tt) continue;
+                    const int ns = hs.wfs[g].n, np1 = ns + 1;
+                    for (int ii = 0; ii <= ns; ++ii)
+                        for (int jj = 0; jj <= ns; ++jj) {
+                            double ax = 0.0, ay = 0.0;
+                            for (int a = ii - 1; a <= ii; ++a)
+                                for (int b = jj - 1; b <= jj; ++b) {
+                                    if (a < 0 || a >= ns || b < 0 || b >= ns) continue;
+                                    if (!hs.mask[hs.wfs[g].moff + (long)a * ns + b]) continue;
+                                    ax += (b == jj - 1) ? 0.5 : -0.5;
+                                    ay += (a == ii - 1) ? 0.5 : -0.5;
+                                }
+                            ttv[hs.wfs[g].noff + (long)ii * np1 + jj] = (float)ax;
+                            ttv[hs.NW + hs.wfs[g].noff + (long)ii * np1 + jj] = (float)ay;
+                        }
+                }
+                ok = ok && dupload(pl, d_ttv, ttv, err) && dupload(pl, d_ttt, tt_tiles[i], err);
+            }
+            I.ttv = d_ttv;
+            I.tt_tiles = d_ttt;
+            ok = ok && dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) && dalloc(pl, I.preA, 12, err) &&
                  dalloc(pl, I.pubAB, 8, err) &&
                  dupload(pl, d_gtab, preps[i].gtab, err) && dupload(pl, d_gtab_off, preps[i].gtab_off, err);
             I.gtab = d_gtab;
@@ -2097,11 +2179,13 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         int4* ds4 = nullptr;
         int* dcs = nullptr;
         float2* wp = nullptr;
+        float4* tp = nullptr;
         float4* lp = nullptr;
         unsigned* bar = nullptr;
         ok = ok && dupload(pl, dw, witems, err) && dupload(pl, dl, litems, err) && dupload(pl, ds, stg, err) &&
              dupload(pl, ds4, stg4, err) && dupload(pl, dcs, cshape, err) &&
-             dalloc(pl, wp, witems.size(), err) && dalloc(pl, lp, 2 * litems.size() * C, err) &&
+             dalloc(pl, wp, witems.size(), err) && dalloc(pl, tp, witems.size(), err) &&
+             dalloc(pl, lp, 2 * litems.size() * C, err) &&
              dalloc(pl, bar, 2, err) && dupload(pl, pl->d_inst, pl->inst, err);
         if (!ok) {
             fused_destroy(pl);
@@ -2121,6 +2205,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         P.res_first = tile_ctas;
         P.n_res = n_res;
         P.wpart = wp;
+        P.tpart = tp;
         P.lpart = lp;
         P.bar = bar;
         P.errw = fbs[0].errw;

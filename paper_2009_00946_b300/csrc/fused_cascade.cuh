@@ -441,6 +441,53 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
         cp_async_wait_all();
         if (tabs && tid == 0) cc->ltkey = li;
         __syncthreads();
+        if (I.tt_any) {
+            // LGS tip-tilt filter (R15): Gamma^T C^{-1} s = Gamma^T (w mask s) -
+            // (w / n_act) (M_x Gamma^T (mask 1_x) + M_y Gamma^T (mask 1_y)) with
+            // M the sensor's masked slope sums (from its tiles' partials): the
+            // staged fields of a filtered sensor get the rank-2 term here
+            float* ttc = reinterpret_cast<float*>(red);   // [g][2]
+            const int wid = tid >> 5, lane = tid & 31;
+            if (wid < G) {
+                float cx = 0.f, cy = 0.f;
+                if (I.tt[wid]) {
+                    const int2 tr = I.tt_tiles[wid];
+                    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
+                    for (int e = lane; e < tr.y; e += 32) {
+                        const float4 v = __ldcg(P.tpart + tr.x + e);
+                        df_add(xh, xl, v.x, v.y);
+                        df_add(yh, yl, v.z, v.w);
+                    }
+                    warp_df_sum(xh, xl);
+                    warp_df_sum(yh, yl);
+                    const double f = (double)I.wfs_w[wid] / (double)I.nact[wid];
+                    cx = (float)(f * df_to_double(xh, xl));
+                    cy = (float)(f * df_to_double(yh, yl));
+                }
+                if (lane == 0) {
+                    ttc[2 * wid] = cx;
+                    ttc[2 * wid + 1] = cy;
+                }
+            }
+            __syncthreads();
+            for (int g = 0; g < G; ++g) {
+                if (!I.tt[g]) continue;
+                const int ilo = sgi[g * 8], rows = sgi[g * 8 + 1] - ilo, W = sgi[g * 8 + 5];
+                if (rows <= 0 || W == 0) continue;
+                const int np1 = sgi[g * 8 + 3], jlo = sgi[g * 8 + 4], s0 = sgi[g * 8 + 6];
+                const int wc = P.stg4[cc->LI.stg + rank * G + g].w - jlo;   // staged columns
+                const float cx = ttc[2 * g], cy = ttc[2 * g + 1];
+                const float* vx = I.ttv + I.wfs_noff[g];
+                const float* vy = vx + I.NW;
+                float* dst = stg + sgi[g * 8 + 2];
+                for (int e = tid; e < rows * wc; e += NT) {
+                    const int rr = e / wc, jj = e - rr * wc, i = ilo + rr;
+                    const int node = i * np1 + jlo + jj;
+                    dst[rr * W + ((s0 + i * np1) & 3) + jj] -= cx * __ldg(vx + node) + cy * __ldg(vy + node);
+                }
+            }
+            __syncthreads();
+        }
         fmark(P, 11);
         switch (KG) {
             case 1: pt_gather_cols<1>(sgi, stg, xt, yt, Z, G, n, R); break;

@@ -1989,10 +1989,10 @@ SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& e
         fb.errw = s->errw;
         std::string ferr;
         s->fbuf = fb;
-        s->fused = hs.any_tt ? nullptr : fused_create(hs, s->G, fb, ferr);
+        s->fused = fused_create(hs, s->G, fb, ferr);
         s->path = s->fused ? FEWHA_PATH_FUSED : FEWHA_PATH_PLAIN;
         s->fused_available = s->fused != nullptr;
-        s->fused_reason = hs.any_tt ? "the fused path does not model the LGS tip-tilt filter" : ferr;
+        s->fused_reason = ferr;
         out = s;
     }
     status = FEWHA_OK;
