@@ -176,6 +176,48 @@ def cpu_oracle_latency(cfg, n_frames, pool_np, keep=None):
     return times
 
 
+def _oracle_stream(args):
+    """One worker of the all-core baseline: the unmodified oracle over its own
+    frozen-flow frames (its own seed), per-frame latencies (us)."""
+    cfg, seed, n = args
+    pool = slope_pool(cfg, n, seed=seed)
+    return cpu_oracle_latency(cfg, n, pool)
+
+
+def cpu_oracle_all_cores(cfg, frames_per_core=6):
+    """The oracle on every host core at once: one independent frame stream per
+    core (spawned processes, each the unmodified one-thread oracle), wall time
+    of the whole, aggregate frames per second.  The oracle's per-frame work is
+    not split over layers or sensors: its numpy operators on 128^2 layers are
+    too small for threads (the interpreter lock serialises them) or for
+    process fan-out (each task would move about 1 MB for 5 ms of work)."""
+    import multiprocessing as mp
+    cores = max(1, os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    jobs = [(cfg, int(cfg["seed"]) + 1000 + i, frames_per_core) for i in range(cores)]
+    # one thread per process (the children inherit the environment)
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        t0 = time.perf_counter()
+        with ctx.Pool(cores) as p:
+            res = p.map(_oracle_stream, jobs)
+        wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    lat = [x for r in res for x in r[1:]]   # first frame of each stream: warm-up
+    return {"frames_per_s": cores * frames_per_core / wall, "wall_s": wall, "cores": cores,
+            "per_frame_p50_us": float(np.percentile(lat, 50)), "kind": "oracle",
+            "sample": "%d independent streams x %d ELT frames (one per host core, spawned processes; process "
+                      "start and frame synthesis inside the wall time)" % (cores, frames_per_core)}
+
+
 def parity_vs_oracle(fewha, cfg, pool, oracle_layers):
     """The same frames through a fresh FP32 fused handle (host buffers, one
     graph per frame): relative L2 error of the layers against the oracle's."""
@@ -193,15 +235,24 @@ def parity_vs_oracle(fewha, cfg, pool, oracle_layers):
 
 # DRAM bytes (read + write) of one k_fused_frame launch on this workload from
 # the committed full ncu capture, valid only for the kernel source it was
-# taken on (sha256 prefix of csrc/fused.cu); any other source reports null.
-NCU_TRAFFIC = {"fused_cu_sha256": "6a19b73df3f994f9", "dram_bytes": 5561344,
+# taken on (sha256 prefix of csrc/fused.cu + csrc/fused_cascade.cuh); any
+# other source reports null.
+NCU_TRAFFIC = {"fused_cu_sha256": "8cf59ab2f52e2aca", "dram_bytes": 5647616,
                "summary": "profiles/k_fused_frame_elt_full.md"}
 
 
-def fused_traffic():
+def fused_source_sha():
+    """sha256 of the fused frame kernel's sources (fused.cu + fused_cascade.cuh)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2009_00946_b300", "csrc", "fused.cu"), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("fused.cu", "fused_cascade.cuh"):
+        with open(os.path.join(ROOT, "paper_2009_00946_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def fused_traffic():
+    sha = fused_source_sha()
     return NCU_TRAFFIC["dram_bytes"] if sha.startswith(NCU_TRAFFIC["fused_cu_sha256"]) else None
 
 
@@ -586,6 +637,23 @@ def profile_mode(args):
     S.close()
 
 
+def profile_batch_mode(args):
+    """Stream launches of the 64-instance batch (for ncu): W + K batch frames
+    on device buffers with the default plan (no autotuning)."""
+    import torch
+    from paper_2009_00946_b300 import fewha
+    cfgs = configs.c4_batch(64)
+    per = [synth.random_slopes(c, 7).astype(np.float32) for c in cfgs]
+    B = fewha.Batch(cfgs, k_rr=K_RR)
+    s = torch.from_numpy(B.concat_slopes(per)).cuda()
+    lay = torch.empty(B.N, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        B.frame(s, N_ITER, True, lay)
+    B.sync()
+    print(json.dumps({"profile_batch": True, "frames": args.warmup + args.steps, "plan": B.describe()}), flush=True)
+    B.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -596,6 +664,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the 35-layer fit and 64-instance batch lines")
     ap.add_argument("--profile", action="store_true", help="stream launches only (for ncu), no timing")
+    ap.add_argument("--profile-batch", action="store_true", help="batch launches only (for ncu), no timing")
     ap.add_argument("--sweep", action="store_true", help="operator and frame timings against the size")
     ap.add_argument("--trace-out", default=None, help="with --profile: save the raw phase traces (.npy)")
     args = ap.parse_args()
@@ -606,6 +675,9 @@ def main():
         return
     if args.profile:
         profile_mode(args)
+        return
+    if args.profile_batch:
+        profile_batch_mode(args)
         return
     if args.sweep:
         sweep_mode(args)
@@ -626,6 +698,7 @@ def main():
         cpu = {"value": float(np.percentile(t, 50)), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "28 ELT frames (after 2 warm-up frames), FP64 numpy oracle, one host thread (%d cores "
                          "on the host)" % os.cpu_count()}
+        cpu_all = cpu_oracle_all_cores(cfg)
 
     import torch
     torch.cuda.set_device(local_rank)
@@ -674,7 +747,7 @@ def main():
     # ---- end to end: pinned host slopes in, layers out, through fewha_frame ----
     pin_s = torch.empty(S.S, dtype=torch.float32).pin_memory()
     pin_l = torch.empty(S.N, dtype=torch.float32).pin_memory()
-    e2e = []
+    e2e, e2e_ft = [], []
     n_e2e = min(K, 300)
     for k in range(n_e2e + 5):
         pin_s.numpy()[:] = pool[(W + K + k) % len(pool)]
@@ -684,7 +757,32 @@ def main():
         t0 = time.perf_counter()
         S.frame(pin_s.numpy(), N_ITER, warm=True, layers_out=pin_l.numpy())
         e2e.append((time.perf_counter() - t0) * 1e6)
-    e2e = e2e[5:]
+        e2e_ft.append(S.frame_timing())
+    e2e, e2e_ft = e2e[5:], e2e_ft[5:]
+    # the same host frames bracketed by CUDA events (the kernel reading and
+    # writing the pinned buffers through their device mapping), the GPU kept
+    # busy by the flush so the host's side does not show as idle time
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
+    for k in range(50):
+        with torch.cuda.stream(S.stream):
+            flush.fill_(3.0)
+        ev[k][0].record(S.stream)
+        S.frame(pin_s.numpy(), N_ITER, warm=True, layers_out=pin_l.numpy())
+        ev[k][1].record(S.stream)
+    S.stream.synchronize()
+    e2e_dev = float(np.percentile([a.elapsed_time(b) * 1e3 for a, b in ev], 50))
+    e2e_breakdown = {
+        "host_prep_us": float(np.median([f["prep_us"] for f in e2e_ft])),
+        "host_launch_us": float(np.median([f["launch_us"] for f in e2e_ft])),
+        "host_wait_us": float(np.median([f["wait_us"] for f in e2e_ft])),
+        "library_call_us": float(np.median([f["total_us"] for f in e2e_ft])),
+        "device_frame_with_host_io_us": e2e_dev,
+        "host_io_in_kernel_us": e2e_dev - p50,
+        "host_io_bytes": (S.S + S.N) * 4,
+        "host_io_gbs": (S.S + S.N) * 4 / max(e2e_dev - p50, 1e-3) / 1e3,
+        "what": "library_call = prep + launch + wait (host steady clock inside fewha_frame); the rest of the "
+                "e2e value is the Python call; host_io_in_kernel = device time of a host frame minus the device "
+                "p50 (slopes read, layers written through the pinned buffers' device mapping)"}
 
     # ---- the plain FP64 path (one kernel per operator) on the same frames ----
     P64 = fewha.Solver(cfg, precision=fewha.FP64, k_rr=K_RR)
@@ -735,6 +833,7 @@ def main():
                        "frames": n64},
         "e2e": {"value": float(np.percentile(e2e, 50)), "unit": UNIT, "p99": float(np.percentile(e2e, 99)),
                 "h2d_bytes_per_step": S.S * 4, "d2h_bytes_per_step": S.N * 4, "frames": n_e2e,
+                "breakdown": e2e_breakdown,
                 "how": "fewha_frame with pinned host slopes and layers (read and written by the kernel through their device mapping; the host waits on the mapped completion word), host wall clock per frame"},
         "gpu_launches": int(launches),
         "roofline": roofline,
@@ -746,6 +845,7 @@ def main():
     }
     if cpu:
         line["cpu_baseline"] = cpu
+        line["cpu_baseline_all_cores"] = cpu_all
     if parity:
         line["parity"] = parity
     print(json.dumps(line), flush=True)

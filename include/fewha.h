@@ -222,6 +222,15 @@ int fewha_time_operator(fewha_handle* h, int op, int reps, double* us_per_applic
 int fewha_frame(fewha_handle* h, const void* slopes, int n_iter, int warm_start,
                 double gain, int n_fit, void* layers_out, void* dm_out, int on_device);
 
+/* Profiling aid: host-side timing of the last fewha_frame on this handle, in
+ * microseconds of the host's steady clock: out[0] preparation (argument
+ * checks, pointer lookups, graph capture or re-pointing), out[1] the graph
+ * launch call, out[2] the wait for the results (host frames on the fused
+ * path: until the completion word is seen; 0 for device frames), out[3] the
+ * whole call; out[4] = 1 if the captured kernel node was re-pointed at other
+ * buffers, out[5] = 1 if the graph was (re)captured.  Errors: ARG. */
+int fewha_get_frame_timing(fewha_handle* h, double* out);
+
 /* Loop mode of Alg. 1 (default open).  closed = 1: every frame first forms
  * the pseudo-open-loop slopes s + Gamma P_DM a^(-1) -- the measurements the
  * mirror shapes of two frames back add in every sensor: mirror m (height h_m)

@@ -170,6 +170,11 @@ int fewha_frame(fewha_handle* h, const void* slopes, int n_iter, int warm_start,
     return done(h, h->s->frame(slopes, n_iter, warm_start, gain, n_fit, layers_out, dm_out, on_device));
 }
 
+int fewha_get_frame_timing(fewha_handle* h, double* out) {
+    if (!h || !out) return FEWHA_ERR_ARG;
+    return done(h, h->s->get_frame_timing(out));
+}
+
 int fewha_operator_dims(fewha_handle* h, int op, long* n_in, long* n_out) {
     if (!h || !n_in || !n_out) return FEWHA_ERR_ARG;
     return done(h, h->s->operator_dims(op, *n_in, *n_out));

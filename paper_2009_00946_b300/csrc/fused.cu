@@ -84,12 +84,14 @@ struct FInst {
     unsigned long long* pubAB;
     // LGS tip-tilt filter (reading R15; level-stacked plans): per sensor the
     // flag, its active subapertures, its tiles [x, x + y) in the item list,
-    // and the node fields Gamma^T (mask 1_x), Gamma^T (mask 1_y) ([2][NW])
+    // and the nodes where Gamma^T (mask 1_x) or Gamma^T (mask 1_y) is nonzero
+    // (entries [x, x + y) of tt_nz: node in the sensor, the two values' bits)
     int tt_any;
     const int* tt;
     const int* nact;
     const int2* tt_tiles;
-    const float* ttv;
+    const int2* tt_nzr;
+    const int4* tt_nz;
 };
 
 struct WItem { int inst, g, i0, i1, j0, j1; };
@@ -2120,10 +2122,13 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             I.tt = G.wfs_tt;
             I.nact = G.wfs_nact;
             int2* d_ttt = nullptr;
-            float* d_ttv = nullptr;
+            int2* d_nzr = nullptr;
+            int4* d_nz = nullptr;
             if (hs.any_tt) {
-                std::vector<float> ttv(2 * (size_t)hs.NW, 0.f);
+                std::vector<int4> nz;
+                std::vector<int2> nzr(hs.G, make_int2(0, 0));
                 for (int g = 0; g < hs.G; ++g) {
+                    nzr[g].x = (int)nz.size();
                     if (!hs.wfs[g].tt) continue;
                     const int ns = hs.wfs[g].n, np1 = ns + 1;
                     for (int ii = 0; ii <= ns; ++ii)
@@ -2136,13 +2141,21 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
                                     ax += (b == jj - 1) ? 0.5 : -0.5;
                                     ay += (a == ii - 1) ? 0.5 : -0.5;
                                 }
-                            ttv[hs.wfs[g].noff + (long)ii * np1 + jj] = (float)ax;
-                            ttv[hs.NW + hs.wfs[g].noff + (long)ii * np1 + jj] = (float)ay;
+                            if (ax != 0.0 || ay != 0.0) {
+                                const float fx = (float)ax, fy = (float)ay;
+                                int bx, by;
+                                std::memcpy(&bx, &fx, 4);
+                                std::memcpy(&by, &fy, 4);
+                                nz.push_back(make_int4(ii * np1 + jj, bx, by, 0));
+                            }
                         }
+                    nzr[g].y = (int)nz.size() - nzr[g].x;
                 }
-                ok = ok && dupload(pl, d_ttv, ttv, err) && dupload(pl, d_ttt, tt_tiles[i], err);
+                ok = ok && dupload(pl, d_nz, nz, err) && dupload(pl, d_nzr, nzr, err) &&
+                     dupload(pl, d_ttt, tt_tiles[i], err);
             }
-            I.ttv = d_ttv;
+            I.tt_nz = d_nz;
+            I.tt_nzr = d_nzr;
             I.tt_tiles = d_ttt;
             ok = ok && dalloc(pl, I.psi, hs.NW + 8, err) && dalloc(pl, I.scal, 4, err) && dalloc(pl, I.preA, 12, err) &&
                  dalloc(pl, I.pubAB, 8, err) &&

@@ -472,18 +472,21 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
             __syncthreads();
             for (int g = 0; g < G; ++g) {
                 if (!I.tt[g]) continue;
-                const int ilo = sgi[g * 8], rows = sgi[g * 8 + 1] - ilo, W = sgi[g * 8 + 5];
-                if (rows <= 0 || W == 0) continue;
+                const int ilo = sgi[g * 8], ihi = sgi[g * 8 + 1], W = sgi[g * 8 + 5];
+                if (ihi <= ilo || W == 0) continue;
                 const int np1 = sgi[g * 8 + 3], jlo = sgi[g * 8 + 4], s0 = sgi[g * 8 + 6];
-                const int wc = P.stg4[cc->LI.stg + rank * G + g].w - jlo;   // staged columns
+                const int jhi = P.stg4[cc->LI.stg + rank * G + g].w;   // staged columns [jlo, jhi)
                 const float cx = ttc[2 * g], cy = ttc[2 * g + 1];
-                const float* vx = I.ttv + I.wfs_noff[g];
-                const float* vy = vx + I.NW;
                 float* dst = stg + sgi[g * 8 + 2];
-                for (int e = tid; e < rows * wc; e += NT) {
-                    const int rr = e / wc, jj = e - rr * wc, i = ilo + rr;
-                    const int node = i * np1 + jlo + jj;
-                    dst[rr * W + ((s0 + i * np1) & 3) + jj] -= cx * __ldg(vx + node) + cy * __ldg(vy + node);
+                // only nodes next to a mask edge have a nonzero term: the sensor's
+                // list of them (node, Gamma^T (mask 1_x), Gamma^T (mask 1_y))
+                const int2 nr = I.tt_nzr[g];
+                for (int e = tid; e < nr.y; e += NT) {
+                    const int4 nz = __ldg(I.tt_nz + nr.x + e);
+                    const int i = nz.x / np1, j = nz.x - i * np1;
+                    if (i < ilo || i >= ihi || j < jlo || j >= jhi) continue;
+                    dst[(i - ilo) * W + ((s0 + i * np1) & 3) + (j - jlo)] -=
+                        cx * __int_as_float(nz.y) + cy * __int_as_float(nz.z);
                 }
             }
             __syncthreads();

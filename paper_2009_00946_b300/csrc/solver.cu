@@ -1745,8 +1745,39 @@ class Solver : public SolverBase {
         return FEWHA_OK;
     }
 
+    // host-side timing of the last fewha_frame (us): preparation (pointer
+    // lookups, graph capture or re-pointing), the graph launch call, the wait
+    // for the results, the whole call; then 1 if the kernel node was
+    // re-pointed, 1 if the graph was captured
+    double ftime[6] = {0, 0, 0, 0, 0, 0};
+
+    int get_frame_timing(double* out) override {
+        for (int i = 0; i < 6; ++i) out[i] = ftime[i];
+        return FEWHA_OK;
+    }
+
     int frame(const void* s_in, int n_iter, int warm, double gain, int n_fit, void* lout, void* dout,
               int on_device) override {
+        using clk = std::chrono::steady_clock;
+        const auto T0 = clk::now();
+        auto T1 = T0, T2 = T0, T3 = T0;
+        auto us = [](clk::time_point a, clk::time_point b) {
+            return std::chrono::duration<double, std::micro>(b - a).count();
+        };
+        struct Stamp {   // fills ftime however the call returns
+            double* f;
+            clk::time_point t0;
+            clk::time_point *t1, *t2, *t3;
+            decltype(us)& u;
+            ~Stamp() {
+                const auto t4 = clk::now();
+                f[0] = u(t0, *t1);
+                f[1] = u(*t1, *t2);
+                f[2] = u(*t2, *t3);
+                f[3] = u(t0, t4);
+            }
+        } stamp{ftime, T0, &T1, &T2, &T3, us};
+        ftime[4] = ftime[5] = 0.0;
         if (!s_in) {
             err = "null slopes";
             return FEWHA_ERR_ARG;
@@ -1809,7 +1840,10 @@ class Solver : public SolverBase {
         key.k_rr = k_rr;
         if (gexec[slot] && !(gkey[slot] == key) && gknode[slot] && direct && gkey[slot].same_work(key) &&
             fused_repoint_node(gexec[slot], gknode[slot], (const float*)sin_dev, (float*)lo_dev) == 0)
+        {
             gkey[slot] = key;   // the same frame on other buffers: re-pointed in place
+            ftime[4] = 1.0;
+        }
         if (!gexec[slot] || !(gkey[slot] == key)) {
             if (stream == 0) {
                 err = "fewha_frame needs a non-default stream (graph capture)";
@@ -1891,12 +1925,15 @@ class Solver : public SolverBase {
             cudaGetLastError();
             gkey[slot] = key;
             graph_launch_count[slot] = gl;
+            ftime[5] = 1.0;
         }
         if (use_done) {
             *(volatile unsigned long long*)done_host = 0ull;   // before the launch that sets it
             std::atomic_thread_fence(std::memory_order_seq_cst);
         }
+        T1 = clk::now();
         FEWHA_CUDA(cudaGraphLaunch(gexec[slot], stream));
+        T2 = T3 = clk::now();
         launches += graph_launch_count[slot];
         frame_count += 1;
         have_frame = true;
@@ -1909,7 +1946,10 @@ class Solver : public SolverBase {
             const auto t0 = std::chrono::steady_clock::now();
             for (long it = 0;; ++it) {
                 v = *(volatile unsigned long long*)done_host;
-                if (v >> 32) break;
+                if (v >> 32) {
+                    T3 = clk::now();
+                    break;
+                }
                 if ((it & 1023) == 1023 && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) break;
             }
             if (!(v >> 32)) {

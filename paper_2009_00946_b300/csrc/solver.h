@@ -113,6 +113,7 @@ class SolverBase {
     virtual int get_fine_trace(unsigned long long* out, int max_entries, int* per_cta, int* grid) = 0;
     virtual int set_cluster_size(int C) = 0;
     virtual int set_layer_transform(int form) = 0;
+    virtual int get_frame_timing(double* out) = 0;
     virtual int autotune(int n_iter, int reps, char* report, int len) = 0;
     virtual int set_params(const double* cn2, double alpha, const double* w) = 0;
     virtual int solve_taped(const void* slopes, int n_iter, void* tape, void* layers_out) = 0;

@@ -102,6 +102,7 @@ def lib():
                                       ctypes.POINTER(ci)]),
         "fewha_set_cluster_size": (ci, [vp, ci]),
         "fewha_set_layer_transform": (ci, [vp, ci]),
+        "fewha_get_frame_timing": (ci, [vp, ctypes.POINTER(cd)]),
         "fewha_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
         "fewha_set_loop": (ci, [vp, ci]),
         "fewha_operator_dims": (ci, [vp, ci, ctypes.POINTER(cl), ctypes.POINTER(cl)]),
@@ -362,6 +363,13 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(lib().fewha_launch_count(self.h))
+
+    def frame_timing(self) -> dict:
+        """Host-side timing of the last frame() (us): prep, launch, wait, total."""
+        t = (ctypes.c_double * 6)()
+        self._check(lib().fewha_get_frame_timing(self.h, t))
+        return {"prep_us": t[0], "launch_us": t[1], "wait_us": t[2], "total_us": t[3],
+                "repointed": bool(t[4]), "captured": bool(t[5])}
 
     def set_cluster_size(self, cluster_size: int):
         self._check(lib().fewha_set_cluster_size(self.h, int(cluster_size)))

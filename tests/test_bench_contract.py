@@ -54,9 +54,7 @@ def test_traffic_is_reported_only_for_the_captured_kernel_source(monkeypatch):
     assert got in (None, rec["dram_bytes"])
     monkeypatch.setitem(bench.NCU_TRAFFIC, "fused_cu_sha256", "0" * 16)
     assert bench.fused_traffic() is None            # another kernel source: no traffic claimed
-    import hashlib
-    with open(os.path.join(ROOT, "paper_2009_00946_b300", "csrc", "fused.cu"), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
+    sha = bench.fused_source_sha()
     monkeypatch.setitem(bench.NCU_TRAFFIC, "fused_cu_sha256", sha[:16])
     assert bench.fused_traffic() == rec["dram_bytes"]
     # the committed summary the figure comes from exists and names the same source
