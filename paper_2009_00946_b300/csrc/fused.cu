@@ -27,12 +27,15 @@
 #include <cstring>
 #include <vector>
 
+#include "debug.cuh"
 #include "fused.h"
 #include "solver.h"
 
 namespace cg = cooperative_groups;
 
 namespace fewha {
+
+FEWHA_DBG_READER(dbg_read_fused)
 
 constexpr int kFThreads = 512;
 constexpr int kMaxC = 16;
@@ -232,7 +235,8 @@ __device__ void grid_barrier(const FParams& P, unsigned& target, int* s_abort, i
 
 // 16-byte global -> shared copy that bypasses L1 (the source was written by
 // other SMs in this launch); both addresses 16-byte aligned.
-__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
+__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc, int site = kDbgStgDst) {
+    if (!FEWHA_IN_SMEM(smem_dst, 16, site)) return;
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
 }
@@ -240,11 +244,13 @@ __device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+    if (!FEWHA_IN_SMEM(smem_dst, 4, kDbgTables)) return;
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
 }
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+    if (!FEWHA_IN_SMEM(smem_dst, 8, kDbgTables)) return;
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
 }
@@ -656,7 +662,9 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 const unsigned loc = (unsigned)(e4 - (wdesc[l * kWd + 4] >> 2));
                 const unsigned mg = (unsigned)wdesc[l * kWd + 7];
                 const int rr = mg ? (int)__umulhi(loc, mg) : (int)loc, c4 = (int)loc - rr * nc4;
-                cp_async16(win + (e4 << 2), I.phi + wdesc[l * kWd + 5] + (long)rr * wdesc[l * kWd + 6] + (c4 << 2));
+                const long si = wdesc[l * kWd + 5] + (long)rr * wdesc[l * kWd + 6] + (c4 << 2);
+                if (!FEWHA_IN(si, I.N, 4, kDbgWinSrc)) return;
+                cp_async16(win + (e4 << 2), I.phi + si, kDbgWinDst);
             };
             int l = 0;
             if (!anyg) {
@@ -682,7 +690,9 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                     const int rp = e / nc, cq = e - rp * nc;
                     const int row = __ldg(I.cy + tb + a_lo + (rp >> 1)) + (rp & 1);
                     const int col = __ldg(I.cx + tb + b_lo + (cq >> 1)) + (cq & 1);
-                    dst[e] = __ldcg(src + (long)row * n + col);
+                    if (FEWHA_IN(wdesc[ll * kWd + 5] + (long)row * n + col, I.N, 1, kDbgWinSrc) &&
+                        FEWHA_IN_SMEM(dst + e, 4, kDbgWinDst))
+                        dst[e] = __ldcg(src + (long)row * n + col);
                 }
             }
             // part A of the next layer phase's CG scalars while the copies fly
@@ -727,6 +737,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 const int nc = wdesc[l * kWd + 3];
                 const float ty = rw[l * P.tile_rows + ii], tx = cw[l * P.tile_cols + jj];
                 const float* f = win + roff[l * P.tile_rows + ii] + coff[l * P.tile_cols + jj];
+                if (!FEWHA_IN_SMEM(f, 4 * (nc + 2), kDbgWinP)) continue;
                 acc += (1.f - ty) * ((1.f - tx) * f[0] + tx * f[1]) + ty * ((1.f - tx) * f[nc] + tx * f[nc + 1]);
             }
             psi[e] = acc;
@@ -738,6 +749,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         for (int e = tid; e < nsr * nsc; e += NT) {
             const int aa = e / nsc, bb = e - aa * nsc;
             const int a = a_lo + aa, b = b_lo + bb;
+            if (!FEWHA_IN(a * ns + b, ns2, 1, kDbgSlopes)) continue;
             const float* pp = psi + aa * pc + bb;
             float sx = ((pp[1] - pp[0]) + (pp[pc + 1] - pp[pc])) / 2;
             float sy = ((pp[pc] - pp[0]) + (pp[pc + 1] - pp[1])) / 2;
@@ -768,6 +780,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         for (int e = tid; e < nsr * nsc; e += NT) {
             const int aa = e / nsc, bb = e - aa * nsc;
             const int a = a_lo + aa, b = b_lo + bb;
+            if (!FEWHA_IN(a * ns + b, ns2, 1, kDbgSlopes)) continue;
             const bool on = I.mask[cc->w_moff + a * ns + b] != 0;
             const float vx = __ldcg(S + a * ns + b), vy = __ldcg(S + ns2 + a * ns + b);
             if (Scopy) {   // the handle keeps the frame's slopes (tiles may overlap: same values)
@@ -801,7 +814,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 acc += (b == j - 1 ? sx : -sx) + (a == i - 1 ? sy : -sy);
             }
         }
-        out[i * np1 + j] = acc / 2;
+        if (FEWHA_IN(cc->w_noff + i * np1 + j, I.NW, 1, kDbgGtOut)) out[i * np1 + j] = acc / 2;
     }
     if (want_mu) {
         const float4 s = block_reduce2(mu, Acc2(), (float4*)red);
@@ -919,7 +932,7 @@ __device__ void fwd_dwt(const FParams& P, const Stripe& s, float* Z, float* P0, 
                 for (int i = 0; i < 12; ++i) {
                     if (i < 2 * kR + 4) {
                         const int src = (2 * k0 + i) & mask;
-                        v[i] = rem[src >> lR][((src & (R - 1)) << ln) + x];
+                        v[i] = FEWHA_IN(src >> lR, P.C, 1, kDbgStripe) ? rem[src >> lR][((src & (R - 1)) << ln) + x] : 0.f;
                     }
                 }
 #pragma unroll
@@ -963,8 +976,9 @@ __device__ float* inv_dwt(const FParams& P, const Stripe& s, float* Z, float* Pb
                 for (int mm = 0; mm < 4; ++mm) {
                     if (mm < (kR >> 1) + 2) {
                         const int k = (k0 - 2 + mm) & hmask, kd = half + k;
-                        va[mm] = ra[k >> lR][((k & (R - 1)) << ln) + x];
-                        vd[mm] = remZ[kd >> lR][((kd & (R - 1)) << ln) + x];
+                        const bool okr = FEWHA_IN(kd >> lR, P.C, 1, kDbgStripe);
+                        va[mm] = okr ? ra[k >> lR][((k & (R - 1)) << ln) + x] : 0.f;
+                        vd[mm] = okr ? remZ[kd >> lR][((kd & (R - 1)) << ln) + x] : 0.f;
                     }
                 }
 #pragma unroll
@@ -1061,7 +1075,8 @@ __device__ __forceinline__ void pt_gather(const int* sgi, const float* stg, cons
                         const float* row = base + max(ye.x, imin) * np1;
                         float racc = 0.f;
 #pragma unroll
-                        for (int b = 0; b < KGT; ++b) racc += xw[b] * row[xj[b]];
+                        for (int b = 0; b < KGT; ++b)
+                            if (FEWHA_IN_SMEM(row + xj[b], 4, kDbgPtRead)) racc += xw[b] * row[xj[b]];
                         acc[u] += __int_as_float(ye.y) * racc;
                     }
                 }
@@ -1119,7 +1134,8 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             const int c4 = sgi[g * 8 + 5];
             const float* src = I.psi + sgi[g * 8 + 4];
             float* dst = stg + sgi[g * 8 + 6];
-            for (int e = tid; e < c4; e += NT) cp_async16(dst + (e << 2), src + (e << 2));
+            for (int e = tid; e < c4; e += NT)
+                if (FEWHA_IN(sgi[g * 8 + 4] + (e << 2), I.NW, 4, kDbgStgSrc)) cp_async16(dst + (e << 2), src + (e << 2));
         }
         // the CG scalars of this iteration, while the copies are in flight
         // (part A from the sensor phase when that CTA computed it there)
@@ -1185,7 +1201,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
 #pragma unroll
             for (int u = 0; u < kE; ++u) {
                 const int e = e0 + u * NT;
-                if (e < total) {
+                if (e < total && FEWHA_IN(gbase + e, I.N, 1, kDbgCoef)) {
                     const long i = gbase + e;
                     vr[u] = I.r[i];
                     vp[u] = I.p[i];
@@ -1243,6 +1259,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
                 const int e = e0 + u * NT;
                 if (e >= total) break;
                 const long i = gbase + e;
+                if (!FEWHA_IN(i, I.N, 1, kDbgCoef)) continue;
                 const float z = vj[u] * vr[u];
                 const float sv = Z[e] + va[u] * z;
                 const float pv = (k == 0) ? z : z + fb * vp[u];
@@ -1267,6 +1284,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     }
     for (int e = tid; mode != kLpIter && e < R * n; e += NT) {
         const long i = gbase + e;
+        if (!FEWHA_IN(i, I.N, 1, kDbgCoef)) continue;
         const float jinv = __ldg(I.Jinv + i), ad = __ldg(I.aD + i);
         float zout = 0.f;
         if (mode == kLpRhsStart) {
@@ -1313,9 +1331,11 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     if (need_phi) {
         float* res = inv_dwt(P, s, Z, B3, B1, B2, rem[0], rem[1], rem[2], cl);
         fmark(P, 15);
-        for (int e = tid; e < R * n; e += NT) I.phi[gbase + e] = res[e];
+        for (int e = tid; e < R * n; e += NT)
+            if (FEWHA_IN(gbase + e, I.N, 1, kDbgPhiOut)) I.phi[gbase + e] = res[e];
         if (last && P.phi_out)
-            for (int e = tid; e < R * n; e += NT) P.phi_out[gbase + e] = res[e];
+            for (int e = tid; e < R * n; e += NT)
+                if (FEWHA_IN(gbase + e, I.N, 1, kDbgPhiOut)) P.phi_out[gbase + e] = res[e];
     }
     if (end_sync) cl.sync();
     fmark(P, 16);

@@ -139,7 +139,8 @@ __device__ __forceinline__ void pt_gather_cols(const int* sgi, const float* stg,
                     const float* row = base + (i - ilo) * W + ((s0 + i * np1) & 3);
                     float racc = 0.f;
 #pragma unroll
-                    for (int b = 0; b < KGT; ++b) racc += xw[b] * row[xj[b]];
+                    for (int b = 0; b < KGT; ++b)
+                        if (FEWHA_IN_SMEM(row + xj[b], 4, kDbgPtRead)) racc += xw[b] * row[xj[b]];
                     acc[u] += __int_as_float(ye.y) * racc;
                 }
             }
@@ -187,8 +188,10 @@ __device__ __forceinline__ void casc_cols_fwd(const FParams& P, const float* Z, 
                 }
                 if (j < J) *reinterpret_cast<float4*>(oa + k * R + c) = a;
                 const int wa = own[ub + k], wd = own[ub + half + k];
-                *reinterpret_cast<float4*>(rUrow[wa >> 16] + (wa & 0xffff) * n + c0 + c) = a;
-                *reinterpret_cast<float4*>(rUrow[wd >> 16] + (wd & 0xffff) * n + c0 + c) = d;
+                if (FEWHA_IN(wa >> 16, P.C, 1, kDbgCascOwn) && FEWHA_IN((wa & 0xffff) * n + c0 + c, P.v_c - P.v_r, 4, kDbgCascOwn))
+                    *reinterpret_cast<float4*>(rUrow[wa >> 16] + (wa & 0xffff) * n + c0 + c) = a;
+                if (FEWHA_IN(wd >> 16, P.C, 1, kDbgCascOwn) && FEWHA_IN((wd & 0xffff) * n + c0 + c, P.v_c - P.v_r, 4, kDbgCascOwn))
+                    *reinterpret_cast<float4*>(rUrow[wd >> 16] + (wd & 0xffff) * n + c0 + c) = d;
             }
         } else {
             const int items = half << lR;
@@ -203,8 +206,10 @@ __device__ __forceinline__ void casc_cols_fwd(const FParams& P, const float* Z, 
                 }
                 if (j < J) oa[e] = a;
                 const int wa = own[ub + k], wd = own[ub + half + k];
-                rUrow[wa >> 16][(wa & 0xffff) * n + c0 + c] = a;
-                rUrow[wd >> 16][(wd & 0xffff) * n + c0 + c] = d;
+                if (FEWHA_IN(wa >> 16, P.C, 1, kDbgCascOwn) && FEWHA_IN((wa & 0xffff) * n + c0 + c, P.v_c - P.v_r, 1, kDbgCascOwn))
+                    rUrow[wa >> 16][(wa & 0xffff) * n + c0 + c] = a;
+                if (FEWHA_IN(wd >> 16, P.C, 1, kDbgCascOwn) && FEWHA_IN((wd & 0xffff) * n + c0 + c, P.v_c - P.v_r, 1, kDbgCascOwn))
+                    rUrow[wd >> 16][(wd & 0xffff) * n + c0 + c] = d;
             }
         }
         __syncthreads();
@@ -331,11 +336,15 @@ __device__ __forceinline__ void casc_rows_inv(const FParams& P, const int* tab, 
             if (i > 1) {
                 *reinterpret_cast<float4*>(out + s * outs + x) = o;
             } else if (lR >= 2) {
-                *reinterpret_cast<float4*>(rUcol[x >> lR] + sl.x * R + (x & (R - 1))) = o;
+                if (FEWHA_IN(x >> lR, P.C, 1, kDbgCascCol) && FEWHA_IN(sl.x * R + (x & (R - 1)), P.v_r - P.v_u, 4, kDbgCascCol))
+                    *reinterpret_cast<float4*>(rUcol[x >> lR] + sl.x * R + (x & (R - 1))) = o;
             } else {
                 const float ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-                for (int t = 0; t < 4; ++t) rUcol[(x + t) >> lR][sl.x * R + ((x + t) & (R - 1))] = ov[t];
+                for (int t = 0; t < 4; ++t)
+                    if (FEWHA_IN((x + t) >> lR, P.C, 1, kDbgCascCol) &&
+                        FEWHA_IN(sl.x * R + ((x + t) & (R - 1)), P.v_r - P.v_u, 1, kDbgCascCol))
+                        rUcol[(x + t) >> lR][sl.x * R + ((x + t) & (R - 1))] = ov[t];
             }
         }
         __syncthreads();
@@ -421,7 +430,7 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
             for (int e = tid; e < rows * w4; e += NT) {
                 const int rr = mg ? (int)__umulhi((unsigned)e, mg) : e, x = e - rr * w4;
                 const int a0 = (s0 + (ilo + rr) * np1) & ~3;
-                cp_async16(dst + rr * W + 4 * x, I.psi + a0 + 4 * x);
+                if (FEWHA_IN(a0 + 4 * x, I.NW, 4, kDbgStgSrc)) cp_async16(dst + rr * W + 4 * x, I.psi + a0 + 4 * x);
             }
         }
         if (mode == kLpIter && tid < 32 && I.preA_cta < 0) {
@@ -485,6 +494,7 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
                     const int4 nz = __ldg(I.tt_nz + nr.x + e);
                     const int i = nz.x / np1, j = nz.x - i * np1;
                     if (i < ilo || i >= ihi || j < jlo || j >= jhi) continue;
+                    if (!FEWHA_IN_SMEM(dst + (i - ilo) * W + ((s0 + i * np1) & 3) + (j - jlo), 4, kDbgTT)) continue;
                     dst[(i - ilo) * W + ((s0 + i * np1) & 3) + (j - jlo)] -=
                         cx * __int_as_float(nz.y) + cy * __int_as_float(nz.z);
                 }
@@ -530,7 +540,7 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
 #pragma unroll
             for (int u = 0; u < kE; ++u) {
                 const int e = e0 + u * NT;
-                if (e < ncoef) {
+                if (e < ncoef && FEWHA_IN(off + gix[e], I.N, 1, kDbgCoef)) {
                     const int i = off + gix[e];
                     gi[u] = i;
                     vr[u] = I.r[i];
@@ -586,6 +596,7 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
                 const int e = e0 + u * NT;
                 if (e >= ncoef) break;
                 const int i = gi[u];
+                if (!FEWHA_IN(off + gix[e], I.N, 1, kDbgCoef)) continue;
                 const float z = vj[u] * vr[u];
                 const float sv = Zc[e] + va[u] * z;
                 const float pv = (k == 0) ? z : z + fb * vp[u];
@@ -611,6 +622,7 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
     if (mode != kLpIter) {
         for (int e = tid; e < ncoef; e += NT) {
             const int i = off + gix[e];
+            if (!FEWHA_IN(i, I.N, 1, kDbgCoef)) continue;
             const float jinv = __ldg(I.Jinv + i), ad = __ldg(I.aD + i);
             float zout = 0.f;
             if (mode == kLpRhsStart) {
@@ -663,6 +675,7 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
         casc_cols_inv(P, Ucol, Z, T, n, J, R, lR);
         fmark(P, 15);
         float* dst = I.phi + off + c0;
+        if (!FEWHA_IN(off + c0 + (n - 1) * n, I.N, R, kDbgPhiOut)) return;   // after the last cluster barrier
         casc_copy(n, lR, true, [&](int p) { return (const float*)(Z + (p << lR)); }, [&](int p) { return dst + p * n; });
         if (last && P.phi_out) {   // the caller's buffer: 16-byte pieces when it is 16-byte aligned
             float* d2 = P.phi_out + off + c0;

@@ -22,8 +22,15 @@
 #include <cstring>
 #include <mutex>
 
+#include "debug.cuh"
 #include "fewha.h"
 #include "setup.h"
+
+namespace fewha {
+FEWHA_DBG_READER(dbg_read_noalloc)
+}  // namespace fewha
+
+using fewha::kDbgNoalloc;
 
 namespace {
 
@@ -40,6 +47,7 @@ std::mutex g_scratch_mutex;
 
 struct LayerStack {
     int L, Jmax, nmax;
+    long total;   // coefficients of the stack (the source and destination length)
     int n[FEWHA_MAX_LAYERS];
     int J[FEWHA_MAX_LAYERS];
     int off[FEWHA_MAX_LAYERS];
@@ -62,9 +70,10 @@ __global__ void k_noalloc_inv_cols(LayerStack S, int j, const float* __restrict_
         const int r = ((i - t) % m + m) % m;
         if (r & 1) continue;
         const int k = r >> 1;
+        if (!FEWHA_IN(S.off[l] + (long)(half + k) * n + x, S.total, 1, kDbgNoalloc)) continue;
         acc += S.h[t] * s[(long)k * n] + S.g[t] * s[(long)(half + k) * n];
     }
-    dst[S.off[l] + (long)i * n + x] = acc;
+    if (FEWHA_IN(S.off[l] + (long)i * n + x, S.total, 1, kDbgNoalloc)) dst[S.off[l] + (long)i * n + x] = acc;
 }
 
 // inverse row pass of level j
@@ -82,9 +91,10 @@ __global__ void k_noalloc_inv_rows(LayerStack S, int j, const float* __restrict_
         const int r = ((i - t) % m + m) % m;
         if (r & 1) continue;
         const int k = r >> 1;
+        if (!FEWHA_IN(S.off[l] + (long)y * n + half + k, S.total, 1, kDbgNoalloc)) continue;
         acc += S.h[t] * s[k] + S.g[t] * s[half + k];
     }
-    dst[S.off[l] + (long)y * n + i] = acc;
+    if (FEWHA_IN(S.off[l] + (long)y * n + i, S.total, 1, kDbgNoalloc)) dst[S.off[l] + (long)y * n + i] = acc;
 }
 
 int fail(char* errbuf, int errlen, int code, const char* msg) {
@@ -118,6 +128,7 @@ extern "C" int fewha_layers_noalloc(const float* coeffs, float* layers, int n_la
         S.nmax = n > S.nmax ? n : S.nmax;
         total += (long)n * n;
     }
+    S.total = total;
     if (total > kScratchFloats) {
         char msg[160];
         snprintf(msg, sizeof msg, "%ld coefficients exceed the fixed scratch of %ld floats (4 MiB)", total,

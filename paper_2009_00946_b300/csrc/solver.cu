@@ -12,11 +12,14 @@
 #include <memory>
 #include <type_traits>
 
+#include "debug.cuh"
 #include "fitcg.h"
 #include "fused.h"
 #include "solver.h"
 
 namespace fewha {
+
+FEWHA_DBG_READER(dbg_read_solver)
 
 #define FEWHA_CUDA(call)                                                                   \
     do {                                                                                   \
@@ -242,10 +245,12 @@ __global__ void k_P(DevGeo<T> G, const T* __restrict__ phi, T* __restrict__ psi)
         int base = G.tab_off[g * G.L + l], n = G.lay_n[l];
         int cy = G.cy[base + i], cx = G.cx[base + jx];
         T ty = G.ty[base + i], tx = G.tx[base + jx];
-        const T* f = phi + G.lay_off[l] + (long)cy * n + cx;
+        const long fi = G.lay_off[l] + (long)cy * n + cx;
+        if (!FEWHA_IN(fi, G.N, n + 2, kDbgPlainP)) continue;
+        const T* f = phi + fi;
         acc += (1 - ty) * ((1 - tx) * f[0] + tx * f[1]) + ty * ((1 - tx) * f[n] + tx * f[n + 1]);
     }
-    psi[G.wfs_noff[g] + idx] = acc;
+    if (FEWHA_IN(G.wfs_noff[g] + idx, G.NW, 1, kDbgPlainP)) psi[G.wfs_noff[g] + idx] = acc;
 }
 
 // weighted slopes w_g mask (Gamma psi)  (C^{-1} Gamma, Sec. 2.1 / Sec. 2.2)
@@ -255,6 +260,9 @@ __global__ void k_gamma_w(DevGeo<T> G, const T* __restrict__ psi, T* __restrict_
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ns * ns) return;
     int a = idx / ns, b = idx - a * ns;
+    if (!FEWHA_IN(G.wfs_noff[g] + (long)a * np1 + b, G.NW, np1 + 2, kDbgPlainGam) ||
+        !FEWHA_IN(G.wfs_soff[g] + ns * ns + idx, G.S, 1, kDbgPlainGam))
+        return;
     const T* p = psi + G.wfs_noff[g] + (long)a * np1 + b;
     T sx = ((p[1] - p[0]) + (p[np1 + 1] - p[np1])) / 2;
     T sy = ((p[np1] - p[0]) + (p[np1 + 1] - p[1])) / 2;
@@ -272,6 +280,9 @@ __global__ void k_resid_w(DevGeo<T> G, const T* __restrict__ s, const T* __restr
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ns * ns) return;
     int a = idx / ns, b = idx - a * ns;
+    if (!FEWHA_IN(G.wfs_noff[g] + (long)a * np1 + b, G.NW, np1 + 2, kDbgPlainGam) ||
+        !FEWHA_IN(G.wfs_soff[g] + ns * ns + idx, G.S, 1, kDbgPlainGam))
+        return;
     const T* p = psi + G.wfs_noff[g] + (long)a * np1 + b;
     T sx = ((p[1] - p[0]) + (p[np1 + 1] - p[np1])) / 2;
     T sy = ((p[np1] - p[0]) + (p[np1 + 1] - p[1])) / 2;
@@ -339,11 +350,12 @@ __global__ void k_gammaT(DevGeo<T> G, const T* __restrict__ sl, T* __restrict__ 
         if (a < 0 || a >= ns) continue;
         for (int b = jx - 1; b <= jx; ++b) {
             if (b < 0 || b >= ns) continue;
+            if (!FEWHA_IN(G.wfs_soff[g] + ns * ns + a * ns + b, G.S, 1, kDbgPlainGam)) continue;
             T sx = SX[a * ns + b], sy = SY[a * ns + b];
             acc += (b == jx - 1 ? sx : -sx) + (a == i - 1 ? sy : -sy);
         }
     }
-    psi[G.wfs_noff[g] + idx] = acc / 2;
+    if (FEWHA_IN(G.wfs_noff[g] + idx, G.NW, 1, kDbgPlainGam)) psi[G.wfs_noff[g] + idx] = acc / 2;
 }
 
 // y_l(p, q) = sum_g (P_gl^T psi'_g)(p, q): deterministic gather over the
@@ -365,12 +377,12 @@ __global__ void k_PT(DevGeo<T> G, const T* __restrict__ psi, T* __restrict__ y) 
             T row = 0;
             for (int jx = j0; jx < j1; ++jx) {
                 T wx = (G.cx[base + jx] == q) ? 1 - G.tx[base + jx] : G.tx[base + jx];
-                row += wx * P[(long)i * np1 + jx];
+                if (FEWHA_IN(G.wfs_noff[g] + (long)i * np1 + jx, G.NW, 1, kDbgPlainPT)) row += wx * P[(long)i * np1 + jx];
             }
             acc += wy * row;
         }
     }
-    y[G.lay_off[l] + idx] = acc;
+    if (FEWHA_IN(G.lay_off[l] + idx, G.N, 1, kDbgPlainPT)) y[G.lay_off[l] + idx] = acc;
 }
 
 // ---------------------------------------------------------------------------

@@ -197,7 +197,7 @@ def _ptr(a, dtype, count, on_device):
     arr = a
     if arr.dtype != dtype[0] or arr.size != count or not arr.flags["C_CONTIGUOUS"]:
         raise ValueError("array must be C-contiguous %s with %d elements" % (dtype[0], count))
-    return ctypes.c_void_p(arr.ctypes.data), 0
+    return ctypes.c_void_p(arr.__array_interface__["data"][0]), 0
 
 
 class Solver:
