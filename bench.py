@@ -415,6 +415,86 @@ def bench_mode_frame(torch, fewha, dev, flush, n_frames, mode):
     return out
 
 
+def bench_autograd(torch, fewha, dev, flush, reps=20):
+    """The differentiable solve on the autograd configuration (D = 16 m, 4 LGS
+    40x40, 5 layers 64^2, J = 3, 4 cold-start iterations): a batch of 32
+    frames, taped forward and reverse mode (gradients in gamma, alpha, w and
+    the slopes), FP32 vectors with FP64 scalars and in FP64; the frame batch
+    in one launch sequence against the same frames one call each."""
+    from paper_2009_00946_b300 import synth
+    cfg = configs.c5_autograd()
+    B = 32
+    S_np, T_np = synth.frames(cfg, B)
+    out = {"workload": "autograd configuration: D=16 m, 4 LGS (90 km) at 60 arcsec, 40x40 subapertures, 5 layers "
+                       "64^2 (J=3), 4 cold-start PCG iterations, batch of 32 frames, loss sum |phi - phi_true|^2",
+           "frames": B}
+    for name, prec, dt in (("fp32", fewha.FP32, torch.float32), ("fp64", fewha.FP64, torch.float64)):
+        S = fewha.Solver(cfg, precision=prec)
+        st = S.stream
+        with torch.cuda.stream(st):
+            sd = torch.from_numpy(S_np).to(dev, dt).contiguous()
+            phit = torch.from_numpy(T_np.reshape(B, -1)).to(dev, dt)
+            tape = torch.empty(S.tape_bytes_batch(N_ITER, B), dtype=torch.uint8, device=dev)
+            tapes1 = [torch.empty(S.tape_bytes(N_ITER), dtype=torch.uint8, device=dev) for _ in range(B)]
+            phi = torch.empty(B, S.N, dtype=dt, device=dev)
+            gg = torch.empty(B, S.n_layers, dtype=torch.float64, device=dev)
+            ga = torch.empty(B, dtype=torch.float64, device=dev)
+            gw = torch.empty(B, S.n_wfs, dtype=torch.float64, device=dev)
+            gs = torch.empty_like(sd)
+        st.synchronize()
+
+        def fwd_batch():
+            S.solve_taped_batch(sd, N_ITER, tape, phi)
+
+        def bwd_batch():
+            S.backward_batch(sd, N_ITER, tape, phibar, gg, ga, gw, gs)
+
+        def fwd_loop():
+            for b in range(B):
+                S.solve_taped(sd[b], N_ITER, tapes1[b], phi[b])
+
+        def bwd_loop():
+            for b in range(B):
+                S.backward(sd[b], N_ITER, tapes1[b], phibar[b], gg[b], ga[b:b + 1], gw[b], gs[b])
+
+        def timed(fn):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for k in range(reps):
+                with torch.cuda.stream(st):
+                    flush.fill_(float(k & 7))
+                ev[k][0].record(st)
+                fn()
+                ev[k][1].record(st)
+            st.synchronize()
+            return float(np.percentile([a.elapsed_time(b) * 1e3 for a, b in ev], 50))
+
+        fwd_batch()
+        with torch.cuda.stream(st):
+            phibar = (2.0 * (phi - phit)).contiguous()
+        st.synchronize()
+        for fn in (bwd_batch, fwd_loop, bwd_loop):
+            fn()
+        st.synchronize()
+        n0 = S.launch_count()
+        fwd_batch()
+        bwd_batch()
+        st.synchronize()
+        launches = S.launch_count() - n0
+        rec = {"forward_us": timed(fwd_batch), "backward_us": timed(bwd_batch),
+               "one_call_per_frame_forward_us": timed(fwd_loop), "one_call_per_frame_backward_us": timed(bwd_loop),
+               "kernel_launches_forward_and_backward": launches}
+        rec["speedup_forward_and_backward"] = ((rec["one_call_per_frame_forward_us"] +
+                                                rec["one_call_per_frame_backward_us"]) /
+                                               (rec["forward_us"] + rec["backward_us"]))
+        S.sync()
+        out[name] = rec
+        S.close()
+    out["how"] = ("CUDA events around fewha_solve_taped_batch / fewha_backward_batch on the solver's stream, device "
+                  "tensors, L2 flushed before each, median of %d; the one-call-per-frame lines run the same frames "
+                  "through fewha_solve_taped / fewha_backward one frame at a time" % reps)
+    return out
+
+
 def bench_batch(torch, fewha, dev, flush, n_frames):
     """64 uneven instances advanced by one fused launch per frame, against the
     same 64 instances solved one after another on the plain FP64 path."""
@@ -757,8 +837,12 @@ def main():
         S.stream.synchronize()
         t0 = time.perf_counter()
         S.frame(host_s, N_ITER, warm=True, layers_out=host_l)
-        e2e.append((time.perf_counter() - t0) * 1e6)
-        e2e_ft.append(S.frame_timing())
+        t3 = time.perf_counter()
+        e2e.append((t3 - t0) * 1e6)
+        ft = S.frame_timing()
+        c0, c1, c2 = S.last_call
+        ft.update(py_args_us=(c1 - t0) * 1e6, ctypes_call_us=(c2 - c1) * 1e6, py_after_us=(t3 - c2) * 1e6)
+        e2e_ft.append(ft)
     e2e, e2e_ft = e2e[5:], e2e_ft[5:]
     # the same host frames bracketed by CUDA events (the kernel reading and
     # writing the pinned buffers through their device mapping), the GPU kept
@@ -778,6 +862,9 @@ def main():
         "host_wait_us": float(np.median([f["wait_us"] for f in e2e_ft])),
         "library_call_us": float(np.median([f["total_us"] for f in e2e_ft])),
         "python_call_us": float(np.median([e - f["total_us"] for e, f in zip(e2e, e2e_ft)])),
+        "python_args_us": float(np.median([f["py_args_us"] for f in e2e_ft])),
+        "ctypes_call_us": float(np.median([f["ctypes_call_us"] for f in e2e_ft])),
+        "python_after_us": float(np.median([f["py_after_us"] for f in e2e_ft])),
         "library_call_p99_us": float(np.percentile([f["total_us"] for f in e2e_ft], 99)),
         "host_wait_p99_us": float(np.percentile([f["wait_us"] for f in e2e_ft], 99)),
         "device_frame_with_host_io_us": e2e_dev,
@@ -785,7 +872,8 @@ def main():
         "host_io_bytes": (S.S + S.N) * 4,
         "host_io_gbs": (S.S + S.N) * 4 / max(e2e_dev - p50, 1e-3) / 1e3,
         "what": "library_call = prep + launch + wait (host steady clock inside fewha_frame); python_call = "
-                "the e2e time of a frame minus its library_call (binding and interpreter); host_io_in_kernel = device time of a host frame minus the device "
+                "the e2e time of a frame minus its library_call (binding and interpreter; python_args before the "
+                "library call, ctypes_call around it, python_after after it); host_io_in_kernel = device time of a host frame minus the device "
                 "p50 (slopes read, layers written through the pinned buffers' device mapping)"}
 
     # ---- the plain FP64 path (one kernel per operator) on the same frames ----
@@ -809,6 +897,7 @@ def main():
         extra["maory_frame"] = bench_maory_frame(torch, fewha, dev, flush, min(K, 200))
         extra["ltao_frame"] = bench_mode_frame(torch, fewha, dev, flush, min(K, 200), "ltao")
         extra["moao_frame"] = bench_mode_frame(torch, fewha, dev, flush, min(K, 200), "moao")
+        extra["autograd_batch32"] = bench_autograd(torch, fewha, dev, flush)
         if world > 1:
             extra["batch64_sharded"] = bench_batch_sharded(torch, fewha, dev, flush, min(K, 30), dist, rank, world)
         else:

@@ -345,6 +345,30 @@ int fewha_solve_taped(fewha_handle* h, const void* slopes, int n_iter, void* tap
 int fewha_backward(fewha_handle* h, const void* slopes, int n_iter, const void* tape, const void* layers_bar,
                    double* grad_cn2, double* grad_alpha, double* grad_w, void* grad_slopes);
 
+/* Bytes of device memory a taped solve of n_frames frames records together
+ * (5 n_iter n_frames vectors of N plus 8 n_iter n_frames doubles); equal to
+ * fewha_tape_bytes for one frame; -1 on bad arguments. */
+long fewha_tape_bytes_batch(const fewha_handle* h, int n_iter, int n_frames);
+
+/* fewha_solve_taped for n_frames frames at once (1..65535; the autograd batch
+ * of a training step): slopes [n_frames][S], layers_out [n_frames][N] (may be
+ * NULL), one tape of fewha_tape_bytes_batch bytes holding every frame's
+ * iterates.  Each frame is its own cold-started solve with the same
+ * operator; every kernel of the chain processes all frames in one launch
+ * (the frame is the grid's third axis), so the launch count does not grow
+ * with n_frames.  Errors: ARG; BREAKDOWN / INPUT by fewha_sync. */
+int fewha_solve_taped_batch(fewha_handle* h, int n_frames, const void* slopes, int n_iter, void* tape,
+                            void* layers_out);
+
+/* Reverse mode of fewha_solve_taped_batch (same n_frames, slopes, n_iter,
+ * tape and parameters): layers_bar [n_frames][N]; per frame gradients, each
+ * overwritten: grad_cn2 [n_frames][n_layers], grad_alpha [n_frames],
+ * grad_w [n_frames][n_wfs], and, if not NULL, grad_slopes [n_frames][S].
+ * Errors: ARG. */
+int fewha_backward_batch(fewha_handle* h, int n_frames, const void* slopes, int n_iter, const void* tape,
+                         const void* layers_bar, double* grad_cn2, double* grad_alpha, double* grad_w,
+                         void* grad_slopes);
+
 /* ------------------------------------------------------------------------
  * Batch of independent instances.  Sec. 4 finds the global parallelism of a
  * single reconstruction (a handful of layers and sensors) far too small to
@@ -438,6 +462,37 @@ int fewha_measure_l2(long bytes, int passes, int reps, double* read_gbs, double*
  * Errors: ARG (null, aliasing or out-of-range sizes), CUDA. */
 int fewha_layers_noalloc(const float* coeffs, float* layers, int n_layers, const int* n_side,
                          const int* levels, void* stream, char* errbuf, int errlen);
+
+/* Sites of the debug build's bounds checks (fewha_debug_bounds): the sensor
+ * tile's window source and staging, its bilinear reads, slope indices and
+ * Gamma^T output; the layer phase's field staging source and destination,
+ * P^T gather reads, level-stacked DWT stores into row and column owners,
+ * coefficient indices, tip-tilt correction nodes, layer output; the
+ * row-stripe DWT's peer reads; table staging; the plain path's P, P^T and
+ * Gamma / Gamma^T; the fit; the no-allocation transform. */
+enum {
+    FEWHA_DBG_WIN_SRC = 1, FEWHA_DBG_WIN_DST = 2, FEWHA_DBG_WIN_P = 3, FEWHA_DBG_SLOPES = 4,
+    FEWHA_DBG_GT_OUT = 5, FEWHA_DBG_STG_SRC = 6, FEWHA_DBG_STG_DST = 7, FEWHA_DBG_PT_READ = 8,
+    FEWHA_DBG_CASC_OWN = 9, FEWHA_DBG_CASC_COL = 10, FEWHA_DBG_COEF = 11, FEWHA_DBG_TT = 12,
+    FEWHA_DBG_PHI_OUT = 13, FEWHA_DBG_STRIPE = 14, FEWHA_DBG_TABLES = 15, FEWHA_DBG_PLAIN_P = 16,
+    FEWHA_DBG_PLAIN_PT = 17, FEWHA_DBG_PLAIN_GAMMA = 18, FEWHA_DBG_FIT = 19, FEWHA_DBG_NOALLOC = 20
+};
+
+/* The paper has no counterpart: the memory checker of the debug build.  A
+ * library built with -DFEWHA_DEBUG (libfewha_debug.so, made next to the
+ * release library) checks at every gather and scatter of the hot path --
+ * the fused kernel's window and field staging, bilinear reads, P^T gather,
+ * DWT exchange stores and coefficient indices; the plain path's P, P^T,
+ * Gamma and Gamma^T; the fit's sparse products and layer samples; the
+ * no-allocation transform -- that the index lies inside the buffer it
+ * addresses, and skips the access where it does not.  This call reports and
+ * clears the violations recorded since the last call, over every kernel of
+ * the library: *count their number, *first the first one as
+ * (site << 48) | (index & (2^48 - 1)), site one of the FEWHA_DBG_* values
+ * below.  Synchronises with the device.  Returns 1 in a debug build, 0 in
+ * the release build (which checks nothing: both outputs 0), FEWHA_ERR_CUDA
+ * if reading the records failed, FEWHA_ERR_ARG for null pointers. */
+int fewha_debug_bounds(unsigned long long* first, unsigned long long* count);
 
 #ifdef __cplusplus
 }

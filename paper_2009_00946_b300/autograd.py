@@ -8,10 +8,12 @@ regularisation weight alpha (0-d) and the sensor weights w_g = 1/sigma_g^2
 ([G]), all float64 tensors.  Gradients flow to the slopes and to the three
 parameter tensors; the Jacobi preconditioner is a constant of the map.
 
-Every step runs in libfewha's kernels (fewha_solve_taped / fewha_backward):
-this module only orders the solver's stream against torch's current stream,
-allocates the tapes (one per frame, kept until backward) and sums the
-per-frame parameter gradients.
+Every step runs in libfewha's kernels (fewha_solve_taped_batch /
+fewha_backward_batch): the frames of a batch are solved together, every kernel
+of the operator chain taking all of them in one launch.  This module only
+orders the solver's stream against torch's current stream, allocates the tape
+(one for the batch, kept until backward) and sums the per-frame parameter
+gradients.
 """
 
 from __future__ import annotations
@@ -38,14 +40,13 @@ class FewhaSolve(torch.autograd.Function):
         solver.set_params(*params)
         cur = torch.cuda.current_stream()
         solver.stream.wait_stream(cur)
-        nb = solver.tape_bytes(n_iter)
-        tapes = [torch.empty(nb, dtype=torch.uint8, device=slopes.device) for _ in range(S2.shape[0])]
-        out = torch.empty(S2.shape[0], solver.N, dtype=solver.torch_dtype, device=slopes.device)
-        for b in range(S2.shape[0]):
-            solver.solve_taped(S2[b], n_iter, tapes[b], out[b])
+        B = S2.shape[0]
+        tape = torch.empty(solver.tape_bytes_batch(n_iter, B), dtype=torch.uint8, device=slopes.device)
+        out = torch.empty(B, solver.N, dtype=solver.torch_dtype, device=slopes.device)
+        solver.solve_taped_batch(S2, n_iter, tape, out)
         cur.wait_stream(solver.stream)
         solver.sync()   # BREAKDOWN / INPUT of the solve surface here
-        ctx.solver, ctx.n_iter, ctx.params, ctx.tapes, ctx.single = solver, n_iter, params, tapes, single
+        ctx.solver, ctx.n_iter, ctx.params, ctx.tape, ctx.single = solver, n_iter, params, tape, single
         ctx.save_for_backward(S2)
         return out[0] if single else out
 
@@ -60,14 +61,12 @@ class FewhaSolve(torch.autograd.Function):
         cur = torch.cuda.current_stream()
         solver.stream.wait_stream(cur)
         gg = torch.empty(B, solver.n_layers, dtype=torch.float64, device=dev)
-        ga = torch.empty(B, 1, dtype=torch.float64, device=dev)
+        ga = torch.empty(B, dtype=torch.float64, device=dev)
         gw = torch.empty(B, solver.n_wfs, dtype=torch.float64, device=dev)
         gs = torch.empty_like(S2) if ctx.needs_input_grad[2] else None
-        for b in range(B):
-            solver.backward(S2[b], ctx.n_iter, ctx.tapes[b], phibar[b], gg[b], ga[b], gw[b],
-                            None if gs is None else gs[b])
+        solver.backward_batch(S2, ctx.n_iter, ctx.tape, phibar, gg, ga, gw, gs)
         cur.wait_stream(solver.stream)
-        ctx.tapes = None
+        ctx.tape = None
         g_slopes = None if gs is None else (gs[0] if ctx.single else gs)
         return None, None, g_slopes, gg.sum(0), ga.sum(), gw.sum(0)
 

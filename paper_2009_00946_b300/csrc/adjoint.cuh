@@ -6,30 +6,34 @@
 // scalar slots.
 #pragma once
 
-// Tape of one differentiable solve: per iteration k the vectors r_k (before
-// the update), z_k = J^{-1} r_k, s_k = M z_k, p_k, q_k (after the update),
-// then per iteration 8 doubles (rho, mu, beta, d, alpha, rho_{k-1},
-// alpha_{k-1}, unused).
+// Tape of B differentiable solves run together (B = 1: one solve): per
+// iteration k the vectors r_k (before the update), z_k = J^{-1} r_k,
+// s_k = M z_k, p_k, q_k (after the update), each as B frames of N values
+// ([k][vector][frame][N]), then per iteration and frame 8 doubles (rho, mu,
+// beta, d, alpha, rho_{k-1}, alpha_{k-1}, unused), [k][frame][8].
 enum TapeVec { kTapeR = 0, kTapeZ, kTapeS, kTapeP, kTapeQ, kTapeVecs };
 enum TapeScalar { kTRho = 0, kTMu, kTBeta, kTD, kTAlpha, kTRhoOld, kTAlphaOld, kTapeScalars = 8 };
 
-inline size_t tape_vec_bytes(long N, int n_iter, size_t elem) {
-    const size_t b = (size_t)n_iter * kTapeVecs * (size_t)N * elem;
+inline size_t tape_vec_bytes(long N, int n_iter, size_t elem, int B = 1) {
+    const size_t b = (size_t)n_iter * kTapeVecs * (size_t)N * (size_t)B * elem;
     return (b + 255) & ~(size_t)255;
 }
-inline size_t tape_bytes(long N, int n_iter, size_t elem) {
-    return tape_vec_bytes(N, n_iter, elem) + (size_t)n_iter * kTapeScalars * sizeof(double);
+inline size_t tape_bytes(long N, int n_iter, size_t elem, int B = 1) {
+    return tape_vec_bytes(N, n_iter, elem, B) + (size_t)n_iter * (size_t)B * kTapeScalars * sizeof(double);
 }
 
-// Record the scalars of iteration k (after k_alg2_scalars).
+// Record the scalars of iteration k (after k_alg2_scalars); one block per
+// frame of the batch (gridDim.x frames).
 __global__ void k_tape_scalars(const double* __restrict__ sc, double* __restrict__ ts, int k) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double* t = ts + (size_t)k * kTapeScalars;
+    if (threadIdx.x != 0) return;
+    const int f = blockIdx.x, B = gridDim.x;
+    sc += (size_t)f * kNumScalars;
+    double* t = ts + ((size_t)k * B + f) * kTapeScalars;
     const double rho = sc[kRho], mu = sc[kMu], beta = sc[kBeta], alpha = sc[kAlphaK];
     double rho_old = 0.0, alpha_old = 0.0, d = mu;
     if (k > 0) {
-        rho_old = ts[(size_t)(k - 1) * kTapeScalars + kTRho];
-        alpha_old = ts[(size_t)(k - 1) * kTapeScalars + kTAlpha];
+        rho_old = ts[((size_t)(k - 1) * B + f) * kTapeScalars + kTRho];
+        alpha_old = ts[((size_t)(k - 1) * B + f) * kTapeScalars + kTAlpha];
         d = mu - rho * beta / alpha_old;
     }
     t[kTRho] = rho;
@@ -49,6 +53,18 @@ __global__ void k_adj_dots(int N, const T* __restrict__ cb, const T* __restrict_
                            const T* __restrict__ qb, const T* __restrict__ pk, const T* __restrict__ qk,
                            const T* __restrict__ pold, const T* __restrict__ qold, double* __restrict__ part) {
     __shared__ double sh[32];
+    const long fo = (long)blockIdx.z * N;   // frame blockIdx.z of a batch
+    cb += fo;
+    rb += fo;
+    pb += fo;
+    qb += fo;
+    pk += fo;
+    qk += fo;
+    if (pold) {
+        pold += fo;
+        qold += fo;
+    }
+    part += (size_t)blockIdx.z * 6 * kRedBlocks;
     double a[6] = {0, 0, 0, 0, 0, 0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const double c = cb[i], r = rb[i];
@@ -74,6 +90,9 @@ __global__ void k_adj_dots(int N, const T* __restrict__ cb, const T* __restrict_
 __global__ void k_adj_scalars(const double* __restrict__ part, const double* __restrict__ ts, int k,
                               double* __restrict__ asc) {
     __shared__ double sh[32];
+    const int f = blockIdx.x, B = gridDim.x;   // one block per frame
+    part += (size_t)f * 6 * kRedBlocks;
+    asc += (size_t)f * 8;
     double D[6];
     for (int j = 0; j < 6; ++j) {
         double acc = 0.0;
@@ -82,7 +101,7 @@ __global__ void k_adj_scalars(const double* __restrict__ part, const double* __r
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
-    const double* t = ts + (size_t)k * kTapeScalars;
+    const double* t = ts + ((size_t)k * B + f) * kTapeScalars;
     const double rho = t[kTRho], beta = t[kTBeta], d = t[kTD], alpha = t[kTAlpha];
     const double alphab = asc[4] + D[0] - D[1];
     double betab = k > 0 ? (D[2] + alpha * D[3]) + (D[4] - alpha * D[5]) : 0.0;
@@ -109,6 +128,14 @@ __global__ void k_adj_scalars(const double* __restrict__ part, const double* __r
 template <typename T>
 __global__ void k_adj_vec1(int N, const double* __restrict__ asc, const T* __restrict__ cb, const T* __restrict__ rb,
                            T* __restrict__ pb, T* __restrict__ qb, const T* __restrict__ zk, T* __restrict__ sb) {
+    const long fo = (long)blockIdx.z * N;
+    asc += (size_t)blockIdx.z * 8;
+    cb += fo;
+    rb += fo;
+    pb += fo;
+    qb += fo;
+    zk += fo;
+    sb += fo;
     const T a = (T)asc[0], mub = (T)asc[2];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         pb[i] += a * cb[i];
@@ -124,6 +151,15 @@ template <typename T>
 __global__ void k_adj_vec2(int N, const double* __restrict__ asc, T* __restrict__ pb, T* __restrict__ qb,
                            T* __restrict__ rb, const T* __restrict__ zk, const T* __restrict__ sk,
                            const T* __restrict__ rk, const T* __restrict__ Msb, const T* __restrict__ Jinv) {
+    const long fo = (long)blockIdx.z * N;
+    asc += (size_t)blockIdx.z * 8;
+    pb += fo;
+    qb += fo;
+    rb += fo;
+    zk += fo;
+    sk += fo;
+    rk += fo;
+    Msb += fo;
     const T beta = (T)asc[1], mub = (T)asc[2], rhob = (T)asc[3];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const T zb = pb[i] + mub * sk[i] + rhob * rk[i] + Msb[i];
@@ -139,6 +175,9 @@ __global__ void k_layer_dot(DevGeo<T> G, const T* __restrict__ a, const T* __res
                             double* __restrict__ part) {
     __shared__ double sh[32];
     const int l = blockIdx.y, n = G.lay_n[l], off = G.lay_off[l];
+    a += (long)blockIdx.z * G.N;   // w (alpha D) is shared by the frames
+    b += (long)blockIdx.z * G.N;
+    part += (size_t)blockIdx.z * G.L * kRedBlocks;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x)
         acc += (double)a[off + i] * (double)w[off + i] * (double)b[off + i];
@@ -153,6 +192,10 @@ __global__ void k_wfs_dot(DevGeo<T> G, const T* __restrict__ psiA, const T* __re
                           const T* __restrict__ s, double* __restrict__ part) {
     __shared__ double sh[32];
     const int g = blockIdx.y, ns = G.wfs_n[g], np1 = ns + 1;
+    psiA += (long)blockIdx.z * G.NW;
+    if (psiB) psiB += (long)blockIdx.z * G.NW;
+    else s += (long)blockIdx.z * G.S;
+    part += (size_t)blockIdx.z * G.G * kRedBlocks;
     double acc = 0.0;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < ns * ns; idx += gridDim.x * blockDim.x) {
         if (!G.mask[G.wfs_moff[g] + idx]) continue;
@@ -183,6 +226,12 @@ __global__ void k_adj_accum(const double* __restrict__ lpart, int L, const doubl
                             const double* __restrict__ gam, double alpha, double* __restrict__ g_gam,
                             double* __restrict__ g_alpha, double* __restrict__ g_w) {
     __shared__ double sh[32];
+    const int f = blockIdx.x;   // one block per frame: its own gradients
+    if (lpart) lpart += (size_t)f * L * kRedBlocks;
+    if (wpart) wpart += (size_t)f * G * kRedBlocks;
+    g_gam += (size_t)f * L;
+    g_alpha += f;
+    g_w += (size_t)f * G;
     double alpha_acc = 0.0;
     for (int l = 0; l < L && lpart; ++l) {
         double acc = 0.0;

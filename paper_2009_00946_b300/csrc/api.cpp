@@ -11,6 +11,14 @@
 #include "setup.h"
 #include "solver.h"
 
+namespace fewha {
+// records of the debug build's bounds checks, one reader per CUDA source
+int dbg_read_fused(unsigned long long* first, unsigned long long* count);
+int dbg_read_solver(unsigned long long* first, unsigned long long* count);
+int dbg_read_fitcg(unsigned long long* first, unsigned long long* count);
+int dbg_read_noalloc(unsigned long long* first, unsigned long long* count);
+}  // namespace fewha
+
 struct fewha_handle {
     fewha::SolverBase* s = nullptr;
     std::string msg;
@@ -269,6 +277,25 @@ int fewha_backward(fewha_handle* h, const void* slopes, int n_iter, const void* 
     return done(h, h->s->backward(slopes, n_iter, tape, layers_bar, grad_cn2, grad_alpha, grad_w, grad_slopes));
 }
 
+long fewha_tape_bytes_batch(const fewha_handle* h, int n_iter, int n_frames) {
+    if (!h || n_iter < 1 || n_frames < 1 || n_frames > 65535) return -1;
+    return (long)h->s->tape_size_batch(n_iter, n_frames);
+}
+
+int fewha_solve_taped_batch(fewha_handle* h, int n_frames, const void* slopes, int n_iter, void* tape,
+                            void* layers_out) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->solve_taped_batch(n_frames, slopes, n_iter, tape, layers_out));
+}
+
+int fewha_backward_batch(fewha_handle* h, int n_frames, const void* slopes, int n_iter, const void* tape,
+                         const void* layers_bar, double* grad_cn2, double* grad_alpha, double* grad_w,
+                         void* grad_slopes) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->backward_batch(n_frames, slopes, n_iter, tape, layers_bar, grad_cn2, grad_alpha, grad_w,
+                                        grad_slopes));
+}
+
 long long fewha_launch_count(const fewha_handle* h) {
     if (!h) return -1;
     return h->s->launches;
@@ -383,6 +410,27 @@ long long fewha_batch_launch_count(const fewha_batch* b) {
 int fewha_batch_autotune(fewha_batch* b, int n_iter, int reps, char* report, int len) {
     if (!b) return FEWHA_ERR_ARG;
     return bdone(b, b->b->autotune(n_iter, reps, report, len));
+}
+
+int fewha_debug_bounds(unsigned long long* first, unsigned long long* count) {
+    if (!first || !count) return FEWHA_ERR_ARG;
+    int (*const readers[])(unsigned long long*, unsigned long long*) = {
+        fewha::dbg_read_fused, fewha::dbg_read_solver, fewha::dbg_read_fitcg, fewha::dbg_read_noalloc};
+    *first = 0ull;
+    *count = 0ull;
+    int built = 0;
+    for (auto rd : readers) {
+        unsigned long long f = 0ull, c = 0ull;
+        const int st = rd(&f, &c);
+        if (st < 0) {
+            cudaGetLastError();
+            return FEWHA_ERR_CUDA;
+        }
+        built = st;
+        if (!*first) *first = f;
+        *count += c;
+    }
+    return built;
 }
 
 }  // extern "C"

@@ -5,7 +5,7 @@
 // debug build checks, at every gather and scatter of the hot path, that the
 // computed index lies inside the buffer it addresses: the global state and
 // field vectors (against the instance's sizes) and the CTA's own or a cluster
-// peer's shared memory (against the launch's shared-memory size).  A failed
+// peer's shared memory (against the launch's dynamic shared-memory size).  A failed
 // check records the site and index, counts the violation and SKIPS the
 // access, so the kernel never touches memory outside its buffers; the host
 // reads the record with fewha_debug_bounds.
@@ -48,30 +48,35 @@ enum DbgSite {
 static __device__ unsigned long long g_dbg_first;   // site << 48 | (index & (2^48 - 1)) of the first violation
 static __device__ unsigned long long g_dbg_count;
 
-__device__ __noinline__ void dbg_fail(int site, long long idx) {
+static __device__ __noinline__ void dbg_fail(int site, long long idx) {
     atomicCAS(&g_dbg_first, 0ull, ((unsigned long long)site << 48) | ((unsigned long long)idx & 0xffffffffffffull));
     atomicAdd(&g_dbg_count, 1ull);
 }
 
 // index i of an access of `width` elements inside [0, n)
-__device__ __forceinline__ bool dbg_in(long long i, long long n, int width, int site) {
+static __device__ __forceinline__ bool dbg_in(long long i, long long n, int width, int site) {
     if (i >= 0 && i + width <= n) return true;
     dbg_fail(site, i);
     return false;
 }
 
-__device__ __forceinline__ unsigned dbg_smem_bytes() {
+static __device__ __forceinline__ unsigned dbg_dyn_smem_bytes() {
     unsigned b;
-    asm("mov.u32 %0, %%total_smem_size;" : "=r"(b));
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(b));
     return b;
 }
 
-// `bytes` bytes at the generic address p inside this CTA's shared memory
-__device__ __forceinline__ bool dbg_in_smem(const void* p, int bytes, int site) {
+// `bytes` bytes at the generic address p inside this CTA's dynamic shared
+// memory (every checked shared-memory buffer lives there).  The offset is
+// taken from the start of the dynamic region in the shared window: the
+// window's own addresses do not start at 0 on this architecture.
+static __device__ __forceinline__ bool dbg_in_smem(const void* p, int bytes, int site) {
+    extern __shared__ __align__(16) unsigned char dbg_dyn_smem[];
     if (__isShared(p)) {
-        const unsigned long long a = (unsigned long long)__cvta_generic_to_shared(p);
-        if (a + (unsigned)bytes <= dbg_smem_bytes()) return true;
-        dbg_fail(site, (long long)a);
+        const long long a =
+            (long long)__cvta_generic_to_shared(p) - (long long)__cvta_generic_to_shared(dbg_dyn_smem);
+        if (a >= 0 && a + bytes <= (long long)dbg_dyn_smem_bytes()) return true;
+        dbg_fail(site, a);
     } else {
         dbg_fail(site, -1);
     }

@@ -26,12 +26,15 @@
 // B are bounded grid barriers; every CTA sums the same per-CTA partials in the
 // same order, so all hold bit-identical CG scalars (deterministic result).
 // The last step applies the gain in place of its barrier.
+#include "debug.cuh"
 #include "fitcg.h"
 
 #include <algorithm>
 #include <vector>
 
 namespace fewha {
+
+FEWHA_DBG_READER(dbg_read_fitcg)
 
 namespace {
 
@@ -178,7 +181,7 @@ constexpr int kFitTabMax = 2048;
 // sum_l bilinear(phi_l) along direction t at pupil node (i, jx); toff, ln,
 // loff: the direction-layer table offsets [T][L], layer sides and offsets
 __device__ __forceinline__ float lay_sample(const DevFit<float>& F, const float* phi, const int* toff, const int* ln,
-                                            const int* loff, int t, int i, int jx) {
+                                            const int* loff, int t, int i, int jx, long nphi) {
     float acc = 0.f;
     for (int l0 = 0; l0 < F.L; l0 += kFitLU) {
         int cy[kFitLU], cx[kFitLU], n[kFitLU], o[kFitLU];
@@ -199,6 +202,12 @@ __device__ __forceinline__ float lay_sample(const DevFit<float>& F, const float*
 #pragma unroll
         for (int u = 0; u < kFitLU; ++u) {
             if (l0 + u < F.L) {
+                if (!FEWHA_IN(o[u] + (long)cy[u] * n[u] + cx[u], nphi, n[u] + 2, kDbgFit)) {
+                    cy[u] = cx[u] = 0;   // a valid node; its value is not used
+                    ty[u] = tx[u] = 0.f;
+                    o[u] = 0;
+                    n[u] = 0;
+                }
                 const float* f = phi + o[u] + (long)cy[u] * n[u] + cx[u];
                 v[u][0] = f[0];
                 v[u][1] = f[1];
@@ -223,7 +232,7 @@ constexpr int kFitU = 8;
 
 // A lane's share of row i of a CSR matrix times x: entries sub, sub + gsz, ...
 __device__ __forceinline__ float csr_dot(const int* row, const int* col, const float* val, const float* x, int i,
-                                         int sub, int gsz) {
+                                         int sub, int gsz, int nx) {
     float s = 0.f;
     const int j1 = row[i + 1];
     for (int j0 = row[i] + sub; j0 < j1; j0 += kFitU * gsz) {
@@ -234,6 +243,7 @@ __device__ __forceinline__ float csr_dot(const int* row, const int* col, const f
             const int j = j0 + u * gsz;
             c[u] = j < j1 ? __ldg(col + j) : 0;
             a[u] = j < j1 ? __ldg(val + j) : 0.f;
+            if (!FEWHA_IN(c[u], nx, 1, kDbgFit)) c[u] = 0;
         }
 #pragma unroll
         for (int u = 0; u < kFitU; ++u) xv[u] = x[c[u]];
@@ -297,9 +307,10 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_cg(const __grid_constant
         const int* toff = staged ? s_toff : F.ftab_off;
         const int* lns = staged ? s_ln : F.lay_n;
         const int* loff = staged ? s_loff : F.lay_off;
+        [[maybe_unused]] const long nphi = (long)loff[F.L - 1] + (long)lns[F.L - 1] * lns[F.L - 1];
         for (int e = gtid; e < Tn; e += nthr) {
             const int t = e / nn, idx = e - t * nn, i = idx / np1, jx = idx - i * np1;
-            B.v[e] = lay_sample(F, P.phi, toff, lns, loff, t, i, jx);
+            B.v[e] = lay_sample(F, P.phi, toff, lns, loff, t, i, jx, nphi);
         }
         fit_barrier(P, target, &s_abort);
         // 2: r = sum_t P^DM_t^T v_t - A x, p = r (groups of lanes per row, as in A)
@@ -309,8 +320,8 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_cg(const __grid_constant
             const int i = i0 + (lane >> lp);
             float s = 0.f;
             if (i < NA) {
-                s = csr_dot(P.prow, P.pcol, P.pval, B.v, i, subp, gpz);
-                s -= csr_dot(P.row, P.col, P.val, B.x, i, subp, gpz);
+                s = csr_dot(P.prow, P.pcol, P.pval, B.v, i, subp, gpz, Tn);
+                s -= csr_dot(P.row, P.col, P.val, B.x, i, subp, gpz, NA);
             }
             s = group_sum(s, lp);
             if (subp == 0 && i < NA) {
@@ -350,6 +361,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_cg(const __grid_constant
                 const int j = nb + u * gsz;
                 nc[u] = j < ne ? __ldg(P.col + j) : 0;
                 na[u] = j < ne ? __ldg(P.val + j) : 0.f;
+                if (!FEWHA_IN(nc[u], NA, 1, kDbgFit)) nc[u] = 0;
             }
         };
         first_round(gwarp << (5 - lg));
@@ -377,6 +389,7 @@ __global__ void __launch_bounds__(kFitThreads, 1) k_fit_cg(const __grid_constant
                         const int j = j0 + u * gsz;
                         c[u] = j < j1 ? __ldg(P.col + j) : 0;
                         a[u] = j < j1 ? __ldg(P.val + j) : 0.f;
+                        if (!FEWHA_IN(c[u], NA, 1, kDbgFit)) c[u] = 0;
                     }
 #pragma unroll
                     for (int u = 0; u < kFitU; ++u) {

@@ -1135,7 +1135,8 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
             const float* src = I.psi + sgi[g * 8 + 4];
             float* dst = stg + sgi[g * 8 + 6];
             for (int e = tid; e < c4; e += NT)
-                if (FEWHA_IN(sgi[g * 8 + 4] + (e << 2), I.NW, 4, kDbgStgSrc)) cp_async16(dst + (e << 2), src + (e << 2));
+                if (FEWHA_IN(sgi[g * 8 + 4] + (e << 2), I.NW + 8, 4, kDbgStgSrc))   // 8 floats of padding past NW
+                    cp_async16(dst + (e << 2), src + (e << 2));
         }
         // the CG scalars of this iteration, while the copies are in flight
         // (part A from the sensor phase when that CTA computed it there)

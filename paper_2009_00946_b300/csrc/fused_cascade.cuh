@@ -430,7 +430,8 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
             for (int e = tid; e < rows * w4; e += NT) {
                 const int rr = mg ? (int)__umulhi((unsigned)e, mg) : e, x = e - rr * w4;
                 const int a0 = (s0 + (ilo + rr) * np1) & ~3;
-                if (FEWHA_IN(a0 + 4 * x, I.NW, 4, kDbgStgSrc)) cp_async16(dst + rr * W + 4 * x, I.psi + a0 + 4 * x);
+                // (the field buffer carries 8 floats past NW for the 16-byte rows)
+                if (FEWHA_IN(a0 + 4 * x, I.NW + 8, 4, kDbgStgSrc)) cp_async16(dst + rr * W + 4 * x, I.psi + a0 + 4 * x);
             }
         }
         if (mode == kLpIter && tid < 32 && I.preA_cta < 0) {

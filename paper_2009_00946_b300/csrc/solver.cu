@@ -63,6 +63,10 @@ template <typename T>
 __global__ void k_precond_dot(int N, const T* __restrict__ Jinv, const T* __restrict__ r, T* __restrict__ z,
                               double* __restrict__ part) {
     __shared__ double sh[32];
+    const long fo = (long)blockIdx.z * N;   // frame blockIdx.z of a batch
+    r += fo;
+    z += fo;
+    part += (size_t)blockIdx.z * gridDim.x;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         T zi = Jinv[i] * r[i];
@@ -78,6 +82,10 @@ template <typename T>
 __global__ void k_reg_dot(int N, const T* __restrict__ aD, const T* __restrict__ z, T* __restrict__ s,
                           double* __restrict__ part) {
     __shared__ double sh[32];
+    const long fo = (long)blockIdx.z * N;
+    z += fo;
+    s += fo;
+    part += (size_t)blockIdx.z * gridDim.x;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         T si = s[i] + aD[i] * z[i];
@@ -108,6 +116,9 @@ __device__ double sum_partials(const double* part, int n, double* sh) {
 // Alg. 2 scalar recurrence: beta = rho/rho_old, alpha = rho/(mu - rho beta/alpha_old).
 __global__ void k_alg2_scalars(const double* part_rho, const double* part_mu, double* sc, int k, int* errw) {
     __shared__ double sh[32];
+    part_rho += (size_t)blockIdx.x * kRedBlocks;   // one block per frame of a batch
+    part_mu += (size_t)blockIdx.x * kRedBlocks;
+    sc += (size_t)blockIdx.x * kNumScalars;
     double rho = sum_partials(part_rho, kRedBlocks, sh);
     __syncthreads();
     double mu = sum_partials(part_mu, kRedBlocks, sh);
@@ -137,6 +148,14 @@ template <typename T>
 __global__ void k_alg2_update(int N, const double* __restrict__ sc, int first, const T* __restrict__ z,
                               const T* __restrict__ s, T* __restrict__ p, T* __restrict__ q, T* __restrict__ c,
                               T* __restrict__ r) {
+    const long fo = (long)blockIdx.z * N;
+    sc += (size_t)blockIdx.z * kNumScalars;
+    z += fo;
+    s += fo;
+    p += fo;
+    q += fo;
+    c += fo;
+    r += fo;
     const T beta = (T)sc[kBeta], a = (T)sc[kAlphaK];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         T pi = first ? z[i] : z[i] + beta * p[i];
@@ -157,6 +176,8 @@ template <typename T>
 __global__ void k_fwd_rows(DevGeo<T> G, int j, const T* __restrict__ src, T* __restrict__ dst) {
     int l = blockIdx.y;
     if (j > G.lay_J[l]) return;
+    src += (long)blockIdx.z * G.N;   // frame blockIdx.z of a batch
+    dst += (long)blockIdx.z * G.N;
     int n = G.lay_n[l], m = n >> (j - 1), half = m >> 1;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m * m) return;
@@ -174,6 +195,8 @@ template <typename T>
 __global__ void k_fwd_cols(DevGeo<T> G, int j, const T* __restrict__ src, T* __restrict__ dst) {
     int l = blockIdx.y;
     if (j > G.lay_J[l]) return;
+    src += (long)blockIdx.z * G.N;   // frame blockIdx.z of a batch
+    dst += (long)blockIdx.z * G.N;
     int n = G.lay_n[l], m = n >> (j - 1), half = m >> 1;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m * m) return;
@@ -193,6 +216,8 @@ template <typename T>
 __global__ void k_inv_cols(DevGeo<T> G, int j, const T* __restrict__ src, T* __restrict__ dst) {
     int l = blockIdx.y;
     if (j > G.lay_J[l]) return;
+    src += (long)blockIdx.z * G.N;   // frame blockIdx.z of a batch
+    dst += (long)blockIdx.z * G.N;
     int n = G.lay_n[l], m = n >> (j - 1), half = m >> 1;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m * m) return;
@@ -213,6 +238,8 @@ template <typename T>
 __global__ void k_inv_rows(DevGeo<T> G, int j, const T* __restrict__ src, T* __restrict__ dst) {
     int l = blockIdx.y;
     if (j > G.lay_J[l]) return;
+    src += (long)blockIdx.z * G.N;   // frame blockIdx.z of a batch
+    dst += (long)blockIdx.z * G.N;
     int n = G.lay_n[l], m = n >> (j - 1), half = m >> 1;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m * m) return;
@@ -237,6 +264,8 @@ __global__ void k_inv_rows(DevGeo<T> G, int j, const T* __restrict__ src, T* __r
 template <typename T>
 __global__ void k_P(DevGeo<T> G, const T* __restrict__ phi, T* __restrict__ psi) {
     int g = blockIdx.y, ns = G.wfs_n[g], np1 = ns + 1;
+    phi += (long)blockIdx.z * G.N;
+    psi += (long)blockIdx.z * G.NW;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= np1 * np1) return;
     int i = idx / np1, jx = idx - i * np1;
@@ -257,6 +286,8 @@ __global__ void k_P(DevGeo<T> G, const T* __restrict__ phi, T* __restrict__ psi)
 template <typename T>
 __global__ void k_gamma_w(DevGeo<T> G, const T* __restrict__ psi, T* __restrict__ sl) {
     int g = blockIdx.y, ns = G.wfs_n[g], np1 = ns + 1;
+    psi += (long)blockIdx.z * G.NW;
+    sl += (long)blockIdx.z * G.S;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ns * ns) return;
     int a = idx / ns, b = idx - a * ns;
@@ -299,6 +330,8 @@ __global__ void k_resid_w(DevGeo<T> G, const T* __restrict__ s, const T* __restr
 template <typename T>
 __global__ void k_weight_meas(DevGeo<T> G, const T* __restrict__ s, T* __restrict__ sl, int* errw) {
     int g = blockIdx.y, ns = G.wfs_n[g];
+    s += (long)blockIdx.z * G.S;
+    sl += (long)blockIdx.z * G.S;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ns * ns) return;
     bool on = G.mask[G.wfs_moff[g] + idx] != 0;
@@ -340,6 +373,8 @@ __global__ void k_tt_apply(DevGeo<T> G, const double* __restrict__ sums, T* __re
 template <typename T>
 __global__ void k_gammaT(DevGeo<T> G, const T* __restrict__ sl, T* __restrict__ psi) {
     int g = blockIdx.y, ns = G.wfs_n[g], np1 = ns + 1;
+    sl += (long)blockIdx.z * G.S;
+    psi += (long)blockIdx.z * G.NW;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= np1 * np1) return;
     int i = idx / np1, jx = idx - i * np1;
@@ -363,6 +398,8 @@ __global__ void k_gammaT(DevGeo<T> G, const T* __restrict__ sl, T* __restrict__ 
 template <typename T>
 __global__ void k_PT(DevGeo<T> G, const T* __restrict__ psi, T* __restrict__ y) {
     int l = blockIdx.y, n = G.lay_n[l];
+    psi += (long)blockIdx.z * G.NW;
+    y += (long)blockIdx.z * G.N;
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * n) return;
     int p = idx / n, q = idx - p * n;
@@ -940,10 +977,14 @@ class Solver : public SolverBase {
     }
 
     // ---- building blocks (all enqueued on `stream`) ----
-    dim3 grid_layers(int count) const { return dim3((count + 255) / 256, G.L); }
+    // frames of the current launch sequence: 1, or the frame count of a batched
+    // taped solve / reverse mode (every kernel of the operator chain takes
+    // frame blockIdx.z, the frames' vectors contiguous)
+    int nb = 1;
+    dim3 grid_layers(int count) const { return dim3((count + 255) / 256, G.L, nb); }
 
     int inv_dwt(const T* src, T* dst) {   // dst = W^T src (dst != src)
-        FEWHA_CUDA(cudaMemcpyAsync(dst, src, (size_t)G.N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+        FEWHA_CUDA(cudaMemcpyAsync(dst, src, (size_t)G.N * nb * sizeof(T), cudaMemcpyDeviceToDevice, stream));
         for (int j = G.Jmax; j >= 1; --j) {
             int m = G.nmax >> (j - 1);
             k_inv_cols<T><<<grid_layers(m * m), 256, 0, stream>>>(G, j, dst, tmp);
@@ -955,7 +996,7 @@ class Solver : public SolverBase {
     }
 
     int fwd_dwt(const T* src, T* dst) {   // dst = W src (dst != src)
-        FEWHA_CUDA(cudaMemcpyAsync(dst, src, (size_t)G.N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+        FEWHA_CUDA(cudaMemcpyAsync(dst, src, (size_t)G.N * nb * sizeof(T), cudaMemcpyDeviceToDevice, stream));
         for (int j = 1; j <= G.Jmax; ++j) {
             int m = G.nmax >> (j - 1);
             k_fwd_rows<T><<<grid_layers(m * m), 256, 0, stream>>>(G, j, dst, tmp);
@@ -969,6 +1010,10 @@ class Solver : public SolverBase {
     // LGS tip-tilt filter on weighted slopes (no-op without filtered sensors)
     int tt_filter(T* sl) {
         if (!G.any_tt) return FEWHA_OK;
+        if (nb != 1) {
+            err = "the LGS tip-tilt filter runs on single frames";
+            return FEWHA_ERR_STATE;
+        }
         k_tt_sums<T><<<dim3(G.G, 2), 256, 0, stream>>>(G, sl, ttsums);
         FEWHA_LAUNCHED();
         k_tt_apply<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, ttsums, sl);
@@ -978,7 +1023,7 @@ class Solver : public SolverBase {
 
     int backproject(const T* weighted_slopes, T* out) {   // out = W P^T Gamma^T sl
         int np1 = G.nsmax + 1;
-        k_gammaT<T><<<dim3((np1 * np1 + 255) / 256, G.G), 256, 0, stream>>>(G, weighted_slopes, wpsi2);
+        k_gammaT<T><<<dim3((np1 * np1 + 255) / 256, G.G, nb), 256, 0, stream>>>(G, weighted_slopes, wpsi2);
         FEWHA_LAUNCHED();
         k_PT<T><<<grid_layers(G.nmax * G.nmax), 256, 0, stream>>>(G, wpsi2, y);
         FEWHA_LAUNCHED();
@@ -988,9 +1033,9 @@ class Solver : public SolverBase {
     int data_term(const T* x, T* out) {   // out = W P^T Gamma^T C^{-1} Gamma P W^T x
         TRY(inv_dwt(x, phi));
         int np1 = G.nsmax + 1;
-        k_P<T><<<dim3((np1 * np1 + 255) / 256, G.G), 256, 0, stream>>>(G, phi, wpsi);
+        k_P<T><<<dim3((np1 * np1 + 255) / 256, G.G, nb), 256, 0, stream>>>(G, phi, wpsi);
         FEWHA_LAUNCHED();
-        k_gamma_w<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, wpsi, wsl);
+        k_gamma_w<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G, nb), 256, 0, stream>>>(G, wpsi, wsl);
         FEWHA_LAUNCHED();
         TRY(tt_filter(wsl));
         return backproject(wsl, out);
@@ -1024,7 +1069,7 @@ class Solver : public SolverBase {
 
     int apply_M_dev(const T* x, T* out) {
         TRY(data_term(x, out));
-        k_reg_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(G.N, aD, x, out, part2);
+        k_reg_dot<T><<<dim3(kRedBlocks, 1, nb), kRedThreads, 0, stream>>>(G.N, aD, x, out, part2);
         FEWHA_LAUNCHED();
         return FEWHA_OK;
     }
@@ -1583,30 +1628,88 @@ class Solver : public SolverBase {
     }
 
     // ---- differentiation: set_params, taped solve, reverse mode ----
+    // Work of up to adj_cap frames differentiated together (one solve is a
+    // batch of 1): forward iterates and adjoint vectors, their partials and
+    // scalars, and frame-batched copies of the operator chain's scratch
+    // (phi, wpsi, wpsi2, wsl, y, tmp, part, part2) that stand in for the
+    // single-frame buffers while a batch runs.
     T *ac = nullptr, *ar = nullptr, *ap = nullptr, *aq = nullptr, *ab = nullptr;   // forward work
     T *cb = nullptr, *rb = nullptr, *pb = nullptr, *qb = nullptr, *sb = nullptr, *My = nullptr, *psiz = nullptr;
+    T *bphi = nullptr, *bwpsi = nullptr, *bwpsi2 = nullptr, *bwsl = nullptr, *by = nullptr, *btmp = nullptr;
     double *tsc = nullptr, *asc = nullptr, *apart = nullptr, *alpart = nullptr, *awpart = nullptr, *gam = nullptr;
-    bool adj_ready = false;
+    double *bpart = nullptr, *bpart2 = nullptr;
+    int adj_cap = 0;
 
-    int adj_init() {
-        if (adj_ready) return FEWHA_OK;
-        const size_t N = hs.N;
-        for (T** v : {&ac, &ar, &ap, &aq, &ab, &cb, &rb, &pb, &qb, &sb, &My}) TRY(alloc(*v, N));
-        TRY(alloc(psiz, hs.NW));
-        TRY(alloc(tsc, kNumScalars));
-        TRY(alloc(asc, 8));
-        TRY(alloc(apart, 6 * kRedBlocks));
-        TRY(alloc(alpart, (size_t)hs.L * kRedBlocks));
-        TRY(alloc(awpart, (size_t)hs.G * kRedBlocks));
-        std::vector<double> g(hs.L);
-        for (int l = 0; l < hs.L; ++l) g[l] = hs.lay[l].cn2;
-        TRY(upload(gam, g));
-        FEWHA_CUDA(cudaMemset(tsc, 0, kNumScalars * sizeof(double)));
-        adj_ready = true;
+    template <typename U>
+    void release(U*& ptr) {
+        if (!ptr) return;
+        cudaFree(ptr);
+        allocs.erase(std::remove(allocs.begin(), allocs.end(), (void*)ptr), allocs.end());
+        ptr = nullptr;
+    }
+
+    int adj_init(int B) {
+        if (!gam) {
+            std::vector<double> g(hs.L);
+            for (int l = 0; l < hs.L; ++l) g[l] = hs.lay[l].cn2;
+            TRY(upload(gam, g));
+        }
+        if (adj_cap >= B) return FEWHA_OK;
+        FEWHA_CUDA(cudaStreamSynchronize(stream));   // the smaller buffers may still be in use
+        for (T** v : {&ac, &ar, &ap, &aq, &ab, &cb, &rb, &pb, &qb, &sb, &My, &psiz, &bphi, &bwpsi, &bwpsi2, &bwsl, &by,
+                      &btmp})
+            release(*v);
+        for (double** v : {&tsc, &asc, &apart, &alpart, &awpart, &bpart, &bpart2}) release(*v);
+        adj_cap = 0;
+        const size_t N = (size_t)hs.N * B, NW = (size_t)hs.NW * B, S = (size_t)hs.S * B;
+        for (T** v : {&ac, &ar, &ap, &aq, &ab, &cb, &rb, &pb, &qb, &sb, &My, &bphi, &by, &btmp}) TRY(alloc(*v, N));
+        for (T** v : {&psiz, &bwpsi, &bwpsi2}) TRY(alloc(*v, NW));
+        TRY(alloc(bwsl, S));
+        TRY(alloc(tsc, (size_t)kNumScalars * B));
+        TRY(alloc(asc, (size_t)8 * B));
+        TRY(alloc(apart, (size_t)6 * kRedBlocks * B));
+        TRY(alloc(alpart, (size_t)hs.L * kRedBlocks * B));
+        TRY(alloc(awpart, (size_t)hs.G * kRedBlocks * B));
+        TRY(alloc(bpart, (size_t)kRedBlocks * B));
+        TRY(alloc(bpart2, (size_t)kRedBlocks * B));
+        FEWHA_CUDA(cudaMemset(tsc, 0, (size_t)kNumScalars * B * sizeof(double)));
+        adj_cap = B;
         return FEWHA_OK;
     }
 
+    // The operator chain on B frames: the batch scratch swapped in, nb = B.
+    struct FrameBatch {
+        Solver* sv;
+        T *phi, *wpsi, *wpsi2, *wsl, *y, *tmp;
+        double *part, *part2;
+        FrameBatch(Solver* s_, int B)
+            : sv(s_), phi(s_->phi), wpsi(s_->wpsi), wpsi2(s_->wpsi2), wsl(s_->wsl), y(s_->y), tmp(s_->tmp),
+              part(s_->part), part2(s_->part2) {
+            sv->nb = B;
+            sv->phi = sv->bphi;
+            sv->wpsi = sv->bwpsi;
+            sv->wpsi2 = sv->bwpsi2;
+            sv->wsl = sv->bwsl;
+            sv->y = sv->by;
+            sv->tmp = sv->btmp;
+            sv->part = sv->bpart;
+            sv->part2 = sv->bpart2;
+        }
+        ~FrameBatch() {
+            sv->nb = 1;
+            sv->phi = phi;
+            sv->wpsi = wpsi;
+            sv->wpsi2 = wpsi2;
+            sv->wsl = wsl;
+            sv->y = y;
+            sv->tmp = tmp;
+            sv->part = part;
+            sv->part2 = part2;
+        }
+    };
+
     size_t tape_size(int n_iter) const override { return tape_bytes(hs.N, n_iter, sizeof(T)); }
+    size_t tape_size_batch(int n_iter, int B) const override { return tape_bytes(hs.N, n_iter, sizeof(T), B); }
 
     // New gamma_l, alpha, w_g for M and b; the Jacobi preconditioner keeps
     // the values of create (it is a constant of the differentiated solve).
@@ -1646,44 +1749,53 @@ class Solver : public SolverBase {
         return FEWHA_OK;
     }
 
-    // K steps of Alg. 2 from c = 0, r = b(slopes), every iterate on the tape;
-    // the frame state (c, r, b of fewha_solve) is not touched.
+    // K steps of Alg. 2 from c = 0, r = b(slopes) for each of B frames
+    // (slopes [B][S], layers [B][N]), every iterate on the tape (layout in
+    // adjoint.cuh); the frames run together, each kernel of the chain taking
+    // all of them.  The frame state (c, r, b of fewha_solve) is not touched.
     int solve_taped(const void* sl, int n_iter, void* tape, void* lout) override {
+        return solve_taped_batch(1, sl, n_iter, tape, lout);
+    }
+
+    int solve_taped_batch(int B, const void* sl, int n_iter, void* tape, void* lout) override {
         if (G.any_tt) {
             err = "differentiation does not model the LGS tip-tilt filter";
             return FEWHA_ERR_STATE;
         }
-        if (!sl || !tape || n_iter < 1 || n_iter > 100000) {
-            err = "solve_taped needs slopes, a tape and n_iter >= 1";
+        if (!sl || !tape || B < 1 || B > 65535 || n_iter < 1 || n_iter > 100000) {
+            err = "solve_taped needs slopes, a tape, 1 <= frames <= 65535 and n_iter >= 1";
             return FEWHA_ERR_ARG;
         }
-        TRY(adj_init());
+        TRY(adj_init(B));
         fused_layers_ready = false;   // phi is scratch of the operators below
+        FrameBatch fb(this, B);
         const long N = hs.N;
+        const size_t NB = (size_t)N * B;
         T* tv = (T*)tape;
-        double* ts = (double*)((char*)tape + tape_vec_bytes(N, n_iter, sizeof(T)));
-        k_weight_meas<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, (const T*)sl, wsl,
-                                                                                         errw);
+        double* ts = (double*)((char*)tape + tape_vec_bytes(N, n_iter, sizeof(T), B));
+        const dim3 red(kRedBlocks, 1, B);
+        k_weight_meas<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G, B), 256, 0, stream>>>(G, (const T*)sl, wsl,
+                                                                                            errw);
         FEWHA_LAUNCHED();
         TRY(backproject(wsl, ab));
-        FEWHA_CUDA(cudaMemsetAsync(ac, 0, N * sizeof(T), stream));
-        FEWHA_CUDA(cudaMemcpyAsync(ar, ab, N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+        FEWHA_CUDA(cudaMemsetAsync(ac, 0, NB * sizeof(T), stream));
+        FEWHA_CUDA(cudaMemcpyAsync(ar, ab, NB * sizeof(T), cudaMemcpyDeviceToDevice, stream));
         for (int k = 0; k < n_iter; ++k) {
-            T* v = tv + (size_t)k * kTapeVecs * N;
-            T *rk = v + kTapeR * N, *zk = v + kTapeZ * N, *sk = v + kTapeS * N;
-            FEWHA_CUDA(cudaMemcpyAsync(rk, ar, N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
-            k_precond_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, Jinv, ar, zk, part);
+            T* v = tv + (size_t)k * kTapeVecs * NB;
+            T *rk = v + kTapeR * NB, *zk = v + kTapeZ * NB, *sk = v + kTapeS * NB;
+            FEWHA_CUDA(cudaMemcpyAsync(rk, ar, NB * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+            k_precond_dot<T><<<red, kRedThreads, 0, stream>>>(N, Jinv, ar, zk, part);
             FEWHA_LAUNCHED();
             TRY(data_term(zk, sk));
-            k_reg_dot<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, aD, zk, sk, part2);
+            k_reg_dot<T><<<red, kRedThreads, 0, stream>>>(N, aD, zk, sk, part2);
             FEWHA_LAUNCHED();
-            k_alg2_scalars<<<1, 256, 0, stream>>>(part, part2, tsc, k, errw);
+            k_alg2_scalars<<<B, 256, 0, stream>>>(part, part2, tsc, k, errw);
             FEWHA_LAUNCHED();
-            k_alg2_update<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, tsc, k == 0, zk, sk, ap, aq, ac, ar);
+            k_alg2_update<T><<<red, kRedThreads, 0, stream>>>(N, tsc, k == 0, zk, sk, ap, aq, ac, ar);
             FEWHA_LAUNCHED();
-            FEWHA_CUDA(cudaMemcpyAsync(v + kTapeP * N, ap, N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
-            FEWHA_CUDA(cudaMemcpyAsync(v + kTapeQ * N, aq, N * sizeof(T), cudaMemcpyDeviceToDevice, stream));
-            k_tape_scalars<<<1, 32, 0, stream>>>(tsc, ts, k);
+            FEWHA_CUDA(cudaMemcpyAsync(v + kTapeP * NB, ap, NB * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+            FEWHA_CUDA(cudaMemcpyAsync(v + kTapeQ * NB, aq, NB * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+            k_tape_scalars<<<B, 32, 0, stream>>>(tsc, ts, k);
             FEWHA_LAUNCHED();
         }
         if (lout) TRY(inv_dwt(ac, (T*)lout));
@@ -1695,63 +1807,75 @@ class Solver : public SolverBase {
     // overwritten) and the slopes (optional).
     int backward(const void* sl, int n_iter, const void* tape, const void* lbar, double* g_gam, double* g_alpha,
                  double* g_w, void* g_s) override {
+        return backward_batch(1, sl, n_iter, tape, lbar, g_gam, g_alpha, g_w, g_s);
+    }
+
+    // The same for the B frames of solve_taped_batch: layers_bar [B][N]; per
+    // frame gradients g_gam [B][L], g_alpha [B], g_w [B][G], g_s [B][S].
+    int backward_batch(int B, const void* sl, int n_iter, const void* tape, const void* lbar, double* g_gam,
+                       double* g_alpha, double* g_w, void* g_s) override {
         if (G.any_tt) {
             err = "differentiation does not model the LGS tip-tilt filter";
             return FEWHA_ERR_STATE;
         }
-        if (!sl || !tape || !lbar || !g_gam || !g_alpha || !g_w || n_iter < 1 || n_iter > 100000) {
-            err = "backward needs slopes, the tape, the layer cotangent, gradient outputs and n_iter >= 1";
+        if (!sl || !tape || !lbar || !g_gam || !g_alpha || !g_w || B < 1 || B > 65535 || n_iter < 1 ||
+            n_iter > 100000) {
+            err = "backward needs slopes, the tape, the layer cotangent, gradient outputs, 1 <= frames <= 65535 "
+                  "and n_iter >= 1";
             return FEWHA_ERR_ARG;
         }
-        TRY(adj_init());
+        TRY(adj_init(B));
         fused_layers_ready = false;
+        FrameBatch fb(this, B);
         const long N = hs.N;
+        const size_t NB = (size_t)N * B;
         const T* tv = (const T*)tape;
-        const double* ts = (const double*)((const char*)tape + tape_vec_bytes(N, n_iter, sizeof(T)));
-        FEWHA_CUDA(cudaMemsetAsync(g_gam, 0, hs.L * sizeof(double), stream));
-        FEWHA_CUDA(cudaMemsetAsync(g_alpha, 0, sizeof(double), stream));
-        FEWHA_CUDA(cudaMemsetAsync(g_w, 0, hs.G * sizeof(double), stream));
-        FEWHA_CUDA(cudaMemsetAsync(asc, 0, 8 * sizeof(double), stream));
-        for (T* v : {rb, pb, qb}) FEWHA_CUDA(cudaMemsetAsync(v, 0, N * sizeof(T), stream));
+        const double* ts = (const double*)((const char*)tape + tape_vec_bytes(N, n_iter, sizeof(T), B));
+        FEWHA_CUDA(cudaMemsetAsync(g_gam, 0, (size_t)B * hs.L * sizeof(double), stream));
+        FEWHA_CUDA(cudaMemsetAsync(g_alpha, 0, (size_t)B * sizeof(double), stream));
+        FEWHA_CUDA(cudaMemsetAsync(g_w, 0, (size_t)B * hs.G * sizeof(double), stream));
+        FEWHA_CUDA(cudaMemsetAsync(asc, 0, (size_t)B * 8 * sizeof(double), stream));
+        for (T* v : {rb, pb, qb}) FEWHA_CUDA(cudaMemsetAsync(v, 0, NB * sizeof(T), stream));
         TRY(fwd_dwt((const T*)lbar, cb));   // phi = W^T c  ->  c-bar = W phi-bar
         const int np1 = G.nsmax + 1;
-        const dim3 gnodes((np1 * np1 + 255) / 256, G.G);
+        const dim3 gnodes((np1 * np1 + 255) / 256, G.G, B);
+        const dim3 red(kRedBlocks, 1, B);
         for (int k = n_iter - 1; k >= 0; --k) {
-            const T* v = tv + (size_t)k * kTapeVecs * N;
-            const T* vo = k > 0 ? tv + (size_t)(k - 1) * kTapeVecs * N : nullptr;
-            const T *rk = v + kTapeR * N, *zk = v + kTapeZ * N, *sk = v + kTapeS * N;
-            k_adj_dots<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, cb, rb, pb, qb, v + kTapeP * N, v + kTapeQ * N,
-                                                                  vo ? vo + kTapeP * N : nullptr,
-                                                                  vo ? vo + kTapeQ * N : nullptr, apart);
+            const T* v = tv + (size_t)k * kTapeVecs * NB;
+            const T* vo = k > 0 ? tv + (size_t)(k - 1) * kTapeVecs * NB : nullptr;
+            const T *rk = v + kTapeR * NB, *zk = v + kTapeZ * NB, *sk = v + kTapeS * NB;
+            k_adj_dots<T><<<red, kRedThreads, 0, stream>>>(N, cb, rb, pb, qb, v + kTapeP * NB, v + kTapeQ * NB,
+                                                           vo ? vo + kTapeP * NB : nullptr,
+                                                           vo ? vo + kTapeQ * NB : nullptr, apart);
             FEWHA_LAUNCHED();
-            k_adj_scalars<<<1, 256, 0, stream>>>(apart, ts, k, asc);
+            k_adj_scalars<<<B, 256, 0, stream>>>(apart, ts, k, asc);
             FEWHA_LAUNCHED();
-            k_adj_vec1<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, asc, cb, rb, pb, qb, zk, sb);
+            k_adj_vec1<T><<<red, kRedThreads, 0, stream>>>(N, asc, cb, rb, pb, qb, zk, sb);
             FEWHA_LAUNCHED();
             TRY(apply_M_dev(sb, My));   // leaves P W^T sb in wpsi
             // sb^T (dM/dtheta) z_k: alpha D part per layer, C^{-1} part per sensor
-            k_layer_dot<T><<<dim3(kRedBlocks, G.L), kRedThreads, 0, stream>>>(G, sb, aD, zk, alpart);
+            k_layer_dot<T><<<dim3(kRedBlocks, G.L, B), kRedThreads, 0, stream>>>(G, sb, aD, zk, alpart);
             FEWHA_LAUNCHED();
             TRY(inv_dwt(zk, phi));
             k_P<T><<<gnodes, 256, 0, stream>>>(G, phi, psiz);
             FEWHA_LAUNCHED();
-            k_wfs_dot<T><<<dim3(kRedBlocks, G.G), kRedThreads, 0, stream>>>(G, psiz, wpsi, nullptr, awpart);
+            k_wfs_dot<T><<<dim3(kRedBlocks, G.G, B), kRedThreads, 0, stream>>>(G, psiz, wpsi, nullptr, awpart);
             FEWHA_LAUNCHED();
-            k_adj_accum<<<1, 256, 0, stream>>>(alpart, G.L, awpart, G.G, gam, hs.alpha, g_gam, g_alpha, g_w);
+            k_adj_accum<<<B, 256, 0, stream>>>(alpart, G.L, awpart, G.G, gam, hs.alpha, g_gam, g_alpha, g_w);
             FEWHA_LAUNCHED();
-            k_adj_vec2<T><<<kRedBlocks, kRedThreads, 0, stream>>>(N, asc, pb, qb, rb, zk, sk, rk, My, Jinv);
+            k_adj_vec2<T><<<red, kRedThreads, 0, stream>>>(N, asc, pb, qb, rb, zk, sk, rk, My, Jinv);
             FEWHA_LAUNCHED();
         }
         // b-bar = r-bar: b-bar^T (db/dw_g) and the slope gradient C^{-1} Gamma P W^T b-bar
         TRY(inv_dwt(rb, phi));
         k_P<T><<<gnodes, 256, 0, stream>>>(G, phi, psiz);
         FEWHA_LAUNCHED();
-        k_wfs_dot<T><<<dim3(kRedBlocks, G.G), kRedThreads, 0, stream>>>(G, psiz, nullptr, (const T*)sl, awpart);
+        k_wfs_dot<T><<<dim3(kRedBlocks, G.G, B), kRedThreads, 0, stream>>>(G, psiz, nullptr, (const T*)sl, awpart);
         FEWHA_LAUNCHED();
-        k_adj_accum<<<1, 256, 0, stream>>>(nullptr, 0, awpart, G.G, gam, hs.alpha, g_gam, g_alpha, g_w);
+        k_adj_accum<<<B, 256, 0, stream>>>(nullptr, 0, awpart, G.G, gam, hs.alpha, g_gam, g_alpha, g_w);
         FEWHA_LAUNCHED();
         if (g_s) {
-            k_gamma_w<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G), 256, 0, stream>>>(G, psiz, (T*)g_s);
+            k_gamma_w<T><<<dim3((G.nsmax * G.nsmax + 255) / 256, G.G, B), 256, 0, stream>>>(G, psiz, (T*)g_s);
             FEWHA_LAUNCHED();
         }
         return FEWHA_OK;

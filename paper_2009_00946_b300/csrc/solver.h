@@ -120,6 +120,10 @@ class SolverBase {
     virtual int backward(const void* slopes, int n_iter, const void* tape, const void* layers_bar, double* g_gam,
                          double* g_alpha, double* g_w, void* g_slopes) = 0;
     virtual size_t tape_size(int n_iter) const = 0;
+    virtual size_t tape_size_batch(int n_iter, int n_frames) const = 0;
+    virtual int solve_taped_batch(int n_frames, const void* slopes, int n_iter, void* tape, void* layers_out) = 0;
+    virtual int backward_batch(int n_frames, const void* slopes, int n_iter, const void* tape, const void* layers_bar,
+                               double* g_gam, double* g_alpha, double* g_w, void* g_slopes) = 0;
     virtual int set_loop(int closed) = 0;
     virtual int operator_dims(int op, long& n_in, long& n_out) = 0;
     virtual int apply_operator(int op, const void* x, void* y, int on_device) = 0;

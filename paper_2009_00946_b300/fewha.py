@@ -11,11 +11,16 @@ from __future__ import annotations
 import ctypes
 import os
 import re
+import time
 
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfewha.so")
+# FEWHA_DEBUG=1: the debug build (bounds checks at every gather and scatter,
+# reported by fewha_debug_bounds) in place of the release library
+if os.environ.get("FEWHA_DEBUG") == "1":
+    LIB_PATH = os.path.join(HERE, "libfewha_debug.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "fewha.h")
 
 MAX_WFS, MAX_LAYERS, MAX_DMS, MAX_FIT_DIRS, MAX_JACOBI_LEVELS = 16, 64, 8, 64, 16
@@ -70,7 +75,7 @@ def lib():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise OSError("libfewha.so not built: run python -m paper_2009_00946_b300.build")
+        raise OSError("%s not built: run python -m paper_2009_00946_b300.build" % os.path.basename(LIB_PATH))
     L = ctypes.CDLL(LIB_PATH)
     vp, ci, cd, cl, cll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_longlong
     sig = {
@@ -112,6 +117,9 @@ def lib():
         "fewha_tape_bytes": (cl, [vp, ci]),
         "fewha_solve_taped": (ci, [vp, vp, ci, vp, vp]),
         "fewha_backward": (ci, [vp, vp, ci, vp, vp, vp, vp, vp, vp]),
+        "fewha_tape_bytes_batch": (cl, [vp, ci, ci]),
+        "fewha_solve_taped_batch": (ci, [vp, ci, vp, ci, vp, vp]),
+        "fewha_backward_batch": (ci, [vp, ci, vp, ci, vp, vp, vp, vp, vp, vp]),
         "fewha_batch_create": (ci, [ci, ctypes.POINTER(Geometry), ctypes.POINTER(Profile), vp, ci, ci,
                                     ctypes.POINTER(vp)]),
         "fewha_batch_destroy": (ci, [vp]),
@@ -125,6 +133,7 @@ def lib():
         "fewha_batch_launch_count": (cll, [vp]),
         "fewha_batch_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
         "fewha_measure_l2": (ci, [cl, ci, ci, ctypes.POINTER(cd), ctypes.POINTER(cd), ctypes.c_char_p, ci]),
+        "fewha_debug_bounds": (ci, [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -348,6 +357,7 @@ class Solver:
         """One whole frame through the captured CUDA graph.  All arrays host
         (numpy; the call synchronises) or all device (torch CUDA tensors; the
         call only enqueues on the solver's stream)."""
+        t0 = time.perf_counter()
         ps, ds = _ptr(slopes, self._dt(), self.S, None)
         pl = pd = None
         if layers_out is not None:
@@ -358,8 +368,12 @@ class Solver:
             pd, dd = _ptr(dm_out, self._dt(), self.NA, None)
             if dd != ds:
                 raise ValueError("slopes and dm_out must both be host or both be device")
-        self._check(lib().fewha_frame(self.h, ps, int(n_iter), 1 if warm else 0, float(gain), int(n_fit), pl, pd,
-                                      ds))
+        t1 = time.perf_counter()
+        st = lib().fewha_frame(self.h, ps, int(n_iter), 1 if warm else 0, float(gain), int(n_fit), pl, pd, ds)
+        t2 = time.perf_counter()
+        self._check(st)
+        # host clock of this call (s): entry, before and after the library call
+        self.last_call = (t0, t1, t2)
 
     def launch_count(self) -> int:
         return int(lib().fewha_launch_count(self.h))
@@ -438,6 +452,47 @@ class Solver:
         self._check(lib().fewha_backward(self.h, ps, int(n_iter), ctypes.c_void_p(tape.data_ptr()), pb,
                                          ctypes.c_void_p(g_cn2.data_ptr()), ctypes.c_void_p(g_alpha.data_ptr()),
                                          ctypes.c_void_p(g_w.data_ptr()), pg))
+
+    def tape_bytes_batch(self, n_iter: int, n_frames: int) -> int:
+        return int(lib().fewha_tape_bytes_batch(self.h, int(n_iter), int(n_frames)))
+
+    def solve_taped_batch(self, slopes, n_iter: int, tape, layers_out=None):
+        """Taped solves of every frame of slopes ([B, S] device tensor) in one
+        launch sequence; layers_out [B, N] or None."""
+        if not (slopes.is_cuda and slopes.dtype == self.torch_dtype and slopes.dim() == 2 and
+                slopes.shape[1] == self.S and slopes.is_contiguous()):
+            raise ValueError("slopes must be a contiguous [frames, S] device tensor of the solver's dtype")
+        B = int(slopes.shape[0])
+        if not (tape.is_cuda and tape.numel() >= self.tape_bytes_batch(n_iter, B) and tape.data_ptr() % 8 == 0):
+            raise ValueError("an 8-byte aligned device tape of tape_bytes_batch(n_iter, frames) bytes needed")
+        pl = None
+        if layers_out is not None:
+            if not (layers_out.is_cuda and layers_out.dtype == self.torch_dtype and
+                    tuple(layers_out.shape) == (B, self.N) and layers_out.is_contiguous()):
+                raise ValueError("layers_out must be a contiguous [frames, N] device tensor")
+            pl = ctypes.c_void_p(layers_out.data_ptr())
+        self._check(lib().fewha_solve_taped_batch(self.h, B, ctypes.c_void_p(slopes.data_ptr()), int(n_iter),
+                                                  ctypes.c_void_p(tape.data_ptr()), pl))
+
+    def backward_batch(self, slopes, n_iter: int, tape, layers_bar, g_cn2, g_alpha, g_w, g_slopes=None):
+        """Reverse mode of solve_taped_batch: per-frame gradients g_cn2 [B, L],
+        g_alpha [B], g_w [B, G] (float64) and g_slopes [B, S] (or None)."""
+        import torch
+        B = int(slopes.shape[0])
+        for t, shp, dt in ((layers_bar, (B, self.N), self.torch_dtype), (g_cn2, (B, self.n_layers), torch.float64),
+                           (g_alpha, (B,), torch.float64), (g_w, (B, self.n_wfs), torch.float64)):
+            if not (t.is_cuda and t.dtype == dt and tuple(t.shape) == shp and t.is_contiguous()):
+                raise ValueError("layers_bar and the gradients: contiguous device tensors of shape %s" % (shp,))
+        pg = None
+        if g_slopes is not None:
+            if not (g_slopes.is_cuda and g_slopes.dtype == self.torch_dtype and tuple(g_slopes.shape) == (B, self.S)
+                    and g_slopes.is_contiguous()):
+                raise ValueError("g_slopes must be a contiguous [frames, S] device tensor")
+            pg = ctypes.c_void_p(g_slopes.data_ptr())
+        vp = ctypes.c_void_p
+        self._check(lib().fewha_backward_batch(self.h, B, vp(slopes.data_ptr()), int(n_iter), vp(tape.data_ptr()),
+                                               vp(layers_bar.data_ptr()), vp(g_cn2.data_ptr()),
+                                               vp(g_alpha.data_ptr()), vp(g_w.data_ptr()), pg))
 
     def set_trace(self, on: bool = True):
         self._check(lib().fewha_set_trace(self.h, 1 if on else 0))
@@ -582,3 +637,28 @@ def measure_l2(nbytes: int = 48 << 20, passes: int = 40, reps: int = 5) -> dict:
         raise FewhaError(st, msg.value.decode())
     return {"read_gbs": rd.value, "copy_gbs": cp.value, "bytes": int(nbytes), "passes": int(passes),
             "reps": int(reps)}
+
+
+# bounds-check sites of the debug build (include/fewha.h, FEWHA_DBG_*)
+DEBUG_SITES = {1: "sensor window source", 2: "sensor window staging", 3: "sensor bilinear read",
+               4: "slope index", 5: "Gamma^T output", 6: "field staging source", 7: "field staging",
+               8: "P^T gather read", 9: "DWT store into a row owner", 10: "DWT store into a column owner",
+               11: "coefficient index", 12: "tip-tilt correction", 13: "layer output",
+               14: "row-stripe DWT peer read", 15: "table staging", 16: "plain P", 17: "plain P^T",
+               18: "plain Gamma / Gamma^T", 19: "fit", 20: "no-allocation transform"}
+
+
+def debug_bounds() -> dict:
+    """Violations recorded by the debug build's bounds checks since the last
+    call (and clears them): {"debug_build", "count", "site", "index"}.  The
+    release build checks nothing and reports debug_build False."""
+    first, count = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    st = lib().fewha_debug_bounds(ctypes.byref(first), ctypes.byref(count))
+    if st < 0:
+        raise FewhaError(st, "reading the bounds-check records failed")
+    site = int(first.value >> 48)
+    idx = int(first.value & ((1 << 48) - 1))
+    if idx >= 1 << 47:
+        idx -= 1 << 48
+    return {"debug_build": st == 1, "count": int(count.value), "site": DEBUG_SITES.get(site, site) if site else None,
+            "index": idx if site else None}

@@ -98,3 +98,38 @@ def test_batch_rejects_invalid_arguments_on_host():
     assert st == 1 and "instance 0" in L.fewha_batch_last_error(None).decode()
     assert L.fewha_batch_destroy(None) == 1 and L.fewha_batch_frame(None, None, 4, 1, None, 0) == 1
     assert L.fewha_batch_launch_count(None) == -1
+
+
+def test_debug_library_exports_every_declared_symbol():
+    """libfewha_debug.so (the bounds-checked build of the same sources) loads
+    beside the release library and exports the same entry points."""
+    import os
+    path = os.path.join(os.path.dirname(fewha.LIB_PATH), "libfewha_debug.so")
+    assert os.path.exists(path)
+    D = ctypes.CDLL(path)
+    missing = [n for n in fewha.declared_symbols() if not hasattr(D, n)]
+    assert not missing, missing
+
+
+def test_release_build_reports_no_bounds_checks():
+    """The release library compiles every check out: fewha_debug_bounds says
+    so (0) without touching a device."""
+    L = fewha.lib()
+    first, count = ctypes.c_ulonglong(7), ctypes.c_ulonglong(7)
+    if fewha.LIB_PATH.endswith("libfewha.so"):
+        assert L.fewha_debug_bounds(ctypes.byref(first), ctypes.byref(count)) == 0
+        assert first.value == 0 and count.value == 0
+    assert L.fewha_debug_bounds(None, ctypes.byref(count)) == 1   # FEWHA_ERR_ARG
+
+
+def test_debug_site_numbers_agree():
+    """The check sites are numbered alike in include/fewha.h (FEWHA_DBG_*),
+    in the device code's enum and in the binding's names."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    hdr = open(os.path.join(root, "include", "fewha.h")).read()
+    dev = open(os.path.join(root, "paper_2009_00946_b300", "csrc", "debug.cuh")).read()
+    h = sorted(int(v) for v in re.findall(r"FEWHA_DBG_[A-Z_]+ = (\d+)", hdr))
+    d = sorted(int(v) for v in re.findall(r"kDbg[A-Za-z]+ = (\d+)", dev) if int(v) > 0)
+    assert h == d == sorted(fewha.DEBUG_SITES) == list(range(1, len(h) + 1))

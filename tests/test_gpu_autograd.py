@@ -153,3 +153,54 @@ def test_fp32_autograd_batch_of_32_frames_matches_oracle(env):
     assert rel(got[0], ogg) < 2e-3, (got[0], ogg)
     assert abs(got[1] - oga) <= 2e-3 * abs(oga), (got[1], oga)
     assert rel(got[2], ogw) < 2e-3, (got[2], ogw)
+
+
+def _batch_grads(env, S_, dt, s, phit):
+    torch = env[0]
+    B = s.shape[0]
+    with torch.cuda.stream(S_.stream):
+        sd = torch.from_numpy(np.ascontiguousarray(s)).to("cuda", dt)
+        tape = torch.empty(S_.tape_bytes_batch(N_ITER, B), dtype=torch.uint8, device="cuda")
+        phi = torch.empty(B, S_.N, dtype=dt, device="cuda")
+        S_.solve_taped_batch(sd, N_ITER, tape, phi)
+        phibar = (2.0 * (phi - torch.from_numpy(phit.reshape(B, -1)).to("cuda", dt))).contiguous()
+        gg = torch.empty(B, S_.n_layers, dtype=torch.float64, device="cuda")
+        ga = torch.empty(B, dtype=torch.float64, device="cuda")
+        gw = torch.empty(B, S_.n_wfs, dtype=torch.float64, device="cuda")
+        gs = torch.empty_like(sd)
+        S_.backward_batch(sd, N_ITER, tape, phibar, gg, ga, gw, gs)
+    S_.sync()
+    return [t.cpu().numpy() for t in (phi, gg, ga, gw, gs)]
+
+
+def test_frame_batch_equals_single_frames_bit_for_bit_fp64(env):
+    """The frame-batched taped solve and reverse mode (every kernel of the
+    chain taking all frames in one launch) give each frame exactly what the
+    one-frame calls give -- the same kernels and, per frame, the same
+    reduction order -- and match the oracle's adjoint."""
+    torch, fewha, _, cfg, g, pr, Jinv, S, T = env
+    B = 8
+    with fewha.Solver(cfg, precision=fewha.FP64) as S_:
+        phi, gg, ga, gw, gs = _batch_grads(env, S_, torch.float64, S[:B], T[:B])
+        for f in range(B):
+            ph1, _, gg1, ga1, gw1, gs1 = _gpu_grads(env, S_, fewha.FP64, S[f], T[f])
+            assert np.array_equal(phi[f], ph1), f
+            assert np.array_equal(gg[f], gg1) and ga[f] == ga1 and np.array_equal(gw[f], gw1), f
+            assert np.array_equal(gs[f], gs1), f
+    for f in (0, B - 1):
+        _, ogg, oga, ogw, ogs = fo.solve_loss_grad(g, pr, Jinv, S[f], T[f], N_ITER, with_slopes=True)
+        assert rel(gg[f], ogg) < 1e-8 and abs(ga[f] - oga) <= 1e-8 * abs(oga) and rel(gw[f], ogw) < 1e-8, f
+        assert rel(gs[f], ogs) < 1e-8, f
+
+
+def test_frame_batch_launch_count_does_not_grow_with_frames(env):
+    """One launch sequence for the whole batch: 32 frames take as many kernel
+    launches as one frame."""
+    torch, fewha, _, cfg, g, pr, Jinv, S, T = env
+    with fewha.Solver(cfg, precision=fewha.FP32) as S_:
+        n0 = S_.launch_count()
+        _batch_grads(env, S_, torch.float32, S[:1].astype(np.float32), T[:1])
+        n1 = S_.launch_count() - n0
+        _batch_grads(env, S_, torch.float32, S.astype(np.float32), T)
+        n32 = S_.launch_count() - n0 - n1
+        assert n1 > 0 and n32 == n1, (n1, n32)
