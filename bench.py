@@ -828,7 +828,8 @@ def main():
     pin_s = torch.empty(S.S, dtype=torch.float32).pin_memory()
     pin_l = torch.empty(S.N, dtype=torch.float32).pin_memory()
     host_s, host_l = pin_s.numpy(), pin_l.numpy()   # the caller's arrays, made once
-    e2e, e2e_ft = [], []
+    run_frame = S.bind_frame(host_s, N_ITER, warm=True, layers_out=host_l)   # the real-time loop's call
+    e2e, e2e_ft, e2e_unbound = [], [], []
     n_e2e = min(K, 300)
     for k in range(n_e2e + 5):
         host_s[:] = pool[(W + K + k) % len(pool)]
@@ -836,14 +837,20 @@ def main():
             flush.fill_(2.0)
         S.stream.synchronize()
         t0 = time.perf_counter()
-        S.frame(host_s, N_ITER, warm=True, layers_out=host_l)
+        run_frame()
         t3 = time.perf_counter()
         e2e.append((t3 - t0) * 1e6)
-        ft = S.frame_timing()
-        c0, c1, c2 = S.last_call
-        ft.update(py_args_us=(c1 - t0) * 1e6, ctypes_call_us=(c2 - c1) * 1e6, py_after_us=(t3 - c2) * 1e6)
-        e2e_ft.append(ft)
-    e2e, e2e_ft = e2e[5:], e2e_ft[5:]
+        e2e_ft.append(S.frame_timing())
+    # the same frames through the unbound call (arguments checked every frame)
+    for k in range(min(n_e2e, 100) + 5):
+        host_s[:] = pool[(W + K + k) % len(pool)]
+        with torch.cuda.stream(S.stream):
+            flush.fill_(2.0)
+        S.stream.synchronize()
+        t0 = time.perf_counter()
+        S.frame(host_s, N_ITER, warm=True, layers_out=host_l)
+        e2e_unbound.append((time.perf_counter() - t0) * 1e6)
+    e2e, e2e_ft, e2e_unbound = e2e[5:], e2e_ft[5:], e2e_unbound[5:]
     # the same host frames bracketed by CUDA events (the kernel reading and
     # writing the pinned buffers through their device mapping), the GPU kept
     # busy by the flush so the host's side does not show as idle time
@@ -852,29 +859,52 @@ def main():
         with torch.cuda.stream(S.stream):
             flush.fill_(3.0)
         ev[k][0].record(S.stream)
-        S.frame(host_s, N_ITER, warm=True, layers_out=host_l)
+        run_frame()
         ev[k][1].record(S.stream)
     S.stream.synchronize()
     e2e_dev = float(np.percentile([a.elapsed_time(b) * 1e3 for a, b in ev], 50))
+    # host slopes in, layers left on the device: the slope reads alone
+    run_in = S.bind_frame(host_s, N_ITER, warm=True)
+    for k in range(50):
+        with torch.cuda.stream(S.stream):
+            flush.fill_(3.0)
+        ev[k][0].record(S.stream)
+        run_in()
+        ev[k][1].record(S.stream)
+    S.stream.synchronize()
+    e2e_dev_in = float(np.percentile([a.elapsed_time(b) * 1e3 for a, b in ev], 50))
+    # the slopes read by the kernel through the pinned mapping instead of the copy
+    S.set_host_transfer(False)
+    for k in range(50):
+        with torch.cuda.stream(S.stream):
+            flush.fill_(3.0)
+        ev[k][0].record(S.stream)
+        run_in()
+        ev[k][1].record(S.stream)
+    S.stream.synchronize()
+    e2e_dev_in_mapped = float(np.percentile([a.elapsed_time(b) * 1e3 for a, b in ev], 50))
+    S.set_host_transfer(True)
     e2e_breakdown = {
         "host_prep_us": float(np.median([f["prep_us"] for f in e2e_ft])),
         "host_launch_us": float(np.median([f["launch_us"] for f in e2e_ft])),
         "host_wait_us": float(np.median([f["wait_us"] for f in e2e_ft])),
         "library_call_us": float(np.median([f["total_us"] for f in e2e_ft])),
         "python_call_us": float(np.median([e - f["total_us"] for e, f in zip(e2e, e2e_ft)])),
-        "python_args_us": float(np.median([f["py_args_us"] for f in e2e_ft])),
-        "ctypes_call_us": float(np.median([f["ctypes_call_us"] for f in e2e_ft])),
-        "python_after_us": float(np.median([f["py_after_us"] for f in e2e_ft])),
+        "unbound_call_p50_us": float(np.percentile(e2e_unbound, 50)),
         "library_call_p99_us": float(np.percentile([f["total_us"] for f in e2e_ft], 99)),
         "host_wait_p99_us": float(np.percentile([f["wait_us"] for f in e2e_ft], 99)),
         "device_frame_with_host_io_us": e2e_dev,
         "host_io_in_kernel_us": e2e_dev - p50,
+        "slopes_in_us": e2e_dev_in - p50,
+        "slopes_in_through_mapping_us": e2e_dev_in_mapped - p50,
+        "layers_write_in_kernel_us": e2e_dev - e2e_dev_in,
         "host_io_bytes": (S.S + S.N) * 4,
         "host_io_gbs": (S.S + S.N) * 4 / max(e2e_dev - p50, 1e-3) / 1e3,
         "what": "library_call = prep + launch + wait (host steady clock inside fewha_frame); python_call = "
-                "the e2e time of a frame minus its library_call (binding and interpreter; python_args before the "
-                "library call, ctypes_call around it, python_after after it); host_io_in_kernel = device time of a host frame minus the device "
-                "p50 (slopes read, layers written through the pinned buffers' device mapping)"}
+                "the e2e time of a frame minus its library_call (the bound call's interpreter and ctypes share); "
+                "unbound_call = the same frames through Solver.frame, whose arguments are checked every frame; host_io_in_kernel = device time of a host frame minus the device "
+                "p50: slopes_in (one copy-engine transfer; slopes_in_through_mapping: read by the kernel through the "
+                "pinned mapping instead) and layers_write_in_kernel (written through the mapping)"}
 
     # ---- the plain FP64 path (one kernel per operator) on the same frames ----
     P64 = fewha.Solver(cfg, precision=fewha.FP64, k_rr=K_RR)
@@ -927,7 +957,7 @@ def main():
         "e2e": {"value": float(np.percentile(e2e, 50)), "unit": UNIT, "p99": float(np.percentile(e2e, 99)),
                 "h2d_bytes_per_step": S.S * 4, "d2h_bytes_per_step": S.N * 4, "frames": n_e2e,
                 "breakdown": e2e_breakdown,
-                "how": "fewha_frame with pinned host slopes and layers (read and written by the kernel through their device mapping; the host waits on the mapped completion word), host wall clock per frame"},
+                "how": "fewha_frame through Solver.bind_frame (the buffers bound once, the slopes refilled in place each frame) with pinned host slopes and layers (read and written by the kernel through their device mapping; the host waits on the mapped completion word), host wall clock per frame"},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "l2_measured": l2,

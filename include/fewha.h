@@ -242,6 +242,17 @@ int fewha_get_frame_timing(fewha_handle* h, double* out);
  * mirrors are sized for the fitting directions), ARG. */
 int fewha_set_loop(fewha_handle* h, int closed);
 
+/* The paper has no counterpart: how a host frame's slopes reach the fused
+ * kernel (fewha_frame with host buffers).  slopes_by_copy = 1 (default): one
+ * copy-engine transfer of the pinned slopes into the handle's slope buffer
+ * precedes the kernel in the frame's graph; 0: the kernel reads them through
+ * the pinned buffer's device mapping.  The layers come back through the
+ * mapping either way (posted writes), and the host waits on the completion
+ * word.  On a host link where the kernel's reads wait a round trip each,
+ * the copy is the faster of the two.  Drops the captured frame graphs.
+ * Errors: ARG. */
+int fewha_set_host_transfer(fewha_handle* h, int slopes_by_copy);
+
 /* Wait for the handle's stream and return the device error word (OK, INPUT,
  * BREAKDOWN, TIMEOUT).  The word is cleared after it has been read. */
 int fewha_sync(fewha_handle* h);

@@ -296,6 +296,11 @@ int fewha_backward_batch(fewha_handle* h, int n_frames, const void* slopes, int 
                                         grad_slopes));
 }
 
+int fewha_set_host_transfer(fewha_handle* h, int slopes_by_copy) {
+    if (!h || (slopes_by_copy != 0 && slopes_by_copy != 1)) return FEWHA_ERR_ARG;
+    return done(h, h->s->set_host_transfer(slopes_by_copy));
+}
+
 long long fewha_launch_count(const fewha_handle* h) {
     if (!h) return -1;
     return h->s->launches;

@@ -481,6 +481,7 @@ __device__ void alg2_part_b(const FParams& P, const FInst& I, int k, const ScalA
 struct CtaCache {
     int wkey, lkey, wtab;       // cached sensor item, layer item; window tables built
     int ltkey;                  // layer item whose staging ranges and gather tables are built
+    int ltx;                    // layer item whose gather tables are rewritten to staging offsets
     int lres, il_valid;         // the CTA has one layer item for the launch; IL holds it
     int pre_k;                  // iteration whose scalar part A is in pre (-1: none)
     double pre[6];              // rho, beta, t, alpha_{k-1}, mu part (as two floats)
@@ -580,7 +581,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                             CtaCache* cc, int k) {
     const int tid = threadIdx.x, NT = blockDim.x;
     fmark(P, mode == kModeRhs ? 30 : 20);
-    if (P.shared_tables && tid == 0) cc->lkey = cc->ltkey = -1;   // this phase overwrites the layer tables
+    if (P.shared_tables && tid == 0) cc->lkey = cc->ltkey = cc->ltx = -1;   // this phase overwrites the layer tables
     if (cc->wkey != item) {
         __syncthreads();   // the previous item's data may still be in use
         if (tid == 0) sensor_desc(P, item, cc);
@@ -1409,7 +1410,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     if (threadIdx.x == 0) {
         s_abort = 0;
         *fmark_counter() = 0;
-        cc.wkey = cc.lkey = cc.ltkey = -1;
+        cc.wkey = cc.lkey = cc.ltkey = cc.ltx = -1;
         cc.wtab = 0;
         cc.lres = (l_hi - l_lo == 1) ? 1 : 0;
         cc.il_valid = 0;

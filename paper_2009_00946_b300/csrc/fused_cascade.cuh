@@ -100,8 +100,56 @@ __device__ void layer_tables_v1(const FParams& P, int rank, const CtaCache* cc, 
     for (int e = tid; e < nc; e += NT) cp_async4(gix + e, rb + hs + e);
 }
 
-// P^T gather into the column stripe: thread (column c, rows rr0, rr0 + rstep,
-// ...); per sensor the column entries are read once for all its rows.
+// The gather tables of a freshly staged layer item, rewritten once for the
+// gather below: a row entry's sensor row i becomes the offset in the staged
+// fields of that row's column 0 (its slot + (i - ilo) W + the row's 16-byte
+// shift - jlo), clamped to a staged row, and a padding column entry (weight
+// 0) points at a staged column, so that the gather does no index arithmetic
+// per tap.  The caller synchronises the CTA before the tables are read.
+__device__ __forceinline__ void pt_tables_to_offsets(const int* sgi, int2* xt, int2* yt, int G, int n, int R, int KG) {
+    const int tid = threadIdx.x, NT = blockDim.x;
+    for (int e = tid; e < G * n * KG; e += NT) {
+        const int g = e / (n * KG);
+        const int ilo = sgi[g * 8], ihi = sgi[g * 8 + 1];
+        if (ihi <= ilo) continue;
+        const int np1 = sgi[g * 8 + 3], jlo = sgi[g * 8 + 4], W = sgi[g * 8 + 5], s0 = sgi[g * 8 + 6];
+        int2 ye = yt[e];
+        const int i = min(max(ye.x, ilo), ihi - 1);
+        ye.x = sgi[g * 8 + 2] + (i - ilo) * W + ((s0 + i * np1) & 3) - jlo;
+        yt[e] = ye;
+    }
+    for (int e = tid; e < G * R * KG; e += NT) {
+        const int g = e / (R * KG);
+        const int2 xe = xt[e];
+        if (__int_as_float(xe.y) == 0.f) xt[e] = make_int2(sgi[g * 8 + 4], xe.y);
+    }
+}
+
+// KGT (j, w) or (offset, w) entries at e: two per 16-byte load when KGT is even
+template <int KGT>
+__device__ __forceinline__ void pt_entries(const int2* e, int* idx, float* w) {
+    if constexpr (KGT % 2 == 0) {
+#pragma unroll
+        for (int b = 0; b < KGT; b += 2) {
+            const int4 v = *reinterpret_cast<const int4*>(e + b);
+            idx[b] = v.x;
+            w[b] = __int_as_float(v.y);
+            idx[b + 1] = v.z;
+            w[b + 1] = __int_as_float(v.w);
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < KGT; ++b) {
+            const int2 v = e[b];
+            idx[b] = v.x;
+            w[b] = __int_as_float(v.y);
+        }
+    }
+}
+
+// P^T gather into the column stripe from the rewritten tables: thread
+// (column c, rows rr0, rr0 + rstep, ...); per sensor the column entries are
+// read once for all its rows.
 template <int KGT>
 __device__ __forceinline__ void pt_gather_cols(const int* sgi, const float* stg, const int2* xt, const int2* yt,
                                                float* Z, int G, int n, int R) {
@@ -115,33 +163,25 @@ __device__ __forceinline__ void pt_gather_cols(const int* sgi, const float* stg,
 #pragma unroll
         for (int u = 0; u < kRows; ++u) acc[u] = 0.f;
         for (int g = 0; g < G; ++g) {
-            const int ilo = sgi[g * 8], ihi = sgi[g * 8 + 1];
-            if (ihi <= ilo) continue;
-            const int np1 = sgi[g * 8 + 3], jlo = sgi[g * 8 + 4], W = sgi[g * 8 + 5], s0 = sgi[g * 8 + 6];
-            const float* base = stg + sgi[g * 8 + 2] - jlo;
+            if (sgi[g * 8 + 1] <= sgi[g * 8]) continue;
             int xj[KGT];
             float xw[KGT];
-#pragma unroll
-            for (int b = 0; b < KGT; ++b) {
-                const int2 xe = xt[(g * R + q) * KGT + b];
-                xw[b] = __int_as_float(xe.y);
-                xj[b] = (xw[b] != 0.f) ? xe.x : jlo;   // padding entries: any staged column
-            }
+            pt_entries<KGT>(xt + (g * R + q) * KGT, xj, xw);
 #pragma unroll
             for (int u = 0; u < kRows; ++u) {
                 const int rr = rb + u * rstep;
                 if (rr >= n) break;
-                const int2* yr = yt + (g * n + rr) * KGT;
+                int yo[KGT];
+                float yw[KGT];
+                pt_entries<KGT>(yt + (g * n + rr) * KGT, yo, yw);
 #pragma unroll
                 for (int a = 0; a < KGT; ++a) {
-                    const int2 ye = yr[a];
-                    const int i = max(ye.x, ilo);
-                    const float* row = base + (i - ilo) * W + ((s0 + i * np1) & 3);
+                    const float* row = stg + yo[a];
                     float racc = 0.f;
 #pragma unroll
                     for (int b = 0; b < KGT; ++b)
                         if (FEWHA_IN_SMEM(row + xj[b], 4, kDbgPtRead)) racc += xw[b] * row[xj[b]];
-                    acc[u] += __int_as_float(ye.y) * racc;
+                    acc[u] += yw[a] * racc;
                 }
             }
         }
@@ -451,6 +491,12 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
         cp_async_wait_all();
         if (tabs && tid == 0) cc->ltkey = li;
         __syncthreads();
+        if (cc->ltx != li) {   // tables copied here or at launch start: rewritten once
+            pt_tables_to_offsets(sgi, const_cast<int2*>(xt), const_cast<int2*>(yt), G, n, R, KG);
+            __syncthreads();
+            if (tid == 0) cc->ltx = li;
+        }
+
         if (I.tt_any) {
             // LGS tip-tilt filter (R15): Gamma^T C^{-1} s = Gamma^T (w mask s) -
             // (w / n_act) (M_x Gamma^T (mask 1_x) + M_y Gamma^T (mask 1_y)) with

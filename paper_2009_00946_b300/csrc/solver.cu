@@ -1200,6 +1200,16 @@ class Solver : public SolverBase {
         return FEWHA_OK;
     }
 
+    // host frames on the fused path: slopes by a copy-engine transfer (1) or
+    // read by the kernel through the pinned buffer's mapping (0)
+    bool host_slopes_copy = true;
+
+    int set_host_transfer(int slopes_by_copy) override {
+        host_slopes_copy = slopes_by_copy != 0;
+        drop_graphs();
+        return FEWHA_OK;
+    }
+
     int set_loop(int c) override {
         if (c && hs.M == 0) {
             err = "the closed loop needs deformable mirrors";
@@ -1955,10 +1965,14 @@ class Solver : public SolverBase {
         const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         // the fused kernel reads the slopes and writes the layers where they
         // are: device buffers, or pinned host buffers through their device
-        // mapping (the transfers happen inside the kernel, no copy nodes)
+        // mapping (the transfers happen inside the kernel, no copy nodes) --
+        // except host slopes under host_slopes_copy, which one copy-engine
+        // transfer brings into the handle's slope buffer first: the kernel's
+        // reads across the host link wait a round trip each, the copy streams
         const void* sin_dev = on_device ? sin : (stage_in ? host_dev_ptr(sin) : sin_map);
         void* lo_dev = !lo ? nullptr : on_device ? lo : (stage_l ? host_dev_ptr(lo) : lo_map);
         const bool direct = use_fused() && !closed && sin_dev && (!lo || lo_dev);
+        const bool copy_in = direct && !on_device && host_slopes_copy;
         // a host frame that is the fused launch alone reports through the
         // completion word (no error-word copy node, no stream wait)
         const bool use_done = direct && !on_device && !dm && done_dev;
@@ -1991,7 +2005,7 @@ class Solver : public SolverBase {
             int st = FEWHA_OK;
             long long l0 = launches;
             do {
-                if (!direct) {
+                if (!direct || copy_in) {
                     cudaError_t e = cudaMemcpyAsync(slopes, sin, hs.S * sizeof(T), kin, stream);
                     if (e != cudaSuccess) {
                         err = cudaGetErrorString(e);
@@ -2000,7 +2014,7 @@ class Solver : public SolverBase {
                     }
                 }
                 pol_pending = true;
-                ov_slopes = direct ? (const float*)sin_dev : nullptr;
+                ov_slopes = (direct && !copy_in) ? (const float*)sin_dev : nullptr;
                 ov_layers = (direct && lo) ? (float*)lo_dev : nullptr;
                 ov_done = use_done ? done_dev : nullptr;
                 st = solve_enqueue(n_iter, warm);

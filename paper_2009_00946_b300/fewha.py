@@ -11,7 +11,6 @@ from __future__ import annotations
 import ctypes
 import os
 import re
-import time
 
 import numpy as np
 
@@ -107,6 +106,7 @@ def lib():
                                       ctypes.POINTER(ci)]),
         "fewha_set_cluster_size": (ci, [vp, ci]),
         "fewha_set_layer_transform": (ci, [vp, ci]),
+        "fewha_set_host_transfer": (ci, [vp, ci]),
         "fewha_get_frame_timing": (ci, [vp, ctypes.POINTER(cd)]),
         "fewha_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
         "fewha_set_loop": (ci, [vp, ci]),
@@ -357,7 +357,6 @@ class Solver:
         """One whole frame through the captured CUDA graph.  All arrays host
         (numpy; the call synchronises) or all device (torch CUDA tensors; the
         call only enqueues on the solver's stream)."""
-        t0 = time.perf_counter()
         ps, ds = _ptr(slopes, self._dt(), self.S, None)
         pl = pd = None
         if layers_out is not None:
@@ -368,12 +367,38 @@ class Solver:
             pd, dd = _ptr(dm_out, self._dt(), self.NA, None)
             if dd != ds:
                 raise ValueError("slopes and dm_out must both be host or both be device")
-        t1 = time.perf_counter()
-        st = lib().fewha_frame(self.h, ps, int(n_iter), 1 if warm else 0, float(gain), int(n_fit), pl, pd, ds)
-        t2 = time.perf_counter()
-        self._check(st)
-        # host clock of this call (s): entry, before and after the library call
-        self.last_call = (t0, t1, t2)
+        self._check(lib().fewha_frame(self.h, ps, int(n_iter), 1 if warm else 0, float(gain), int(n_fit), pl, pd,
+                                      ds))
+
+    def bind_frame(self, slopes, n_iter: int, warm: bool = True, gain: float = 1.0, n_fit: int = 8,
+                   layers_out=None, dm_out=None):
+        """frame() bound to fixed buffers, for a real-time loop: the arguments
+        are checked and converted once, and each call of the returned function
+        runs one frame on what the buffers hold then (the caller refills the
+        slopes array in place).  Host arrays: the call returns with the
+        results in layers_out / dm_out; device tensors: it only enqueues."""
+        ps, ds = _ptr(slopes, self._dt(), self.S, None)
+        pl = pd = None
+        if layers_out is not None:
+            pl, dl = _ptr(layers_out, self._dt(), self.N, None)
+            if dl != ds:
+                raise ValueError("slopes and layers_out must both be host or both be device")
+        if dm_out is not None:
+            pd, dd = _ptr(dm_out, self._dt(), self.NA, None)
+            if dd != ds:
+                raise ValueError("slopes and dm_out must both be host or both be device")
+        fn = lib().fewha_frame
+        args = (self.h, ps, ctypes.c_int(int(n_iter)), ctypes.c_int(1 if warm else 0), ctypes.c_double(float(gain)),
+                ctypes.c_int(int(n_fit)), pl, pd, ctypes.c_int(ds))
+        check = self._check
+
+        def run():
+            st = fn(*args)
+            if st:
+                check(st)
+
+        run.buffers = (slopes, layers_out, dm_out)   # kept alive with the function
+        return run
 
     def launch_count(self) -> int:
         return int(lib().fewha_launch_count(self.h))
@@ -387,6 +412,11 @@ class Solver:
 
     def set_cluster_size(self, cluster_size: int):
         self._check(lib().fewha_set_cluster_size(self.h, int(cluster_size)))
+
+    def set_host_transfer(self, slopes_by_copy: bool):
+        """Host frames on the fused path: slopes by one copy-engine transfer
+        (True, default) or read by the kernel through the pinned mapping."""
+        self._check(lib().fewha_set_host_transfer(self.h, 1 if slopes_by_copy else 0))
 
     def set_layer_transform(self, form: int):
         """Fused layer phase: 0 row stripes (a cluster barrier per DWT level),
