@@ -601,10 +601,9 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     float* slx = psi + P.tile_nodes;
     float* sly = slx + P.tile_subaps;
     // per-tile interpolation tables: [l][row] window offset / weight, [l][col]
-    int* roff = (int*)(sm + P.stab_off);
-    float* rw = (float*)(roff + L * P.tile_rows);
-    int* coff = (int*)(rw + L * P.tile_rows);
-    float* cw = (float*)(coff + L * P.tile_cols);
+    // (window offset, weight bits) pairs, one 8-byte load each
+    int2* rtab = (int2*)(sm + P.stab_off);
+    int2* ctab = rtab + L * P.tile_rows;
     Acc2 mu, tmx, tmy;   // tmx, tmy: masked slope sums of a tip-tilt filtered sensor
     const bool ttg = I.tt_any && I.tt[g];
     const int ns2 = ns * ns;
@@ -719,12 +718,12 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 const bool gath = wdesc[l * kWd] < 0;
                 if (k < pr) {
                     const int rr = gath ? 2 * k : __ldg(I.cy + base + a_lo + k) - wdesc[l * kWd];
-                    roff[l * P.tile_rows + k] = rr * wdesc[l * kWd + 3] + wdesc[l * kWd + 4];
-                    rw[l * P.tile_rows + k] = __ldg(I.ty + base + a_lo + k);
+                    rtab[l * P.tile_rows + k] =
+                        make_int2(rr * wdesc[l * kWd + 3] + wdesc[l * kWd + 4], __float_as_int(__ldg(I.ty + base + a_lo + k)));
                 } else {
                     const int kk = k - pr;
-                    coff[l * P.tile_cols + kk] = gath ? 2 * kk : __ldg(I.cx + base + b_lo + kk) - wdesc[l * kWd + 1];
-                    cw[l * P.tile_cols + kk] = __ldg(I.tx + base + b_lo + kk);
+                    ctab[l * P.tile_cols + kk] = make_int2(gath ? 2 * kk : __ldg(I.cx + base + b_lo + kk) - wdesc[l * kWd + 1],
+                                                           __float_as_int(__ldg(I.tx + base + b_lo + kk)));
                 }
             }
             if (tid == 0) cc->wtab = 1;
@@ -734,10 +733,12 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         for (int e = tid; e < pr * pc; e += NT) {
             const int ii = e / pc, jj = e - ii * pc;
             float acc = 0.f;
+#pragma unroll 3
             for (int l = 0; l < L; ++l) {
                 const int nc = wdesc[l * kWd + 3];
-                const float ty = rw[l * P.tile_rows + ii], tx = cw[l * P.tile_cols + jj];
-                const float* f = win + roff[l * P.tile_rows + ii] + coff[l * P.tile_cols + jj];
+                const int2 rt = rtab[l * P.tile_rows + ii], ct = ctab[l * P.tile_cols + jj];
+                const float ty = __int_as_float(rt.y), tx = __int_as_float(ct.y);
+                const float* f = win + rt.x + ct.x;
                 if (!FEWHA_IN_SMEM(f, 4 * (nc + 2), kDbgWinP)) continue;
                 acc += (1.f - ty) * ((1.f - tx) * f[0] + tx * f[1]) + ty * ((1.f - tx) * f[nc] + tx * f[nc + 1]);
             }
