@@ -237,7 +237,7 @@ def parity_vs_oracle(fewha, cfg, pool, oracle_layers):
 # the committed full ncu capture, valid only for the kernel source it was
 # taken on (sha256 prefix of csrc/fused.cu + csrc/fused_cascade.cuh); any
 # other source reports null.
-NCU_TRAFFIC = {"fused_cu_sha256": "8cf59ab2f52e2aca", "dram_bytes": 5647616,
+NCU_TRAFFIC = {"fused_cu_sha256": "413640181c9bbd97", "dram_bytes": 5648128,
                "summary": "profiles/k_fused_frame_elt_full.md"}
 
 
@@ -497,7 +497,8 @@ def bench_autograd(torch, fewha, dev, flush, reps=20):
 
 def bench_batch(torch, fewha, dev, flush, n_frames):
     """64 uneven instances advanced by one fused launch per frame, against the
-    same 64 instances solved one after another on the plain FP64 path."""
+    same 64 instances solved one after another on the plain FP64 path and one
+    fused FP32 launch each (one frame graph per instance, back to back)."""
     cfgs = configs.c4_batch(64)
     per = [synth.random_slopes(c, 7).astype(np.float32) for c in cfgs]
     B = fewha.Batch(cfgs, k_rr=K_RR)
@@ -542,6 +543,26 @@ def bench_batch(torch, fewha, dev, flush, n_frames):
     seq = (time.perf_counter() - t0) / reps * 1e6
     for S in solvers:
         S.close()
+    # the same instances one fused FP32 launch each, back to back on one stream
+    st1 = torch.cuda.Stream()
+    solvers = [fewha.Solver(c, precision=fewha.FP32, path=fewha.PATH_FUSED, k_rr=K_RR, stream=st1) for c in cfgs]
+    s32 = [torch.from_numpy(x).to(dev) for x in per]
+    l32 = [torch.empty(S.N, dtype=torch.float32, device=dev) for S in solvers]
+    for S, x, y in zip(solvers, s32, l32):
+        S.frame(x, N_ITER, warm=True, layers_out=y)
+    ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for k in range(5):
+        with torch.cuda.stream(st1):
+            flush.fill_(float(k & 7))
+        ev1[k][0].record(st1)
+        for S, x, y in zip(solvers, s32, l32):
+            S.frame(x, N_ITER, warm=True, layers_out=y)
+        ev1[k][1].record(st1)
+    st1.synchronize()
+    seq32 = float(np.percentile([a.elapsed_time(b) * 1e3 for a, b in ev1], 50))
+    for S in solvers:
+        S.sync()
+        S.close()
     hbm, _ = measured_peaks()
     return {"workload": "64 independent instances: D 8-39 m, 16-84 subapertures, 2-9 layers on 32^2-256^2 grids, "
                         "3-6 LGS, 4 warm-started iterations each, FP32, one fused launch per frame",
@@ -549,6 +570,7 @@ def bench_batch(torch, fewha, dev, flush, n_frames):
             "instance_frames_per_s": 64 * 1e6 / p50, "frames": n_frames, "autotune": tuned,
             "sequential_fp64_us": seq, "sequential_fp64_instance_frames_per_s": 64 * 1e6 / seq,
             "speedup_vs_sequential_fp64": seq / p50,
+            "sequential_fused_fp32_us": seq32, "speedup_vs_sequential_fused_fp32": seq32 / p50,
             "roofline": {"bound": "hbm", "achieved": alg / (p50 * 1e-6) / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": alg / (p50 * 1e-6) / 1e9 / hbm, "algorithmic_bytes": alg},
             "plan": plan}

@@ -202,6 +202,36 @@ def test_fused_host_frames_pinned_and_completion_word(fw, elt_frames):
         assert rel(pin_l.numpy(), ref[11][0]) < 1e-4
 
 
+def test_bound_frames_and_both_host_transfers_bit_identical(fw, elt_frames):
+    """Solver.bind_frame (buffers bound once, the slopes refilled in place
+    each frame) and both ways host slopes reach the kernel -- one copy-engine
+    transfer (the default) or the kernel's reads through the pinned mapping --
+    give the device frames' layers bit for bit, across the replacement frame."""
+    import torch
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as A, _fused(fw, cfg, k_rr=10) as B, _fused(fw, cfg, k_rr=10) as C:
+        C.set_host_transfer(False)
+        bufs = [(torch.empty(A.S, dtype=torch.float32).pin_memory(), torch.empty(A.N, dtype=torch.float32).pin_memory())
+                for _ in range(2)]
+        runA = A.bind_frame(bufs[0][0].numpy(), 4, warm=True, layers_out=bufs[0][1].numpy())
+        runC = C.bind_frame(bufs[1][0].numpy(), 4, warm=True, layers_out=bufs[1][1].numpy())
+        dev_s = torch.empty(A.S, dtype=torch.float32, device="cuda")
+        dev_l = torch.empty(A.N, dtype=torch.float32, device="cuda")
+        for k in range(12):
+            for s_, _ in bufs:
+                s_.numpy()[:] = S_in[k]
+            runA()
+            runC()
+            dev_s.copy_(torch.from_numpy(S_in[k]).cuda())
+            torch.cuda.synchronize()
+            B.frame(dev_s, 4, warm=True, layers_out=dev_l)
+            B.sync()
+            want = dev_l.cpu().numpy()
+            assert np.array_equal(bufs[0][1].numpy(), want), k
+            assert np.array_equal(bufs[1][1].numpy(), want), k
+            assert rel(want, ref[k][0]) < 1e-4, k
+
+
 def test_fused_graph_frames_on_rotating_buffers(fw, elt_frames):
     """A new slopes and layers buffer every frame, enqueued back to back (the
     cached graph is updated in place, not re-instantiated): the layers are
