@@ -146,6 +146,12 @@ struct FParams {
     int v_z, v_t, v_u, v_r, v_c, v_tab;   // shared-memory offsets (floats)
     int v_rmax, v_smax;       // widest column stripe, most slots of a rank
     int v_tumax;              // own-map capacity (a multiple of 4)
+    // resident iteration state (level-stacked plans whose clusters keep one
+    // layer item for the launch): r, p, q, c, J^{-1}, alpha D of the owned
+    // coefficients live in 6 arrays of v_sts floats at v_st from the first
+    // layer phase of the frame on; c and r go back to global memory in the
+    // last iteration (-1: the state is read and written in place)
+    int v_st, v_sts;
 };
 
 // ---------------------------------------------------------------------------
@@ -2206,6 +2212,19 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         lpt_schedule(wcost, tile_ctas, wsched, wsched_off);
         for (int r = 0; r < n_res; ++r) wsched_off.push_back(wsched_off.back());   // reserved: no tiles
         lpt_schedule(lcost, pl->nclusters, lsched, lsched_off);
+        // resident state: one layer item per cluster and room in shared memory
+        int st_off = -1, st_stride = 0;
+        if (V == 1 && !shared_tables) {
+            int most = 0;
+            for (size_t k = 0; k + 1 < lsched_off.size(); ++k) most = std::max(most, lsched_off[k + 1] - lsched_off[k]);
+            const size_t stride = (cst.ncoef_max + 3) & ~(size_t)3;
+            const size_t with_st = (size_t)pl->smem + 6 * stride * sizeof(float);
+            if (most <= 1 && with_st <= smem_cap) {
+                st_off = pl->smem / (int)sizeof(float);
+                st_stride = (int)stride;
+                pl->smem = (int)with_st;
+            }
+        }
         int *dws = nullptr, *dwo = nullptr, *dls = nullptr, *dlo = nullptr;
         ok = ok && dupload(pl, dws, wsched, err) && dupload(pl, dwo, wsched_off, err) &&
              dupload(pl, dls, lsched, err) && dupload(pl, dlo, lsched_off, err);
@@ -2270,6 +2289,8 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         P.v_smax = cst.smax;
         P.v_tumax = (int)r4(cst.tu_max);
         P.v_tab = P.ltab_off + (int)(2 * (size_t)Gmax * (Rmax + nmax) * KGmax);
+        P.v_st = st_off;
+        P.v_sts = st_stride;
         for (int i = 0; i < 6; ++i) {
             P.h[i] = (float)hss[0]->h[i];
             P.g[i] = (float)hss[0]->g[i];

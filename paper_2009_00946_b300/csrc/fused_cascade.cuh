@@ -579,6 +579,8 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
     Acc2 rho_p, dz_p;
     const int ncoef = tab[1];
     const int* gix = tab + 20 + 4 * P.v_smax + P.v_tumax;
+    float* st = (P.v_st >= 0) ? sm + P.v_st : nullptr;   // resident r, p, q, c, J^{-1}, alpha D
+    const int sts = P.v_sts;
     if (mode == kLpIter) {
         constexpr int kE = 4;
         float vr[kE], vp[kE], vq[kE], vc[kE], vj[kE], va[kE];
@@ -590,12 +592,21 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
                 if (e < ncoef && FEWHA_IN(off + gix[e], I.N, 1, kDbgCoef)) {
                     const int i = off + gix[e];
                     gi[u] = i;
-                    vr[u] = I.r[i];
-                    vp[u] = I.p[i];
-                    vq[u] = I.q[i];
-                    vc[u] = I.c[i];
-                    vj[u] = __ldg(I.Jinv + i);
-                    va[u] = __ldg(I.aD + i);
+                    if (st) {
+                        vr[u] = st[e];
+                        vp[u] = st[sts + e];
+                        vq[u] = st[2 * sts + e];
+                        vc[u] = st[3 * sts + e];
+                        vj[u] = st[4 * sts + e];
+                        va[u] = st[5 * sts + e];
+                    } else {
+                        vr[u] = I.r[i];
+                        vp[u] = I.p[i];
+                        vq[u] = I.q[i];
+                        vc[u] = I.c[i];
+                        vj[u] = __ldg(I.Jinv + i);
+                        va[u] = __ldg(I.aD + i);
+                    }
                 }
             }
         };
@@ -650,10 +661,21 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
                 const float qv = (k == 0) ? sv : sv + fb * vq[u];
                 const float cv = vc[u] + fa * pv;
                 const float rv = vr[u] - fa * qv;
-                I.p[i] = pv;
-                I.q[i] = qv;
-                I.c[i] = cv;
-                I.r[i] = rv;
+                if (st) {   // the frame's later iterations read them here; c, r persist from the last
+                    st[e] = rv;
+                    st[sts + e] = pv;
+                    st[2 * sts + e] = qv;
+                    st[3 * sts + e] = cv;
+                    if (last) {
+                        I.c[i] = cv;
+                        I.r[i] = rv;
+                    }
+                } else {
+                    I.p[i] = pv;
+                    I.q[i] = qv;
+                    I.c[i] = cv;
+                    I.r[i] = rv;
+                }
                 float zout;
                 if (!last) {
                     zout = vj[u] * rv;
@@ -684,6 +706,12 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
                 I.b[i] = bv;
                 I.bprev[i] = bv;
                 I.r[i] = rv;
+                if (st) {
+                    st[e] = rv;
+                    st[3 * sts + e] = P.warm ? I.c[i] : 0.f;
+                    st[4 * sts + e] = jinv;
+                    st[5 * sts + e] = ad;
+                }
                 zout = jinv * rv;
                 rho_p.add_prod(rv, zout);
                 dz_p.add_prod3(ad, zout, zout);
@@ -696,6 +724,12 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
                 const float rv = (float)((double)Zc[e] - (double)ad * (double)cv);
                 I.bprev[i] = I.b[i];
                 I.r[i] = rv;
+                if (st) {
+                    st[e] = rv;
+                    st[3 * sts + e] = cv;
+                    st[4 * sts + e] = jinv;
+                    st[5 * sts + e] = ad;
+                }
                 zout = jinv * rv;
                 rho_p.add_prod(rv, zout);
                 dz_p.add_prod3(ad, zout, zout);
@@ -705,9 +739,10 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
     }
     if (mode == kLpIter) fmark(P, 18);
     if (make_z) {
-        const int par = (mode == kLpIter) ? ((k + 1) & 1) : 0;
+        // the partials go out after the inverse's cluster barrier, whose
+        // release would otherwise wait for this global store
         const float4 rd = block_reduce2(rho_p, dz_p, (float4*)red);
-        if (tid == 0) P.lpart[(size_t)par * P.n_litems * C + (size_t)li * C + rank] = rd;
+        if (tid == 0) reinterpret_cast<float4*>(red)[31] = rd;
     }
 
     // ---- inverse W^T -> phi: row synthesis, exchange, column synthesis ----
@@ -718,6 +753,10 @@ __device__ void layer_phase_v1(const FParams& P, int li, int mode, int k, float*
         casc_rows_inv(P, tab, Zc, Urow, T, rem[1], n, R, lR);
         fmark(P, 53);
         cl.sync();     // inverse 2. every owner's stores into this CTA's columns of U have landed
+        if (make_z && tid == 0) {
+            const int par = (mode == kLpIter) ? ((k + 1) & 1) : 0;
+            P.lpart[(size_t)par * P.n_litems * C + (size_t)li * C + rank] = reinterpret_cast<const float4*>(red)[31];
+        }
         fmark(P, 54);
         casc_cols_inv(P, Ucol, Z, T, n, J, R, lR);
         fmark(P, 15);
