@@ -439,6 +439,14 @@ long long fewha_batch_launch_count(const fewha_batch* b);
  * the timings (NUL-terminated, truncated to len).  Synchronises. */
 int fewha_batch_autotune(fewha_batch* b, int n_iter, int reps, char* report, int len);
 
+/* Sub-phase marks of a batch's fused launches, as fewha_set_trace /
+ * fewha_get_fine_trace for one handle (the same tags; a CTA's marks follow
+ * its sensor tiles and layer items in order, up to the per-CTA capacity
+ * *per_cta).  fewha_batch_get_fine_trace synchronises and copies the last
+ * traced launch's marks.  Errors: ARG. */
+int fewha_batch_set_trace(fewha_batch* b, int on);
+int fewha_batch_get_fine_trace(fewha_batch* b, unsigned long long* out, int max_entries, int* per_cta, int* grid);
+
 /* Profiling aid for the roofline of the fused kernel (Sec. 4.3 places the
  * operators of M against a memory roofline; the fused kernel's working set
  * stays in L2, so the L2, not HBM, is its bandwidth bound): the achievable

@@ -412,6 +412,16 @@ long long fewha_batch_launch_count(const fewha_batch* b) {
     return b->b->launches;
 }
 
+int fewha_batch_set_trace(fewha_batch* b, int on) {
+    if (!b) return FEWHA_ERR_ARG;
+    return bdone(b, b->b->set_trace(on));
+}
+
+int fewha_batch_get_fine_trace(fewha_batch* b, unsigned long long* out, int max_entries, int* per_cta, int* grid) {
+    if (!b || !per_cta || !grid || max_entries < 0) return FEWHA_ERR_ARG;
+    return bdone(b, b->b->get_fine_trace(out, max_entries, per_cta, grid));
+}
+
 int fewha_batch_autotune(fewha_batch* b, int n_iter, int reps, char* report, int len) {
     if (!b) return FEWHA_ERR_ARG;
     return bdone(b, b->b->autotune(n_iter, reps, report, len));

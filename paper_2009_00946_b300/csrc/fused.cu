@@ -41,7 +41,7 @@ constexpr int kFThreads = 512;
 constexpr int kMaxC = 16;
 constexpr int kMaxLayersFused = 64;
 constexpr int kMaxWfsFused = 16;
-constexpr int kFineCap = 1024;   // sub-phase marks per CTA per traced launch
+constexpr int kFineCap = 4096;   // sub-phase marks per CTA per traced launch (a batch's CTAs take many items)
 constexpr int kWd = 8;     // ints per layer in a sensor tile's window descriptor
 constexpr int kMaxKG = 4;        // P^T gather entries per layer row / column
 
@@ -131,6 +131,11 @@ struct FParams {
     int n_inst, n_witems, n_litems;
     int grid;              // planned grid (the work lists have grid + 1 / grid / C + 1 offsets)
     int res_first, n_res;  // CTAs res_first + i publish part A of instance i's CG scalars
+    // many instances (no reserved CTAs): duty[cta] = the instance whose CG
+    // scalars that CTA computes once per iteration and publishes (part A after
+    // its sensor tiles, part B first thing in the layer phase), or -1; NULL:
+    // the reserved CTAs above, or every layer item computing its own
+    const int* duty;
     int n_iter, warm, replace, out_layers;
     int C;
     int stripe_floats, stage_floats, win_floats, tile_nodes, tile_subaps, tile_rows, tile_cols;
@@ -1424,8 +1429,9 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
         cc.pre_k = -1;
     }
     unsigned target = 0;
-    const int res_inst = ((int)blockIdx.x >= P.res_first && (int)blockIdx.x < P.res_first + P.n_res)
-                             ? (int)blockIdx.x - P.res_first : -1;
+    const int res_inst = P.duty ? P.duty[blockIdx.x]
+                                : ((int)blockIdx.x >= P.res_first && (int)blockIdx.x < P.res_first + P.n_res)
+                                      ? (int)blockIdx.x - P.res_first : -1;
     // the published alpha / beta words restart at tag 0 with every launch
     // (read only after the first grid barrier)
     if (res_inst >= 0 && threadIdx.x < 8) P.inst[res_inst].pubAB[threadIdx.x] = 0ull;
@@ -2022,6 +2028,16 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         // scalars (one per instance) instead of a sensor tile
         const int n_res = (ninst <= 4 && ninst * 8 <= pl->grid) ? ninst : 0;
         const int tile_ctas = pl->grid - n_res;
+        // more instances: each gets a duty CTA among the working ones (one
+        // instance per CTA, spread over the grid), so that its layer items
+        // find the scalars published instead of each computing them again
+        const bool use_duty = n_res == 0 && ninst > 1 && ninst <= pl->grid;
+        auto duty_cta = [&](int i) { return (int)(((long)i * pl->grid) / ninst); };
+        std::vector<int> duty;
+        if (use_duty) {
+            duty.assign(pl->grid, -1);
+            for (int i = 0; i < ninst; ++i) duty[duty_cta(i)] = i;
+        }
         const int per = std::max(1, tile_ctas / std::max(1, Gtot));
         for (int i = 0; i < ninst; ++i) {
             const HostSetup& hs = *hss[i];
@@ -2142,7 +2158,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             int2* d_gtab = nullptr;
             int* d_gtab_off = nullptr;
             // sensor fields (+8 floats: aligned copies may read up to 3 past the end)
-            I.preA_cta = (i < n_res) ? tile_ctas + i : -1;
+            I.preA_cta = (i < n_res) ? tile_ctas + i : use_duty ? duty_cta(i) : -1;
             I.preA = nullptr;
             I.pubAB = nullptr;
             // LGS tip-tilt filter: per sensor flag, active count, tile range, and
@@ -2259,6 +2275,15 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         P.grid = pl->grid;
         P.res_first = tile_ctas;
         P.n_res = n_res;
+        P.duty = nullptr;
+        if (use_duty) {
+            int* dd = nullptr;
+            if (!dupload(pl, dd, duty, err)) {
+                fused_destroy(pl);
+                return nullptr;
+            }
+            P.duty = dd;
+        }
         P.wpart = wp;
         P.tpart = tp;
         P.lpart = lp;

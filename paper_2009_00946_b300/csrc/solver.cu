@@ -2229,6 +2229,28 @@ class Batch : public BatchBase {
         if (pin_out) cudaFreeHost(pin_out);
     }
 
+    int set_trace(int on) override {
+        if (!plan) {
+            err = "no fused plan";
+            return FEWHA_ERR_STATE;
+        }
+        fused_set_trace(plan, on != 0);
+        return FEWHA_OK;
+    }
+
+    int get_fine_trace(unsigned long long* out, int max_entries, int* per_cta, int* grid) override {
+        if (!plan) {
+            err = "no fused plan";
+            return FEWHA_ERR_STATE;
+        }
+        FEWHA_CUDA(cudaStreamSynchronize(stream));
+        if (fused_get_fine_trace(plan, out, max_entries, per_cta, grid)) {
+            err = "trace copy failed";
+            return FEWHA_ERR_CUDA;
+        }
+        return FEWHA_OK;
+    }
+
     int frame(const void* sl, int n_iter, int warm, void* lout, int on_device) override {
         if (!sl) {
             err = "null slopes";

@@ -154,6 +154,8 @@ class BatchBase {
     virtual int sync() = 0;
     virtual int describe(char* buf, int len) = 0;
     virtual int get_state(int inst, void* c, void* b, void* r, int on_device) = 0;
+    virtual int set_trace(int on) = 0;
+    virtual int get_fine_trace(unsigned long long* out, int max_entries, int* per_cta, int* grid) = 0;
     virtual int autotune(int n_iter, int reps, char* report, int len) = 0;
 
     std::vector<long> coeff_off, slope_off;   // count + 1 offsets

@@ -132,6 +132,9 @@ def lib():
         "fewha_batch_describe": (ci, [vp, ctypes.c_char_p, ci]),
         "fewha_batch_launch_count": (cll, [vp]),
         "fewha_batch_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
+        "fewha_batch_set_trace": (ci, [vp, ci]),
+        "fewha_batch_get_fine_trace": (ci, [vp, ctypes.POINTER(ctypes.c_ulonglong), ci, ctypes.POINTER(ci),
+                                            ctypes.POINTER(ci)]),
         "fewha_measure_l2": (ci, [cl, ci, ci, ctypes.POINTER(cd), ctypes.POINTER(cd), ctypes.c_char_p, ci]),
         "fewha_debug_bounds": (ci, [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
     }
@@ -207,6 +210,15 @@ def _ptr(a, dtype, count, on_device):
     if arr.dtype != dtype[0] or arr.size != count or not arr.flags["C_CONTIGUOUS"]:
         raise ValueError("array must be C-contiguous %s with %d elements" % (dtype[0], count))
     return ctypes.c_void_p(arr.__array_interface__["data"][0]), 0
+
+
+def _marks(rows):
+    """Per CTA a list of (tag, ns) from the packed fine-trace words."""
+    marks = []
+    for r in rows:
+        r = r[r != 0]
+        marks.append([(int(v >> np.uint64(56)), int(v & np.uint64(0x00FFFFFFFFFFFFFF))) for v in r])
+    return marks
 
 
 class Solver:
@@ -545,12 +557,7 @@ class Solver:
         out = np.zeros(max(n, 1), np.uint64)
         self._check(lib().fewha_get_fine_trace(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), n,
                                                ctypes.byref(per), ctypes.byref(grid)))
-        rows = out[:n].reshape(grid.value, per.value)
-        marks = []
-        for r in rows:
-            r = r[r != 0]
-            marks.append([(int(v >> np.uint64(56)), int(v & np.uint64(0x00FFFFFFFFFFFFFF))) for v in r])
-        return marks
+        return _marks(out[:n].reshape(grid.value, per.value))
 
 
 class Batch:
@@ -639,6 +646,19 @@ class Batch:
 
     def sync(self):
         self._check(lib().fewha_batch_sync(self.h))
+
+    def set_trace(self, on: bool = True):
+        self._check(lib().fewha_batch_set_trace(self.h, 1 if on else 0))
+
+    def fine_trace(self):
+        """Last traced launch: per CTA a list of (tag, ns) marks inside the phases."""
+        per, grid = ctypes.c_int(), ctypes.c_int()
+        self._check(lib().fewha_batch_get_fine_trace(self.h, None, 0, ctypes.byref(per), ctypes.byref(grid)))
+        n = per.value * grid.value
+        out = np.zeros(max(n, 1), np.uint64)
+        self._check(lib().fewha_batch_get_fine_trace(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)),
+                                                     n, ctypes.byref(per), ctypes.byref(grid)))
+        return _marks(out[:n].reshape(grid.value, per.value))
 
     def describe(self) -> str:
         buf = ctypes.create_string_buffer(512)
