@@ -253,6 +253,28 @@ int fewha_set_loop(fewha_handle* h, int closed);
  * Errors: ARG. */
 int fewha_set_host_transfer(fewha_handle* h, int slopes_by_copy);
 
+/* The paper has no counterpart: a host frame armed ahead of its slopes, for a
+ * real-time loop (Alg. 1 per frame, as fewha_frame with host buffers and no
+ * mirror fit, open loop, fused path).  fewha_frame_arm launches the frame's
+ * kernel now; it does its set-up (L2 prefetch, descriptors, first tables)
+ * and then waits, at most wait_s seconds (0 < wait_s <= 60), for
+ * fewha_frame_fire before it reads the slopes.  The caller fills the slopes
+ * array between the two calls (it must stay valid until fire returns);
+ * fewha_frame_fire lets the kernel go, waits for the frame's completion word
+ * and returns its status, with the layers in layers_out.  slopes / layers_out:
+ * pinned host buffers (device-mapped), read and written by the kernel
+ * through the mapping.  The launch latency is thereby taken off the path
+ * from the slopes' arrival to the layers.  The armed kernel occupies the GPU
+ * while it waits; every other call on the handle but fewha_frame_fire,
+ * fewha_sync and the queries returns STATE until the frame is fired.
+ * Without a fire by the deadline the frame does no work and fire reports
+ * TIMEOUT (the state is untouched; the frame counter has advanced: restore
+ * it with fewha_set_state if the replacement schedule matters).
+ * Errors: ARG (null or unmapped buffers, wait_s), STATE (no fused plan,
+ * closed loop, already armed / nothing armed), then the frame's own. */
+int fewha_frame_arm(fewha_handle* h, const void* slopes, int n_iter, int warm_start, void* layers_out, double wait_s);
+int fewha_frame_fire(fewha_handle* h);
+
 /* Wait for the handle's stream and return the device error word (OK, INPUT,
  * BREAKDOWN, TIMEOUT).  The word is cleared after it has been read. */
 int fewha_sync(fewha_handle* h);

@@ -111,6 +111,7 @@ int fewha_sizes(const fewha_handle* h, long* n_coeff, long* n_slopes, long* n_ac
 
 int fewha_set_path(fewha_handle* h, int path) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     if (path != FEWHA_PATH_PLAIN && path != FEWHA_PATH_FUSED) return fail(h, FEWHA_ERR_ARG, "unknown path");
     if (path == FEWHA_PATH_FUSED && h->s->hs.prec != FEWHA_FP32)
         return fail(h, FEWHA_ERR_ARG, "the fused path is FP32 only");
@@ -122,6 +123,7 @@ int fewha_set_path(fewha_handle* h, int path) {
 
 int fewha_set_residual_replacement(fewha_handle* h, int k_rr) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     if (k_rr < 0) return fail(h, FEWHA_ERR_ARG, "k_rr must be >= 0");
     h->s->k_rr = k_rr;
     return FEWHA_OK;
@@ -129,36 +131,43 @@ int fewha_set_residual_replacement(fewha_handle* h, int k_rr) {
 
 int fewha_set_frame(fewha_handle* h, const void* slopes, int on_device) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->set_frame(slopes, on_device));
 }
 
 int fewha_solve(fewha_handle* h, int n_iter, int warm_start) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->solve(n_iter, warm_start));
 }
 
 int fewha_fit_dm(fewha_handle* h, double gain, int n_fit, void* dm_out, int on_device) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->fit(gain, n_fit, dm_out, on_device));
 }
 
 int fewha_get_layers(fewha_handle* h, void* out, int on_device) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->get_layers(out, on_device));
 }
 
 int fewha_get_vector(fewha_handle* h, int which, void* out, int on_device) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->get_vector(which, out, on_device));
 }
 
 int fewha_get_state(fewha_handle* h, void* c, void* b, void* r, int on_device) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->get_state(c, b, r, on_device));
 }
 
 int fewha_set_state(fewha_handle* h, const void* c, const void* b, const void* r, int on_device, long frame_count) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     if (frame_count < 0) return fail(h, FEWHA_ERR_ARG, "frame_count must be >= 0");
     int st = h->s->set_state(c, b, r, on_device, frame_count);
     if (!st) h->s->have_frame = h->s->have_frame;
@@ -167,12 +176,14 @@ int fewha_set_state(fewha_handle* h, const void* c, const void* b, const void* r
 
 int fewha_apply_M(fewha_handle* h, const void* x, void* y, int on_device) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->apply_M(x, y, on_device));
 }
 
 int fewha_frame(fewha_handle* h, const void* slopes, int n_iter, int warm_start, double gain, int n_fit,
                 void* layers_out, void* dm_out, int on_device) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     if (dm_out && (n_fit < 0 || !(gain >= 0.0 && gain <= 1.0)))
         return fail(h, FEWHA_ERR_ARG, "gain must be in [0, 1] and n_fit >= 0");
     return done(h, h->s->frame(slopes, n_iter, warm_start, gain, n_fit, layers_out, dm_out, on_device));
@@ -190,11 +201,13 @@ int fewha_operator_dims(fewha_handle* h, int op, long* n_in, long* n_out) {
 
 int fewha_apply_operator(fewha_handle* h, int op, const void* x, void* y, int on_device) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->apply_operator(op, x, y, on_device));
 }
 
 int fewha_time_operator(fewha_handle* h, int op, int reps, double* us_per_application) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->time_operator(op, reps, us_per_application));
 }
 
@@ -234,6 +247,7 @@ int fewha_get_fine_trace(fewha_handle* h, unsigned long long* out, int max_entri
 
 int fewha_set_cluster_size(fewha_handle* h, int cluster_size) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 && cluster_size != 16)
         return fail(h, FEWHA_ERR_ARG, "cluster size must be 1, 2, 4, 8 or 16");
     return done(h, h->s->set_cluster_size(cluster_size));
@@ -241,23 +255,27 @@ int fewha_set_cluster_size(fewha_handle* h, int cluster_size) {
 
 int fewha_set_layer_transform(fewha_handle* h, int form) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     if (form < -1 || form > 1) return fail(h, FEWHA_ERR_ARG, "layer transform must be -1, 0 or 1");
     return done(h, h->s->set_layer_transform(form));
 }
 
 int fewha_autotune(fewha_handle* h, int n_iter, int reps, char* report, int len) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->autotune(n_iter, reps, report, len));
 }
 
 int fewha_set_loop(fewha_handle* h, int closed) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     if (closed != 0 && closed != 1) return fail(h, FEWHA_ERR_ARG, "closed must be 0 or 1");
     return done(h, h->s->set_loop(closed));
 }
 
 int fewha_set_params(fewha_handle* h, const double* cn2_frac, double alpha, const double* w) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->set_params(cn2_frac, alpha, w));
 }
 
@@ -268,12 +286,14 @@ long fewha_tape_bytes(const fewha_handle* h, int n_iter) {
 
 int fewha_solve_taped(fewha_handle* h, const void* slopes, int n_iter, void* tape, void* layers_out) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->solve_taped(slopes, n_iter, tape, layers_out));
 }
 
 int fewha_backward(fewha_handle* h, const void* slopes, int n_iter, const void* tape, const void* layers_bar,
                    double* grad_cn2, double* grad_alpha, double* grad_w, void* grad_slopes) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->backward(slopes, n_iter, tape, layers_bar, grad_cn2, grad_alpha, grad_w, grad_slopes));
 }
 
@@ -285,6 +305,7 @@ long fewha_tape_bytes_batch(const fewha_handle* h, int n_iter, int n_frames) {
 int fewha_solve_taped_batch(fewha_handle* h, int n_frames, const void* slopes, int n_iter, void* tape,
                             void* layers_out) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->solve_taped_batch(n_frames, slopes, n_iter, tape, layers_out));
 }
 
@@ -292,12 +313,24 @@ int fewha_backward_batch(fewha_handle* h, int n_frames, const void* slopes, int 
                          const void* layers_bar, double* grad_cn2, double* grad_alpha, double* grad_w,
                          void* grad_slopes) {
     if (!h) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->backward_batch(n_frames, slopes, n_iter, tape, layers_bar, grad_cn2, grad_alpha, grad_w,
                                         grad_slopes));
 }
 
+int fewha_frame_arm(fewha_handle* h, const void* slopes, int n_iter, int warm_start, void* layers_out, double wait_s) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->frame_arm(slopes, n_iter, warm_start, layers_out, wait_s));
+}
+
+int fewha_frame_fire(fewha_handle* h) {
+    if (!h) return FEWHA_ERR_ARG;
+    return done(h, h->s->frame_fire());
+}
+
 int fewha_set_host_transfer(fewha_handle* h, int slopes_by_copy) {
     if (!h || (slopes_by_copy != 0 && slopes_by_copy != 1)) return FEWHA_ERR_ARG;
+    if (h->s && h->s->is_armed()) return fail(h, FEWHA_ERR_STATE, "a frame is armed: fire it first");
     return done(h, h->s->set_host_transfer(slopes_by_copy));
 }
 

@@ -115,13 +115,20 @@ struct FParams {
     const int* wsched_off;
     const int* lsched;
     const int* lsched_off;
-    unsigned* bar;         // [0] grid-barrier arrivals, [1] exits (the last CTA out zeroes both)
+    unsigned* bar;         // [0] grid-barrier arrivals, [1] exits (the last CTA out zeroes both),
+                           // [2] the go of an armed frame passed on in device memory
     const float* slopes_in;   // single instance: read the frame's slopes here (and copy them to I.slopes)
     float* phi_out;           // single instance: also write the final layers here
     // single instance, may be NULL: a word in mapped pinned host memory that
     // the last CTA out sets to (1 << 32) | error word once every result of
     // the launch (host-mapped layers included) is visible to the host
     unsigned long long* done_host;
+    // single instance, may be NULL: an armed frame (launched ahead of its
+    // slopes) waits after its set-up until this mapped host word equals
+    // doorbell_want, at most doorbell_ns nanoseconds (then TIMEOUT, no frame)
+    const unsigned* doorbell;
+    unsigned doorbell_want;
+    long long doorbell_ns;
     int* errw;
     unsigned long long* trace;   // optional: [slot][cta][arrive, depart] globaltimer (ns)
     int trace_slots;
@@ -162,6 +169,12 @@ struct FParams {
 // ---------------------------------------------------------------------------
 // grid barrier with a clock budget
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_sys(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -1398,6 +1411,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     __shared__ int wdesc[(kMaxLayersFused + 1) * kWd];
     __shared__ CtaCache cc;
     __shared__ int s_abort;
+    __shared__ int s_go;
     cg::cluster_group cl = cg::this_cluster();
     const int C = P.C;
     // every shared-memory address below assumes the planned cluster shape
@@ -1409,10 +1423,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     const int w_lo = P.wsched_off[blockIdx.x], w_hi = P.wsched_off[blockIdx.x + 1];
     const int l_lo = P.lsched_off[cid], l_hi = P.lsched_off[cid + 1];
     int slot = 0;
-    if (threadIdx.x == 0) {
-        trace_mark(P, 0, 0);
-        trace_mark(P, 0, 1);
-    }
+    if (threadIdx.x == 0) trace_mark(P, 0, 0);   // slot 0: start, and (below) set-up done / go seen
     ++slot;
     if (threadIdx.x < 4 * C) {
         const int b = threadIdx.x / C, r = threadIdx.x % C;
@@ -1466,7 +1477,36 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     //   CTA computes part A of the scalars), then the layer phase (the reserved
     //   CTA first publishes part B)
     const int base = P.replace ? 4 : 2, nph = base + 2 * P.n_iter;
-    for (int ph = 0; ph < nph; ++ph) {
+    // an armed frame waits here for the host's go (its set-up above -- the L2
+    // prefetch, descriptors, first tables -- done meanwhile); without it by the
+    // deadline every phase is skipped and the frame reports TIMEOUT
+    int nph_run = nph;
+    if (P.doorbell) {
+        // CTA 0 alone polls the host word (a read across the host link each
+        // time) and passes the go on through a device word the others poll in
+        // the L2: with every CTA polling the host the last ones saw the go
+        // ~130 us after the first
+        if (threadIdx.x == 0) {
+            const unsigned long long t0 = global_ns();
+            const unsigned* src = blockIdx.x == 0 ? P.doorbell : P.bar + 2;
+            int go = 1;
+            while ((blockIdx.x == 0 ? ld_acquire_sys(src) : ld_acquire_gpu(src)) != P.doorbell_want) {
+                if ((long long)(global_ns() - t0) > P.doorbell_ns) {
+                    go = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            if (go && blockIdx.x == 0)
+                asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(P.bar + 2), "r"(P.doorbell_want) : "memory");
+            s_go = go;
+            if (!go) atomicOr(P.errw, kErrTimeout);
+        }
+        __syncthreads();
+        if (!s_go) nph_run = 0;
+    }
+    if (threadIdx.x == 0) trace_mark(P, 0, 1);
+    for (int ph = 0; ph < nph_run; ++ph) {
         const bool it = ph >= base;
         const int k = it ? (ph - base) >> 1 : 0;
         const bool sensor_ph = it ? ((ph - base) & 1) == 0 : (ph & 1) == 0;
@@ -1529,7 +1569,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
                 if (V == 0) layer_phase(P, P.lsched[t], lmode, k, sm, rem, cl, red, sh, &cc, t + 1 < l_hi || last_ph);
                 else layer_phase_v1(P, P.lsched[t], lmode, k, sm, rem, cl, red, sh, &cc, false);
         }
-        if (ph + 1 < nph) grid_barrier(P, target, &s_abort, slot);
+        if (ph + 1 < nph_run) grid_barrier(P, target, &s_abort, slot);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -2257,7 +2297,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
              dupload(pl, ds4, stg4, err) && dupload(pl, dcs, cshape, err) &&
              dalloc(pl, wp, witems.size(), err) && dalloc(pl, tp, witems.size(), err) &&
              dalloc(pl, lp, 2 * litems.size() * C, err) &&
-             dalloc(pl, bar, 2, err) && dupload(pl, pl->d_inst, pl->inst, err);
+             dalloc(pl, bar, 3, err) && dupload(pl, pl->d_inst, pl->inst, err);
         if (!ok) {
             fused_destroy(pl);
             return nullptr;
@@ -2473,12 +2513,13 @@ int fused_repoint_node(cudaGraphExec_t exec, cudaGraphNode_t node, const float* 
 
 int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int replace, long long budget,
                 cudaStream_t stream, std::string& err, long long& launches, float* layers_out,
-                unsigned long long* done_host) {
+                unsigned long long* done_host, const unsigned* doorbell, unsigned doorbell_want,
+                long long doorbell_ns) {
     // a completed launch leaves the barrier counters at zero (the last CTA out
     // resets them); after a failed or first launch they are zeroed here
     cudaError_t e = cudaSuccess;
     if (pl->bar_dirty) {
-        e = cudaMemsetAsync(pl->P.bar, 0, 2 * sizeof(unsigned), stream);
+        e = cudaMemsetAsync(pl->P.bar, 0, 3 * sizeof(unsigned), stream);
         if (e != cudaSuccess) {
             err = std::string("fused setup copy: ") + cudaGetErrorString(e);
             return FEWHA_ERR_CUDA;
@@ -2490,6 +2531,9 @@ int fused_solve(FusedPlan* pl, const float* slopes, int n_iter, int warm, int re
     P.slopes_in = (P.n_inst == 1) ? slopes : nullptr;
     P.phi_out = (P.n_inst == 1) ? layers_out : nullptr;
     P.done_host = (P.n_inst == 1) ? done_host : nullptr;
+    P.doorbell = (P.n_inst == 1) ? doorbell : nullptr;
+    P.doorbell_want = doorbell_want;
+    P.doorbell_ns = doorbell_ns;
     P.trace = nullptr;
     P.trace_slots = 0;
     P.ftrace = nullptr;

@@ -50,9 +50,13 @@ void fused_destroy(FusedPlan* plan);
 // done_host (device alias of a mapped pinned host word, may be NULL; single
 // instance): set to (1 << 32) | error word by the launch once all of its
 // results are visible to the host, so a host caller can wait on the word.
+// doorbell (device alias of a mapped pinned host word, may be NULL; single
+// instance): the launch does its set-up, then waits until the word equals
+// doorbell_want (at most doorbell_ns ns; then TIMEOUT and no frame work).
 int fused_solve(FusedPlan* plan, const float* slopes, int n_iter, int warm, int replace, long long budget,
                 cudaStream_t stream, std::string& err, long long& launches, float* layers_out = nullptr,
-                unsigned long long* done_host = nullptr);
+                unsigned long long* done_host = nullptr, const unsigned* doorbell = nullptr,
+                unsigned doorbell_want = 0, long long doorbell_ns = 0);
 // After a kernel error the barrier counters may be left set: zero them first
 // at the next launch.
 void fused_mark_dirty(FusedPlan* plan);

@@ -680,6 +680,15 @@ class Solver : public SolverBase {
     // results are visible, so the host waits on it instead of the stream)
     unsigned long long* done_host = nullptr;
     unsigned long long* done_dev = nullptr;
+    // armed frames: a mapped pinned doorbell word the launched kernel waits on
+    unsigned* bell_host = nullptr;
+    unsigned* bell_dev = nullptr;
+    unsigned bell_seq = 0;
+    bool armed = false;
+    double armed_wait_s = 0.0;
+    const unsigned* ov_bell = nullptr;
+    unsigned ov_bell_want = 0;
+    long long ov_bell_ns = 0;
     unsigned long long* ov_done = nullptr;
     FusedPlan* fused = nullptr;
     FitCgPlan* fitcg = nullptr;     // persistent FP32 fit (fused path)
@@ -719,6 +728,10 @@ class Solver : public SolverBase {
     }
 
     ~Solver() override {
+        if (armed && bell_host) {   // an armed frame still waiting: let it run rather than wait out its deadline
+            std::atomic_thread_fence(std::memory_order_seq_cst);
+            *(volatile unsigned*)bell_host = bell_seq;
+        }
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
         for (int i = 0; i < 2; ++i) drop_graph(i);
@@ -730,6 +743,7 @@ class Solver : public SolverBase {
         if (pinned_dm) cudaFreeHost(pinned_dm);
         if (errw_host) cudaFreeHost(errw_host);
         if (done_host) cudaFreeHost(done_host);
+        if (bell_host) cudaFreeHost(bell_host);
     }
 
     template <typename U>
@@ -1233,7 +1247,7 @@ class Solver : public SolverBase {
         if (use_fused()) {
             bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
             int st = fused_solve(fused, ov_slopes, n_iter, warm, replace ? 1 : 0, barrier_budget, stream, err,
-                                 launches, ov_layers, ov_done);
+                                 launches, ov_layers, ov_done, ov_bell, ov_bell_want, ov_bell_ns);
             if (st) return st;
             fused_layers_ready = true;
         } else {
@@ -2117,6 +2131,88 @@ class Solver : public SolverBase {
         if (stage_l) std::memcpy(lout, pinned_out, hs.N * sizeof(T));
         if (stage_d) std::memcpy(dout, pinned_dm, hs.NA * sizeof(T));
         return decode_err(*errw_host);   // copied by the graph
+    }
+
+    // Armed host frame: the fused launch is issued now, does its set-up, and
+    // waits (bounded) for frame_fire before it reads the pinned slopes, which
+    // the caller fills in between; the kernel reads them and writes the
+    // pinned layers through their device mapping, and frame_fire waits on the
+    // completion word.  The launch latency is then off the slopes-to-layers path.
+    int frame_arm(const void* s_in, int n_iter, int warm, void* lout, double wait_s) override {
+        if (armed) {
+            err = "a frame is already armed: fire it first";
+            return FEWHA_ERR_STATE;
+        }
+        if (!s_in || !lout || n_iter < 1 || n_iter > 100000 || !(wait_s > 0.0 && wait_s <= 60.0)) {
+            err = "frame_arm needs slopes, layers, n_iter >= 1 and 0 < wait_s <= 60";
+            return FEWHA_ERR_ARG;
+        }
+        if (!use_fused() || closed || !done_dev) {
+            err = "armed frames run on the fused path in open loop";
+            return FEWHA_ERR_STATE;
+        }
+        void* sdev = host_dev_ptr(s_in);
+        void* ldev = host_dev_ptr(lout);
+        if (!sdev || !ldev) {
+            err = "armed frames need pinned (device-mapped) host slopes and layers";
+            return FEWHA_ERR_ARG;
+        }
+        if (!bell_host) {
+            FEWHA_CUDA(cudaHostAlloc((void**)&bell_host, sizeof(unsigned), cudaHostAllocMapped));
+            FEWHA_CUDA(cudaHostGetDevicePointer((void**)&bell_dev, bell_host, 0));
+            *(volatile unsigned*)bell_host = 0u;
+        }
+        bell_seq = (bell_seq + 1u) ? bell_seq + 1u : 1u;
+        *(volatile unsigned long long*)done_host = 0ull;   // before the launch that sets it
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        pol_pending = true;
+        ov_slopes = (const float*)sdev;
+        ov_layers = (float*)ldev;
+        ov_done = done_dev;
+        ov_bell = bell_dev;
+        ov_bell_want = bell_seq;
+        ov_bell_ns = (long long)(wait_s * 1e9);
+        const int st = solve_enqueue(n_iter, warm);
+        ov_slopes = nullptr;
+        ov_layers = nullptr;
+        ov_done = nullptr;
+        ov_bell = nullptr;
+        if (st) return st;
+        have_frame = true;
+        armed = true;
+        armed_wait_s = wait_s;
+        return FEWHA_OK;
+    }
+
+    bool is_armed() const override { return armed; }
+
+    int frame_fire() override {
+        using clk = std::chrono::steady_clock;
+        if (!armed) {
+            err = "no armed frame";
+            return FEWHA_ERR_STATE;
+        }
+        armed = false;
+        const auto t0 = clk::now();
+        std::atomic_thread_fence(std::memory_order_seq_cst);   // the caller's slopes before the go
+        *(volatile unsigned*)bell_host = bell_seq;
+        unsigned long long v = 0ull;
+        const auto limit = std::chrono::duration<double>(armed_wait_s + 2.0);
+        for (long it = 0;; ++it) {
+            v = *(volatile unsigned long long*)done_host;
+            if (v >> 32) break;
+            if ((it & 1023) == 1023 && clk::now() - t0 > limit) break;
+        }
+        ftime[2] = std::chrono::duration<double, std::micro>(clk::now() - t0).count();
+        if (!(v >> 32)) {
+            FEWHA_CUDA(cudaStreamSynchronize(stream));
+            v = *(volatile unsigned long long*)done_host;
+            if (!(v >> 32)) {
+                FEWHA_CUDA(cudaMemcpy(errw_host, errw, sizeof(int), cudaMemcpyDeviceToHost));
+                v = (unsigned)*errw_host;
+            }
+        }
+        return decode_err((int)(unsigned)(v & 0xffffffffull));
     }
 
     // device alias of a pinned host pointer (nullptr for other memory)

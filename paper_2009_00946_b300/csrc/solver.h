@@ -126,6 +126,9 @@ class SolverBase {
                                double* g_gam, double* g_alpha, double* g_w, void* g_slopes) = 0;
     virtual int set_loop(int closed) = 0;
     virtual int set_host_transfer(int slopes_by_copy) = 0;
+    virtual int frame_arm(const void* slopes, int n_iter, int warm, void* layers_out, double wait_s) = 0;
+    virtual int frame_fire() = 0;
+    virtual bool is_armed() const = 0;
     virtual int operator_dims(int op, long& n_in, long& n_out) = 0;
     virtual int apply_operator(int op, const void* x, void* y, int on_device) = 0;
     virtual int time_operator(int op, int reps, double* us) = 0;

@@ -107,6 +107,8 @@ def lib():
         "fewha_set_cluster_size": (ci, [vp, ci]),
         "fewha_set_layer_transform": (ci, [vp, ci]),
         "fewha_set_host_transfer": (ci, [vp, ci]),
+        "fewha_frame_arm": (ci, [vp, vp, ci, ci, vp, cd]),
+        "fewha_frame_fire": (ci, [vp]),
         "fewha_get_frame_timing": (ci, [vp, ctypes.POINTER(cd)]),
         "fewha_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
         "fewha_set_loop": (ci, [vp, ci]),
@@ -411,6 +413,23 @@ class Solver:
 
         run.buffers = (slopes, layers_out, dm_out)   # kept alive with the function
         return run
+
+    def arm_frame(self, slopes, n_iter: int, warm: bool = True, layers_out=None, wait_s: float = 1.0):
+        """Launch a host frame ahead of its slopes (fewha_frame_arm): fill
+        `slopes` in place, then fire_frame().  Pinned host arrays only."""
+        ps, ds = _ptr(slopes, self._dt(), self.S, None)
+        pl, dl = _ptr(layers_out, self._dt(), self.N, None)
+        if ds or dl:
+            raise ValueError("armed frames take pinned host arrays")
+        self._armed_buffers = (slopes, layers_out)
+        self._check(lib().fewha_frame_arm(self.h, ps, int(n_iter), 1 if warm else 0, pl, float(wait_s)))
+
+    def fire_frame(self):
+        """Let the armed frame run and wait for its layers (fewha_frame_fire)."""
+        try:
+            self._check(lib().fewha_frame_fire(self.h))
+        finally:
+            self._armed_buffers = None
 
     def launch_count(self) -> int:
         return int(lib().fewha_launch_count(self.h))

@@ -65,6 +65,8 @@ def test_null_pointers_rejected():
     assert L.fewha_sync(None) == 1
     assert L.fewha_launch_count(None) == -1
     assert L.fewha_set_host_transfer(None, 1) == 1
+    assert L.fewha_frame_arm(None, None, 4, 1, None, 1.0) == 1
+    assert L.fewha_frame_fire(None) == 1
     assert L.fewha_tape_bytes_batch(None, 4, 32) == -1
     assert L.fewha_solve_taped_batch(None, 32, None, 4, None, None) == 1
     assert L.fewha_backward_batch(None, 32, None, 4, None, None, None, None, None, None) == 1

@@ -232,6 +232,66 @@ def test_bound_frames_and_both_host_transfers_bit_identical(fw, elt_frames):
             assert rel(want, ref[k][0]) < 1e-4, k
 
 
+def test_armed_frames_bit_identical(fw, elt_frames):
+    """Frames armed ahead of their slopes (fewha_frame_arm: the kernel launched
+    and waiting; the slopes written afterwards; fewha_frame_fire) give the
+    device frames' layers bit for bit, across the replacement frame; while a
+    frame is armed the handle refuses other work."""
+    import torch
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as A, _fused(fw, cfg, k_rr=10) as B:
+        pin_s = torch.empty(A.S, dtype=torch.float32).pin_memory()
+        pin_l = torch.empty(A.N, dtype=torch.float32).pin_memory()
+        dev_s = torch.empty(A.S, dtype=torch.float32, device="cuda")
+        dev_l = torch.empty(A.N, dtype=torch.float32, device="cuda")
+        for k in range(12):
+            A.arm_frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy(), wait_s=5.0)
+            if k == 3:
+                with pytest.raises(fw.FewhaError) as ei:
+                    A.solve(4)
+                assert ei.value.name == "STATE"
+            pin_s.numpy()[:] = S_in[k]
+            A.fire_frame()
+            dev_s.copy_(torch.from_numpy(S_in[k]).cuda())
+            torch.cuda.synchronize()
+            B.frame(dev_s, 4, warm=True, layers_out=dev_l)
+            B.sync()
+            assert np.array_equal(pin_l.numpy(), dev_l.cpu().numpy()), k
+            assert rel(pin_l.numpy(), ref[k][0]) < 1e-4, k
+
+
+def test_armed_frame_deadline_reported_and_recoverable(fw, elt_frames):
+    """An armed frame that is not fired within its deadline does no work and
+    reports TIMEOUT (the kernel's wait is bounded); the state is untouched
+    and the next frames run normally."""
+    import time
+
+    import torch
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as A:
+        pin_s = torch.empty(A.S, dtype=torch.float32).pin_memory()
+        pin_l = torch.empty(A.N, dtype=torch.float32).pin_memory()
+        for k in range(3):
+            A.arm_frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy(), wait_s=5.0)
+            pin_s.numpy()[:] = S_in[k]
+            A.fire_frame()
+        state = A.get_state()
+        A.arm_frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy(), wait_s=0.002)
+        time.sleep(0.1)
+        pin_s.numpy()[:] = S_in[3]
+        with pytest.raises(fw.FewhaError) as ei:
+            A.fire_frame()
+        assert ei.value.name == "TIMEOUT"
+        for got, want in zip(A.get_state(), state):
+            assert np.array_equal(got, want)
+        A.set_state(*state, frame_count=3)
+        for k in range(3, 5):
+            A.arm_frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy(), wait_s=5.0)
+            pin_s.numpy()[:] = S_in[k]
+            A.fire_frame()
+            assert rel(pin_l.numpy(), ref[k][0]) < 1e-4, k
+
+
 def test_fused_graph_frames_on_rotating_buffers(fw, elt_frames):
     """A new slopes and layers buffer every frame, enqueued back to back (the
     cached graph is updated in place, not re-instantiated): the layers are
