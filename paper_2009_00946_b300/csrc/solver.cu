@@ -1,6 +1,7 @@
 // Plain FEWHA path: one simple kernel per operator (Sec. 3.2 matrix-free
 // operators), templated on float / double, with FP64 reductions; plus the
 // solver object that owns the device state of one instance.
+#include <cuda.h>   // the types of the driver's stream write (taken through the runtime's entry-point query)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -689,6 +690,16 @@ class Solver : public SolverBase {
     const unsigned* ov_bell = nullptr;
     unsigned ov_bell_want = 0;
     long long ov_bell_ns = 0;
+    // armed frames with host_slopes_copy: at the fire, the slopes go in by a
+    // copy-engine transfer on a second stream and a stream write of the go
+    // into a device word follows it (no SM work: the armed kernel holds them all)
+    using WriteValue32 = CUresult (*)(CUstream, CUdeviceptr, cuuint32_t, unsigned int);
+    WriteValue32 write_value = nullptr;
+    bool write_value_tried = false;
+    cudaStream_t aux_stream = nullptr;
+    unsigned* go_dev = nullptr;
+    bool armed_copy = false;
+    const void* armed_src = nullptr;
     unsigned long long* ov_done = nullptr;
     FusedPlan* fused = nullptr;
     FitCgPlan* fitcg = nullptr;     // persistent FP32 fit (fused path)
@@ -728,9 +739,10 @@ class Solver : public SolverBase {
     }
 
     ~Solver() override {
-        if (armed && bell_host) {   // an armed frame still waiting: let it run rather than wait out its deadline
-            std::atomic_thread_fence(std::memory_order_seq_cst);
-            *(volatile unsigned*)bell_host = bell_seq;
+        if (armed) frame_fire();   // an armed frame still waiting: let it run rather than wait out its deadline
+        if (aux_stream) {
+            cudaStreamSynchronize(aux_stream);
+            cudaStreamDestroy(aux_stream);
         }
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
@@ -2162,15 +2174,29 @@ class Solver : public SolverBase {
             FEWHA_CUDA(cudaHostGetDevicePointer((void**)&bell_dev, bell_host, 0));
             *(volatile unsigned*)bell_host = 0u;
         }
+        if (host_slopes_copy && !write_value_tried) {
+            write_value_tried = true;
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &fn, 12000, cudaEnableDefault, &q) ==
+                    cudaSuccess &&
+                q == cudaDriverEntryPointSuccess && fn &&
+                cudaStreamCreateWithFlags(&aux_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                alloc(go_dev, 1) == FEWHA_OK && cudaMemset(go_dev, 0, sizeof(unsigned)) == cudaSuccess)
+                write_value = (WriteValue32)fn;
+            cudaGetLastError();
+        }
+        armed_copy = host_slopes_copy && write_value && go_dev && aux_stream;
         bell_seq = (bell_seq + 1u) ? bell_seq + 1u : 1u;
         *(volatile unsigned long long*)done_host = 0ull;   // before the launch that sets it
         std::atomic_thread_fence(std::memory_order_seq_cst);
         pol_pending = true;
-        ov_slopes = (const float*)sdev;
+        ov_slopes = armed_copy ? nullptr : (const float*)sdev;   // copy mode: the handle's slope buffer
         ov_layers = (float*)ldev;
         ov_done = done_dev;
-        ov_bell = bell_dev;
+        ov_bell = armed_copy ? go_dev : bell_dev;
         ov_bell_want = bell_seq;
+        armed_src = s_in;
         ov_bell_ns = (long long)(wait_s * 1e9);
         const int st = solve_enqueue(n_iter, warm);
         ov_slopes = nullptr;
@@ -2195,7 +2221,21 @@ class Solver : public SolverBase {
         armed = false;
         const auto t0 = clk::now();
         std::atomic_thread_fence(std::memory_order_seq_cst);   // the caller's slopes before the go
-        *(volatile unsigned*)bell_host = bell_seq;
+        bool rung = false;
+        if (armed_copy) {
+            // slopes in by the copy engine, then the go written behind them in stream order
+            // (the stream write fences the copy's data before the word)
+            if (cudaMemcpyAsync(slopes, armed_src, hs.S * sizeof(T), cudaMemcpyHostToDevice, aux_stream) ==
+                    cudaSuccess &&
+                write_value((CUstream)aux_stream, (CUdeviceptr)go_dev, bell_seq, 0) == CUDA_SUCCESS)
+                rung = true;
+            cudaGetLastError();
+        }
+        if (!rung) {
+            // host doorbell: the kernel polls it only in the mapped mode, so in the
+            // copy mode a failed transfer leaves the frame to its deadline
+            *(volatile unsigned*)bell_host = bell_seq;
+        }
         unsigned long long v = 0ull;
         const auto limit = std::chrono::duration<double>(armed_wait_s + 2.0);
         for (long it = 0;; ++it) {

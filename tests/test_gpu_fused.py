@@ -235,29 +235,35 @@ def test_bound_frames_and_both_host_transfers_bit_identical(fw, elt_frames):
 def test_armed_frames_bit_identical(fw, elt_frames):
     """Frames armed ahead of their slopes (fewha_frame_arm: the kernel launched
     and waiting; the slopes written afterwards; fewha_frame_fire) give the
-    device frames' layers bit for bit, across the replacement frame; while a
-    frame is armed the handle refuses other work."""
+    device frames' layers bit for bit, across the replacement frame, with the
+    slopes brought in at the fire by the copy engine (default) or read by the
+    kernel through the pinned mapping; while a frame is armed the handle
+    refuses other work."""
     import torch
     cfg, S_in, ref = elt_frames
-    with _fused(fw, cfg, k_rr=10) as A, _fused(fw, cfg, k_rr=10) as B:
-        pin_s = torch.empty(A.S, dtype=torch.float32).pin_memory()
-        pin_l = torch.empty(A.N, dtype=torch.float32).pin_memory()
+    with _fused(fw, cfg, k_rr=10) as A, _fused(fw, cfg, k_rr=10) as B, _fused(fw, cfg, k_rr=10) as C:
+        C.set_host_transfer(False)
+        bufs = [(torch.empty(A.S, dtype=torch.float32).pin_memory(), torch.empty(A.N, dtype=torch.float32).pin_memory())
+                for _ in range(2)]
         dev_s = torch.empty(A.S, dtype=torch.float32, device="cuda")
         dev_l = torch.empty(A.N, dtype=torch.float32, device="cuda")
         for k in range(12):
-            A.arm_frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy(), wait_s=5.0)
-            if k == 3:
-                with pytest.raises(fw.FewhaError) as ei:
-                    A.solve(4)
-                assert ei.value.name == "STATE"
-            pin_s.numpy()[:] = S_in[k]
-            A.fire_frame()
+            for S_, (ps, pl) in ((A, bufs[0]), (C, bufs[1])):
+                S_.arm_frame(ps.numpy(), 4, warm=True, layers_out=pl.numpy(), wait_s=5.0)
+                if k == 3:
+                    with pytest.raises(fw.FewhaError) as ei:
+                        S_.solve(4)
+                    assert ei.value.name == "STATE"
+                ps.numpy()[:] = S_in[k]
+                S_.fire_frame()
             dev_s.copy_(torch.from_numpy(S_in[k]).cuda())
             torch.cuda.synchronize()
             B.frame(dev_s, 4, warm=True, layers_out=dev_l)
             B.sync()
-            assert np.array_equal(pin_l.numpy(), dev_l.cpu().numpy()), k
-            assert rel(pin_l.numpy(), ref[k][0]) < 1e-4, k
+            want = dev_l.cpu().numpy()
+            for _, pl in bufs:
+                assert np.array_equal(pl.numpy(), want), k
+            assert rel(want, ref[k][0]) < 1e-4, k
 
 
 def test_armed_frame_deadline_reported_and_recoverable(fw, elt_frames):
