@@ -237,7 +237,7 @@ def parity_vs_oracle(fewha, cfg, pool, oracle_layers):
 # the committed full ncu capture, valid only for the kernel source it was
 # taken on (sha256 prefix of csrc/fused.cu + csrc/fused_cascade.cuh); any
 # other source reports null.
-NCU_TRAFFIC = {"fused_cu_sha256": "1b008da43af0a69b", "dram_bytes": 5649920,
+NCU_TRAFFIC = {"fused_cu_sha256": "8488acce3221cddd", "dram_bytes": 5650688,
                "summary": "profiles/k_fused_frame_elt_full.md"}
 
 
