@@ -298,6 +298,29 @@ def test_armed_frame_deadline_reported_and_recoverable(fw, elt_frames):
             assert rel(pin_l.numpy(), ref[k][0]) < 1e-4, k
 
 
+def test_armed_frame_released_when_handle_closes(fw, elt_frames):
+    """Closing a handle with a frame still armed fires it (the kernel runs the
+    frame instead of holding the GPU until its deadline), so the close returns
+    promptly and the next handle works."""
+    import time
+
+    import torch
+    cfg, S_in, ref = elt_frames
+    pin_s = torch.empty(int(sum(2 * w["n_sub"] ** 2 for w in cfg["wfs"])), dtype=torch.float32).pin_memory()
+    A = _fused(fw, cfg, k_rr=10)
+    pin_l = torch.empty(A.N, dtype=torch.float32).pin_memory()
+    assert pin_s.numel() == A.S
+    pin_s.numpy()[:] = S_in[0]
+    A.arm_frame(pin_s.numpy(), 4, warm=True, layers_out=pin_l.numpy(), wait_s=30.0)
+    t0 = time.perf_counter()
+    A.close()
+    assert time.perf_counter() - t0 < 5.0
+    with _fused(fw, cfg, k_rr=10) as B:
+        lay = np.empty(B.N, np.float32)
+        B.frame(np.ascontiguousarray(S_in[0]), 4, warm=True, layers_out=lay)
+        assert rel(lay, ref[0][0]) < 1e-4
+
+
 def test_fused_graph_frames_on_rotating_buffers(fw, elt_frames):
     """A new slopes and layers buffer every frame, enqueued back to back (the
     cached graph is updated in place, not re-instantiated): the layers are
