@@ -150,6 +150,7 @@ struct FParams {
     int shared_tables;        // 1: the tables lie in the phases' common working area (rebuilt per phase)
     const PfChunk* pf;        // [grid][pf_per_cta] chunks each CTA prefetches into L2 at the start
     int pf_per_cta;
+    int direct_p;             // 1: a sensor tile's P reads the layers in the L2 directly (no staged windows)
     int G_max, n_max;
     float h[6], g[6];
     // level-stacked layer phase (variant 1; see fused_cascade.cuh)
@@ -678,7 +679,7 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         // layers are one run of float4s (window l starts at float4
         // wdesc[l].off / 4), spread evenly over the threads; a thread's layer
         // index only grows along its run
-        {
+        if (!P.direct_p) {
             const int tot4 = wdesc[L * kWd + 4] >> 2;
             const bool anyg = wdesc[L * kWd + 0] != 0;
             auto dense4 = [&](int l, int e4) {
@@ -719,6 +720,8 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                         dst[e] = __ldcg(src + (long)row * n + col);
                 }
             }
+        }
+        {
             // part A of the next layer phase's CG scalars while the copies fly
             if (want_mu && tid < 32 && cc->lres && cc->il_valid && cc->IL.preA_cta < 0) {
                 ScalA A;
@@ -740,7 +743,15 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
                 const int l = e / (pr + pc), k = e - l * (pr + pc);
                 const int base = I.tab_off[g * L + l];
                 const bool gath = wdesc[l * kWd] < 0;
-                if (k < pr) {
+                if (P.direct_p) {   // offsets into the layer itself
+                    if (k < pr)
+                        rtab[l * P.tile_rows + k] =
+                            make_int2(I.lay_off[l] + __ldg(I.cy + base + a_lo + k) * wdesc[l * kWd + 6],
+                                      __float_as_int(__ldg(I.ty + base + a_lo + k)));
+                    else
+                        ctab[l * P.tile_cols + k - pr] = make_int2(__ldg(I.cx + base + b_lo + k - pr),
+                                                                   __float_as_int(__ldg(I.tx + base + b_lo + k - pr)));
+                } else if (k < pr) {
                     const int rr = gath ? 2 * k : __ldg(I.cy + base + a_lo + k) - wdesc[l * kWd];
                     rtab[l * P.tile_rows + k] =
                         make_int2(rr * wdesc[l * kWd + 3] + wdesc[l * kWd + 4], __float_as_int(__ldg(I.ty + base + a_lo + k)));
@@ -754,7 +765,24 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
         }
         __syncthreads();
         fmark(P, 21);
-        for (int e = tid; e < pr * pc; e += NT) {
+        for (int e = tid; P.direct_p && e < pr * pc; e += NT) {
+            // the layers read in the L2 (written by other SMs in this launch:
+            // not through L1), every node's four cells per layer
+            const int ii = e / pc, jj = e - ii * pc;
+            float acc = 0.f;
+#pragma unroll 3
+            for (int l = 0; l < L; ++l) {
+                const int n = wdesc[l * kWd + 6];
+                const int2 rt = rtab[l * P.tile_rows + ii], ct = ctab[l * P.tile_cols + jj];
+                const float ty = __int_as_float(rt.y), tx = __int_as_float(ct.y);
+                if (!FEWHA_IN(rt.x + ct.x, I.N, n + 2, kDbgWinSrc)) continue;
+                const float* f = I.phi + rt.x + ct.x;
+                acc += (1.f - ty) * ((1.f - tx) * __ldcg(f) + tx * __ldcg(f + 1)) +
+                       ty * ((1.f - tx) * __ldcg(f + n) + tx * __ldcg(f + n + 1));
+            }
+            psi[e] = acc;
+        }
+        for (int e = tid; !P.direct_p && e < pr * pc; e += NT) {
             const int ii = e / pc, jj = e - ii * pc;
             float acc = 0.f;
 #pragma unroll 3
@@ -2361,6 +2389,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             P.g[i] = (float)hss[0]->g[i];
         }
         P.inst = pl->d_inst;
+        P.direct_p = (ninst == 1) ? 1 : 0;
         {
             // L2 prefetch list: descriptors first, then tables, then the state,
             // up to a quarter of the L2 (a large batch keeps only its head)
