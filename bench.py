@@ -496,7 +496,8 @@ def bench_autograd(torch, fewha, dev, flush, reps=20):
 
 
 def bench_batch(torch, fewha, dev, flush, n_frames):
-    """64 uneven instances advanced by one fused launch per frame, against the
+    """64 uneven instances advanced by one fused launch per group (the
+    autotuner's grouping by layer size) per frame, against the
     same 64 instances solved one after another on the plain FP64 path and one
     fused FP32 launch each (one frame graph per instance, back to back)."""
     cfgs = configs.c4_batch(64)
@@ -565,7 +566,8 @@ def bench_batch(torch, fewha, dev, flush, n_frames):
         S.close()
     hbm, _ = measured_peaks()
     return {"workload": "64 independent instances: D 8-39 m, 16-84 subapertures, 2-9 layers on 32^2-256^2 grids, "
-                        "3-6 LGS, 4 warm-started iterations each, FP32, one fused launch per frame",
+                        "3-6 LGS, 4 warm-started iterations each, FP32, one fused launch per group of instances "
+                        "(the autotuner's grouping by layer size) per frame",
             "n_coeff": N, "n_slopes": S_tot, "p50_us": p50, "p99_us": float(np.percentile(t, 99)),
             "instance_frames_per_s": 64 * 1e6 / p50, "frames": n_frames, "autotune": tuned,
             "sequential_fp64_us": seq, "sequential_fp64_instance_frames_per_s": 64 * 1e6 / seq,

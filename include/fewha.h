@@ -408,9 +408,12 @@ int fewha_backward_batch(fewha_handle* h, int n_frames, const void* slopes, int 
  * fill a GPU; a batch advances many unrelated FP32 instances (different
  * telescopes, sensors, layer grids) together, each by the frame of Alg. 1
  * (RHS, warm restart with residual replacement every k_rr frames, n_iter
- * steps of Alg. 2) exactly as fewha_solve does for one handle, in ONE launch
- * of the persistent fused kernel per frame.  Instances share nothing but the
- * launch: every one keeps its own tables, state and CG scalars.
+ * steps of Alg. 2) exactly as fewha_solve does for one handle, in one launch
+ * of the persistent fused kernel per frame -- or one launch per group of
+ * instances, one after another on the stream, when the batch is split
+ * (fewha_batch_set_groups, or the autotuner splitting it by layer size).
+ * Instances share nothing but a launch: every one keeps its own tables,
+ * state and CG scalars.
  *   slopes: the instances' slope vectors concatenated in instance order
  *           (slope_off[i] .. slope_off[i+1]), each laid out as for a handle;
  *   layers: the instances' layer stacks concatenated (coeff_off[i] ..).
@@ -436,8 +439,8 @@ int fewha_batch_sizes(const fewha_batch* b, int* count, long* coeff_off, long* s
 /* Residual replacement period of the batch (as fewha_set_residual_replacement). */
 int fewha_batch_set_residual_replacement(fewha_batch* b, int k_rr);
 
-/* One frame for every instance: copy the slopes in, one fused launch, copy the
- * layers phi = W^T c out (layers_out may be NULL).  on_device = 0: host
+/* One frame for every instance: copy the slopes in, the fused launches (one
+ * per group), copy the layers phi = W^T c out (layers_out may be NULL).  on_device = 0: host
  * buffers, the call synchronises and returns the device error word (INPUT if
  * any instance's slopes are non-finite, BREAKDOWN if any instance's CG step
  * broke down -- that instance keeps its state -- or TIMEOUT). */
@@ -453,19 +456,34 @@ int fewha_batch_sync(fewha_batch* b);
 int fewha_batch_describe(fewha_batch* b, char* buf, int len);
 long long fewha_batch_launch_count(const fewha_batch* b);
 
-/* Autotuner of the batch's launch: builds the plan for every cluster size
- * (8, 4, 16) and sensor-tile bound (none, 32, 24, 20, 16) that fits shared
- * memory, times each on the current slopes (n_iter warm-started iterations
- * from the same state, CUDA events, median of reps launches after one
- * warm-up), keeps the fastest and restores the instances' state.  report:
- * the timings (NUL-terminated, truncated to len).  Synchronises. */
+/* Autotuner of the batch's launches.  The instances are grouped by layer
+ * size (an instance's largest layer side; a group is a range of the sorted
+ * distinct sides: every split between them for up to four sides, at most one
+ * split for more); for every group it builds the plan for every cluster size
+ * (8, 4, 16, 2) and sensor-tile bound (none, 32, 24, 20, 16) that fits
+ * shared memory and times each on the current slopes (n_iter warm-started
+ * iterations from the same state, CUDA events, median of reps launches after
+ * one warm-up).  A grouping costs the sum of its groups' best launches; the
+ * cheapest replaces the current launches if it beats them (timed the same
+ * way), and the instances' state is restored.  report: the timings
+ * (NUL-terminated, truncated to len).  Synchronises. */
 int fewha_batch_autotune(fewha_batch* b, int n_iter, int reps, char* report, int len);
+
+/* Split the batch into launches by hand: group[i] (count = the instance
+ * count entries) is the launch of instance i, 0 .. G - 1 with every launch
+ * non-empty; launches run in index order, each with its own plan built with
+ * the batch's max_tile_side and cluster_size.  The instances keep their
+ * state.  Synchronises.  Errors: ARG (a bad or missing index), GEOMETRY (no
+ * plan fits a group: the current launches stay), CUDA. */
+int fewha_batch_set_groups(fewha_batch* b, const int* group, int count);
 
 /* Sub-phase marks of a batch's fused launches, as fewha_set_trace /
  * fewha_get_fine_trace for one handle (the same tags; a CTA's marks follow
  * its sensor tiles and layer items in order, up to the per-CTA capacity
  * *per_cta).  fewha_batch_get_fine_trace synchronises and copies the last
- * traced launch's marks.  Errors: ARG. */
+ * traced frame's marks: the CTAs of the first launch, then those of the
+ * next (*grid counts them all; the timestamps share one clock).  Errors:
+ * ARG. */
 int fewha_batch_set_trace(fewha_batch* b, int on);
 int fewha_batch_get_fine_trace(fewha_batch* b, unsigned long long* out, int max_entries, int* per_cta, int* grid);
 

@@ -460,6 +460,11 @@ int fewha_batch_autotune(fewha_batch* b, int n_iter, int reps, char* report, int
     return bdone(b, b->b->autotune(n_iter, reps, report, len));
 }
 
+int fewha_batch_set_groups(fewha_batch* b, const int* group, int count) {
+    if (!b) return FEWHA_ERR_ARG;
+    return bdone(b, b->b->set_groups(group, count));
+}
+
 int fewha_debug_bounds(unsigned long long* first, unsigned long long* count) {
     if (!first || !count) return FEWHA_ERR_ARG;
     int (*const readers[])(unsigned long long*, unsigned long long*) = {

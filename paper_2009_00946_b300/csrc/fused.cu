@@ -2132,6 +2132,9 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             }
             nw[i] = (int)witems.size() - w0[i];
         }
+        // a sensor tile's P reads the layers in the L2 directly (every plan) or
+        // from windows staged in shared memory first
+        const bool direct_p = true;
         int tile_nodes = 0, tile_sub = 0, win_max = 0, tile_rows = 0, tile_cols = 0;
         for (auto& w : witems) {
             const HostSetup& hs = *hss[w.inst];
@@ -2155,7 +2158,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         }
         tile_nodes = (tile_nodes + 3) & ~3;
         tile_sub = (tile_sub + 3) & ~3;
-        win_max = (win_max + 3) & ~3;
+        win_max = direct_p ? 0 : (win_max + 3) & ~3;   // direct P stages no windows
         const size_t sensor_floats = (size_t)win_max + tile_nodes + 2 * (size_t)tile_sub;
         const size_t stab_floats = 2 * (size_t)Lmax * (tile_rows + tile_cols);
         // [working set of either phase][layer gather tables][sensor tables]:
@@ -2389,7 +2392,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             P.g[i] = (float)hss[0]->g[i];
         }
         P.inst = pl->d_inst;
-        P.direct_p = (ninst == 1) ? 1 : 0;
+        P.direct_p = direct_p ? 1 : 0;
         {
             // L2 prefetch list: descriptors first, then tables, then the state,
             // up to a quarter of the L2 (a large batch keeps only its head)

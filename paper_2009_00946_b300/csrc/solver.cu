@@ -2343,7 +2343,16 @@ bool host_pinned(const void* ptr) {
 class Batch : public BatchBase {
   public:
     std::vector<std::unique_ptr<Solver<float>>> inst;   // tables and state of each instance
-    FusedPlan* plan = nullptr;
+    // The instances advance as one or more fused launches per frame, one after
+    // another on the stream; a group of instances shares one plan.  One group
+    // is the default; the autotuner may split the batch by layer size, so that
+    // the small layers take the cluster shape and layer-phase form that suit
+    // them while the large ones keep theirs.
+    struct Group {
+        std::vector<int> idx;   // instances, ascending
+        FusedPlan* plan = nullptr;
+    };
+    std::vector<Group> groups;
     std::vector<const HostSetup*> hp;   // what a plan is built from (the autotuner rebuilds it)
     std::vector<DevGeo<float>> Gs;
     std::vector<FusedBuffers> fbs;
@@ -2358,32 +2367,62 @@ class Batch : public BatchBase {
     ~Batch() override {
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
-        if (plan) fused_destroy(plan);
+        for (Group& g : groups) fused_destroy(g.plan);
         if (s_all) cudaFree(s_all);
         if (phi_all) cudaFree(phi_all);
         if (pin_in) cudaFreeHost(pin_in);
         if (pin_out) cudaFreeHost(pin_out);
     }
 
+    // a plan over the instances idx (a sub-batch)
+    FusedPlan* make_plan(const std::vector<int>& idx, int max_tile_side, int C, std::string& e) {
+        std::vector<const HostSetup*> h;
+        std::vector<DevGeo<float>> g;
+        std::vector<FusedBuffers> f;
+        for (int i : idx) {
+            h.push_back(hp[i]);
+            g.push_back(Gs[i]);
+            f.push_back(fbs[i]);
+        }
+        return fused_create_multi(h, g, f, max_tile_side, e, C);
+    }
+
     int set_trace(int on) override {
-        if (!plan) {
+        if (groups.empty()) {
             err = "no fused plan";
             return FEWHA_ERR_STATE;
         }
-        fused_set_trace(plan, on != 0);
+        for (Group& g : groups) fused_set_trace(g.plan, on != 0);
         return FEWHA_OK;
     }
 
+    // the launches' traces one after another: the CTAs of the first launch,
+    // then those of the next (the timestamps are on one clock)
     int get_fine_trace(unsigned long long* out, int max_entries, int* per_cta, int* grid) override {
-        if (!plan) {
+        if (groups.empty()) {
             err = "no fused plan";
             return FEWHA_ERR_STATE;
         }
         FEWHA_CUDA(cudaStreamSynchronize(stream));
-        if (fused_get_fine_trace(plan, out, max_entries, per_cta, grid)) {
-            err = "trace copy failed";
-            return FEWHA_ERR_CUDA;
+        int tot = 0, pc = 0;
+        for (Group& g : groups) {
+            int p = 0, gr = 0;
+            const long done = (long)pc * tot;
+            unsigned long long* dst = (out && max_entries > done) ? out + done : nullptr;
+            if (fused_get_fine_trace(g.plan, dst, dst ? (int)(max_entries - done) : 0, &p, &gr)) {
+                err = "trace copy failed";
+                return FEWHA_ERR_CUDA;
+            }
+            if (p == 0) {   // a launch without a trace buffer: no trace for the batch
+                pc = 0;
+                tot = 0;
+                break;
+            }
+            pc = p;   // the same number of entries per CTA in every plan
+            tot += gr;
         }
+        *per_cta = pc;
+        *grid = tot;
         return FEWHA_OK;
     }
 
@@ -2408,8 +2447,11 @@ class Batch : public BatchBase {
             FEWHA_CUDA(cudaMemcpyAsync(s_all, src, sb, cudaMemcpyHostToDevice, stream));
         }
         const bool replace = warm && k_rr > 0 && frame_count > 0 && frame_count % k_rr == 0;
-        int st = fused_solve(plan, nullptr, n_iter, warm, replace ? 1 : 0, barrier_budget, stream, err, launches);
-        if (st) return st;
+        int st = FEWHA_OK;
+        for (Group& g : groups)
+            if ((st = fused_solve(g.plan, nullptr, n_iter, warm, replace ? 1 : 0, barrier_budget, stream, err,
+                                  launches)))
+                return st;
         frame_count += 1;
         if (on_device) {
             if (lout) FEWHA_CUDA(cudaMemcpyAsync(lout, phi_all, nb, cudaMemcpyDeviceToDevice, stream));
@@ -2428,18 +2470,28 @@ class Batch : public BatchBase {
 
     int sync() override {
         FEWHA_CUDA(cudaStreamSynchronize(stream));
-        const int st = inst[0]->check_err();   // the plan's error word is instance 0's
-        if (st) {
-            err = inst[0]->err;
-            fused_mark_dirty(plan);
+        int first = FEWHA_OK;
+        for (Group& g : groups) {
+            Solver<float>& s = *inst[g.idx[0]];   // a plan's error word is its first instance's
+            const int st = s.check_err();
+            if (st) {
+                if (!first) {
+                    first = st;
+                    err = s.err;
+                }
+                fused_mark_dirty(g.plan);
+            }
         }
-        return st;
+        return first;
     }
 
-    // Plans for every cluster shape and sensor-tile bound that fit, timed on the
-    // current slopes (n_iter warm-started iterations from the same state per
-    // launch, CUDA events, median of reps); the fastest is kept and the
-    // instances' state is restored.
+    // Groupings of the instances by layer size (an instance's largest layer
+    // side; groups are contiguous ranges of the sorted sides, one launch each)
+    // and, per group, every cluster shape and sensor-tile bound that fit, timed
+    // on the current slopes (n_iter warm-started iterations from the same state
+    // per launch, CUDA events, median of reps).  A grouping costs the sum of
+    // its groups' launches; the fastest is kept if it beats the current
+    // launches timed the same way, and the instances' state is restored.
     int autotune(int n_iter, int reps, char* report, int len) override {
         if (n_iter < 1 || reps < 1 || !report || len <= 0) {
             err = "autotune needs n_iter >= 1, reps >= 1 and a report buffer";
@@ -2469,10 +2521,9 @@ class Batch : public BatchBase {
         };
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         int st = FEWHA_OK;
-        FusedPlan* best = plan;
-        float best_t = -1.f;
         std::string rep;
-        auto time_plan = [&](FusedPlan* pl) -> float {
+        // median launch time of a plan over the instances whose first is lead
+        auto time_plan = [&](FusedPlan* pl, int lead) -> float {
             std::vector<float> ts;
             long long dummy = 0;
             for (int r = 0; r <= reps && st == FEWHA_OK; ++r) {
@@ -2485,7 +2536,7 @@ class Batch : public BatchBase {
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (r > 0) ts.push_back(ms * 1e3f);   // the first launch warms up
             }
-            if (st == FEWHA_OK && (st = inst[0]->check_err()) != FEWHA_OK) err = inst[0]->err;
+            if (st == FEWHA_OK && (st = inst[lead]->check_err()) != FEWHA_OK) err = inst[lead]->err;
             if (ts.empty()) return -1.f;
             std::sort(ts.begin(), ts.end());
             return ts[ts.size() / 2];
@@ -2495,40 +2546,103 @@ class Batch : public BatchBase {
             st = FEWHA_ERR_CUDA;
             err = "autotune: events or state copy";
         }
-        if (st == FEWHA_OK) {
-            best_t = time_plan(plan);
+        float cur_t = 0.f;
+        for (Group& g : groups) {
+            if (st != FEWHA_OK) break;
+            const float t = time_plan(g.plan, g.idx[0]);
+            cur_t = (t > 0.f && cur_t >= 0.f) ? cur_t + t : -1.f;
+        }
+        {
             char b[96];
-            snprintf(b, sizeof b, "current: %.1f us", best_t);
+            snprintf(b, sizeof b, "current: %.1f us in %d launch%s", cur_t, (int)groups.size(),
+                     groups.size() == 1 ? "" : "es");
             rep = b;
         }
-        for (int C : {8, 4, 16}) {
-            for (int tile : {0, 32, 24, 20, 16}) {
-                if (st != FEWHA_OK) break;
-                std::string e;
-                FusedPlan* pl = fused_create_multi(hp, Gs, fbs, tile, e, C);
-                if (!pl) continue;
-                const float t = time_plan(pl);
-                char b[96];
-                snprintf(b, sizeof b, "; C=%d tile<=%d: %.1f us", C, tile, t);
-                rep += b;
-                if (t > 0.f && (best_t <= 0.f || t < best_t)) {
-                    if (best != plan) fused_destroy(best);
-                    best = pl;
-                    best_t = t;
-                } else {
-                    fused_destroy(pl);
+        // the sorted distinct sides; a range [a, b] of them is a group
+        const int ni = (int)inst.size();
+        std::vector<int> side(ni, 0);
+        for (int i = 0; i < ni; ++i)
+            for (int l = 0; l < inst[i]->hs.L; ++l) side[i] = std::max(side[i], inst[i]->hs.lay[l].n);
+        std::vector<int> sides(side);
+        std::sort(sides.begin(), sides.end());
+        sides.erase(std::unique(sides.begin(), sides.end()), sides.end());
+        const int k = (int)sides.size();
+        struct Cand {
+            std::vector<int> idx;
+            FusedPlan* plan = nullptr;
+            float t = -1.f;
+            int C = 0, tile = 0;
+        };
+        std::vector<Cand> ranges((size_t)k * k);   // [a * k + b], filled on first use
+        std::vector<char> tuned((size_t)k * k, 0);
+        auto tune_range = [&](int a, int b) -> Cand& {
+            Cand& c = ranges[(size_t)a * k + b];
+            if (tuned[(size_t)a * k + b]) return c;
+            tuned[(size_t)a * k + b] = 1;
+            for (int i = 0; i < ni; ++i)
+                if (side[i] >= sides[a] && side[i] <= sides[b]) c.idx.push_back(i);
+            for (int C : {8, 4, 16, 2}) {
+                for (int tile : {0, 32, 24, 20, 16}) {
+                    if (st != FEWHA_OK) break;
+                    std::string e;
+                    FusedPlan* pl = make_plan(c.idx, tile, C, e);
+                    if (!pl) continue;
+                    const float t = time_plan(pl, c.idx[0]);
+                    if (t > 0.f && (c.t <= 0.f || t < c.t)) {
+                        if (c.plan) fused_destroy(c.plan);
+                        c.plan = pl;
+                        c.t = t;
+                        c.C = C;
+                        c.tile = tile;
+                    } else {
+                        fused_destroy(pl);
+                    }
                 }
             }
-        }
-        if (best != plan) {
-            if (st == FEWHA_OK) {
-                fused_destroy(plan);
-                plan = best;
-                rep += "; chosen: the fastest above";
-            } else {
-                fused_destroy(best);
+            char b2[128];
+            snprintf(b2, sizeof b2, "; sides %d-%d (%d instances): C=%d tile<=%d %.1f us", sides[a], sides[b],
+                     (int)c.idx.size(), c.C, c.tile, c.t);
+            rep += b2;
+            return c;
+        };
+        // groupings: cuts between consecutive sides (all of them for up to
+        // four sides, else one cut at most)
+        int best_mask = -1;
+        float best_t = -1.f;
+        const int max_cuts = k <= 4 ? k - 1 : 1;
+        for (int mask = 0; k > 0 && mask < (1 << (k - 1)) && st == FEWHA_OK; ++mask) {
+            if (__builtin_popcount(mask) > max_cuts) continue;
+            float tot = 0.f;
+            for (int a = 0, j = 0; j < k; ++j) {
+                if (j < k - 1 && !(mask >> j & 1)) continue;
+                const Cand& c = tune_range(a, j);
+                tot = (c.t > 0.f && tot >= 0.f) ? tot + c.t : -1.f;
+                a = j + 1;
+            }
+            if (tot > 0.f && (best_t <= 0.f || tot < best_t)) {
+                best_t = tot;
+                best_mask = mask;
             }
         }
+        if (st == FEWHA_OK && best_mask >= 0 && (cur_t <= 0.f || best_t < cur_t)) {
+            for (Group& g : groups) fused_destroy(g.plan);
+            groups.clear();
+            for (int a = 0, j = 0; j < k; ++j) {
+                if (j < k - 1 && !(best_mask >> j & 1)) continue;
+                Cand& c = ranges[(size_t)a * k + j];
+                groups.push_back(Group{c.idx, c.plan});
+                c.plan = nullptr;   // owned by the group now
+                a = j + 1;
+            }
+            char b[96];
+            snprintf(b, sizeof b, "; chosen: %d launch%s, %.1f us", (int)groups.size(),
+                     groups.size() == 1 ? "" : "es", best_t);
+            rep += b;
+        } else {
+            rep += "; kept the current launches";
+        }
+        for (Cand& c : ranges)
+            if (c.plan) fused_destroy(c.plan);
         if (!copy_state(false)) st = st ? st : FEWHA_ERR_CUDA;
         cudaStreamSynchronize(stream);
         cudaFree(saved);
@@ -2538,13 +2652,64 @@ class Batch : public BatchBase {
         return st;
     }
 
+    // group[i]: the launch of instance i (0 .. G - 1, every launch non-empty);
+    // one plan per launch, built with the batch's tile bound and cluster
+    // shape.  On any failure the current launches stay.
+    int set_groups(const int* group, int count) override {
+        const int ni = (int)inst.size();
+        if (!group || count != ni) {
+            err = "set_groups needs one launch index per instance";
+            return FEWHA_ERR_ARG;
+        }
+        int G = 0;
+        for (int i = 0; i < ni; ++i) {
+            if (group[i] < 0 || group[i] >= ni) {
+                err = "launch index out of range";
+                return FEWHA_ERR_ARG;
+            }
+            G = std::max(G, group[i] + 1);
+        }
+        std::vector<Group> ng(G);
+        for (int i = 0; i < ni; ++i) ng[group[i]].idx.push_back(i);
+        for (Group& g : ng)
+            if (g.idx.empty()) {
+                err = "every launch index below the largest must have an instance";
+                return FEWHA_ERR_ARG;
+            }
+        FEWHA_CUDA(cudaStreamSynchronize(stream));   // the current plans may be in flight
+        for (size_t g = 0; g < ng.size(); ++g) {
+            std::string e;
+            ng[g].plan = make_plan(ng[g].idx, max_tile_side, cluster_size, e);
+            if (!ng[g].plan) {
+                for (Group& h : ng)
+                    if (h.plan) fused_destroy(h.plan);
+                err = "no fused plan for launch " + std::to_string(g) + ": " + e;
+                return FEWHA_ERR_GEOMETRY;
+            }
+        }
+        for (Group& g : groups) fused_destroy(g.plan);
+        groups = std::move(ng);
+        return FEWHA_OK;
+    }
+
     int describe(char* buf, int len) override {
         if (!buf || len <= 0) {
             err = "null buffer";
             return FEWHA_ERR_ARG;
         }
-        int k = snprintf(buf, len, "batch of %d fp32 instances, N %ld, S %ld; ", (int)inst.size(), N_tot(), S_tot());
-        if (k >= 0 && k < len) fused_describe(plan, buf + k, len - k);
+        int k = snprintf(buf, len, "batch of %d fp32 instances, N %ld, S %ld, %d launch%s per frame", (int)inst.size(),
+                         N_tot(), S_tot(), (int)groups.size(), groups.size() == 1 ? "" : "es");
+        for (size_t g = 0; g < groups.size() && k >= 0 && k < len; ++g) {
+            const int m = groups.size() == 1 ? snprintf(buf + k, len - k, "; ")
+                                             : snprintf(buf + k, len - k, "; launch %d (%d instances): ", (int)g,
+                                                        (int)groups[g].idx.size());
+            if (m < 0) break;
+            k += m;
+            if (k >= len) break;
+            const int f = fused_describe(groups[g].plan, buf + k, len - k);
+            if (f < 0) break;
+            k += f;
+        }
         return FEWHA_OK;
     }
 
@@ -2563,6 +2728,8 @@ BatchBase* make_batch(const std::vector<HostSetup>& hss, cudaStream_t stream, in
                       int cluster_size, std::string& err, int& status) {
     std::unique_ptr<Batch> B(new Batch());
     B->stream = stream;
+    B->max_tile_side = max_tile_side;
+    B->cluster_size = cluster_size;
     B->coeff_off.assign(1, 0);
     B->slope_off.assign(1, 0);
     for (size_t i = 0; i < hss.size(); ++i) {
@@ -2620,8 +2787,11 @@ BatchBase* make_batch(const std::vector<HostSetup>& hss, cudaStream_t stream, in
         Gs.push_back(s.G);
         fbs.push_back(fb);
     }
-    B->plan = fused_create_multi(hp, Gs, fbs, max_tile_side, err, cluster_size);
-    if (!B->plan) {
+    Batch::Group all;
+    for (int i = 0; i < (int)B->inst.size(); ++i) all.idx.push_back(i);
+    all.plan = B->make_plan(all.idx, max_tile_side, cluster_size, err);
+    if (all.plan) B->groups.push_back(all);
+    if (!all.plan) {
         err = "no fused plan for this batch: " + err;
         status = FEWHA_ERR_GEOMETRY;
         return nullptr;

@@ -160,8 +160,10 @@ class BatchBase {
     virtual int set_trace(int on) = 0;
     virtual int get_fine_trace(unsigned long long* out, int max_entries, int* per_cta, int* grid) = 0;
     virtual int autotune(int n_iter, int reps, char* report, int len) = 0;
+    virtual int set_groups(const int* group, int count) = 0;
 
     std::vector<long> coeff_off, slope_off;   // count + 1 offsets
+    int max_tile_side = 0, cluster_size = 0;  // as created: the plans of new groups follow them
     cudaStream_t stream = 0;
     int k_rr = 10;
     long long barrier_budget = (1LL << 31);

@@ -134,6 +134,7 @@ def lib():
         "fewha_batch_describe": (ci, [vp, ctypes.c_char_p, ci]),
         "fewha_batch_launch_count": (cll, [vp]),
         "fewha_batch_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
+        "fewha_batch_set_groups": (ci, [vp, ctypes.POINTER(ci), ci]),
         "fewha_batch_set_trace": (ci, [vp, ci]),
         "fewha_batch_get_fine_trace": (ci, [vp, ctypes.POINTER(ctypes.c_ulonglong), ci, ctypes.POINTER(ci),
                                             ctypes.POINTER(ci)]),
@@ -581,8 +582,9 @@ class Solver:
 
 class Batch:
     """Many independent FP32 instances advanced together, one fused launch per
-    frame (a fewha_batch).  Slopes and layers are concatenated in instance
-    order; `slope_off` / `coeff_off` give each instance's slice."""
+    frame or one per group of instances (a fewha_batch).  Slopes and layers
+    are concatenated in instance order; `slope_off` / `coeff_off` give each
+    instance's slice."""
 
     def __init__(self, cfgs: list, stream=None, max_tile_side: int = 24, cluster_size: int = 0,
                  k_rr: int | None = None):
@@ -670,7 +672,8 @@ class Batch:
         self._check(lib().fewha_batch_set_trace(self.h, 1 if on else 0))
 
     def fine_trace(self):
-        """Last traced launch: per CTA a list of (tag, ns) marks inside the phases."""
+        """Last traced frame: per CTA a list of (tag, ns) marks inside the
+        phases (the CTAs of every launch of the frame, in launch order)."""
         per, grid = ctypes.c_int(), ctypes.c_int()
         self._check(lib().fewha_batch_get_fine_trace(self.h, None, 0, ctypes.byref(per), ctypes.byref(grid)))
         n = per.value * grid.value
@@ -680,19 +683,28 @@ class Batch:
         return _marks(out[:n].reshape(grid.value, per.value))
 
     def describe(self) -> str:
-        buf = ctypes.create_string_buffer(512)
-        self._check(lib().fewha_batch_describe(self.h, buf, 512))
+        buf = ctypes.create_string_buffer(1024)
+        self._check(lib().fewha_batch_describe(self.h, buf, 1024))
         return buf.value.decode()
 
     def launch_count(self) -> int:
         return int(lib().fewha_batch_launch_count(self.h))
 
     def autotune(self, n_iter: int = 4, reps: int = 3) -> str:
-        """Time the feasible cluster shapes and sensor-tile bounds on the
-        current slopes (after a frame), keep the fastest."""
-        buf = ctypes.create_string_buffer(1024)
-        self._check(lib().fewha_batch_autotune(self.h, int(n_iter), int(reps), buf, 1024))
+        """Time the groupings of the instances by layer size and, per group,
+        the feasible cluster shapes and sensor-tile bounds on the current
+        slopes (after a frame); keep the fastest."""
+        buf = ctypes.create_string_buffer(2048)
+        self._check(lib().fewha_batch_autotune(self.h, int(n_iter), int(reps), buf, 2048))
         return buf.value.decode()
+
+    def set_groups(self, group):
+        """group[i]: the launch (0 .. G - 1) that advances instance i."""
+        g = np.ascontiguousarray(group, np.int32)
+        if g.shape != (self.count,):
+            raise ValueError("one launch index per instance")
+        self._check(lib().fewha_batch_set_groups(self.h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                 self.count))
 
 
 def measure_l2(nbytes: int = 48 << 20, passes: int = 40, reps: int = 5) -> dict:

@@ -1,6 +1,7 @@
 """Batched instances (64 uneven telescopes, 4 warm-started iterations, FP32)
-advanced by one fused launch per frame, against the FP64 oracle run instance
-by instance: layers <= 1e-4 relative L2 for every instance and frame."""
+advanced by one fused launch per frame (or one per group of instances),
+against the FP64 oracle run instance by instance: layers <= 1e-4 relative L2
+for every instance and frame."""
 
 import numpy as np
 import pytest
@@ -103,19 +104,64 @@ def test_batch_device_buffers_and_state(fw, subset_frames):
 
 
 def test_batch_autotune_keeps_state_and_parity(fw, subset_frames):
-    """The batch autotuner times the feasible cluster shapes and tile bounds on
-    the current frame, keeps the fastest and restores the state: the frames
-    that follow still match the oracle."""
+    """The batch autotuner times the groupings by layer size and, per group,
+    the feasible cluster shapes and tile bounds on the current frame, keeps
+    the fastest and restores the state: the frames that follow still match
+    the oracle."""
     cfgs, slopes, ref = subset_frames
     with fw.Batch(cfgs, k_rr=10) as B:
         out = np.empty(B.N, np.float32)
         B.frame(B.concat_slopes([s[0] for s in slopes]), 4, warm=True, layers_out=out)
         report = B.autotune(4, 2)
-        assert report.startswith("current:") and "C=8" in report, report
+        # four distinct sides (32 .. 256): all ten ranges of them are tuned
+        assert report.startswith("current:") and report.count("; sides ") == 10, report
+        assert "sides 32-256 (8 instances): C=" in report, report
+        n0 = B.launch_count()
         for k in range(1, 4):
             B.frame(B.concat_slopes([s[k] for s in slopes]), 4, warm=True, layers_out=out)
             for i, lay in enumerate(B.split_layers(out)):
                 assert rel(lay, ref[i][k]) < 1e-4, (SUBSET[i], k)
+        n_launch = int(B.describe().split(" launch")[0].rsplit(" ", 1)[1])
+        assert B.launch_count() - n0 == 3 * n_launch
+
+
+def test_batch_split_into_launches_by_hand(fw, subset_frames):
+    """The instances with 256^2 layers in one launch, the rest in another:
+    every instance still matches the oracle over 12 frames (across the
+    residual replacement), two launches per frame; bad groupings are refused
+    and leave the launches as they were."""
+    cfgs, slopes, ref = subset_frames
+    side = [max(l["n"] for l in c["layers"]) for c in cfgs]
+    group = [0 if n == 256 else 1 for n in side]
+    assert 0 < sum(group) < len(group)
+    with fw.Batch(cfgs, k_rr=10) as B:
+        B.set_groups(group)
+        d = B.describe()
+        assert "2 launches per frame" in d and "launch 0 (%d instances)" % group.count(0) in d, d
+        for bad in ([0] * (B.count - 1), [0] * (B.count - 1) + [2], [0] * (B.count - 1) + [-1]):
+            with pytest.raises((fw.FewhaError, ValueError)):
+                B.set_groups(bad)
+        assert B.describe() == d
+        out = np.empty(B.N, np.float32)
+        for k in range(12):
+            B.frame(B.concat_slopes([s[k] for s in slopes]), 4, warm=True, layers_out=out)
+            for i, lay in enumerate(B.split_layers(out)):
+                assert rel(lay, ref[i][k]) < 1e-4, (SUBSET[i], k)
+                elementwise_check(lay, ref[i][k], [l["n"] for l in cfgs[i]["layers"]], 1e-3, what=(SUBSET[i], k))
+        assert B.launch_count() == 24
+        B.set_trace(True)
+        B.frame(B.concat_slopes([s[0] for s in slopes]), 4, warm=True, layers_out=out)
+        B.set_trace(False)
+        marks = B.fine_trace()
+        assert len(marks) > 0 and sum(len(m) for m in marks) > 0
+        # a non-finite slope of an instance that does not lead its launch
+        i = next(j for j in range(len(cfgs)) if group[j] == 0 and j != group.index(0))
+        g = fo.Geometry(cfgs[i])
+        per = [s[1].copy() for s in slopes]
+        per[i][g.soff[0] + int(np.flatnonzero(g.mask[0].ravel() == 1)[5])] = np.nan
+        with pytest.raises(fw.FewhaError) as ei:
+            B.frame(B.concat_slopes(per), 4, warm=False)
+        assert ei.value.name == "INPUT"
 
 
 def test_batch_nan_in_one_instance_reported(fw, subset_frames):
@@ -133,12 +179,15 @@ def test_batch_nan_in_one_instance_reported(fw, subset_frames):
 @pytest.mark.slow
 def test_batch_all_64_instances_match_oracle(fw):
     """The whole 64-instance batch in the launch configuration the benchmark
-    times (default tiles and cluster shape): two frames, every instance."""
+    times (default tiles, then the autotuner's launches): two frames, every
+    instance."""
     cfgs = configs.c4_batch(64)
     slopes, ref = _oracle_frames(cfgs, 2)
     with fw.Batch(cfgs, k_rr=10) as B:
         out = np.empty(B.N, np.float32)
         for k in range(2):
+            if k == 1:
+                B.autotune(4, 1)
             B.frame(B.concat_slopes([s[k] for s in slopes]), 4, warm=True, layers_out=out)
             errs = [rel(lay, ref[i][k]) for i, lay in enumerate(B.split_layers(out))]
             assert max(errs) < 1e-4, (k, int(np.argmax(errs)), max(errs))
