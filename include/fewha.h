@@ -477,6 +477,12 @@ int fewha_batch_autotune(fewha_batch* b, int n_iter, int reps, char* report, int
  * plan fits a group: the current launches stay), CUDA. */
 int fewha_batch_set_groups(fewha_batch* b, const int* group, int count);
 
+/* Bound on the launches per frame that fewha_batch_autotune may choose
+ * (0 = none, the default; 1 = the whole batch in one launch).  The current
+ * launches are replaced by the autotuner's choice when they exceed the
+ * bound.  Errors: ARG (NULL handle or a negative bound). */
+int fewha_batch_set_max_launches(fewha_batch* b, int max_launches);
+
 /* Sub-phase marks of a batch's fused launches, as fewha_set_trace /
  * fewha_get_fine_trace for one handle (the same tags; a CTA's marks follow
  * its sensor tiles and layer items in order, up to the per-CTA capacity

@@ -465,6 +465,16 @@ int fewha_batch_set_groups(fewha_batch* b, const int* group, int count) {
     return bdone(b, b->b->set_groups(group, count));
 }
 
+int fewha_batch_set_max_launches(fewha_batch* b, int max_launches) {
+    if (!b) return FEWHA_ERR_ARG;
+    if (max_launches < 0) {
+        b->msg = "max_launches must be >= 0";
+        return FEWHA_ERR_ARG;
+    }
+    b->b->max_launches = max_launches;
+    return FEWHA_OK;
+}
+
 int fewha_debug_bounds(unsigned long long* first, unsigned long long* count) {
     if (!first || !count) return FEWHA_ERR_ARG;
     int (*const readers[])(unsigned long long*, unsigned long long*) = {

@@ -2606,10 +2606,11 @@ class Batch : public BatchBase {
             return c;
         };
         // groupings: cuts between consecutive sides (all of them for up to
-        // four sides, else one cut at most)
+        // four sides, else one cut at most; fewer under a launch bound)
         int best_mask = -1;
         float best_t = -1.f;
-        const int max_cuts = k <= 4 ? k - 1 : 1;
+        int max_cuts = k <= 4 ? k - 1 : 1;
+        if (max_launches > 0) max_cuts = std::min(max_cuts, max_launches - 1);
         for (int mask = 0; k > 0 && mask < (1 << (k - 1)) && st == FEWHA_OK; ++mask) {
             if (__builtin_popcount(mask) > max_cuts) continue;
             float tot = 0.f;
@@ -2624,7 +2625,8 @@ class Batch : public BatchBase {
                 best_mask = mask;
             }
         }
-        if (st == FEWHA_OK && best_mask >= 0 && (cur_t <= 0.f || best_t < cur_t)) {
+        const bool cur_ok = max_launches <= 0 || (int)groups.size() <= max_launches;
+        if (st == FEWHA_OK && best_mask >= 0 && (cur_t <= 0.f || best_t < cur_t || !cur_ok)) {
             for (Group& g : groups) fused_destroy(g.plan);
             groups.clear();
             for (int a = 0, j = 0; j < k; ++j) {

@@ -164,6 +164,7 @@ class BatchBase {
 
     std::vector<long> coeff_off, slope_off;   // count + 1 offsets
     int max_tile_side = 0, cluster_size = 0;  // as created: the plans of new groups follow them
+    int max_launches = 0;                     // the autotuner's bound on launches per frame (0: none)
     cudaStream_t stream = 0;
     int k_rr = 10;
     long long barrier_budget = (1LL << 31);

@@ -135,6 +135,7 @@ def lib():
         "fewha_batch_launch_count": (cll, [vp]),
         "fewha_batch_autotune": (ci, [vp, ci, ci, ctypes.c_char_p, ci]),
         "fewha_batch_set_groups": (ci, [vp, ctypes.POINTER(ci), ci]),
+        "fewha_batch_set_max_launches": (ci, [vp, ci]),
         "fewha_batch_set_trace": (ci, [vp, ci]),
         "fewha_batch_get_fine_trace": (ci, [vp, ctypes.POINTER(ctypes.c_ulonglong), ci, ctypes.POINTER(ci),
                                             ctypes.POINTER(ci)]),
@@ -697,6 +698,10 @@ class Batch:
         buf = ctypes.create_string_buffer(2048)
         self._check(lib().fewha_batch_autotune(self.h, int(n_iter), int(reps), buf, 2048))
         return buf.value.decode()
+
+    def set_max_launches(self, m: int):
+        """Bound on the launches per frame the autotuner may choose (0: none)."""
+        self._check(lib().fewha_batch_set_max_launches(self.h, int(m)))
 
     def set_groups(self, group):
         """group[i]: the launch (0 .. G - 1) that advances instance i."""

@@ -105,6 +105,7 @@ def test_batch_rejects_invalid_arguments_on_host():
     assert L.fewha_batch_destroy(None) == 1 and L.fewha_batch_frame(None, None, 4, 1, None, 0) == 1
     assert L.fewha_batch_launch_count(None) == -1
     assert L.fewha_batch_set_groups(None, None, 0) == 1
+    assert L.fewha_batch_set_max_launches(None, 1) == 1
 
 
 def test_debug_library_exports_every_declared_symbol():

@@ -162,6 +162,17 @@ def test_batch_split_into_launches_by_hand(fw, subset_frames):
         with pytest.raises(fw.FewhaError) as ei:
             B.frame(B.concat_slopes(per), 4, warm=False)
         assert ei.value.name == "INPUT"
+        # under a bound of one launch the autotuner brings the batch back to one
+        # (after a finite frame: the autotuner times the current slopes)
+        B.set_max_launches(1)
+        B.frame(B.concat_slopes([s[2] for s in slopes]), 4, warm=True, layers_out=out)
+        report = B.autotune(4, 1)
+        assert "1 launch per frame" in B.describe() and report.count("; sides ") == 1, report
+        B.frame(B.concat_slopes([s[3] for s in slopes]), 4, warm=True, layers_out=out)
+        assert np.isfinite(out).all()
+        B.set_max_launches(0)
+        with pytest.raises(fw.FewhaError):
+            B.set_max_launches(-1)
 
 
 def test_batch_nan_in_one_instance_reported(fw, subset_frames):
