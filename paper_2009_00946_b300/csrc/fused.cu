@@ -1309,6 +1309,26 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
         const float fa = (float)alpha, fb = (float)beta;
         for (int e0 = tid; e0 < total; e0 += kE * NT) {
             if (e0 != tid) load(e0);
+            {
+                // the next batch's lines into the L2 while this one computes
+                // (one lane per warp: a warp's 32 elements are one 128-byte line)
+                const int en = e0 + kE * NT;
+                if ((tid & 31) == 0 && en < total) {
+#pragma unroll
+                    for (int u = 0; u < kE; ++u) {
+                        const int e = en + u * NT;
+                        if (e < total) {
+                            const long i = gbase + e;
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(I.r + i));
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(I.p + i));
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(I.q + i));
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(I.c + i));
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(I.Jinv + i));
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(I.aD + i));
+                        }
+                    }
+                }
+            }
 #pragma unroll
             for (int u = 0; u < kE; ++u) {
                 const int e = e0 + u * NT;
@@ -1336,42 +1356,70 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
                 Z[e] = zout;
             }
         }
-    }
-    for (int e = tid; mode != kLpIter && e < R * n; e += NT) {
-        const long i = gbase + e;
-        if (!FEWHA_IN(i, I.N, 1, kDbgCoef)) continue;
-        const float jinv = __ldg(I.Jinv + i), ad = __ldg(I.aD + i);
-        float zout = 0.f;
-        if (mode == kLpRhsStart) {
-            const float bv = Z[e];
-            float rv;
-            if (!P.warm) {
-                rv = bv;
-                I.c[i] = 0.f;
-            } else {
-                rv = (bv - I.bprev[i]) + I.r[i];
+    } else {
+        // RHS, its replacement form and the restart: batches of kE elements
+        // per thread, every load of a batch issued before its arithmetic
+        constexpr int kE = 3;
+        const int total = R * n;
+        const bool need_ja = mode != kLpRhsRepl;
+        const bool need_12 = mode != kLpRhsStart || P.warm;
+        for (int e0 = tid; e0 < total; e0 += kE * NT) {
+            float vj[kE], va[kE], v1[kE], v2[kE];
+#pragma unroll
+            for (int u = 0; u < kE; ++u) {
+                const int e = e0 + u * NT;
+                if (e < total && FEWHA_IN(gbase + e, I.N, 1, kDbgCoef)) {
+                    const long i = gbase + e;
+                    if (need_ja) {
+                        vj[u] = __ldg(I.Jinv + i);
+                        va[u] = __ldg(I.aD + i);
+                    }
+                    if (need_12) {
+                        // RhsStart: bprev, r; RhsRepl: c; ReplStart: c, b
+                        v1[u] = (mode == kLpRhsStart ? I.bprev : I.c)[i];
+                        if (mode != kLpRhsRepl) v2[u] = (mode == kLpRhsStart ? I.r : I.b)[i];
+                    }
+                }
             }
-            I.b[i] = bv;
-            I.bprev[i] = bv;
-            I.r[i] = rv;
-            zout = jinv * rv;
-            rho_p.add_prod(rv, zout);
-            dz_p.add_prod3(ad, zout, zout);
-        } else if (mode == kLpRhsRepl) {
-            I.b[i] = Z[e];
-            zout = I.c[i];
-        } else if (mode == kLpReplStart) {
-            // r = b - M c = W P^T Gamma^T C^{-1} (s - Gamma P W^T c) - alpha D c
-            // (the data part arrives as the transformed slope residual)
-            const float cv = I.c[i];
-            const float rv = (float)((double)Z[e] - (double)ad * (double)cv);
-            I.bprev[i] = I.b[i];
-            I.r[i] = rv;
-            zout = jinv * rv;
-            rho_p.add_prod(rv, zout);
-            dz_p.add_prod3(ad, zout, zout);
+#pragma unroll
+            for (int u = 0; u < kE; ++u) {
+                const int e = e0 + u * NT;
+                if (e >= total) break;
+                const long i = gbase + e;
+                if (!FEWHA_IN(i, I.N, 1, kDbgCoef)) continue;
+                float zout = 0.f;
+                if (mode == kLpRhsStart) {
+                    const float bv = Z[e];
+                    float rv;
+                    if (!P.warm) {
+                        rv = bv;
+                        I.c[i] = 0.f;
+                    } else {
+                        rv = (bv - v1[u]) + v2[u];
+                    }
+                    I.b[i] = bv;
+                    I.bprev[i] = bv;
+                    I.r[i] = rv;
+                    zout = vj[u] * rv;
+                    rho_p.add_prod(rv, zout);
+                    dz_p.add_prod3(va[u], zout, zout);
+                } else if (mode == kLpRhsRepl) {
+                    I.b[i] = Z[e];
+                    zout = v1[u];
+                } else if (mode == kLpReplStart) {
+                    // r = b - M c = W P^T Gamma^T C^{-1} (s - Gamma P W^T c) - alpha D c
+                    // (the data part arrives as the transformed slope residual)
+                    const float cv = v1[u];
+                    const float rv = (float)((double)Z[e] - (double)va[u] * (double)cv);
+                    I.bprev[i] = v2[u];
+                    I.r[i] = rv;
+                    zout = vj[u] * rv;
+                    rho_p.add_prod(rv, zout);
+                    dz_p.add_prod3(va[u], zout, zout);
+                }
+                Z[e] = zout;
+            }
         }
-        Z[e] = zout;
     }
     if (mode == kLpIter) fmark(P, 18);
     if (make_z) {
