@@ -529,8 +529,9 @@ int fewha_layers_noalloc(const float* coeffs, float* layers, int n_layers, const
                          const int* levels, void* stream, char* errbuf, int errlen);
 
 /* Sites of the debug build's bounds checks (fewha_debug_bounds): the sensor
- * tile's window source and staging, its bilinear reads, slope indices and
- * Gamma^T output; the layer phase's field staging source and destination,
+ * tile's bilinear reads of the layers (WIN_SRC; WIN_DST and WIN_P belonged
+ * to the staged windows the tile no longer uses and stay reserved), slope
+ * indices and Gamma^T output; the layer phase's field staging source and destination,
  * P^T gather reads, level-stacked DWT stores into row and column owners,
  * coefficient indices, tip-tilt correction nodes, layer output; the
  * row-stripe DWT's peer reads; table staging; the plain path's P, P^T and
@@ -546,7 +547,7 @@ enum {
 /* The paper has no counterpart: the memory checker of the debug build.  A
  * library built with -DFEWHA_DEBUG (libfewha_debug.so, made next to the
  * release library) checks at every gather and scatter of the hot path --
- * the fused kernel's window and field staging, bilinear reads, P^T gather,
+ * the fused kernel's field staging, bilinear reads, P^T gather,
  * DWT exchange stores and coefficient indices; the plain path's P, P^T,
  * Gamma and Gamma^T; the fit's sparse products and layer samples; the
  * no-allocation transform -- that the index lies inside the buffer it

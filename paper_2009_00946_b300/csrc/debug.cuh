@@ -21,9 +21,9 @@ namespace fewha {
 // check sites (the high 16 bits of the first-violation word)
 enum DbgSite {
     kDbgNone = 0,
-    kDbgWinSrc = 1,      // fused sensor tile: layer window staged from phi
-    kDbgWinDst = 2,      //   ... into shared memory
-    kDbgWinP = 3,        // fused sensor tile: bilinear read of a staged window
+    kDbgWinSrc = 1,      // fused sensor tile: bilinear read of the layer cells (phi)
+    kDbgWinDst = 2,      //   reserved (staged windows, no longer used)
+    kDbgWinP = 3,        //   reserved (staged windows, no longer used)
     kDbgSlopes = 4,      // fused sensor tile: slope / mask index
     kDbgGtOut = 5,       // fused sensor tile: Gamma^T output node
     kDbgStgSrc = 6,      // fused layer phase: sensor field staged from psi

@@ -9,8 +9,8 @@
 //     fields), the forward db3 DWT W, the Alg. 2 update, z = J^{-1} r and the
 //     inverse DWT W^T run there; the column passes of the DWT read the other
 //     stripes through distributed shared memory, one cluster barrier per level.
-//   * sensor phase: one CTA per sensor tile: bilinear P of every layer (the
-//     layer windows are staged in shared memory), Gamma, C^{-1}, Gamma^T; the
+//   * sensor phase: one CTA per sensor tile: bilinear P of every layer (each
+//     node's four cells per layer read in the L2), Gamma, C^{-1}, Gamma^T; the
 //     data part of mu = (M z, z) = sum_g w_g |mask Gamma P W^T z|^2 is reduced
 //     here, the regulariser part alpha (D z, z) in the layer phase.
 // Per iteration: layer phase -> barrier -> sensor phase -> barrier.  Every sum
@@ -42,7 +42,6 @@ constexpr int kMaxC = 16;
 constexpr int kMaxLayersFused = 64;
 constexpr int kMaxWfsFused = 16;
 constexpr int kFineCap = 4096;   // sub-phase marks per CTA per traced launch (a batch's CTAs take many items)
-constexpr int kWd = 8;     // ints per layer in a sensor tile's window descriptor
 constexpr int kMaxKG = 4;        // P^T gather entries per layer row / column
 
 // sensor phases: the RHS (weighted slopes), the data term of M on the
@@ -145,12 +144,11 @@ struct FParams {
     const int* duty;
     int n_iter, warm, replace, out_layers;
     int C;
-    int stripe_floats, stage_floats, win_floats, tile_nodes, tile_subaps, tile_rows, tile_cols;
+    int stripe_floats, stage_floats, tile_nodes, tile_subaps, tile_rows, tile_cols;
     int ltab_off, stab_off;   // dynamic shared memory (floats) of the layer / sensor tables
     int shared_tables;        // 1: the tables lie in the phases' common working area (rebuilt per phase)
     const PfChunk* pf;        // [grid][pf_per_cta] chunks each CTA prefetches into L2 at the start
     int pf_per_cta;
-    int direct_p;             // 1: a sensor tile's P reads the layers in the L2 directly (no staged windows)
     int G_max, n_max;
     float h[6], g[6];
     // level-stacked layer phase (variant 1; see fused_cascade.cuh)
@@ -500,11 +498,11 @@ __device__ void alg2_part_b(const FParams& P, const FInst& I, int k, const ScalA
 }
 
 // Static data of the work items a CTA is on, in shared memory: descriptors,
-// window layout and gather tables are (re)built only when the item changes,
+// interpolation and gather tables are (re)built only when the item changes,
 // so a CTA that owns one sensor tile and one layer item for the whole launch
 // reads them from global memory once.
 struct CtaCache {
-    int wkey, lkey, wtab;       // cached sensor item, layer item; window tables built
+    int wkey, lkey, wtab;       // cached sensor item, layer item; interpolation tables built
     int ltkey;                  // layer item whose staging ranges and gather tables are built
     int ltx;                    // layer item whose gather tables are rewritten to staging offsets
     int lres, il_valid;         // the CTA has one layer item for the launch; IL holds it
@@ -602,8 +600,8 @@ __device__ void layer_tables(const FParams& P, int rank, const CtaCache* cc, flo
 // ---------------------------------------------------------------------------
 // sensor phase: P, Gamma, C^{-1}, Gamma^T on one tile of nodes
 // ---------------------------------------------------------------------------
-__device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, bool want_mu, int* wdesc, double* red,
-                            CtaCache* cc, int k) {
+__device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, bool want_mu, double* red, CtaCache* cc,
+                            int k) {
     const int tid = threadIdx.x, NT = blockDim.x;
     fmark(P, mode == kModeRhs ? 30 : 20);
     if (P.shared_tables && tid == 0) cc->lkey = cc->ltkey = cc->ltx = -1;   // this phase overwrites the layer tables
@@ -621,178 +619,65 @@ __device__ void sensor_tile(const FParams& P, int item, float* sm, int mode, boo
     const int sa_hi = min(W.i1, ns), sb_hi = min(W.j1, ns);
     const int nsr = max(sa_hi - a_lo, 0), nsc = max(sb_hi - b_lo, 0);
     const int pr = a_hi - a_lo + 1, pc = b_hi - b_lo + 1;
-    float* win = sm;
-    float* psi = sm + P.win_floats;
+    float* psi = sm;
     float* slx = psi + P.tile_nodes;
     float* sly = slx + P.tile_subaps;
-    // per-tile interpolation tables: [l][row] window offset / weight, [l][col]
-    // (window offset, weight bits) pairs, one 8-byte load each
+    // per-tile interpolation tables: [l][row] (layer offset, weight bits),
+    // [l][col] (column, weight bits) pairs, one 8-byte load each
     int2* rtab = (int2*)(sm + P.stab_off);
     int2* ctab = rtab + L * P.tile_rows;
     Acc2 mu, tmx, tmy;   // tmx, tmy: masked slope sums of a tip-tilt filtered sensor
     const bool ttg = I.tt_any && I.tt[g];
     const int ns2 = ns * ns;
     if (mode != kModeRhs) {
-        const bool build = !cc->wtab;
-        if (build) {
-            if (tid < L) {
-                // window of layer tid: rows r0..r1, columns widened to 16-byte
-                // boundaries (c0 down, width up to a multiple of 4 floats; layer
-                // rows are multiples of 4 floats, so the widened window stays inside)
-                const int base = I.tab_off[g * L + tid];
-                const int r0 = I.cy[base + a_lo], r1 = I.cy[base + a_hi] + 1;
-                const int c0 = I.cx[base + b_lo] & ~3, c1 = I.cx[base + b_hi] + 1;
-                const int n = I.lay_n[tid];
-                const int nr = r1 - r0 + 1, nc = (c1 - c0 + 1 + 3) & ~3;
-                // a sparse sensor (nodes several layer cells apart, e.g. a 1x1
-                // tip-tilt sensor) stages only the 2 x 2 cells under each node
-                // (gathered window: row 2 ii + dr, column 2 jj + dc; marked by
-                // r0 = -1); nodes up to ~4 cells apart keep the dense window,
-                // which stages faster at a similar size
-                const bool gath = nr * nc > 16 * pr * pc;
-                wdesc[tid * kWd + 0] = gath ? -1 : r0;
-                wdesc[tid * kWd + 1] = c0;
-                wdesc[tid * kWd + 2] = gath ? 2 * pr : nr;
-                wdesc[tid * kWd + 3] = gath ? 2 * pc : nc;
-                wdesc[tid * kWd + 5] = gath ? I.lay_off[tid] : I.lay_off[tid] + r0 * n + c0;
-                wdesc[tid * kWd + 6] = n;
-                // row of a window float4 by multiply-high with ceil(2^32 / nc4)
-                // (Granlund-Montgomery, round-up multiplier: exact for q * nc4 < 2^32);
-                // nc4 = 1 (multiplier 2^32) is marked 0 and takes the row directly
-                const unsigned nc4 = (unsigned)nc >> 2;
-                wdesc[tid * kWd + 7] = nc4 > 1 ? (int)(unsigned)(((1ull << 32) + nc4 - 1) / nc4) : 0;
-            }
-            __syncthreads();
+        // part A of the next layer phase's CG scalars
+        if (want_mu && tid < 32 && cc->lres && cc->il_valid && cc->IL.preA_cta < 0) {
+            ScalA A;
+            alg2_part_a(P, cc->IL, k, A);
             if (tid == 0) {
-                int o = 0, anyg = 0;
-                for (int l = 0; l < L; ++l) {
-                    wdesc[l * kWd + 4] = o;
-                    o += wdesc[l * kWd + 2] * wdesc[l * kWd + 3];
-                    anyg |= wdesc[l * kWd] < 0;
-                }
-                wdesc[L * kWd + 4] = o;
-                wdesc[L * kWd + 0] = anyg;   // some layer of the tile has a gathered window
-            }
-            __syncthreads();
-        }
-        // 16-byte asynchronous copies (through L2, not L1): the windows of all
-        // layers are one run of float4s (window l starts at float4
-        // wdesc[l].off / 4), spread evenly over the threads; a thread's layer
-        // index only grows along its run
-        if (!P.direct_p) {
-            const int tot4 = wdesc[L * kWd + 4] >> 2;
-            const bool anyg = wdesc[L * kWd + 0] != 0;
-            auto dense4 = [&](int l, int e4) {
-                const int nc4 = wdesc[l * kWd + 3] >> 2;
-                const unsigned loc = (unsigned)(e4 - (wdesc[l * kWd + 4] >> 2));
-                const unsigned mg = (unsigned)wdesc[l * kWd + 7];
-                const int rr = mg ? (int)__umulhi(loc, mg) : (int)loc, c4 = (int)loc - rr * nc4;
-                const long si = wdesc[l * kWd + 5] + (long)rr * wdesc[l * kWd + 6] + (c4 << 2);
-                if (!FEWHA_IN(si, I.N, 4, kDbgWinSrc)) return;
-                cp_async16(win + (e4 << 2), I.phi + si, kDbgWinDst);
-            };
-            int l = 0;
-            if (!anyg) {
-                for (int e4 = tid; e4 < tot4; e4 += NT) {
-                    while (e4 >= (wdesc[(l + 1) * kWd + 4] >> 2)) ++l;
-                    dense4(l, e4);
-                }
-            } else {
-                for (int e4 = tid; e4 < tot4; e4 += NT) {
-                    while (e4 >= (wdesc[(l + 1) * kWd + 4] >> 2)) ++l;
-                    if (wdesc[l * kWd] >= 0) dense4(l, e4);   // gathered layers below
-                }
-            }
-            // gathered windows: 4-byte reads through L2 (the layers were written
-            // by other SMs in this launch)
-            for (int ll = 0; anyg && ll < L; ++ll) {
-                if (wdesc[ll * kWd] >= 0) continue;
-                const int tb = I.tab_off[g * L + ll], nc = wdesc[ll * kWd + 3], n = wdesc[ll * kWd + 6];
-                const int cnt = wdesc[ll * kWd + 2] * nc;
-                const float* src = I.phi + wdesc[ll * kWd + 5];
-                float* dst = win + wdesc[ll * kWd + 4];
-                for (int e = tid; e < cnt; e += NT) {
-                    const int rp = e / nc, cq = e - rp * nc;
-                    const int row = __ldg(I.cy + tb + a_lo + (rp >> 1)) + (rp & 1);
-                    const int col = __ldg(I.cx + tb + b_lo + (cq >> 1)) + (cq & 1);
-                    if (FEWHA_IN(wdesc[ll * kWd + 5] + (long)row * n + col, I.N, 1, kDbgWinSrc) &&
-                        FEWHA_IN_SMEM(dst + e, 4, kDbgWinDst))
-                        dst[e] = __ldcg(src + (long)row * n + col);
-                }
+                cc->pre[0] = A.rho;
+                cc->pre[1] = A.beta;
+                cc->pre[2] = A.t;
+                cc->pre[3] = A.aold;
+                cc->pre[4] = (double)A.mh;
+                cc->pre[5] = (double)A.ml;
+                cc->pre_k = k;
             }
         }
-        {
-            // part A of the next layer phase's CG scalars while the copies fly
-            if (want_mu && tid < 32 && cc->lres && cc->il_valid && cc->IL.preA_cta < 0) {
-                ScalA A;
-                alg2_part_a(P, cc->IL, k, A);
-                if (tid == 0) {
-                    cc->pre[0] = A.rho;
-                    cc->pre[1] = A.beta;
-                    cc->pre[2] = A.t;
-                    cc->pre[3] = A.aold;
-                    cc->pre[4] = (double)A.mh;
-                    cc->pre[5] = (double)A.ml;
-                    cc->pre_k = k;
-                }
-            }
-            cp_async_wait_all();
-        }
-        if (build) {
+        cp_async_wait_all();   // copies issued at launch start for the first layer item
+        if (!cc->wtab) {
+            // interpolation tables of the tile: per layer and node row the
+            // offset of the row's cells in the layer and the weight; per node
+            // column the column and the weight
             for (int e = tid; e < L * (pr + pc); e += NT) {
                 const int l = e / (pr + pc), k = e - l * (pr + pc);
                 const int base = I.tab_off[g * L + l];
-                const bool gath = wdesc[l * kWd] < 0;
-                if (P.direct_p) {   // offsets into the layer itself
-                    if (k < pr)
-                        rtab[l * P.tile_rows + k] =
-                            make_int2(I.lay_off[l] + __ldg(I.cy + base + a_lo + k) * wdesc[l * kWd + 6],
-                                      __float_as_int(__ldg(I.ty + base + a_lo + k)));
-                    else
-                        ctab[l * P.tile_cols + k - pr] = make_int2(__ldg(I.cx + base + b_lo + k - pr),
-                                                                   __float_as_int(__ldg(I.tx + base + b_lo + k - pr)));
-                } else if (k < pr) {
-                    const int rr = gath ? 2 * k : __ldg(I.cy + base + a_lo + k) - wdesc[l * kWd];
+                if (k < pr)
                     rtab[l * P.tile_rows + k] =
-                        make_int2(rr * wdesc[l * kWd + 3] + wdesc[l * kWd + 4], __float_as_int(__ldg(I.ty + base + a_lo + k)));
-                } else {
-                    const int kk = k - pr;
-                    ctab[l * P.tile_cols + kk] = make_int2(gath ? 2 * kk : __ldg(I.cx + base + b_lo + kk) - wdesc[l * kWd + 1],
-                                                           __float_as_int(__ldg(I.tx + base + b_lo + kk)));
-                }
+                        make_int2(I.lay_off[l] + __ldg(I.cy + base + a_lo + k) * I.lay_n[l],
+                                  __float_as_int(__ldg(I.ty + base + a_lo + k)));
+                else
+                    ctab[l * P.tile_cols + k - pr] = make_int2(__ldg(I.cx + base + b_lo + k - pr),
+                                                               __float_as_int(__ldg(I.tx + base + b_lo + k - pr)));
             }
             if (tid == 0) cc->wtab = 1;
         }
         __syncthreads();
         fmark(P, 21);
-        for (int e = tid; P.direct_p && e < pr * pc; e += NT) {
+        for (int e = tid; e < pr * pc; e += NT) {
             // the layers read in the L2 (written by other SMs in this launch:
             // not through L1), every node's four cells per layer
             const int ii = e / pc, jj = e - ii * pc;
             float acc = 0.f;
 #pragma unroll 3
             for (int l = 0; l < L; ++l) {
-                const int n = wdesc[l * kWd + 6];
+                const int n = I.lay_n[l];
                 const int2 rt = rtab[l * P.tile_rows + ii], ct = ctab[l * P.tile_cols + jj];
                 const float ty = __int_as_float(rt.y), tx = __int_as_float(ct.y);
                 if (!FEWHA_IN(rt.x + ct.x, I.N, n + 2, kDbgWinSrc)) continue;
                 const float* f = I.phi + rt.x + ct.x;
                 acc += (1.f - ty) * ((1.f - tx) * __ldcg(f) + tx * __ldcg(f + 1)) +
                        ty * ((1.f - tx) * __ldcg(f + n) + tx * __ldcg(f + n + 1));
-            }
-            psi[e] = acc;
-        }
-        for (int e = tid; !P.direct_p && e < pr * pc; e += NT) {
-            const int ii = e / pc, jj = e - ii * pc;
-            float acc = 0.f;
-#pragma unroll 3
-            for (int l = 0; l < L; ++l) {
-                const int nc = wdesc[l * kWd + 3];
-                const int2 rt = rtab[l * P.tile_rows + ii], ct = ctab[l * P.tile_cols + jj];
-                const float ty = __int_as_float(rt.y), tx = __int_as_float(ct.y);
-                const float* f = win + rt.x + ct.x;
-                if (!FEWHA_IN_SMEM(f, 4 * (nc + 2), kDbgWinP)) continue;
-                acc += (1.f - ty) * ((1.f - tx) * f[0] + tx * f[1]) + ty * ((1.f - tx) * f[nc] + tx * f[nc + 1]);
             }
             psi[e] = acc;
         }
@@ -1152,7 +1037,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     const int tid = threadIdx.x, NT = blockDim.x;
     fmark(P, 10);
     const bool fresh = cc->lkey != li;   // else the descriptors are cached
-    if (P.shared_tables && tid == 0) cc->wtab = 0;   // this phase overwrites the window tables
+    if (P.shared_tables && tid == 0) cc->wtab = 0;   // this phase overwrites the interpolation tables
     if (fresh) {
         __syncthreads();   // the previous item's tables may still be in use
         if (tid == 0) layer_desc(P, li, cc);
@@ -1359,7 +1244,7 @@ __device__ void layer_phase(const FParams& P, int li, int mode, int k, float* sm
     } else {
         // RHS, its replacement form and the restart: batches of kE elements
         // per thread, every load of a batch issued before its arithmetic
-        constexpr int kE = 3;
+        constexpr int kE = 2;
         const int total = R * n;
         const bool need_ja = mode != kLpRhsRepl;
         const bool need_12 = mode != kLpRhsStart || P.warm;
@@ -1484,7 +1369,6 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
     __shared__ float* rem[4][kMaxC];
     __shared__ __align__(16) double red[64];   // 32 float4 for the block reductions
     __shared__ double sh[8];
-    __shared__ int wdesc[(kMaxLayersFused + 1) * kWd];
     __shared__ CtaCache cc;
     __shared__ int s_abort;
     __shared__ int s_go;
@@ -1588,7 +1472,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kFThreads, 1)
         const bool sensor_ph = it ? ((ph - base) & 1) == 0 : (ph & 1) == 0;
         if (sensor_ph) {
             const int smode = (ph == 0) ? kModeRhs : (!it && ph == 2) ? kModeResid : kModeData;
-            for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, smode, it, wdesc, red, &cc, k);
+            for (int t = w_lo; t < w_hi; ++t) sensor_tile(P, P.wsched[t], sm, smode, it, red, &cc, k);
             if (it && res_inst >= 0 && threadIdx.x < 32) {
                 // part A of instance res_inst's scalars for this iteration's layer phase
                 const FInst& RI = P.inst[res_inst];
@@ -2136,7 +2020,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         pl->grid = pl->nclusters * C;
 
         // sensor tiles: near-square, about one round over the grid, and with
-        // max_tile_side > 0 no side longer than that (bounded windows)
+        // max_tile_side > 0 no side longer than that
         std::vector<WItem> witems;
         std::vector<int> w0(ninst), nw(ninst);
         std::vector<std::vector<int2>> tt_tiles(ninst);   // per instance, per sensor: its tiles
@@ -2180,34 +2064,21 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             }
             nw[i] = (int)witems.size() - w0[i];
         }
-        // a sensor tile's P reads the layers in the L2 directly (every plan) or
-        // from windows staged in shared memory first
-        const bool direct_p = true;
-        int tile_nodes = 0, tile_sub = 0, win_max = 0, tile_rows = 0, tile_cols = 0;
+        // a sensor tile's working set: its nodes' psi and its subapertures'
+        // weighted slopes (P reads the layers in the L2 directly)
+        int tile_nodes = 0, tile_sub = 0, tile_rows = 0, tile_cols = 0;
         for (auto& w : witems) {
-            const HostSetup& hs = *hss[w.inst];
-            const int ns = hs.wfs[w.g].n;
+            const int ns = hss[w.inst]->wfs[w.g].n;
             const int a_lo = std::max(w.i0 - 1, 0), a_hi = std::min(w.i1, ns);
             const int b_lo = std::max(w.j0 - 1, 0), b_hi = std::min(w.j1, ns);
             tile_rows = std::max(tile_rows, a_hi - a_lo + 1);
             tile_cols = std::max(tile_cols, b_hi - b_lo + 1);
             tile_nodes = std::max(tile_nodes, (a_hi - a_lo + 1) * (b_hi - b_lo + 1));
             tile_sub = std::max(tile_sub, (std::min(w.i1, ns) - a_lo) * (std::min(w.j1, ns) - b_lo));
-            int win = 0;
-            const int pr = a_hi - a_lo + 1, pc = b_hi - b_lo + 1;
-            for (int l = 0; l < hs.L; ++l) {
-                const int base = hs.tab_off[w.g * hs.L + l];
-                const int nr = hs.cy[base + a_hi] + 1 - hs.cy[base + a_lo] + 1;
-                const int c0 = hs.cx[base + b_lo] & ~3;   // as in the kernel: 16-byte aligned
-                const int nc = (hs.cx[base + b_hi] + 1 - c0 + 1 + 3) & ~3;
-                win += nr * nc > 16 * pr * pc ? 4 * pr * pc : nr * nc;   // dense, or 2 x 2 cells per node
-            }
-            win_max = std::max(win_max, win);
         }
         tile_nodes = (tile_nodes + 3) & ~3;
         tile_sub = (tile_sub + 3) & ~3;
-        win_max = direct_p ? 0 : (win_max + 3) & ~3;   // direct P stages no windows
-        const size_t sensor_floats = (size_t)win_max + tile_nodes + 2 * (size_t)tile_sub;
+        const size_t sensor_floats = (size_t)tile_nodes + 2 * (size_t)tile_sub;
         const size_t stab_floats = 2 * (size_t)Lmax * (tile_rows + tile_cols);
         // [working set of either phase][layer gather tables][sensor tables]:
         // the tables persist across phases for a CTA that keeps its items
@@ -2222,7 +2093,7 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             smem = std::max(lw + gtab_floats, sensor_floats + stab_floats) * sizeof(float);
         }
         if (smem > smem_cap) {
-            if (err.empty()) err = "the staged windows do not fit in shared memory";
+            if (err.empty()) err = "the working sets and tables of the phases do not fit in shared memory";
             delete pl;
             continue;
         }
@@ -2414,7 +2285,6 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
         P.C = C;
         P.stripe_floats = stripe;
         P.stage_floats = stage_max;
-        P.win_floats = win_max;
         P.tile_nodes = tile_nodes;
         P.tile_subaps = tile_sub;
         P.shared_tables = shared_tables ? 1 : 0;
@@ -2440,7 +2310,6 @@ FusedPlan* fused_create_multi(const std::vector<const HostSetup*>& hss, const st
             P.g[i] = (float)hss[0]->g[i];
         }
         P.inst = pl->d_inst;
-        P.direct_p = direct_p ? 1 : 0;
         {
             // L2 prefetch list: descriptors first, then tables, then the state,
             // up to a quarter of the L2 (a large batch keeps only its head)

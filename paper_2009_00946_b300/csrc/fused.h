@@ -29,7 +29,7 @@ FusedPlan* fused_create(const HostSetup& hs, const DevGeo<float>& G, const Fused
 
 // One plan over several independent instances (solved together in one
 // launch; every instance has its own tables, state and scalars).
-// max_tile_side > 0 bounds the sensor tiles (and so the staged windows).
+// max_tile_side > 0 bounds the sensor tiles (nodes per side).
 // forced_C > 0 builds only that cluster size (the autotuner's candidates);
 // forced_V >= 0 only that layer-phase form (0 row stripes, 1 level-stacked),
 // else the level-stacked form wherever it fits.

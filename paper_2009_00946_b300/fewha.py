@@ -726,7 +726,7 @@ def measure_l2(nbytes: int = 48 << 20, passes: int = 40, reps: int = 5) -> dict:
 
 
 # bounds-check sites of the debug build (include/fewha.h, FEWHA_DBG_*)
-DEBUG_SITES = {1: "sensor window source", 2: "sensor window staging", 3: "sensor bilinear read",
+DEBUG_SITES = {1: "sensor bilinear read of the layers", 2: "reserved", 3: "reserved",
                4: "slope index", 5: "Gamma^T output", 6: "field staging source", 7: "field staging",
                8: "P^T gather read", 9: "DWT store into a row owner", 10: "DWT store into a column owner",
                11: "coefficient index", 12: "tip-tilt correction", 13: "layer output",
