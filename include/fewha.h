@@ -214,10 +214,14 @@ int fewha_time_operator(fewha_handle* h, int op, int reps, double* us_per_applic
  * dm_out returns as soon as the kernel has set the handle's completion word
  * (mapped pinned memory, written after every result is visible to the host):
  * the results and the error status are final then, while the launch may
- * still be retiring on the stream (later calls are ordered after it).  The
- * graph is captured on the first call
- * and re-captured when n_iter, the flags or the pointers change; frames that
- * fall on the residual-replacement period use a second graph.
+ * still be retiring on the stream (later calls are ordered after it).  With
+ * pinned slopes and layers there (open loop, slopes by copy, the default of
+ * fewha_set_host_transfer) the frame runs as an armed frame fired at once
+ * (fewha_frame_arm + fewha_frame_fire below): the kernel is launched first
+ * and does its set-up while the copy engine brings the slopes in, on a
+ * second stream, and lets it go.  Otherwise the graph is captured on the
+ * first call and re-captured when n_iter, the flags or the pointers change;
+ * frames that fall on the residual-replacement period use a second graph.
  * layers_out / dm_out may be NULL. */
 int fewha_frame(fewha_handle* h, const void* slopes, int n_iter, int warm_start,
                 double gain, int n_fit, void* layers_out, void* dm_out, int on_device);
@@ -225,7 +229,8 @@ int fewha_frame(fewha_handle* h, const void* slopes, int n_iter, int warm_start,
 /* Profiling aid: host-side timing of the last fewha_frame on this handle, in
  * microseconds of the host's steady clock: out[0] preparation (argument
  * checks, pointer lookups, graph capture or re-pointing), out[1] the graph
- * launch call, out[2] the wait for the results (host frames on the fused
+ * launch call (the kernel's launch for a frame run as an armed one), out[2]
+ * the wait for the results (host frames on the fused
  * path: until the completion word is seen; 0 for device frames), out[3] the
  * whole call; out[4] = 1 if the captured kernel node was re-pointed at other
  * buffers, out[5] = 1 if the graph was (re)captured.  Errors: ARG. */

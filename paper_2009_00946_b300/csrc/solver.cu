@@ -1987,6 +1987,20 @@ class Solver : public SolverBase {
                 dm = pinned_dm;
             }
         }
+        // pinned host slopes and layers on the fused path (open loop, no fit,
+        // slopes brought in by the copy engine): the frame runs as an armed
+        // frame fired at once, so the kernel is launched first and does its
+        // set-up while the copy engine brings the slopes in, instead of
+        // starting behind the copy
+        if (!on_device && !dout && sin_map && lo_map && use_fused() && !closed && done_dev && host_slopes_copy) {
+            T1 = clk::now();
+            int st = frame_arm(s_in, n_iter, warm, lout, 2.0);
+            T2 = T3 = clk::now();
+            if (st) return st;
+            st = frame_fire();
+            T3 = clk::now();
+            return st;
+        }
         const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         // the fused kernel reads the slopes and writes the layers where they
