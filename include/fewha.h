@@ -465,7 +465,7 @@ long long fewha_batch_launch_count(const fewha_batch* b);
  * size (an instance's largest layer side; a group is a range of the sorted
  * distinct sides: every split between them for up to four sides, at most one
  * split for more); for every group it builds the plan for every cluster size
- * (8, 4, 16, 2) and sensor-tile bound (none, 32, 24, 20, 16) that fits
+ * (8, 4, 16, 2) and sensor-tile bound (none, 64, 48, 32, 24, 16) that fits
  * shared memory and times each on the current slopes (n_iter warm-started
  * iterations from the same state, CUDA events, median of reps launches after
  * one warm-up).  A grouping costs the sum of its groups' best launches; the

@@ -2596,7 +2596,7 @@ class Batch : public BatchBase {
             for (int i = 0; i < ni; ++i)
                 if (side[i] >= sides[a] && side[i] <= sides[b]) c.idx.push_back(i);
             for (int C : {8, 4, 16, 2}) {
-                for (int tile : {0, 32, 24, 20, 16}) {
+                for (int tile : {0, 64, 48, 32, 24, 16}) {
                     if (st != FEWHA_OK) break;
                     std::string e;
                     FusedPlan* pl = make_plan(c.idx, tile, C, e);
