@@ -697,6 +697,7 @@ class Solver : public SolverBase {
     WriteValue32 write_value = nullptr;
     bool write_value_tried = false;
     cudaStream_t aux_stream = nullptr;
+    cudaEvent_t prior_done = nullptr;   // the handle's stream before the armed launch: the copy waits for it
     unsigned* go_dev = nullptr;
     bool armed_copy = false;
     const void* armed_src = nullptr;
@@ -744,6 +745,7 @@ class Solver : public SolverBase {
             cudaStreamSynchronize(aux_stream);
             cudaStreamDestroy(aux_stream);
         }
+        if (prior_done) cudaEventDestroy(prior_done);
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
         for (int i = 0; i < 2; ++i) drop_graph(i);
@@ -2196,11 +2198,16 @@ class Solver : public SolverBase {
                     cudaSuccess &&
                 q == cudaDriverEntryPointSuccess && fn &&
                 cudaStreamCreateWithFlags(&aux_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&prior_done, cudaEventDisableTiming) == cudaSuccess &&
                 alloc(go_dev, 1) == FEWHA_OK && cudaMemset(go_dev, 0, sizeof(unsigned)) == cudaSuccess)
                 write_value = (WriteValue32)fn;
             cudaGetLastError();
         }
-        armed_copy = host_slopes_copy && write_value && go_dev && aux_stream;
+        armed_copy = host_slopes_copy && write_value && go_dev && aux_stream && prior_done;
+        // the copy at the fire overwrites the handle's slope buffer: it waits
+        // for the work enqueued before this frame (a device frame still
+        // running copies its slopes into that buffer)
+        if (armed_copy) FEWHA_CUDA(cudaEventRecord(prior_done, stream));
         bell_seq = (bell_seq + 1u) ? bell_seq + 1u : 1u;
         *(volatile unsigned long long*)done_host = 0ull;   // before the launch that sets it
         std::atomic_thread_fence(std::memory_order_seq_cst);
@@ -2239,7 +2246,8 @@ class Solver : public SolverBase {
         if (armed_copy) {
             // slopes in by the copy engine, then the go written behind them in stream order
             // (the stream write fences the copy's data before the word)
-            if (cudaMemcpyAsync(slopes, armed_src, hs.S * sizeof(T), cudaMemcpyHostToDevice, aux_stream) ==
+            if (cudaStreamWaitEvent(aux_stream, prior_done, 0) == cudaSuccess &&
+                cudaMemcpyAsync(slopes, armed_src, hs.S * sizeof(T), cudaMemcpyHostToDevice, aux_stream) ==
                     cudaSuccess &&
                 write_value((CUstream)aux_stream, (CUdeviceptr)go_dev, bell_seq, 0) == CUDA_SUCCESS)
                 rung = true;

@@ -232,6 +232,32 @@ def test_bound_frames_and_both_host_transfers_bit_identical(fw, elt_frames):
             assert rel(want, ref[k][0]) < 1e-4, k
 
 
+def test_host_frame_after_enqueued_device_frame(fw, elt_frames):
+    """A pinned host frame (run as an armed frame fired at once, its slopes
+    copied into the handle's buffer on a second stream) issued while a device
+    frame of the same handle is still enqueued -- a device frame copies its
+    slopes into that buffer as it runs -- gives the same layers, bit for bit,
+    as the two frames run one after the other with a synchronisation between."""
+    import torch
+    cfg, S_in, ref = elt_frames
+    with _fused(fw, cfg, k_rr=10) as A, _fused(fw, cfg, k_rr=10) as B:
+        ps = torch.empty(A.S, dtype=torch.float32).pin_memory()
+        pl = torch.empty(A.N, dtype=torch.float32).pin_memory()
+        ql = torch.empty(A.N, dtype=torch.float32).pin_memory()
+        dev_s = [torch.from_numpy(S_in[k]).cuda() for k in range(6)]
+        dev_l = torch.empty(A.N, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        for k in range(0, 6, 2):
+            A.frame(dev_s[k], 4, warm=True, layers_out=dev_l)   # enqueued only
+            ps.numpy()[:] = S_in[k + 1]
+            A.frame(ps.numpy(), 4, warm=True, layers_out=pl.numpy())
+            B.frame(dev_s[k], 4, warm=True, layers_out=dev_l)
+            B.sync()
+            B.frame(ps.numpy(), 4, warm=True, layers_out=ql.numpy())
+            assert np.array_equal(pl.numpy(), ql.numpy()), k
+            assert rel(pl.numpy(), ref[k + 1][0]) < 1e-4, k
+
+
 def test_armed_frames_bit_identical(fw, elt_frames):
     """Frames armed ahead of their slopes (fewha_frame_arm: the kernel launched
     and waiting; the slopes written afterwards; fewha_frame_fire) give the
