@@ -153,7 +153,13 @@ def test_batch_split_into_launches_by_hand(fw, subset_frames):
         B.frame(B.concat_slopes([s[0] for s in slopes]), 4, warm=True, layers_out=out)
         B.set_trace(False)
         marks = B.fine_trace()
-        assert len(marks) > 0 and sum(len(m) for m in marks) > 0
+        # the CTAs of both launches, the first launch's first
+        grids = [int(x.split(",")[0]) for x in d.split("(grid ")[1:]]
+        assert len(grids) == 2 and len(marks) == sum(grids), (grids, len(marks))
+        assert any(len(m) > 0 for m in marks[:grids[0]]) and any(len(m) > 0 for m in marks[grids[0]:])
+        t_first = max(t for m in marks[:grids[0]] for _, t in m)
+        t_second = min(t for m in marks[grids[0]:] for _, t in m)
+        assert t_first <= t_second, "the second launch starts after the first ends"
         # a non-finite slope of an instance that does not lead its launch
         i = next(j for j in range(len(cfgs)) if group[j] == 0 and j != group.index(0))
         g = fo.Geometry(cfgs[i])
