@@ -4,9 +4,10 @@ GPU, against the FP64 oracle.
 Run with FEWHA_DEBUG=1 in the environment, so that the binding loads
 libfewha_debug.so: every case below drives one part of the hot path through
 the C ABI -- the fused frame kernel with both layer transforms, ragged tiles,
-the LGS tip-tilt filter and the mirror fit; the plain operator kernels in
-FP64 and FP32; the batched launch; the taped solve and its reverse mode; the
-no-allocation transform -- compares its results with the oracle and reads the
+the LGS tip-tilt filter and the mirror fit; pinned host frames (armed and
+fired at once) and an explicitly armed frame; the plain operator kernels in
+FP64 and FP32; the batched launch, one and two launches per frame; the taped
+solve and its reverse mode; the no-allocation transform -- compares its results with the oracle and reads the
 violations the checks recorded (fewha_debug_bounds).  A check that fails
 skips its access, so a violation shows here as a count (and usually as a
 parity error), never as a memory fault.
@@ -99,6 +100,46 @@ def case_batch(fw, n_frames=3):
     refs = [_oracle_frames(c, n_frames) for c in cfgs]
     worst = 0.0
     with fw.Batch(cfgs, k_rr=10) as B:
+        out = np.empty(B.N, np.float32)
+        for k in range(n_frames):
+            B.frame(B.concat_slopes([r[0][k].astype(np.float32) for r in refs]), 4, warm=True, layers_out=out)
+            _stop_on_violation(fw)
+            for i, lay in enumerate(B.split_layers(out)):
+                worst = max(worst, rel(lay, refs[i][1][k][0]))
+    return worst
+
+
+def case_frames_pinned(fw, torch, cfg, n_frames):
+    """Host frames on pinned buffers (run as armed frames fired at once: the
+    kernel launched first, the slopes copied in on a second stream) and one
+    explicitly armed frame; the worst relative error of the layers."""
+    S_in, ref = _oracle_frames(cfg, n_frames)
+    worst = 0.0
+    with fw.Solver(cfg, precision=fw.FP32, path=fw.PATH_FUSED, k_rr=10) as S:
+        ps = torch.empty(S.S, dtype=torch.float32).pin_memory()
+        pl = torch.empty(S.N, dtype=torch.float32).pin_memory()
+        for k in range(n_frames):
+            if k == n_frames - 1:
+                S.arm_frame(ps.numpy(), 4, warm=True, layers_out=pl.numpy(), wait_s=5.0)
+                ps.numpy()[:] = S_in[k]
+                S.fire_frame()
+            else:
+                ps.numpy()[:] = S_in[k]
+                S.frame(ps.numpy(), 4, warm=True, layers_out=pl.numpy())
+            _stop_on_violation(fw)
+            worst = max(worst, rel(pl.numpy(), ref[k][0]))
+    return worst
+
+
+def case_batch_grouped(fw, n_frames=3):
+    """A batch split by hand into two launches (the 256^2 instances apart)."""
+    from paper_2009_00946_b300 import configs
+    cfgs = [configs.c4_instance(i) for i in (1, 6, 7, 24, 8)]
+    refs = [_oracle_frames(c, n_frames) for c in cfgs]
+    group = [0 if max(l["n"] for l in c["layers"]) == 256 else 1 for c in cfgs]
+    worst = 0.0
+    with fw.Batch(cfgs, k_rr=10, max_tile_side=48) as B:
+        B.set_groups(group)
         out = np.empty(B.N, np.float32)
         for k in range(n_frames):
             B.frame(B.concat_slopes([r[0][k].astype(np.float32) for r in refs]), 4, warm=True, layers_out=out)
@@ -204,6 +245,8 @@ def main():
         ("ltao_fit_fused", 1e-4, lambda: case_frames(fw, configs.ao_mode_small("ltao"), 3, fw.FP32, fw.PATH_FUSED,
                                                      fit=True)),
         ("batch_4_instances", 1e-4, lambda: case_batch(fw)),
+        ("batch_grouped_two_launches", 1e-4, lambda: case_batch_grouped(fw)),
+        ("elt_fused_pinned_host_and_armed", 1e-4, lambda: case_frames_pinned(fw, torch, configs.c2_elt(), 4)),
         ("operators_fp64", 1e-12, lambda: case_operators(fw)),
         ("autograd_fp64", 1e-8, lambda: case_autograd(fw, torch)),
         ("noalloc_mixed_levels", 1e-6, lambda: case_noalloc(fw, torch)),

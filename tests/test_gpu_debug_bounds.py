@@ -23,7 +23,7 @@ def test_debug_build_records_no_violation_and_matches_oracle():
     assert p.returncode == 0, p.stderr[-3000:]
     res = json.loads(p.stdout.strip().splitlines()[-1])
     assert res["debug_build"], "FEWHA_DEBUG=1 must load the debug build"
-    assert len(res["cases"]) >= 13
+    assert len(res["cases"]) >= 15
     for name, rec in res["cases"].items():
         assert rec.get("exception") is None, (name, rec)
         assert rec["count"] == 0, (name, rec)
