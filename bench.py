@@ -596,7 +596,7 @@ def bench_batch(torch, fewha, dev, flush, n_frames):
 
 def bench_batch_sharded(torch, fewha, dev, flush, n_frames, dist, rank, world):
     """The 64 uneven instances partitioned over the ranks (no collective in
-    the solve: each rank one fused launch per frame over its own instances);
+    the solve: each rank its own batch's fused launch per frame);
     the slowest rank's p50 sets the job's batch-frame time."""
     from paper_2009_00946_b300 import shard
     cfgs = configs.c4_batch(64)

@@ -2348,7 +2348,7 @@ SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& e
 }
 
 // ---------------------------------------------------------------------------
-// batch: independent FP32 instances, one fused launch per frame
+// batch: independent FP32 instances, one fused launch per group of instances per frame
 // ---------------------------------------------------------------------------
 
 namespace {

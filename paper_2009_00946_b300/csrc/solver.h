@@ -149,7 +149,8 @@ class SolverBase {
 SolverBase* make_solver(const HostSetup& hs, cudaStream_t stream, std::string& err, int& status);
 
 // Many independent FP32 instances advanced together by one fused launch per
-// frame: slopes and layers are concatenated in instance order.
+// group of instances (one group unless split) per frame: slopes and layers
+// are concatenated in instance order.
 class BatchBase {
   public:
     virtual ~BatchBase() {}

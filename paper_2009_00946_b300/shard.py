@@ -52,7 +52,7 @@ class ShardedBatch:
     cfgs: every instance of the whole batch (each rank passes the same list);
     rank / world: this process's place.  `mine` lists this rank's instances;
     frame() takes their slopes (a list in the order of `mine`) and advances
-    them by one fused launch; gather_layers() returns, on rank dst, every
+    them by the batch's fused launches; gather_layers() returns, on rank dst, every
     instance's layers in global instance order."""
 
     def __init__(self, cfgs: list, rank: int, world: int, n_iter: int = 4, batch_factory=None, **batch_kw):
